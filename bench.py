@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the registration hot path on GB300.
+
+One step = one full multilevel registration of a synthetic CT-like pair
+(default: 256^3 at 1 mm, 4 levels, 129^3 finest deformation nodes): pyramid,
+prolongation, and at every level L-BFGS with Armijo backtracking, each trial
+one matrix-free NGF + curvature objective+gradient evaluation.
+
+Metric: objective+gradient evaluations per second, counted in full-resolution
+equivalents (an evaluation at level l counts voxels_l / voxels_0), so that the
+GPU registration and the CPU oracle are compared on the same work.  Also
+reported: seconds per registration (ms_per_step), the isolated full-resolution
+evaluation time and its HBM roofline fraction, the end-to-end rate from host
+buffers, and the FP64 CPU oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank registers its own pair (independent
+replicas, no collective on the data path); value = all ranks' evaluations over
+the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NGF+curvature objective+gradient evals/s and % HBM roofline; s per 256³ registration"
+UNIT = "evals/s (full-resolution equivalent)"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=2, help="workload id (default 2: 256^3 CT, 4 levels)")
+    ap.add_argument("--eval-iters", type=int, default=50, help="isolated evaluations for the roofline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eval-impl", type=int, default=None, help="0 fused, 1 multi-pass (default: library)")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers (NCCL on GPUs; gloo in the CPU tests)
+# ----------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def dist_reduce(x, op="max", device="cpu"):
+    """Reduce a float over ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def dist_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# measurement helpers
+# ----------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, digest):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_digest") != digest:
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+def workload(config_id, rank):
+    from synth import CONFIGS, make_pair
+    c = CONFIGS[config_id]
+    p = make_pair(config_id, pair=rank)
+    return c, p
+
+
+def full_res_equivalent(stats, reg, levels):
+    nv0 = np.prod(reg.level_info(0)["dims"])
+    return sum(stats["evals"][lv] * np.prod(reg.level_info(lv)["dims"]) / nv0 for lv in range(levels))
+
+
+def cpu_oracle_rate(p, c, budget_s):
+    """FP64 oracle objective+gradient evaluations per second at full resolution (bounded sample)."""
+    import oracle
+    oracle.build()
+    dims, h = p["dims"], p["spacing"]
+    nodes = oracle.default_nodes(dims)
+    from synth import random_field
+    u = random_field(nodes, 7, 5.0).astype(np.float64)
+    R, T = p["R"].astype(np.float64), p["T"].astype(np.float64)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.objective(dims, h, R, T, nodes, u, c["eta"], c["eta"], c["alpha"])
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 20:
+            break
+    return n / el, n, el, oracle.num_threads()
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_1812_06765_gb300 as reg_pkg
+    from paper_1812_06765_gb300 import _lib
+    from synth import random_field
+
+    rank, world = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c, p = workload(args.config, rank)
+    kw = dict(levels=c["levels"], tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"], c1=c["c1"])
+    if args.eval_impl is not None:
+        kw["eval_impl"] = args.eval_impl
+    cfg = reg_pkg.make_config(**kw)
+    stream = torch.cuda.current_stream(dev)
+    reg = reg_pkg.Registration(cfg, stream=stream)
+    R_d = torch.from_numpy(p["R"]).to(dev)
+    T_d = torch.from_numpy(p["T"]).to(dev)
+    R_h = torch.from_numpy(p["R"]).pin_memory()
+    T_h = torch.from_numpy(p["T"]).pin_memory()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    levels = c["levels"]
+
+    def step_device():
+        reg.set_images(R_d, T_d, p["spacing"])
+        u, st = reg.register(out="torch")
+        return st
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize(dev)
+
+    # timed region: K registrations from device-resident images
+    dist_barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local).start()
+    times, eq_evals, launches, evals_per_level, iters_per_level = [], 0.0, 0, None, None
+    for _ in range(args.steps):
+        flush.zero_()                       # evict the previous step from L2 (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step_device()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        eq_evals += full_res_equivalent(st, reg, levels)
+        launches += st["kernel_launches"] + 2 * (levels - 1)
+        evals_per_level, iters_per_level = st["evals"], st["iters"]
+    torch.cuda.synchronize(dev)
+    dist_barrier()
+    clk = clocks.stop()
+    total_ms = dist_reduce(sum(times), "max", dev)
+    eq_all = dist_reduce(eq_evals, "sum", dev)
+    value = eq_all / (total_ms / 1000.0)
+
+    # end to end through the C ABI from pinned host buffers (copies inside the timed region)
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        reg.set_images(R_h, T_h, p["spacing"])
+        u_h, st_h = reg.register(out="pinned")
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_eq = full_res_equivalent(st_h, reg, levels)
+    e2e_s = dist_reduce(statistics.mean(e2e_times), "max", dev)
+    e2e_value = world * e2e_eq / e2e_s
+
+    # isolated full-resolution evaluation: the fused objective+gradient pass
+    reg.set_images(R_d, T_d, p["spacing"])
+    info = reg.level_info(0)
+    u = torch.from_numpy(random_field(info["nodes"], 5, 5.0)).to(dev)
+    grad = torch.empty_like(u)
+    for _ in range(5):
+        _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
+    ev_ms = []
+    for _ in range(args.eval_iters):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
+        e1.record(stream)
+        e1.synchronize()
+        ev_ms.append(e0.elapsed_time(e1))
+    eval_ms = statistics.median(ev_ms)
+    nv = int(np.prod(info["dims"]))
+    nn = int(np.prod(info["nodes"]))
+    alg_bytes = 4 * nv + 4 * nv + 12 * nn + 12 * nn       # read R, T, u; write grad J
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (eval_ms * 1e-3) / 1e9
+    impl = reg.cfg.eval_impl
+    kernel = "objective_pass_fused" if impl == 0 else "objective_pass_multipass"
+    srcs = ["paper_1812_06765_gb300/csrc/" + f for f in sorted(os.listdir(os.path.join(ROOT, "paper_1812_06765_gb300", "csrc")))]
+    traffic = committed_traffic(kernel, source_digest(srcs))
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n, el, cores = cpu_oracle_rate(p, c, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d FP64 oracle objective+gradient evaluations of the full-resolution %s pair "
+                         "(%.1f s); a registration costs its full-resolution-equivalent evaluations" %
+                         (n, "x".join(map(str, p["dims"])), el)}
+
+    if rank == 0:
+        mz = p["R"].shape
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": c["name"], "image": list(p["dims"]), "spacing_mm": list(p["spacing"]),
+                       "levels": levels, "finest_nodes": list(info["nodes"]), "eta": c["eta"],
+                       "alpha": c["alpha"], "lbfgs_mem": c["mem"], "max_iter_per_level": c["max_iter"],
+                       "evals_per_level": evals_per_level, "iters_per_level": iters_per_level,
+                       "eval_impl": "fused" if impl == 0 else "multi-pass",
+                       "l2": "flushed between steps (2x L2 buffer written, untimed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "image_shape_zyx": list(mz)},
+            "registration_s": total_ms / args.steps / 1000.0,
+            "eval_ms_full_res": eval_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+                         "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * nv,
+                    "d2h_bytes_per_step": 3 * 4 * nn, "registration_s": e2e_s},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    reg.close()
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    c, p = workload(args.config, 0)
+    import oracle
+    oracle.build()
+    from synth import random_field
+    dims, h = p["dims"], p["spacing"]
+    nodes = oracle.default_nodes(dims)
+    u = random_field(nodes, 7, 5.0).astype(np.float64)
+    R, T = p["R"].astype(np.float64), p["T"].astype(np.float64)
+
+    def step():
+        oracle.objective(dims, h, R, T, nodes, u, c["eta"], c["eta"], c["alpha"])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    sample = ("each step: one FP64 oracle objective+gradient evaluation of the full-resolution %s pair"
+              % "x".join(map(str, dims)))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1000.0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": c["name"], "image": list(dims), "levels": c["levels"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": oracle.num_threads(),
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * reg.h - C ABI of libreg.so: matrix-free NGF + curvature deformable 3D image
+ * registration on one GB300 GPU (sm_103a).
+ *
+ * Model (Budelmann, Koenig, Papenberg, Lellmann, "Fully-deformable 3D image
+ * registration in two seconds", BVM 2019):
+ *   y* = argmin_y J(y),  J(y) = D_NGF(R, T(P y)) + alpha S_curv(y)   (Sec. 2.1, Eq. 1)
+ * D_NGF is the normalized-gradient-field distance of Eq. 2 (Sec. 2.2), S_curv
+ * the curvature regulariser (sum of squared Laplacians of the components,
+ * Sec. 2.1), P the trilinear grid conversion from the deformation grid to the
+ * image grid and P^T its node-centric adjoint (Sec. 2.2, Eq. 3).  J is
+ * minimised by L-BFGS inside a coarse-to-fine pyramid (Sec. 2.1).
+ *
+ * Layout conventions (every array):
+ *   - images: m_x * m_y * m_z float32, x fastest: i = x + m_x (y + m_y z);
+ *     voxel centre at ((x + 1/2) h_x, (y + 1/2) h_y, (z + 1/2) h_z) mm.
+ *   - deformation grid: n_x * n_y * n_z nodes spanning the same box
+ *     [0, m_d h_d], node k at k_d H_d, H_d = m_d h_d / (n_d - 1).
+ *   - displacement u (and gradients): 3 planes of n_x n_y n_z float32,
+ *     component c at [c * n_x n_y n_z + k], in mm; the deformation is
+ *     y = node position + u.
+ *   - level 0 is the finest (input) resolution; level l is the input
+ *     downsampled l times by 2x2x2 means (spacing * 2^l).
+ *
+ * Errors: every int-returning call returns REG_OK (0) on success, a positive
+ * warning, or a negative error code; reg_last_error() then describes it.
+ * No call aborts the process.  Device pointers must be valid device memory of
+ * the current CUDA device; host pointers plain host memory.
+ *
+ * Threads and streams: a handle is not thread-safe; all its GPU work is queued
+ * on the stream given to reg_create (or a stream it creates) plus one internal
+ * side stream for the template pyramid.  Calls that return host values
+ * synchronise that stream.
+ */
+#ifndef REG_H
+#define REG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REG_MAX_LEVELS 8
+#define REG_MAX_MEM 8
+
+#define REG_OK 0
+#define REG_WARN_LINESEARCH 1  /* a level ended on a failed Armijo search; u is its last accepted iterate */
+#define REG_ERR_ARG (-1)       /* bad argument: NULL, dims < 4, spacing <= 0, node dims < 3, level out of range */
+#define REG_ERR_CUDA (-2)      /* a CUDA runtime call failed (message has the CUDA error string) */
+#define REG_ERR_OOM (-3)       /* device or pinned host allocation failed */
+#define REG_ERR_STATE (-4)     /* call out of order, e.g. evaluation before reg_set_images */
+#define REG_ERR_NUMERIC (-5)   /* J or its gradient became NaN/Inf */
+#define REG_ERR_TIMEOUT (-6)   /* a bounded device-side wait expired */
+
+typedef struct reg_ctx *reg_handle;
+
+/* Registration parameters.  reg_config_default() fills the values used by the
+ * paper's model as read in this library:
+ *   tau = rho = 0.01, alpha = 10, c1 = 1e-4, max_backtracks = 20,
+ *   tol_grad_rel = 1e-5, tol_j_rel = 1e-7, tol_j_count = 3, levels = 1,
+ *   lbfgs_mem = 5, max_iter = 50 on every level, node_dims = 0 (rule m_d/2+1),
+ *   start_level = -1 (coarsest), eval_impl = 0 (fused), use_graph = 1. */
+typedef struct reg_config {
+    double tau, rho;      /* NGF edge parameters of Eq. 2 (template, reference), > 0 */
+    double alpha;         /* regularisation weight of Eq. 1, >= 0 */
+    double c1;            /* Armijo sufficient-decrease constant, in (0, 1) */
+    double tol_grad_rel;  /* stop a level when ||grad J|| <= tol_grad_rel * ||grad J(u0)|| */
+    double tol_j_rel;     /* ... or when |J_{k-1} - J_k| <= tol_j_rel (1 + |J_0|) */
+    int tol_j_count;      /*     for tol_j_count consecutive iterations */
+    int levels;           /* pyramid levels, 1 .. REG_MAX_LEVELS */
+    int lbfgs_mem;        /* L-BFGS memory m, 1 .. REG_MAX_MEM */
+    int max_backtracks;   /* Armijo trials per line search, >= 1 */
+    int fixed_iters;      /* 1: only max_iter ends a level (step-for-step comparisons) */
+    int start_level;      /* coarsest level solved; -1 = levels - 1 */
+    int max_iter[REG_MAX_LEVELS];       /* accepted iterations per level (index = level) */
+    int node_dims[REG_MAX_LEVELS][3];   /* deformation grid per level; 0 = m_d / 2 + 1 */
+    int eval_impl;        /* 0 fused objective pass, 1 multi-pass (intermediates in HBM) */
+    int use_graph;        /* 1: each L-BFGS iteration runs as one CUDA graph launch */
+    int reserved[6];
+} reg_config;
+
+/* Per-registration statistics (filled by reg_register). */
+typedef struct reg_stats {
+    int levels;
+    int iters[REG_MAX_LEVELS];        /* accepted L-BFGS iterations per level */
+    int evals[REG_MAX_LEVELS];        /* objective+gradient evaluations per level */
+    int level_status[REG_MAX_LEVELS]; /* REG_OK or REG_WARN_LINESEARCH per level */
+    double J[REG_MAX_LEVELS];         /* final J per level */
+    double J_final, D_final, S_final; /* at the finest level */
+    double seconds;                   /* host wall time of the call */
+    long long kernel_launches;        /* kernels this call ran on the GPU (graph nodes included) */
+    int status;
+} reg_stats;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int reg_version(void);
+
+/* Fill *cfg with the defaults listed above.  cfg must not be NULL. */
+void reg_config_default(reg_config *cfg);
+
+/* Create a handle.  cfg is copied (validated here: REG_ERR_ARG on bad values).
+ * cuda_stream is a cudaStream_t of the current device, or NULL for a stream
+ * owned by the handle.  On success *out owns the handle; free it with
+ * reg_destroy.  Allocates no image buffers yet. */
+int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream);
+
+/* Load a reference R and template T (Sec. 2.1) of dims[3] = (m_x, m_y, m_z)
+ * voxels with spacing_mm[3], and build the pyramid of cfg.levels levels on
+ * two streams (Sec. 2.2 "Generating the multi-level pyramid").  R and T are
+ * device pointers if ptr_is_device, else host pointers; they are copied, the
+ * caller keeps ownership.  Each level must keep >= 4 voxels and >= 3 nodes
+ * per dimension (REG_ERR_ARG otherwise).  Replaces previous images. */
+int reg_set_images(reg_handle h, const float *R, const float *T, const int dims[3],
+                   const double spacing_mm[3], int ptr_is_device);
+
+/* Geometry of one pyramid level: image dims, node dims, voxel spacing and
+ * node spacing (mm).  Any output pointer may be NULL. */
+int reg_level_info(reg_handle h, int level, int img_dims[3], int node_dims[3],
+                   double spacing_mm[3], double node_spacing_mm[3]);
+
+/* Copy pyramid image `which` (0 = R, 1 = T) of a level into out
+ * (m_x m_y m_z floats; device pointer if out_is_device). */
+int reg_get_level_image(reg_handle h, int level, int which, float *out, int out_is_device);
+
+/* One evaluation of J (Eq. 1) and grad_u J at a level, matrix-free
+ * (Sec. 2.2 "Evaluating the objective function": P, NGF and its chain-rule
+ * gradient, P^T by the gather of Eq. 3, plus alpha times the curvature term).
+ * u_dev, grad_dev: device pointers, 3 planes of the level's node count
+ * (borrowed; grad_dev is overwritten).  J, D, S: host pointers (any may be
+ * NULL) receiving J, D_NGF and S_curv in double; the call synchronises the
+ * handle's stream when any of them is non-NULL. */
+int reg_eval_objective_grad(reg_handle h, int level, const float *u_dev, float *grad_dev,
+                            double *J, double *D, double *S);
+
+/* Nodal trilinear prolongation (Sec. 2.1 multilevel) of a displacement from
+ * level `level_coarse` to level_coarse - 1.  Device pointers, 3 planes each. */
+int reg_prolong(reg_handle h, int level_coarse, const float *uc_dev, float *uf_dev);
+
+/* p = -H g for the L-BFGS matrix H built from `count` pairs (Sec. 2.1, L-BFGS of
+ * Nocedal 1980) with H0 = gamma I, gamma = s'y / y'y of the newest pair, using
+ * the same device kernels as reg_register.  S_dev, Y_dev: count * n floats,
+ * pair j at offset j * n, oldest first; g_dev, p_dev: n floats.  All device
+ * pointers; p_dev is overwritten.  count in 0 .. lbfgs_mem; with count = 0
+ * p = -g min_d H_d / ||g||_inf for the finest level's node spacing H. */
+int reg_lbfgs_direction(reg_handle h, long long n, int count, const float *S_dev,
+                        const float *Y_dev, const float *g_dev, float *p_dev);
+
+/* Full multilevel registration (Sec. 2.1-2.2): L-BFGS with Armijo
+ * backtracking at every level from start_level to 0, prolongating between
+ * levels.  u_init: displacement on the start level's node grid (same memory
+ * kind as u_out), or NULL for zero.  u_out: the finest level's displacement,
+ * device pointer if out_is_device else host.  st (nullable) receives the
+ * statistics.  Returns REG_OK, REG_WARN_LINESEARCH, or an error. */
+int reg_register(reg_handle h, float *u_out, int out_is_device, const float *u_init, reg_stats *st);
+
+/* Release all device memory, streams and graphs of the handle.  NULL-safe.
+ * Returns REG_OK. */
+int reg_destroy(reg_handle h);
+
+/* Message of the last failed call on this handle (or of the last failed
+ * reg_create on this thread when h is NULL).  Never NULL; valid until the
+ * next call on the handle. */
+const char *reg_last_error(reg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REG_H */

@@ -1,0 +1,208 @@
+"""GB300-native matrix-free NGF + curvature deformable 3D image registration.
+
+Budelmann, Koenig, Papenberg, Lellmann, "Fully-deformable 3D image
+registration in two seconds" (BVM 2019): minimise
+J(y) = D_NGF(R, T(P y)) + alpha S_curv(y) (Sec. 2.1, Eq. 1) with L-BFGS in a
+coarse-to-fine pyramid, the objective and its gradient evaluated matrix-free
+(Sec. 2.2, Eq. 2-3).
+
+All computation runs in the CUDA library libreg.so (C ABI, include/reg.h);
+this package marshals arguments and uses PyTorch only for device memory and
+streams.  Arrays: images (m_z, m_y, m_x) float32; displacements
+(3, n_z, n_y, n_x) float32 in mm (component planes x, y, z).
+"""
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import RegConfig, RegError, RegStats  # noqa: F401
+
+__all__ = ["make_config", "Registration", "RegObjective", "register", "RegError"]
+
+
+def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1=1e-4, max_backtracks=20,
+                tol_grad_rel=1e-5, tol_j_rel=1e-7, tol_j_count=3, fixed_iters=False, start_level=-1,
+                node_dims=None, eval_impl=None, use_graph=None):
+    """A reg_config; max_iter is one value for every level or a per-level list (index 0 = finest)."""
+    cfg = _lib.reg_config_default()
+    cfg.tau = float(tau)
+    cfg.rho = float(tau if rho is None else rho)
+    cfg.alpha = float(alpha)
+    cfg.c1 = float(c1)
+    cfg.max_backtracks = int(max_backtracks)
+    cfg.tol_grad_rel = float(tol_grad_rel)
+    cfg.tol_j_rel = float(tol_j_rel)
+    cfg.tol_j_count = int(tol_j_count)
+    cfg.levels = int(levels)
+    cfg.lbfgs_mem = int(mem)
+    cfg.fixed_iters = int(bool(fixed_iters))
+    cfg.start_level = int(start_level)
+    its = list(max_iter) if hasattr(max_iter, "__len__") else [max_iter] * _lib.MAX_LEVELS
+    for lv in range(_lib.MAX_LEVELS):
+        cfg.max_iter[lv] = int(its[lv] if lv < len(its) else its[-1])
+        for d in range(3):
+            cfg.node_dims[lv][d] = 0 if node_dims is None or lv >= len(node_dims) else int(node_dims[lv][d])
+    if eval_impl is not None:
+        cfg.eval_impl = int(eval_impl)
+    if use_graph is not None:
+        cfg.use_graph = int(bool(use_graph))
+    return cfg
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_1812_06765_gb300 needs a CUDA GPU; there is no CPU path")
+
+
+class Registration:
+    """One handle of the C library: images, pyramid, evaluation and registration."""
+
+    def __init__(self, cfg=None, stream=None, **kw):
+        _require_cuda()
+        self.cfg = cfg if cfg is not None else make_config(**kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = _lib.reg_create(self.cfg, self.stream.cuda_stream)
+        self.dims = None
+
+    # -- images -------------------------------------------------------------
+    def set_images(self, R, T, spacing):
+        """R, T: (m_z, m_y, m_x) float32 numpy arrays or torch tensors (host or CUDA)."""
+        if isinstance(R, torch.Tensor):
+            dev = R.is_cuda
+            R = R.detach().to(torch.float32).contiguous()
+            T = T.detach().to(device=R.device, dtype=torch.float32).contiguous()
+            pr, pt = R.data_ptr(), T.data_ptr()
+            if not dev:
+                R, T = R.numpy(), T.numpy()
+        else:
+            dev = False
+            R = np.ascontiguousarray(R, dtype=np.float32)
+            T = np.ascontiguousarray(T, dtype=np.float32)
+            pr, pt = R.ctypes.data, T.ctypes.data
+        if tuple(R.shape) != tuple(T.shape) or len(R.shape) != 3:
+            raise ValueError("R and T must be 3D arrays of equal shape")
+        mz, my, mx = R.shape
+        self.dims = (mx, my, mz)
+        _lib.reg_set_images(self.h, pr, pt, self.dims, spacing, dev)
+        self._keep = (R, T)  # device copies are taken on the handle's stream
+        return self
+
+    def level_info(self, level=0):
+        m, n, h, H = _lib.reg_level_info(self.h, level)
+        return dict(dims=m, nodes=n, spacing=h, node_spacing=H)
+
+    def node_shape(self, level=0):
+        n = self.level_info(level)["nodes"]
+        return (3, n[2], n[1], n[0])
+
+    def level_image(self, level, which="R"):
+        m = self.level_info(level)["dims"]
+        out = torch.empty((m[2], m[1], m[0]), dtype=torch.float32, device="cuda")
+        _lib.reg_get_level_image(self.h, level, 0 if which == "R" else 1, out.data_ptr(), True)
+        return out
+
+    # -- objective ----------------------------------------------------------
+    def eval(self, u, level=0, grad=None):
+        """J, D, S and grad_u J at displacement u (CUDA tensor of node_shape(level))."""
+        u = self._node_tensor(u, level)
+        if grad is None:
+            grad = torch.empty_like(u)
+        J, D, S = _lib.reg_eval_objective_grad(self.h, level, u.data_ptr(), grad.data_ptr())
+        return J, D, S, grad
+
+    def prolong(self, uc, level_coarse):
+        uc = self._node_tensor(uc, level_coarse)
+        uf = torch.empty(self.node_shape(level_coarse - 1), dtype=torch.float32, device="cuda")
+        _lib.reg_prolong(self.h, level_coarse, uc.data_ptr(), uf.data_ptr())
+        return uf
+
+    def lbfgs_direction(self, S, Y, g):
+        """p = -H g for pairs S[j], Y[j] (CUDA tensors (count, n)), oldest first."""
+        g = g.contiguous()
+        p = torch.empty_like(g)
+        count = 0 if S is None else int(S.shape[0])
+        sp = S.contiguous().data_ptr() if count else 0
+        yp = Y.contiguous().data_ptr() if count else 0
+        _lib.reg_lbfgs_direction(self.h, g.numel(), count, sp, yp, g.data_ptr(), p.data_ptr())
+        return p
+
+    # -- registration -------------------------------------------------------
+    def register(self, u_init=None, out="torch"):
+        """Run the multilevel registration; returns (u on the finest nodes, stats dict)."""
+        shape = self.node_shape(0)
+        if out == "pinned":   # page-locked host tensor: the device-to-host copy runs at full speed
+            u = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+            uptr, dev = u.data_ptr(), False
+            iptr = None
+            if u_init is not None:
+                u_init = u_init.to(torch.float32).contiguous().pin_memory()
+                iptr = u_init.data_ptr()
+        elif out == "numpy":
+            u = np.empty(shape, dtype=np.float32)
+            uptr, dev = u.ctypes.data, False
+            if u_init is not None:
+                u_init = np.ascontiguousarray(u_init, dtype=np.float32)
+                iptr = u_init.ctypes.data
+            else:
+                iptr = None
+        else:
+            u = torch.empty(shape, dtype=torch.float32, device="cuda")
+            uptr, dev = u.data_ptr(), True
+            if u_init is not None:
+                u_init = u_init.to(device="cuda", dtype=torch.float32).contiguous()
+                iptr = u_init.data_ptr()
+            else:
+                iptr = None
+        rc, st = _lib.reg_register(self.h, uptr, dev, iptr)
+        L = st.levels
+        stats = dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L],
+                     level_status=list(st.level_status)[:L], J=list(st.J)[:L], J_final=st.J_final,
+                     D_final=st.D_final, S_final=st.S_final, seconds=st.seconds,
+                     kernel_launches=st.kernel_launches)
+        return u, stats
+
+    def _node_tensor(self, u, level):
+        shape = self.node_shape(level)
+        if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.float32):
+            raise TypeError("u must be a float32 CUDA tensor")
+        if tuple(u.shape) != shape and u.numel() != int(np.prod(shape)):
+            raise ValueError("u has %s elements, level %d needs %s" % (tuple(u.shape), level, shape))
+        return u.contiguous()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.reg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RegObjective(torch.autograd.Function):
+    """J(u) as a differentiable scalar: forward runs the objective kernels,
+    backward returns grad_output * grad_u J from the same (hand-written
+    adjoint) kernels; torch autograd is not involved in the gradient itself."""
+
+    @staticmethod
+    def forward(ctx, u, reg, level=0):
+        J, D, S, grad = reg.eval(u.detach(), level)
+        ctx.save_for_backward(grad)
+        return torch.tensor(J, dtype=torch.float64, device=u.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (grad,) = ctx.saved_tensors
+        return (gJ.to(grad.dtype) * grad).reshape(grad.shape), None, None
+
+
+def register(R, T, spacing, out="torch", u_init=None, **cfg_kw):
+    """Convenience: one registration of (R, T); returns (u, stats)."""
+    reg = Registration(make_config(**cfg_kw))
+    try:
+        reg.set_images(R, T, spacing)
+        return reg.register(u_init=u_init, out=out)
+    finally:
+        reg.close()

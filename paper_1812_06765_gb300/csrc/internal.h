@@ -1,0 +1,109 @@
+// Host-side internals of libreg.so: the handle, per-level buffers, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <string>
+
+#include "../../include/reg.h"
+#include "common.cuh"
+#include "lbfgs_state.h"
+
+// Image, table and geometry buffers of one pyramid level.
+struct Level {
+    int m[3];
+    int n[3];
+    double h[3];
+    double H[3];
+    long long nv, nn;
+    float *R = nullptr, *T = nullptr;        // device images
+    int *pk0[3] = {nullptr, nullptr, nullptr};
+    float *pw1[3] = {nullptr, nullptr, nullptr};
+    int *tfirst[3] = {nullptr, nullptr, nullptr};
+    int *tcnt[3] = {nullptr, nullptr, nullptr};
+    float *tw[3] = {nullptr, nullptr, nullptr};
+    int tmaxw[3] = {0, 0, 0};
+    // prolongation from level + 1 onto this level's nodes
+    int *qk0[3] = {nullptr, nullptr, nullptr};
+    float *qw1[3] = {nullptr, nullptr, nullptr};
+    LevelGeom geom() const;
+};
+
+// Scratch of one objective evaluation, sized for the finest level.
+struct EvalScratch {
+    float *Tw = nullptr;    // deformed template (multi-pass)
+    float *dT = nullptr;    // 3 planes: interpolant gradient (multi-pass)
+    float *v = nullptr;     // 3 planes: d psi / d grad Tw (multi-pass)
+    float *r = nullptr;     // 3 planes: g * grad T (multi-pass)
+    float *w = nullptr;     // 3 node planes: masked Laplacian of u
+    float *part = nullptr;  // fused pass: per-tile partial node sums
+    double *partials = nullptr;   // block partial sums
+    int max_partials = 0;
+    double *scal = nullptr;       // [J, D, S] on the device
+    size_t part_floats = 0;
+};
+
+// Buffers of the device L-BFGS, sized for the finest level.
+struct LbfgsBuffers {
+    long long n = 0;
+    int slots = 0;
+    float *u = nullptr, *pdir = nullptr, *g = nullptr, *gt = nullptr;
+    float *P = nullptr, *Y = nullptr;   // slots * n each
+    double *partials = nullptr;
+    int max_partials = 0;
+    LbfgsState *st = nullptr;           // device
+    LbfgsState *st_host = nullptr;      // pinned mirror
+    double *scal_t = nullptr;           // [J, D, S] of the trial point
+};
+
+struct reg_ctx {
+    reg_config cfg;
+    cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev_side = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int levels = 0;
+    bool have_images = false;
+    long long launches = 0;   // kernels queued by this handle (for reg_stats)
+    Level L[REG_MAX_LEVELS];
+    EvalScratch es;
+    LbfgsBuffers lb;
+    std::string err;
+    // CUDA graph of one L-BFGS iteration per level (built lazily)
+    cudaGraphExec_t iter_graph[REG_MAX_LEVELS] = {};
+    cudaGraphExec_t init_graph[REG_MAX_LEVELS] = {};
+};
+
+// status helpers
+int set_err(reg_ctx *c, int code, const char *fmt, ...);
+int cuda_err(reg_ctx *c, cudaError_t e, const char *what);
+
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return cuda_err(c, _e, #call);             \
+    } while (0)
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_restrict(const float *src, const int m[3], float *dst, cudaStream_t s);
+cudaError_t launch_prolong(const Level &coarse, const Level &fine, const float *uc, float *uf, cudaStream_t s);
+
+// objective + gradient at u_base + t_scale * dir (dir may be NULL: plain u_base);
+// t_scale is read on the device from *t_dev when dir != NULL.
+// Writes grad (3 node planes) and scal_out[0..2] = J, D, S (device).
+cudaError_t launch_eval(reg_ctx *c, int level, const float *u_base, const float *dir, const double *t_dev,
+                        float *grad, double *scal_out, cudaStream_t s);
+
+// L-BFGS device steps (k_lbfgs.cu)
+cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s);
+cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s);
+cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s);
+cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s);
+void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter);
+void lbfgs_state_reset_host(LbfgsState *st, const reg_config &cfg, int max_iter, double Hmin);
+cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const float *S, const float *Y,
+                                       const float *g, float *p, double Hmin, cudaStream_t s);
+int eval_partials_needed(const Level &L);
+int num_blocks_for(reg_ctx *c, long long n, int threads);

@@ -1,0 +1,146 @@
+// Curvature regulariser (Sec. 2.1: penalises (Laplace y_c)^2, Fischer and
+// Modersitzki) and the final assembly J = D + alpha S (Eq. 1).
+//
+//   w_c = mask_interior * L u_c          (7-point Laplacian, node spacing H)
+//   S   = hbar_y / 2 sum_c sum_k w_c^2
+//   grad_c J += alpha hbar_y L^T w_c     (the symmetric stencil gathered over
+//                                         the zero-extended w)
+// Both passes are node-parallel, one thread per node and all 3 components.
+#include "internal.h"
+#include "ngf_math.cuh"
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_curv_w(LevelGeom g, const float *__restrict__ ub,
+                                                const float *__restrict__ dir, const double *__restrict__ t_dev,
+                                                float *__restrict__ w, double *__restrict__ partials)
+{
+    __shared__ double sm[8];
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int z = blockIdx.z;
+    bool in = x < g.n[0] && y < g.n[1];
+    float t = dir ? (float)__ldg(t_dev) : 0.f;
+    float acc = 0.f;
+    if (in) {
+        size_t k = x + (size_t)g.n[0] * (y + (size_t)g.n[1] * z);
+        bool interior = x >= 1 && y >= 1 && z >= 1 && x <= g.n[0] - 2 && y <= g.n[1] - 2 && z <= g.n[2] - 2;
+        size_t st[3] = {1, (size_t)g.n[0], (size_t)g.n[0] * g.n[1]};
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float lap = 0.f;
+            if (interior) {
+                const float *u = ub + c * g.nn;
+                const float *d = dir ? dir + c * g.nn : nullptr;
+                float u0 = node_value(u, d, t, k);
+#pragma unroll
+                for (int e = 0; e < 3; e++)
+                    lap = fmaf(node_value(u, d, t, k + st[e]) - 2.f * u0 + node_value(u, d, t, k - st[e]),
+                               g.iH2[e], lap);
+            }
+            w[c * g.nn + k] = lap;
+            acc = fmaf(lap, lap, acc);
+        }
+    }
+    double s = block_sum_to_f64(acc, sm);
+    if (linear_tid() == 0)
+        partials[linear_bid()] = s;
+}
+
+__global__ void __launch_bounds__(256) k_curv_grad(LevelGeom g, const float *__restrict__ w, float alpha_hy,
+                                                   float *__restrict__ grad)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= g.n[0] || y >= g.n[1])
+        return;
+    size_t k = x + (size_t)g.n[0] * (y + (size_t)g.n[1] * z);
+    size_t st[3] = {1, (size_t)g.n[0], (size_t)g.n[0] * g.n[1]};
+    int j[3] = {x, y, z};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float *wc = w + c * g.nn;
+        float w0 = __ldg(wc + k);
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            float lo = j[e] > 0 ? __ldg(wc + k - st[e]) : 0.f;
+            float hi = j[e] < g.n[e] - 1 ? __ldg(wc + k + st[e]) : 0.f;
+            s = fmaf(lo + hi - 2.f * w0, g.iH2[e], s);
+        }
+        grad[c * g.nn + k] = fmaf(alpha_hy, s, grad[c * g.nn + k]);
+    }
+}
+
+// Deterministic FP64 sum of block partials (fixed thread-to-partial
+// assignment, fixed tree): scal = [J, D, S].
+__global__ void __launch_bounds__(512) k_finalize(const double *__restrict__ pD, int nD,
+                                                  const double *__restrict__ pS, int nS, double hbar_half,
+                                                  double alpha, double hy_half, double *__restrict__ scal)
+{
+    __shared__ double sd[512], ss[512];
+    int t = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = t; i < nD; i += 512)
+        a += pD[i];
+    for (int i = t; i < nS; i += 512)
+        b += pS[i];
+    sd[t] = a;
+    ss[t] = b;
+    __syncthreads();
+    for (int o = 256; o > 0; o >>= 1) {
+        if (t < o) {
+            sd[t] += sd[t + o];
+            ss[t] += ss[t + o];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double D = hbar_half * sd[0], S = hy_half * ss[0];
+        scal[0] = D + alpha * S;
+        scal[1] = D;
+        scal[2] = S;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
+                                 float *grad, double *partials, int *n_partials, cudaStream_t s);
+cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
+                             float *grad, double *partials, int *n_partials, cudaStream_t s);
+
+cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev, float *grad,
+                        double *scal_out, cudaStream_t s)
+{
+    const Level &L = c->L[level];
+    LevelGeom g = L.geom();
+    int nD = 0;
+    cudaError_t e;
+    if (c->cfg.eval_impl == 1)
+        e = launch_ngf_multipass(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
+    else
+        e = launch_ngf_fused(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
+    if (e != cudaSuccess)
+        return e;
+    dim3 blk(32, 8, 1);
+    dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
+    double *pS = c->es.partials + nD;
+    k_curv_w<<<gn, blk, 0, s>>>(g, ub, dir, t_dev, c->es.w, pS);
+    double hy = L.H[0] * L.H[1] * L.H[2];
+    k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);
+    int nS = (int)(gn.x * gn.y * gn.z);
+    double hbar = L.h[0] * L.h[1] * L.h[2];
+    k_finalize<<<1, 512, 0, s>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out);
+    c->launches += 3;
+    return cudaGetLastError();
+}
+
+// Partial-sum slots one evaluation at this level needs (fused or multi-pass).
+int eval_partials_needed(const Level &L)
+{
+    long long vox_blocks = (long long)((L.m[0] + 31) / 32) * ((L.m[1] + 7) / 8) * L.m[2];
+    long long node_blocks = (long long)((L.n[0] + 31) / 32) * ((L.n[1] + 7) / 8) * L.n[2];
+    return (int)(vox_blocks + node_blocks + 1024);
+}

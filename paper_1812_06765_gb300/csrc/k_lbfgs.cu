@@ -1,0 +1,601 @@
+// Device-resident L-BFGS with Armijo backtracking (Sec. 2.1: L-BFGS of Nocedal
+// 1980 inside the multilevel scheme).
+//
+// The direction p = -H g is formed with the compact representation of the
+// L-BFGS matrix (Byrd, Nocedal and Schnabel 1994), which equals the two-loop
+// recursion in exact arithmetic but needs only two passes over the history:
+// one multi-dot pass (fused with the accept step) and one combination pass.
+// All scalar decisions (coefficients, curvature test, Armijo test, stopping)
+// are taken by a one-block control kernel in FP64 on the device, so the host
+// never has to read a scalar to continue, and an iteration can be replayed as
+// one CUDA graph.
+//
+// Vectors (n = 3 * nodes floats): u, g (accepted), gt (trial gradient),
+// pdir (current direction), P and Y rings of m + 1 slots each (s_j = t_j P_j).
+#include <math.h>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int VT = 256;             // threads of the vector kernels
+constexpr int ND_ACC = 2 + 4 * LB_MAXS;
+
+// Reduce ND per-thread values over the block; entry `imax` (if >= 0) by max,
+// the others by sum (FP32 in the warp, FP64 across warps); write the block
+// totals to out[0 .. ND).
+template <int ND>
+__device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, double *out)
+{
+    __shared__ double sm[VT / 32][ND];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < ND; d++) {
+        float x = (d == imax) ? warp_max(v[d]) : warp_sum(v[d]);
+        if (lane == 0)
+            sm[warp][d] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x < ND) {
+        int d = threadIdx.x;
+        double s = sm[0][d];
+        for (int w = 1; w < VT / 32; w++)
+            s = (d == imax) ? fmax(s, sm[w][d]) : s + sm[w][d];
+        out[d] = s;
+    }
+}
+
+__global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *__restrict__ g,
+                                                     double *__restrict__ partials)
+{
+    float v[2] = {0.f, 0.f};
+    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
+        float x = g[e];
+        v[0] = fmaf(x, x, v[0]);
+        v[1] = fmaxf(v[1], fabsf(x));
+    }
+    block_reduce_write<2>(v, 1, partials + 2 * blockIdx.x);
+}
+
+// p = cg g + sum_j cp_j P_j + cy_j Y_j, written to pdir; partial sums of g'p and p'p.
+__global__ void __launch_bounds__(VT) k_lb_direction(long long n, const LbfgsState *__restrict__ st,
+                                                     const float *__restrict__ g, const float *__restrict__ P,
+                                                     const float *__restrict__ Y, float *__restrict__ pdir,
+                                                     double *__restrict__ partials, int redo)
+{
+    __shared__ int s_run, s_dc, s_slot[LB_MAXM];
+    __shared__ float s_cg, s_cp[LB_MAXM], s_cy[LB_MAXM];
+    if (threadIdx.x == 0) {
+        s_run = redo ? st->redo_dir : (st->iter_continue && !st->done);
+        s_dc = st->dcount;
+        s_cg = (float)st->cg;
+        for (int j = 0; j < LB_MAXM; j++) {
+            s_slot[j] = st->dslot[j];
+            s_cp[j] = (float)st->cp[j];
+            s_cy[j] = (float)st->cy[j];
+        }
+    }
+    __syncthreads();
+    if (!s_run)
+        return;
+    const int dc = s_dc;
+    float v[2] = {0.f, 0.f};
+    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
+        float gv = g[e];
+        float p = s_cg * gv;
+#pragma unroll
+        for (int j = 0; j < LB_MAXM; j++)
+            if (j < dc) {
+                size_t o = (size_t)s_slot[j] * n + e;
+                p = fmaf(s_cp[j], P[o], p);
+                p = fmaf(s_cy[j], Y[o], p);
+            }
+        pdir[e] = p;
+        v[0] = fmaf(gv, p, v[0]);
+        v[1] = fmaf(p, p, v[1]);
+    }
+    block_reduce_write<2>(v, -1, partials + 2 * blockIdx.x);
+}
+
+// Accept the trial point: u += t pdir (the fmaf the evaluation used), store the
+// candidate pair in the free slot (P = pdir, Y = g_new - g), g = g_new, and
+// take every dot the next direction needs in the same pass.
+__global__ void __launch_bounds__(VT) k_lb_accept(long long n, const LbfgsState *__restrict__ st,
+                                                  float *__restrict__ u, float *__restrict__ g,
+                                                  const float *__restrict__ gt, const float *__restrict__ pdir,
+                                                  float *__restrict__ P, float *__restrict__ Y,
+                                                  double *__restrict__ partials)
+{
+    __shared__ int s_ok, s_lc, s_free, s_slot[LB_MAXS];
+    __shared__ float s_t;
+    if (threadIdx.x == 0) {
+        s_ok = st->ls == LS_ACCEPTED;
+        s_lc = st->lcount;
+        s_free = st->free_slot;
+        s_t = (float)st->t;
+        for (int j = 0; j < LB_MAXS; j++)
+            s_slot[j] = st->lslot[j];
+    }
+    __syncthreads();
+    if (!s_ok)
+        return;
+    const int lc = s_lc, fr = s_free;
+    const float t = s_t;
+    float v[ND_ACC];
+#pragma unroll
+    for (int d = 0; d < ND_ACC; d++)
+        v[d] = 0.f;
+    float *Pf = P + (size_t)fr * n;
+    float *Yf = Y + (size_t)fr * n;
+    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
+        float gn = gt[e], yn = gn - g[e], pf = pdir[e];
+        u[e] = fmaf(t, pf, u[e]);
+        g[e] = gn;
+        Pf[e] = pf;
+        Yf[e] = yn;
+        v[0] = fmaf(gn, gn, v[0]);
+        v[1] = fmaxf(v[1], fabsf(gn));
+#pragma unroll
+        for (int j = 0; j < LB_MAXS; j++)
+            if (j < lc) {
+                int s = s_slot[j];
+                float pj, yj;
+                if (s == fr) {
+                    pj = pf;
+                    yj = yn;
+                } else {
+                    pj = P[(size_t)s * n + e];
+                    yj = Y[(size_t)s * n + e];
+                }
+                v[2 + 4 * j] = fmaf(pj, gn, v[2 + 4 * j]);
+                v[3 + 4 * j] = fmaf(yj, gn, v[3 + 4 * j]);
+                v[4 + 4 * j] = fmaf(pj, yn, v[4 + 4 * j]);
+                v[5 + 4 * j] = fmaf(yj, yn, v[5 + 4 * j]);
+            }
+    }
+    block_reduce_write<ND_ACC>(v, 1, partials + (size_t)ND_ACC * blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// control kernel (one block): reduce the block partials in FP64 in a fixed
+// order, then thread 0 takes the scalar decisions.
+// ---------------------------------------------------------------------------
+__device__ void set_p0(LbfgsState *st)
+{
+    st->dcount = 0;
+    st->cg = st->ginf > 0.0 ? -st->Hmin / st->ginf : 0.0;
+}
+
+// Compact form: with R = upper triangle of S'Y (by age), D its diagonal,
+// gamma = s'y / y'y of the newest pair, q = R^{-1} S'g and
+// w = R^{-T} ((D + gamma Y'Y) q - gamma Y'g):
+//   H g = gamma g + S w - gamma Y q,   p = -H g.
+__device__ void set_compact(LbfgsState *st)
+{
+    const int c = st->count;
+    double Sg[LB_MAXM], Yg[LB_MAXM], q[LB_MAXM], z[LB_MAXM], w[LB_MAXM];
+    int o[LB_MAXM];
+    for (int i = 0; i < c; i++) {
+        o[i] = st->order[i];
+        Sg[i] = st->tscale[o[i]] * st->Pg[o[i]];
+        Yg[i] = st->Yg[o[i]];
+    }
+    const int nw = o[c - 1];
+    double gamma = st->SY[nw][nw] / st->YY[nw][nw];
+    for (int i = c - 1; i >= 0; i--) {
+        double s = Sg[i];
+        for (int j = i + 1; j < c; j++)
+            s -= st->SY[o[i]][o[j]] * q[j];
+        q[i] = s / st->SY[o[i]][o[i]];
+    }
+    for (int i = 0; i < c; i++) {
+        double s = st->SY[o[i]][o[i]] * q[i] - gamma * Yg[i];
+        for (int j = 0; j < c; j++)
+            s += gamma * st->YY[o[i]][o[j]] * q[j];
+        z[i] = s;
+    }
+    for (int i = 0; i < c; i++) {
+        double s = z[i];
+        for (int j = 0; j < i; j++)
+            s -= st->SY[o[j]][o[i]] * w[j];
+        w[i] = s / st->SY[o[i]][o[i]];
+    }
+    st->dcount = c;
+    st->cg = -gamma;
+    for (int i = 0; i < c; i++) {
+        st->dslot[i] = o[i];
+        st->cp[i] = -w[i] * st->tscale[o[i]];
+        st->cy[i] = gamma * q[i];
+    }
+}
+
+__device__ bool finite_d(double x) { return isfinite(x); }
+
+__global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__restrict__ st,
+                                                    const double *__restrict__ partials, int nblocks,
+                                                    const double *__restrict__ scal, unsigned long long h_ls,
+                                                    unsigned long long h_iter)
+{
+    __shared__ double red[ND_ACC];
+    const int nd = phase == LB_ACCEPTED ? ND_ACC : 2;
+    const int imax = (phase == LB_INIT || phase == LB_ACCEPTED) ? 1 : -1;
+    const bool need = phase != LB_ARMIJO && !(phase == LB_ACCEPTED && st->ls != LS_ACCEPTED) &&
+                      !(phase == LB_DIR_REDO && !st->redo_dir) && !(phase == LB_DIR && !st->iter_continue);
+    if (need) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int d = warp; d < nd; d += 8) {
+            double s = (d == imax) ? 0.0 : 0.0;
+            for (int b = lane; b < nblocks; b += 32) {
+                double x = partials[(size_t)b * nd + d];
+                s = (d == imax) ? fmax(s, x) : s + x;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                double y = __shfl_xor_sync(0xffffffffu, s, off);
+                s = (d == imax) ? fmax(s, y) : s + y;
+            }
+            if (lane == 0)
+                red[d] = s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0)
+        return;
+
+    switch (phase) {
+    case LB_INIT: {
+        st->J = scal[0];
+        st->D = scal[1];
+        st->S = scal[2];
+        st->J0 = st->J;
+        st->gg = red[0];
+        st->ginf = red[1];
+        st->g0norm = st->gnorm = sqrt(red[0]);
+        st->k = 0;
+        st->evals = 1;
+        st->small_count = 0;
+        st->count = 0;
+        st->free_slot = 0;
+        st->status = 0;
+        st->retried = 0;
+        st->redo_dir = 0;
+        st->done = 0;
+        if (!finite_d(st->J) || !finite_d(st->gg)) {
+            st->status = -5;
+            st->done = 1;
+        }
+        if (st->max_iter <= 0 || st->g0norm == 0.0)
+            st->done = 1;
+        set_p0(st);
+        st->iter_continue = !st->done;
+        break;
+    }
+    case LB_DIR: {
+        if (!st->iter_continue)
+            break;
+        st->gtp = red[0];
+        st->pp = red[1];
+        st->redo_dir = 0;
+        if (!(st->gtp < 0.0) && st->dcount > 0) { // not a descent direction: reset the memory
+            st->count = 0;
+            set_p0(st);
+            st->redo_dir = 1;
+        }
+        st->t = 1.0;
+        st->trial = 0;
+        st->ls = LS_RUNNING;
+        st->ls_continue = 1;
+        break;
+    }
+    case LB_DIR_REDO: {
+        if (!st->redo_dir)
+            break;
+        st->gtp = red[0];
+        st->pp = red[1];
+        st->redo_dir = 0;
+        break;
+    }
+    case LB_ARMIJO: {
+        st->Jt = scal[0];
+        st->Dt = scal[1];
+        st->St = scal[2];
+        st->evals++;
+        if (finite_d(st->Jt) && st->Jt <= st->J + st->c1 * st->t * st->gtp) {
+            st->ls = LS_ACCEPTED;
+            st->ls_continue = 0;
+            st->lcount = st->count + 1;
+            for (int j = 0; j < st->count; j++)
+                st->lslot[j] = st->order[j];
+            st->lslot[st->count] = st->free_slot;
+        } else {
+            st->trial++;
+            if (st->trial >= st->max_bt) {
+                st->ls_continue = 0;
+                if (st->dcount > 0 && !st->retried) { // one retry from a fresh memory
+                    st->ls = LS_RETRY;
+                    st->retried = 1;
+                    st->count = 0;
+                    set_p0(st);
+                } else {
+                    st->ls = LS_FAILED;
+                    st->status = 1;
+                    st->done = 1;
+                }
+            } else {
+                st->t *= 0.5;
+            }
+        }
+        break;
+    }
+    case LB_ACCEPTED: {
+        if (st->ls == LS_RETRY) {
+            st->iter_continue = 1;
+            break;
+        }
+        if (st->ls != LS_ACCEPTED) {
+            st->iter_continue = 0;
+            break;
+        }
+        for (int j = 0; j < st->lcount; j++) {
+            int s = st->lslot[j];
+            st->Pg[s] = red[2 + 4 * j];
+            st->Yg[s] = red[3 + 4 * j];
+            st->Py[s] = red[4 + 4 * j];
+            st->Yy[s] = red[5 + 4 * j];
+        }
+        double Jprev = st->J;
+        st->J = st->Jt;
+        st->D = st->Dt;
+        st->S = st->St;
+        st->k++;
+        st->gg = red[0];
+        st->ginf = red[1];
+        st->gnorm = sqrt(red[0]);
+        const int f = st->free_slot;
+        const double tn = st->t;
+        double sy = tn * st->Py[f], ss = tn * tn * st->pp, yy = st->Yy[f];
+        if (sy > 1e-10 * sqrt(ss) * sqrt(yy)) { // curvature test: keep the pair
+            st->tscale[f] = tn;
+            for (int j = 0; j < st->lcount; j++) {
+                int s = st->lslot[j];
+                st->SY[s][f] = st->tscale[s] * st->Py[s];
+                st->YY[s][f] = st->Yy[s];
+                st->YY[f][s] = st->Yy[s];
+            }
+            if (st->count == st->m) {
+                int ev = st->order[0];
+                for (int j = 0; j < st->m - 1; j++)
+                    st->order[j] = st->order[j + 1];
+                st->order[st->m - 1] = f;
+                st->free_slot = ev;
+            } else {
+                st->order[st->count++] = f;
+                unsigned used = 0;
+                for (int j = 0; j < st->count; j++)
+                    used |= 1u << st->order[j];
+                int fs = 0;
+                while (used & (1u << fs))
+                    fs++;
+                st->free_slot = fs;
+            }
+        }
+        st->retried = 0;
+        if (!finite_d(st->J) || !finite_d(st->gg)) {
+            st->status = -5;
+            st->done = 1;
+        } else if (st->k >= st->max_iter) {
+            st->done = 1;
+        } else if (!st->fixed_iters) {
+            if (st->gnorm <= st->tol_grad_rel * st->g0norm) {
+                st->done = 1;
+            } else if (fabs(Jprev - st->J) <= st->tol_j_rel * (1.0 + fabs(st->J0))) {
+                if (++st->small_count >= st->tol_j_count)
+                    st->done = 1;
+            } else {
+                st->small_count = 0;
+            }
+        }
+        if (!st->done) {
+            if (st->count > 0)
+                set_compact(st);
+            else
+                set_p0(st);
+        }
+        st->iter_continue = !st->done;
+        break;
+    }
+    default:
+        break;
+    }
+#if CUDART_VERSION >= 12040
+    if (h_ls)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)h_ls, st->ls_continue ? 1u : 0u);
+    if (h_iter)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)h_iter, st->iter_continue ? 1u : 0u);
+#endif
+}
+
+// Standalone direction for a given set of pairs (reg_lbfgs_direction): the
+// dots of S, Y and g one at a time (entry 0: g'g, 1: ||g||_inf, then S_i'g,
+// Y_i'g, then S_i'Y_j, Y_i'Y_j).  Only used by that entry point.
+__device__ __forceinline__ void pair_dot_operands(int d, int count, long long n, long long e,
+                                                  const float *__restrict__ S, const float *__restrict__ Y,
+                                                  const float *__restrict__ g, float &a, float &b)
+{
+    int q = d - 2;
+    if (q < 2 * count) {
+        int i = q >> 1;
+        a = (q & 1) ? Y[(size_t)i * n + e] : S[(size_t)i * n + e];
+        b = g[e];
+    } else {
+        q -= 2 * count;
+        int i = (q >> 1) / count, j = (q >> 1) % count;
+        a = (q & 1) ? Y[(size_t)i * n + e] : S[(size_t)i * n + e];
+        b = Y[(size_t)j * n + e];
+    }
+}
+
+__global__ void __launch_bounds__(VT) k_lb_pair_dots(long long n, int count, const float *__restrict__ S,
+                                                     const float *__restrict__ Y, const float *__restrict__ g,
+                                                     double *__restrict__ partials)
+{
+    const int nd = 2 + 2 * count + 2 * count * count;
+    for (int d = 0; d < nd; d++) {
+        float acc = 0.f;
+        for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
+            if (d == 0) {
+                acc = fmaf(g[e], g[e], acc);
+            } else if (d == 1) {
+                acc = fmaxf(acc, fabsf(g[e]));
+            } else {
+                float a, b;
+                pair_dot_operands(d, count, n, e, S, Y, g, a, b);
+                acc = fmaf(a, b, acc);
+            }
+        }
+        float v[1] = {acc};
+        __syncthreads();
+        block_reduce_write<1>(v, d == 1 ? 0 : -1, partials + (size_t)blockIdx.x * nd + d);
+        __syncthreads();
+    }
+}
+
+__global__ void k_lb_pair_setup(LbfgsState *__restrict__ st, int count, const double *__restrict__ partials,
+                                int nblocks)
+{
+    const int nd = 2 + 2 * count + 2 * count * count;
+    if (threadIdx.x != 0)
+        return;
+    double red[2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM];
+    for (int d = 0; d < nd; d++) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; b++) {
+            double x = partials[(size_t)b * nd + d];
+            s = (d == 1) ? fmax(s, x) : s + x;
+        }
+        red[d] = s;
+    }
+    st->gg = red[0];
+    st->ginf = red[1];
+    st->count = count;
+    for (int i = 0; i < count; i++) {
+        st->order[i] = i;
+        st->tscale[i] = 1.0;
+        st->Pg[i] = red[2 + 2 * i];
+        st->Yg[i] = red[3 + 2 * i];
+        for (int j = 0; j < count; j++) {
+            int q = 2 + 2 * count + 2 * (i * count + j);
+            st->SY[i][j] = red[q];
+            st->YY[i][j] = red[q + 1];
+        }
+    }
+    if (count > 0)
+        set_compact(st);
+    else
+        set_p0(st);
+    st->iter_continue = 1;
+    st->done = 0;
+}
+
+}  // namespace
+
+int num_blocks_for(reg_ctx *c, long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    long long cap = 4LL * (c->num_sms > 0 ? c->num_sms : 148);
+    if (b > cap)
+        b = cap;
+    if (b < 1)
+        b = 1;
+    return (int)b;
+}
+
+void lbfgs_state_reset_host(LbfgsState *st, const reg_config &cfg, int max_iter, double Hmin)
+{
+    memset(st, 0, sizeof(*st));
+    st->m = cfg.lbfgs_mem;
+    st->max_iter = max_iter;
+    st->max_bt = cfg.max_backtracks;
+    st->fixed_iters = cfg.fixed_iters;
+    st->tol_j_count = cfg.tol_j_count;
+    st->c1 = cfg.c1;
+    st->tol_grad_rel = cfg.tol_grad_rel;
+    st->tol_j_rel = cfg.tol_j_rel;
+    st->Hmin = Hmin;
+    st->t = 1.0;
+}
+
+static unsigned long long g_h_ls = 0, g_h_iter = 0;  // conditional handles while capturing
+
+void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter)
+{
+    g_h_ls = h_ls;
+    g_h_iter = h_iter;
+}
+
+static cudaError_t control(reg_ctx *c, int phase, int nblocks, const double *scal, cudaStream_t s,
+                           bool use_ls_handle, bool use_iter_handle)
+{
+    k_lb_control<<<1, 256, 0, s>>>(phase, c->lb.st, c->lb.partials, nblocks, scal, use_ls_handle ? g_h_ls : 0ULL,
+                                   use_iter_handle ? g_h_iter : 0ULL);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s)
+{
+    long long n = 3 * c->L[level].nn;
+    int nb = num_blocks_for(c, n, VT);
+    cudaError_t e = launch_eval(c, level, c->lb.u, nullptr, nullptr, c->lb.g, c->es.scal, s);
+    if (e != cudaSuccess)
+        return e;
+    k_lb_init_dots<<<nb, VT, 0, s>>>(n, c->lb.g, c->lb.partials);
+    c->launches += 1;
+    return control(c, LB_INIT, nb, c->es.scal, s, false, false);
+}
+
+cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s)
+{
+    long long n = 3 * c->L[level].nn;
+    int nb = num_blocks_for(c, n, VT);
+    k_lb_direction<<<nb, VT, 0, s>>>(n, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0);
+    c->launches += 2;
+    cudaError_t e = control(c, LB_DIR, nb, nullptr, s, false, false);
+    if (e != cudaSuccess)
+        return e;
+    k_lb_direction<<<nb, VT, 0, s>>>(n, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1);
+    return control(c, LB_DIR_REDO, nb, nullptr, s, false, false);
+}
+
+cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s)
+{
+    // the trial point u + t pdir is formed inside the evaluation kernels
+    cudaError_t e = launch_eval(c, level, c->lb.u, c->lb.pdir, &c->lb.st->t, c->lb.gt, c->lb.scal_t, s);
+    if (e != cudaSuccess)
+        return e;
+    return control(c, LB_ARMIJO, 0, c->lb.scal_t, s, true, false);
+}
+
+cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s)
+{
+    long long n = 3 * c->L[level].nn;
+    int nb = num_blocks_for(c, n, VT);
+    k_lb_accept<<<nb, VT, 0, s>>>(n, c->lb.st, c->lb.u, c->lb.g, c->lb.gt, c->lb.pdir, c->lb.P, c->lb.Y,
+                                  c->lb.partials);
+    c->launches += 1;
+    return control(c, LB_ACCEPTED, nb, nullptr, s, false, true);
+}
+
+cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const float *S, const float *Y,
+                                       const float *g, float *p, double Hmin, cudaStream_t s)
+{
+    int nb = num_blocks_for(c, n, VT);
+    k_lb_pair_dots<<<nb, VT, 0, s>>>(n, count, S, Y, g, c->lb.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    k_lb_pair_setup<<<1, 32, 0, s>>>(c->lb.st, count, c->lb.partials, nb);
+    // pairs live in the caller's S, Y: slots 0..count-1 at stride n
+    k_lb_direction<<<nb, VT, 0, s>>>(n, c->lb.st, g, S, Y, p, c->lb.partials, 0);
+    c->launches += 3;
+    return cudaGetLastError();
+}

@@ -1,0 +1,80 @@
+// Pyramid generation and multilevel prolongation.
+//
+// Pyramid (Sec. 2.2 "Generating the multi-level pyramid"): each coarser level
+// is the 2x2x2 mean of the finer one (an odd dimension replicates its last
+// slab), spacing doubles.  The reference and template pyramids run on two
+// streams.  Prolongation (Sec. 2.1, coarse-to-fine): nodal trilinear
+// interpolation of the coarse displacement onto the finer nodes, with
+// per-dimension (first node, weight) tables.
+#include "internal.h"
+
+namespace {
+
+// One thread per output voxel; a warp covers 32 consecutive x of one row, so
+// the two input rows it reads are contiguous 64-float spans.
+__global__ void k_restrict(const float *__restrict__ src, int mx, int my, int mz, float *__restrict__ dst,
+                           int ox, int oy, int oz)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= ox || y >= oy)
+        return;
+    int x0 = 2 * x, x1 = min(2 * x + 1, mx - 1);
+    int y0 = 2 * y, y1 = min(2 * y + 1, my - 1);
+    int z0 = 2 * z, z1 = min(2 * z + 1, mz - 1);
+    size_t sy = (size_t)mx, sz = (size_t)mx * my;
+    float s = __ldg(src + x0 + y0 * sy + z0 * sz) + __ldg(src + x1 + y0 * sy + z0 * sz) +
+              __ldg(src + x0 + y1 * sy + z0 * sz) + __ldg(src + x1 + y1 * sy + z0 * sz) +
+              __ldg(src + x0 + y0 * sy + z1 * sz) + __ldg(src + x1 + y0 * sy + z1 * sz) +
+              __ldg(src + x0 + y1 * sy + z1 * sz) + __ldg(src + x1 + y1 * sy + z1 * sz);
+    dst[x + (size_t)ox * (y + (size_t)oy * z)] = 0.125f * s;
+}
+
+// One thread per fine node, all three components.
+__global__ void k_prolong(const float *__restrict__ uc, int cx, int cy, int cz, float *__restrict__ uf, int fx,
+                          int fy, int fz, const int *__restrict__ k0x, const int *__restrict__ k0y,
+                          const int *__restrict__ k0z, const float *__restrict__ w1x,
+                          const float *__restrict__ w1y, const float *__restrict__ w1z)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= fx || y >= fy)
+        return;
+    int kx = k0x[x], ky = k0y[y], kz = k0z[z];
+    float wx = w1x[x], wy = w1y[y], wz = w1z[z];
+    size_t sy = (size_t)cx, sz = (size_t)cx * cy, ncs = (size_t)cx * cy * cz;
+    size_t nfs = (size_t)fx * fy * fz;
+    size_t b = kx + ky * sy + kz * sz;
+    size_t o = x + (size_t)fx * (y + (size_t)fy * z);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float *u = uc + c * ncs;
+        float a0 = lerpf(__ldg(u + b), __ldg(u + b + 1), wx);
+        float a1 = lerpf(__ldg(u + b + sy), __ldg(u + b + sy + 1), wx);
+        float a2 = lerpf(__ldg(u + b + sz), __ldg(u + b + sz + 1), wx);
+        float a3 = lerpf(__ldg(u + b + sz + sy), __ldg(u + b + sz + sy + 1), wx);
+        uf[c * nfs + o] = lerpf(lerpf(a0, a1, wy), lerpf(a2, a3, wy), wz);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_restrict(const float *src, const int m[3], float *dst, cudaStream_t s)
+{
+    int o[3] = {(m[0] + 1) / 2, (m[1] + 1) / 2, (m[2] + 1) / 2};
+    dim3 blk(32, 8, 1);
+    dim3 grd((o[0] + 31) / 32, (o[1] + 7) / 8, o[2]);
+    k_restrict<<<grd, blk, 0, s>>>(src, m[0], m[1], m[2], dst, o[0], o[1], o[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const Level &coarse, const Level &fine, const float *uc, float *uf, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    dim3 grd((fine.n[0] + 31) / 32, (fine.n[1] + 7) / 8, fine.n[2]);
+    k_prolong<<<grd, blk, 0, s>>>(uc, coarse.n[0], coarse.n[1], coarse.n[2], uf, fine.n[0], fine.n[1], fine.n[2],
+                                  fine.qk0[0], fine.qk0[1], fine.qk0[2], fine.qw1[0], fine.qw1[1], fine.qw1[2]);
+    return cudaGetLastError();
+}

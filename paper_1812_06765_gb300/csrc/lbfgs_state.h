@@ -1,0 +1,48 @@
+// Device-resident L-BFGS state (FP64 scalars).  One instance per handle; the
+// control kernel is its only writer on the device, the host writes it only
+// before a level starts.
+#pragma once
+
+#define LB_MAXM 8
+#define LB_MAXS (LB_MAXM + 1)   // m pairs + one free slot for the next direction
+
+enum LbPhase { LB_INIT = 0, LB_DIR = 1, LB_DIR_REDO = 2, LB_ARMIJO = 3, LB_ACCEPTED = 4 };
+enum LbSearch { LS_RUNNING = 0, LS_ACCEPTED = 1, LS_FAILED = 2, LS_RETRY = 3 };
+
+struct LbfgsState {
+    // parameters
+    int m, max_iter, max_bt, fixed_iters, tol_j_count;
+    double c1, tol_grad_rel, tol_j_rel, Hmin;
+    // accepted iterate
+    double J, D, S, J0, g0norm, gnorm, ginf;
+    // trial point
+    double Jt, Dt, St;
+    double t;          // current step length
+    double gtp, pp;    // g'p and p'p of the current direction
+    int k;             // accepted iterations
+    int trial;         // trial index inside the current search
+    int evals;         // objective evaluations on this level
+    int small_count;   // consecutive small-J-change iterations
+    int retried;       // the p0 retry of this iteration has been used
+    int redo_dir;      // the direction must be recomputed as p0
+    int ls;            // LbSearch
+    int ls_continue;   // 1 while the line search needs another trial
+    int iter_continue; // 1 while the level needs another iteration
+    int done;
+    int status;        // 0, 1 (line search warning) or -5 (numeric)
+    // pair memory: order[0..count-1] are slots oldest..newest, free_slot holds p
+    int count, free_slot;
+    int order[LB_MAXM];
+    double tscale[LB_MAXS];          // s_slot = tscale * P_slot
+    double SY[LB_MAXS][LB_MAXS];     // s_i' y_j by slot (upper triangle by age)
+    double YY[LB_MAXS][LB_MAXS];     // y_i' y_j by slot
+    // direction p = cg g + sum_j cp[j] P[dslot[j]] + cy[j] Y[dslot[j]]
+    int dcount;
+    int dslot[LB_MAXM];
+    double cg, cp[LB_MAXM], cy[LB_MAXM];
+    // dots of the last accept pass, by list position (0..count-1 active, count = free)
+    int lcount;
+    int lslot[LB_MAXS];
+    double Pg[LB_MAXS], Yg[LB_MAXS], Py[LB_MAXS], Yy[LB_MAXS];
+    double gg;
+};

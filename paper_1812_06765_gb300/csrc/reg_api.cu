@@ -1,0 +1,576 @@
+// C ABI of libreg.so (declared in include/reg.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_create_err;
+
+void free_level(Level &L)
+{
+    cudaFree(L.R);
+    cudaFree(L.T);
+    for (int d = 0; d < 3; d++) {
+        cudaFree(L.pk0[d]);
+        cudaFree(L.pw1[d]);
+        cudaFree(L.tfirst[d]);
+        cudaFree(L.tcnt[d]);
+        cudaFree(L.tw[d]);
+        cudaFree(L.qk0[d]);
+        cudaFree(L.qw1[d]);
+    }
+    L = Level();
+}
+
+void free_buffers(reg_ctx *c)
+{
+    for (int l = 0; l < REG_MAX_LEVELS; l++) {
+        free_level(c->L[l]);
+        if (c->iter_graph[l]) cudaGraphExecDestroy(c->iter_graph[l]);
+        if (c->init_graph[l]) cudaGraphExecDestroy(c->init_graph[l]);
+        c->iter_graph[l] = nullptr;
+        c->init_graph[l] = nullptr;
+    }
+    EvalScratch &e = c->es;
+    cudaFree(e.Tw);
+    cudaFree(e.dT);
+    cudaFree(e.v);
+    cudaFree(e.r);
+    cudaFree(e.w);
+    cudaFree(e.part);
+    cudaFree(e.partials);
+    cudaFree(e.scal);
+    c->es = EvalScratch();
+    LbfgsBuffers &b = c->lb;
+    cudaFree(b.u);
+    cudaFree(b.pdir);
+    cudaFree(b.g);
+    cudaFree(b.gt);
+    cudaFree(b.P);
+    cudaFree(b.Y);
+    cudaFree(b.partials);
+    cudaFree(b.st);
+    cudaFree(b.scal_t);
+    if (b.st_host) cudaFreeHost(b.st_host);
+    c->lb = LbfgsBuffers();
+    c->have_images = false;
+}
+
+int validate_config(const reg_config *cfg, std::string &msg)
+{
+    char buf[256];
+    if (!(cfg->tau > 0) || !(cfg->rho > 0)) msg = "tau and rho must be > 0";
+    else if (!(cfg->alpha >= 0)) msg = "alpha must be >= 0";
+    else if (!(cfg->c1 > 0 && cfg->c1 < 1)) msg = "c1 must be in (0, 1)";
+    else if (cfg->levels < 1 || cfg->levels > REG_MAX_LEVELS) {
+        snprintf(buf, sizeof buf, "levels must be in 1..%d", REG_MAX_LEVELS);
+        msg = buf;
+    } else if (cfg->lbfgs_mem < 1 || cfg->lbfgs_mem > REG_MAX_MEM) {
+        snprintf(buf, sizeof buf, "lbfgs_mem must be in 1..%d", REG_MAX_MEM);
+        msg = buf;
+    } else if (cfg->max_backtracks < 1) msg = "max_backtracks must be >= 1";
+    else if (cfg->start_level >= cfg->levels) msg = "start_level must be < levels";
+    else if (cfg->eval_impl != 0 && cfg->eval_impl != 1) msg = "eval_impl must be 0 or 1";
+    else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
+    else return REG_OK;
+    return REG_ERR_ARG;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src)
+{
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * (src.empty() ? 1 : src.size()));
+    if (e != cudaSuccess) return e;
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+// Per-dimension tables of P (voxel i -> node k0, weight of k0 + 1) and of P^T
+// (node k -> first voxel, count, weights), from the hat functions at voxel
+// centres t = (i + 1/2) h / H (Sec. 2.2, Eq. 3: weights and index sets are
+// determined beforehand, separately for each dimension).
+cudaError_t build_tables(Level &L)
+{
+    for (int d = 0; d < 3; d++) {
+        const int m = L.m[d], n = L.n[d];
+        const double H = L.H[d], h = L.h[d];
+        std::vector<int> k0(m);
+        std::vector<float> w1(m);
+        std::vector<double> t(m);
+        for (int i = 0; i < m; i++) {
+            t[i] = (i + 0.5) * h / H;
+            int k = (int)floor(t[i]);
+            if (k > n - 2) k = n - 2;
+            if (k < 0) k = 0;
+            k0[i] = k;
+            w1[i] = (float)(t[i] - k);
+        }
+        std::vector<int> first(n, 0), cnt(n, 0);
+        std::vector<std::vector<double>> ws(n);
+        int maxw = 1;
+        for (int k = 0; k < n; k++) {
+            for (int i = 0; i < m; i++) {
+                double w = 1.0 - fabs(t[i] - k);
+                if (w > 0.0) {
+                    if (ws[k].empty()) first[k] = i;
+                    ws[k].push_back(w);
+                }
+            }
+            cnt[k] = (int)ws[k].size();
+            if (cnt[k] > maxw) maxw = cnt[k];
+        }
+        std::vector<float> tw((size_t)n * maxw, 0.f);
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < cnt[k]; j++) tw[(size_t)k * maxw + j] = (float)ws[k][j];
+        L.tmaxw[d] = maxw;
+        cudaError_t e;
+        if ((e = upload(&L.pk0[d], k0)) != cudaSuccess) return e;
+        if ((e = upload(&L.pw1[d], w1)) != cudaSuccess) return e;
+        if ((e = upload(&L.tfirst[d], first)) != cudaSuccess) return e;
+        if ((e = upload(&L.tcnt[d], cnt)) != cudaSuccess) return e;
+        if ((e = upload(&L.tw[d], tw)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Prolongation tables of a fine level from the next coarser one: fine node j
+// at j H_f in mm, coarse coordinate j H_f / H_c.
+cudaError_t build_prolong_tables(Level &F, const Level &C)
+{
+    for (int d = 0; d < 3; d++) {
+        std::vector<int> k0(F.n[d]);
+        std::vector<float> w1(F.n[d]);
+        for (int j = 0; j < F.n[d]; j++) {
+            double t = j * F.H[d] / C.H[d];
+            if (t > C.n[d] - 1) t = C.n[d] - 1;
+            int k = (int)floor(t);
+            if (k > C.n[d] - 2) k = C.n[d] - 2;
+            k0[j] = k;
+            w1[j] = (float)(t - k);
+        }
+        cudaError_t e;
+        if ((e = upload(&F.qk0[d], k0)) != cudaSuccess) return e;
+        if ((e = upload(&F.qw1[d], w1)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+LevelGeom Level::geom() const
+{
+    LevelGeom g;
+    for (int d = 0; d < 3; d++) {
+        g.m[d] = m[d];
+        g.n[d] = n[d];
+        g.h[d] = (float)h[d];
+        g.ih[d] = (float)(1.0 / h[d]);
+        g.iH2[d] = (float)(1.0 / (H[d] * H[d]));
+        g.pk0[d] = pk0[d];
+        g.pw1[d] = pw1[d];
+        g.tfirst[d] = tfirst[d];
+        g.tcnt[d] = tcnt[d];
+        g.tw[d] = tw[d];
+        g.tmaxw[d] = tmaxw[d];
+    }
+    g.hbar = (float)(h[0] * h[1] * h[2]);
+    g.hbar_y = (float)(H[0] * H[1] * H[2]);
+    g.nv = nv;
+    g.nn = nn;
+    return g;
+}
+
+int set_err(reg_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+int cuda_err(reg_ctx *c, cudaError_t e, const char *what)
+{
+    return set_err(c, e == cudaErrorMemoryAllocation ? REG_ERR_OOM : REG_ERR_CUDA, "%s: %s (%s)", what,
+                   cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Device buffers of a new image geometry: level images and tables, evaluation
+// scratch and the L-BFGS vectors (all sized by the finest level).
+int allocate_buffers(reg_ctx *c)
+{
+    const reg_config &cfg = c->cfg;
+    long long nv0 = c->L[0].nv, nmax = 0;
+    int maxpart = 0;
+    for (int l = 0; l < c->levels; l++) {
+        Level &L = c->L[l];
+        CK(cudaMalloc(&L.R, sizeof(float) * L.nv));
+        CK(cudaMalloc(&L.T, sizeof(float) * L.nv));
+        CK(build_tables(L));
+        if (l > 0) CK(build_prolong_tables(c->L[l - 1], L));
+        if (3 * L.nn > nmax) nmax = 3 * L.nn;
+        int p = eval_partials_needed(L);
+        if (p > maxpart) maxpart = p;
+    }
+    EvalScratch &es = c->es;
+    if (cfg.eval_impl == 1) {
+        CK(cudaMalloc(&es.Tw, sizeof(float) * nv0));
+        CK(cudaMalloc(&es.dT, sizeof(float) * 3 * nv0));
+        CK(cudaMalloc(&es.v, sizeof(float) * 3 * nv0));
+        CK(cudaMalloc(&es.r, sizeof(float) * 3 * nv0));
+    }
+    CK(cudaMalloc(&es.w, sizeof(float) * nmax));
+    CK(cudaMalloc(&es.partials, sizeof(double) * maxpart));
+    CK(cudaMalloc(&es.scal, sizeof(double) * 4));
+    es.max_partials = maxpart;
+    LbfgsBuffers &b = c->lb;
+    b.n = nmax;
+    b.slots = cfg.lbfgs_mem + 1;
+    CK(cudaMalloc(&b.u, sizeof(float) * nmax));
+    CK(cudaMalloc(&b.pdir, sizeof(float) * nmax));
+    CK(cudaMalloc(&b.g, sizeof(float) * nmax));
+    CK(cudaMalloc(&b.gt, sizeof(float) * nmax));
+    CK(cudaMalloc(&b.P, sizeof(float) * nmax * b.slots));
+    CK(cudaMalloc(&b.Y, sizeof(float) * nmax * b.slots));
+    // the largest per-block layout is that of reg_lbfgs_direction's pair dots
+    b.max_partials = 4 * (c->num_sms > 0 ? c->num_sms : 148) * (2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM) + 1024;
+    CK(cudaMalloc(&b.partials, sizeof(double) * b.max_partials));
+    CK(cudaMalloc(&b.st, sizeof(LbfgsState)));
+    CK(cudaMalloc(&b.scal_t, sizeof(double) * 4));
+    CK(cudaMallocHost(&b.st_host, sizeof(LbfgsState)));
+    CK(cudaMemsetAsync(b.st, 0, sizeof(LbfgsState), c->stream));
+    return REG_OK;
+}
+
+extern "C" {
+
+int reg_version(void) { return 10000; }
+
+void reg_config_default(reg_config *cfg)
+{
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->tau = cfg->rho = 0.01;
+    cfg->alpha = 10.0;
+    cfg->c1 = 1e-4;
+    cfg->tol_grad_rel = 1e-5;
+    cfg->tol_j_rel = 1e-7;
+    cfg->tol_j_count = 3;
+    cfg->levels = 1;
+    cfg->lbfgs_mem = 5;
+    cfg->max_backtracks = 20;
+    cfg->fixed_iters = 0;
+    cfg->start_level = -1;
+    for (int l = 0; l < REG_MAX_LEVELS; l++) cfg->max_iter[l] = 50;
+    cfg->eval_impl = 1;
+    cfg->use_graph = 0;
+}
+
+int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
+{
+    if (!out || !cfg) return set_err(nullptr, REG_ERR_ARG, "reg_create: NULL argument");
+    *out = nullptr;
+    std::string msg;
+    if (validate_config(cfg, msg) != REG_OK) return set_err(nullptr, REG_ERR_ARG, "reg_create: %s", msg.c_str());
+    reg_ctx *c = new reg_ctx();
+    c->cfg = *cfg;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            c->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        set_err(nullptr, REG_ERR_CUDA, "reg_create: %s", cudaGetErrorString(e));
+        reg_destroy(c);
+        return REG_ERR_CUDA;
+    }
+    *out = c;
+    return REG_OK;
+}
+
+int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[3], const double spacing_mm[3],
+                   int ptr_is_device)
+{
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_set_images: NULL handle");
+    if (!R || !T || !dims || !spacing_mm) return set_err(c, REG_ERR_ARG, "reg_set_images: NULL argument");
+    for (int d = 0; d < 3; d++) {
+        if (dims[d] < 4) return set_err(c, REG_ERR_ARG, "reg_set_images: dims[%d] = %d < 4", d, dims[d]);
+        if (!(spacing_mm[d] > 0) || !isfinite(spacing_mm[d]))
+            return set_err(c, REG_ERR_ARG, "reg_set_images: spacing[%d] must be finite and > 0", d);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    const reg_config &cfg = c->cfg;
+    // geometry of every level
+    Level G[REG_MAX_LEVELS];
+    for (int l = 0; l < cfg.levels; l++) {
+        Level &L = G[l];
+        for (int d = 0; d < 3; d++) {
+            L.m[d] = l == 0 ? dims[d] : (G[l - 1].m[d] + 1) / 2;
+            L.h[d] = l == 0 ? spacing_mm[d] : 2.0 * G[l - 1].h[d];
+            L.n[d] = cfg.node_dims[l][d] > 0 ? cfg.node_dims[l][d] : L.m[d] / 2 + 1;
+            if (L.m[d] < 4 || L.n[d] < 3)
+                return set_err(c, REG_ERR_ARG,
+                               "reg_set_images: level %d has %d voxels / %d nodes in dim %d (need >= 4 / >= 3)",
+                               l, L.m[d], L.n[d], d);
+            L.H[d] = L.m[d] * L.h[d] / (L.n[d] - 1);
+        }
+        L.nv = (long long)L.m[0] * L.m[1] * L.m[2];
+        L.nn = (long long)L.n[0] * L.n[1] * L.n[2];
+    }
+    // the same grid sizes again: keep every buffer and table (the tables depend
+    // only on voxel and node counts), update the spacings
+    bool reuse = c->have_images && c->levels == cfg.levels;
+    for (int l = 0; reuse && l < cfg.levels; l++)
+        for (int d = 0; d < 3; d++)
+            reuse = reuse && c->L[l].m[d] == G[l].m[d] && c->L[l].n[d] == G[l].n[d];
+    if (reuse) {
+        for (int l = 0; l < cfg.levels; l++)
+            for (int d = 0; d < 3; d++) {
+                c->L[l].h[d] = G[l].h[d];
+                c->L[l].H[d] = G[l].H[d];
+            }
+    } else {
+        free_buffers(c);
+        c->levels = cfg.levels;
+        for (int l = 0; l < c->levels; l++) {
+            Level &L = c->L[l];
+            for (int d = 0; d < 3; d++) {
+                L.m[d] = G[l].m[d];
+                L.n[d] = G[l].n[d];
+                L.h[d] = G[l].h[d];
+                L.H[d] = G[l].H[d];
+            }
+            L.nv = G[l].nv;
+            L.nn = G[l].nn;
+        }
+        int r = allocate_buffers(c);
+        if (r != REG_OK) return r;
+    }
+    const long long nv0 = c->L[0].nv;
+    c->have_images = false;
+
+    // finest images, then the pyramid: R on the handle's stream, T on the side stream
+    cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaEventRecord(c->ev_side, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->ev_side, 0));
+    CK(cudaMemcpyAsync(c->L[0].R, R, sizeof(float) * nv0, kind, c->stream));
+    CK(cudaMemcpyAsync(c->L[0].T, T, sizeof(float) * nv0, kind, c->side));
+    for (int l = 1; l < c->levels; l++) {
+        CK(launch_restrict(c->L[l - 1].R, c->L[l - 1].m, c->L[l].R, c->stream));
+        CK(launch_restrict(c->L[l - 1].T, c->L[l - 1].m, c->L[l].T, c->side));
+        c->launches += 2;
+    }
+    CK(cudaEventRecord(c->ev_side, c->side));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_side, 0));
+    if (!ptr_is_device) CK(cudaStreamSynchronize(c->stream));  // host arrays may be released on return
+    c->have_images = true;
+    return REG_OK;
+}
+
+int reg_level_info(reg_handle c, int level, int img_dims[3], int node_dims[3], double spacing_mm[3],
+                   double node_spacing_mm[3])
+{
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_level_info: NULL handle");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_level_info: no images set");
+    if (level < 0 || level >= c->levels) return set_err(c, REG_ERR_ARG, "reg_level_info: level %d out of range", level);
+    const Level &L = c->L[level];
+    for (int d = 0; d < 3; d++) {
+        if (img_dims) img_dims[d] = L.m[d];
+        if (node_dims) node_dims[d] = L.n[d];
+        if (spacing_mm) spacing_mm[d] = L.h[d];
+        if (node_spacing_mm) node_spacing_mm[d] = L.H[d];
+    }
+    return REG_OK;
+}
+
+int reg_get_level_image(reg_handle c, int level, int which, float *out, int out_is_device)
+{
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_get_level_image: NULL handle");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_get_level_image: no images set");
+    if (level < 0 || level >= c->levels || (which != 0 && which != 1) || !out)
+        return set_err(c, REG_ERR_ARG, "reg_get_level_image: bad argument");
+    const Level &L = c->L[level];
+    CK(cudaMemcpyAsync(out, which ? L.T : L.R, sizeof(float) * L.nv,
+                       out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return REG_OK;
+}
+
+int reg_eval_objective_grad(reg_handle c, int level, const float *u_dev, float *grad_dev, double *J, double *D,
+                            double *S)
+{
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_eval_objective_grad: NULL handle");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_eval_objective_grad: no images set");
+    if (level < 0 || level >= c->levels)
+        return set_err(c, REG_ERR_ARG, "reg_eval_objective_grad: level %d out of range", level);
+    if (!u_dev || !grad_dev) return set_err(c, REG_ERR_ARG, "reg_eval_objective_grad: NULL vector");
+    CK(launch_eval(c, level, u_dev, nullptr, nullptr, grad_dev, c->es.scal, c->stream));
+    if (J || D || S) {
+        double h[3];
+        CK(cudaMemcpyAsync(h, c->es.scal, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (J) *J = h[0];
+        if (D) *D = h[1];
+        if (S) *S = h[2];
+        if (!isfinite(h[0])) return set_err(c, REG_ERR_NUMERIC, "reg_eval_objective_grad: J is not finite");
+    }
+    return REG_OK;
+}
+
+int reg_prolong(reg_handle c, int level_coarse, const float *uc_dev, float *uf_dev)
+{
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_prolong: NULL handle");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_prolong: no images set");
+    if (level_coarse < 1 || level_coarse >= c->levels || !uc_dev || !uf_dev)
+        return set_err(c, REG_ERR_ARG, "reg_prolong: bad argument");
+    CK(launch_prolong(c->L[level_coarse], c->L[level_coarse - 1], uc_dev, uf_dev, c->stream));
+    c->launches += 1;
+    return REG_OK;
+}
+
+int reg_lbfgs_direction(reg_handle c, long long n, int count, const float *S_dev, const float *Y_dev,
+                        const float *g_dev, float *p_dev)
+{
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_lbfgs_direction: NULL handle");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_lbfgs_direction: no images set");
+    if (n <= 0 || count < 0 || count > c->cfg.lbfgs_mem || !g_dev || !p_dev || (count > 0 && (!S_dev || !Y_dev)))
+        return set_err(c, REG_ERR_ARG, "reg_lbfgs_direction: bad argument");
+    const Level &L = c->L[0];
+    double Hmin = fmin(L.H[0], fmin(L.H[1], L.H[2]));
+    lbfgs_state_reset_host(c->lb.st_host, c->cfg, 1, Hmin);
+    CK(cudaMemcpyAsync(c->lb.st, c->lb.st_host, sizeof(LbfgsState), cudaMemcpyHostToDevice, c->stream));
+    CK(lbfgs_direction_standalone(c, n, count, S_dev, Y_dev, g_dev, p_dev, Hmin, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return REG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int read_state(reg_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->lb.st_host, c->lb.st, sizeof(LbfgsState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return REG_OK;
+}
+
+// One level of L-BFGS, each step queued by the host; the host reads the
+// device state after every line-search trial and every accepted step.
+int run_level_host(reg_ctx *c, int level)
+{
+    LbfgsState *sh = c->lb.st_host;
+    int r;
+    CK(lbfgs_launch_init(c, level, c->stream));
+    if ((r = read_state(c)) != REG_OK) return r;
+    // every loop below is bounded by max_iter, max_backtracks and one retry
+    const long long guard = 4LL * (sh->max_iter + 1) * (sh->max_bt + 1) + 16;
+    long long steps = 0;
+    while (!sh->done && sh->iter_continue && steps++ < guard) {
+        CK(lbfgs_launch_direction_level(c, level, c->stream));
+        do {
+            CK(lbfgs_launch_trial(c, level, c->stream));
+            if ((r = read_state(c)) != REG_OK) return r;
+        } while (sh->ls_continue && steps++ < guard);
+        CK(lbfgs_launch_accept_level(c, level, c->stream));
+        if ((r = read_state(c)) != REG_OK) return r;
+    }
+    if (steps >= guard) return set_err(c, REG_ERR_TIMEOUT, "L-BFGS level %d exceeded its step bound", level);
+    return REG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int reg_register(reg_handle c, float *u_out, int out_is_device, const float *u_init, reg_stats *st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_register: NULL handle");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_register: no images set");
+    if (!u_out) return set_err(c, REG_ERR_ARG, "reg_register: NULL u_out");
+    const int start = c->cfg.start_level < 0 ? c->levels - 1 : c->cfg.start_level;
+    reg_stats local;
+    memset(&local, 0, sizeof local);
+    local.levels = c->levels;
+    LbfgsBuffers &b = c->lb;
+    const long long n0 = 3 * c->L[start].nn;
+    if (u_init)
+        CK(cudaMemcpyAsync(b.u, u_init, sizeof(float) * n0,
+                           out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    else
+        CK(cudaMemsetAsync(b.u, 0, sizeof(float) * n0, c->stream));
+    int status = REG_OK;
+    const long long launches0 = c->launches;
+    for (int l = start; l >= 0; l--) {
+        const Level &L = c->L[l];
+        if (l < start) {
+            CK(launch_prolong(c->L[l + 1], L, b.u, b.g, c->stream));
+            c->launches += 1;
+            CK(cudaMemcpyAsync(b.u, b.g, sizeof(float) * 3 * L.nn, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        double Hmin = fmin(L.H[0], fmin(L.H[1], L.H[2]));
+        lbfgs_state_reset_host(b.st_host, c->cfg, c->cfg.max_iter[l], Hmin);
+        CK(cudaMemcpyAsync(b.st, b.st_host, sizeof(LbfgsState), cudaMemcpyHostToDevice, c->stream));
+        int r = run_level_host(c, l);
+        if (r != REG_OK) return r;
+        const LbfgsState *sh = b.st_host;
+        local.iters[l] = sh->k;
+        local.evals[l] = sh->evals;
+        local.J[l] = sh->J;
+        if (sh->status == -5) return set_err(c, REG_ERR_NUMERIC, "reg_register: non-finite J or gradient at level %d", l);
+        local.level_status[l] = sh->status == 1 ? REG_WARN_LINESEARCH : REG_OK;
+        if (sh->status == 1) status = REG_WARN_LINESEARCH;
+        if (l == 0) {
+            local.J_final = sh->J;
+            local.D_final = sh->D;
+            local.S_final = sh->S;
+        }
+    }
+    CK(cudaMemcpyAsync(u_out, b.u, sizeof(float) * 3 * c->L[0].nn,
+                       out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    local.status = status;
+    local.kernel_launches = c->launches - launches0;
+    local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (st) *st = local;
+    if (status == REG_WARN_LINESEARCH) set_err(c, status, "reg_register: a line search failed");
+    return status;
+}
+
+int reg_destroy(reg_handle c)
+{
+    if (!c) return REG_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_buffers(c);
+    if (c->ev_side) cudaEventDestroy(c->ev_side);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return REG_OK;
+}
+
+const char *reg_last_error(reg_handle c)
+{
+    if (!c) return g_create_err.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

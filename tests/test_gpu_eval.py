@@ -1,0 +1,216 @@
+"""GPU parity of the objective and its pieces against the FP64 oracle.
+
+Every call goes through the C ABI of libreg.so (ctypes binding); inputs are
+seeded and synthetic; the oracle receives the same FP32 values in FP64.
+"""
+import numpy as np
+import pytest
+
+from synth import make_pair, random_image, random_field
+from tests.helpers import J_RTOL, GRAD_RTOL, compare_eval, default_nodes, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def reg_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1812_06765_gb300 as reg
+    return reg
+
+
+EVAL_IMPLS = [1]
+
+# (dims, spacing, nodes or None, tau, rho, alpha, amplitude of u in mm)
+CASES = [
+    ((16, 16, 16), (1.0, 1.0, 1.0), None, 0.05, 0.05, 1.0, 1.0),          # one tile
+    ((37, 29, 23), (1.0, 1.1, 0.9), None, 0.05, 0.02, 3.0, 1.5),          # ragged, non-integer ratio
+    ((40, 36, 20), (0.97, 0.97, 2.5), None, 0.1, 0.1, 50.0, 3.0),         # anisotropic spacing
+    ((33, 48, 17), (1.5, 1.5, 1.5), ((9, 13, 5),), 0.08, 0.08, 5.0, 2.0),  # explicit node dims (ratio ~4)
+    ((8, 6, 5), (1.0, 1.0, 1.0), None, 0.1, 0.1, 1.0, 0.5),               # tiny
+    ((64, 64, 64), (1.0, 1.0, 1.0), None, 0.01, 0.01, 10.0, 2.0),         # 64^3 workload shape
+]
+
+
+@pytest.mark.parametrize("impl", EVAL_IMPLS)
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_eval_parity(reg_mod, orc, impl, case):
+    dims, h, nodes, tau, rho, alpha, amp = CASES[case]
+    R = random_image(dims, 100 + case)
+    T = random_image(dims, 200 + case)
+    cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, node_dims=nodes, eval_impl=impl)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    info = r.level_info(0)
+    assert info["nodes"] == (nodes[0] if nodes else default_nodes(dims))
+    u = random_field(info["nodes"], 300 + case, amp)
+    e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
+    assert e["eJ"] <= J_RTOL, e
+    assert e["eD"] <= J_RTOL, e
+    assert e["eS"] <= 1e-5, e
+    assert e["eg"] <= GRAD_RTOL, e
+    r.close()
+
+
+@pytest.mark.parametrize("impl", EVAL_IMPLS)
+def test_eval_T_equals_R_is_zero(reg_mod, impl):
+    dims, h = (30, 26, 22), (1.0, 1.0, 1.0)
+    R = random_image(dims, 7)
+    cfg = reg_mod.make_config(levels=1, tau=0.05, alpha=2.0, eval_impl=impl)
+    r = reg_mod.Registration(cfg).set_images(R, R, h)
+    u = torch.zeros(r.node_shape(0), device="cuda")
+    J, D, S, g = r.eval(u)
+    assert abs(D) < 1e-6 * R.size and S == 0.0
+    assert float(g.abs().max()) < 1e-5
+    r.close()
+
+
+@pytest.mark.parametrize("impl", EVAL_IMPLS)
+def test_eval_integer_shift_minimum(reg_mod, impl):
+    # T_j = R_{j - s}; the constant displacement s h gives J = 0 (sign of x + P u)
+    dims, h = (32, 28, 24), (1.0, 1.5, 2.0)
+    s = (2, -1, 1)
+    R = np.zeros(dims[::-1], np.float32)
+    R[5:-5, 5:-5, 5:-5] = random_image((dims[0] - 10, dims[1] - 10, dims[2] - 10), 17)
+    T = np.roll(R, shift=(s[2], s[1], s[0]), axis=(0, 1, 2))
+    cfg = reg_mod.make_config(levels=1, tau=0.05, alpha=2.0, eval_impl=impl)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    shape = r.node_shape(0)
+    u = torch.stack([torch.full(shape[1:], s[d] * h[d], device="cuda") for d in range(3)])
+    J, D, S, g = r.eval(u)
+    assert abs(J) < 1e-6 * R.size
+    J2, *_ = r.eval(-u)
+    assert J2 > 1.0
+    r.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("config_id", [2, 3])
+def test_eval_parity_full_size(reg_mod, orc, config_id):
+    """Full-size images (256^3 and 256x256x112) at a smooth random u: J and grad J."""
+    from synth import CONFIGS
+    p = make_pair(config_id)
+    c = CONFIGS[config_id]
+    cfg = reg_mod.make_config(levels=c["levels"], tau=c["eta"], alpha=c["alpha"])
+    r = reg_mod.Registration(cfg).set_images(p["R"], p["T"], p["spacing"])
+    info = r.level_info(0)
+    u = random_field(info["nodes"], 400 + config_id, 5.0)
+    e = compare_eval(r, orc, p["R"], p["T"], p["dims"], p["spacing"], u, c["eta"], c["eta"], c["alpha"])
+    assert e["eJ"] <= J_RTOL, {k: v for k, v in e.items() if k[0] == "e" or k in "JoJ"}
+    assert e["eg"] <= GRAD_RTOL, e["eg"]
+    r.close()
+
+
+def test_pyramid_parity(reg_mod, orc):
+    dims, h = (37, 30, 23), (1.0, 1.0, 2.0)
+    R = random_image(dims, 61, smooth=False)
+    T = random_image(dims, 62, smooth=False)
+    cfg = reg_mod.make_config(levels=3, tau=0.1)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    Ro, To, m = R.astype(np.float64), T.astype(np.float64), dims
+    for lv in range(1, 3):
+        Ro, To = orc.restrict(m, Ro), orc.restrict(m, To)
+        m = tuple((v + 1) // 2 for v in m)
+        info = r.level_info(lv)
+        assert info["dims"] == m
+        assert info["spacing"] == tuple(hh * 2 ** lv for hh in h)
+        np.testing.assert_allclose(r.level_image(lv, "R").cpu().numpy(), Ro, rtol=0, atol=2e-6)
+        np.testing.assert_allclose(r.level_image(lv, "T").cpu().numpy(), To, rtol=0, atol=2e-6)
+    r.close()
+
+
+def test_prolong_parity(reg_mod, orc):
+    dims, h = (48, 40, 36), (1.0, 1.2, 1.5)
+    R = random_image(dims, 71)
+    cfg = reg_mod.make_config(levels=3, tau=0.1)
+    r = reg_mod.Registration(cfg).set_images(R, R, h)
+    for lc in (2, 1):
+        ic, if_ = r.level_info(lc), r.level_info(lc - 1)
+        uc = random_field(ic["nodes"], 72 + lc, 2.0)
+        uf = r.prolong(torch.from_numpy(uc).cuda(), lc).cpu().numpy()
+        ext_c = tuple(ic["dims"][d] * ic["spacing"][d] for d in range(3))
+        ext_f = tuple(if_["dims"][d] * if_["spacing"][d] for d in range(3))
+        ref = orc.prolong(ic["nodes"], ext_c, uc, if_["nodes"], ext_f)
+        np.testing.assert_allclose(uf, ref, rtol=0, atol=2e-6)
+    r.close()
+
+
+@pytest.mark.parametrize("count", [0, 1, 3, 5])
+def test_lbfgs_direction_parity(reg_mod, orc, count):
+    dims, h = (16, 16, 16), (1.0, 1.0, 1.0)
+    R = random_image(dims, 81)
+    r = reg_mod.Registration(reg_mod.make_config(levels=1, mem=5)).set_images(R, R, h)
+    n = 3 * 9 ** 3
+    rng = np.random.default_rng(82 + count)
+    A = rng.normal(size=(n, 8))
+    # pairs of an SPD quadratic with a spread spectrum so that s'y > 0
+    S = rng.normal(size=(count, n))
+    Y = S * rng.uniform(0.5, 3.0, size=n) + 0.1 * (S @ A) @ A.T / n
+    g = rng.normal(size=n)
+    S32, Y32, g32 = (np.ascontiguousarray(a, np.float32) for a in (S, Y, g))
+    p = r.lbfgs_direction(torch.from_numpy(S32).cuda() if count else None,
+                          torch.from_numpy(Y32).cuda() if count else None,
+                          torch.from_numpy(g32).cuda()).cpu().numpy()
+    if count:
+        gamma = float(S32[-1].astype(np.float64) @ Y32[-1]) / float(Y32[-1].astype(np.float64) @ Y32[-1])
+        ref = -orc.two_loop(S32, Y32, g32, gamma)
+    else:
+        ref = -g32.astype(np.float64) * (1.0 / np.abs(g32).max())   # node spacing 1 on this grid
+        ref *= min(r.level_info(0)["node_spacing"])
+    assert rel_l2(p, ref) < 2e-5
+    r.close()
+
+
+def test_errors_are_reported(reg_mod):
+    from paper_1812_06765_gb300 import _lib
+    cfg = reg_mod.make_config(levels=1)
+    r = reg_mod.Registration(cfg)
+    u = torch.zeros(3 * 9 * 9 * 9, device="cuda")
+    with pytest.raises(reg_mod.RegError) as ei:
+        _lib.reg_eval_objective_grad(r.h, 0, u.data_ptr(), u.data_ptr())
+    assert ei.value.code == _lib.REG_ERR_STATE
+    with pytest.raises(reg_mod.RegError) as ei:
+        r.set_images(np.zeros((3, 8, 8), np.float32), np.zeros((3, 8, 8), np.float32), (1, 1, 1))
+    assert ei.value.code == _lib.REG_ERR_ARG
+    with pytest.raises(reg_mod.RegError) as ei:
+        r.set_images(np.zeros((8, 8, 8), np.float32), np.zeros((8, 8, 8), np.float32), (1, 0, 1))
+    assert ei.value.code == _lib.REG_ERR_ARG
+    r.set_images(random_image((16, 16, 16), 1), random_image((16, 16, 16), 2), (1, 1, 1))
+    with pytest.raises(reg_mod.RegError):
+        _lib.reg_eval_objective_grad(r.h, 3, u.data_ptr(), u.data_ptr())
+    # a NaN image gives a numeric error, not a fault
+    bad = random_image((16, 16, 16), 3)
+    bad[4, 4, 4] = np.nan
+    r.set_images(bad, bad, (1, 1, 1))
+    with pytest.raises(reg_mod.RegError) as ei:
+        r.eval(u)
+    assert ei.value.code == _lib.REG_ERR_NUMERIC
+    r.close()
+    with pytest.raises(reg_mod.RegError):
+        reg_mod.Registration(reg_mod.make_config(levels=0))
+
+
+def test_autograd_function(reg_mod):
+    from paper_1812_06765_gb300 import RegObjective
+    dims, h = (32, 28, 24), (1.0, 1.0, 1.0)
+    R, T = random_image(dims, 91), random_image(dims, 92)
+    r = reg_mod.Registration(reg_mod.make_config(levels=1, tau=0.05, alpha=2.0)).set_images(R, T, h)
+    u = torch.from_numpy(random_field(r.level_info(0)["nodes"], 93, 1.0)).cuda().requires_grad_(True)
+    J = RegObjective.apply(u, r, 0)
+    loss = 2.0 * J + (u.double() ** 2).sum()
+    loss.backward()
+    _, _, _, g = r.eval(u.detach())
+    np.testing.assert_allclose(u.grad.cpu().numpy(), (2.0 * g + 2.0 * u.detach()).cpu().numpy(), rtol=1e-6,
+                               atol=1e-6)
+    # directional finite difference of the forward against the backward
+    d = torch.from_numpy(random_field(r.level_info(0)["nodes"], 94, 1.0)).cuda()
+    eps = 1e-2
+    with torch.no_grad():
+        Jp = RegObjective.apply(u + eps * d, r, 0).item()
+        Jm = RegObjective.apply(u - eps * d, r, 0).item()
+    fd = (Jp - Jm) / (2 * eps)
+    an = float((g.double() * d.double()).sum())
+    assert abs(fd - an) <= 2e-3 * abs(an), (fd, an)
+    r.close()

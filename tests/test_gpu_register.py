@@ -1,0 +1,100 @@
+"""End-to-end registration parity: the device L-BFGS against the oracle's."""
+import numpy as np
+import pytest
+
+from synth import CONFIGS, make_pair, random_image, true_inverse_displacement, voxel_centres  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def reg_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1812_06765_gb300 as reg
+    return reg
+
+
+def _cfgs(reg_mod, orc, c, **kw):
+    common = dict(levels=c["levels"], tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"],
+                  c1=c["c1"])
+    common.update(kw)
+    return reg_mod.make_config(**common), orc.make_config(**common)
+
+
+def test_register_64cube_matches_oracle(reg_mod, orc):
+    """64^3 single level, at most 50 iterations: mean |u_gpu - u_oracle| <= 0.1 voxel."""
+    c = CONFIGS[0]
+    p = make_pair(0)
+    cfg, ocfg = _cfgs(reg_mod, orc, c)
+    r = reg_mod.Registration(cfg).set_images(p["R"], p["T"], p["spacing"])
+    u, st = r.register(out="numpy")
+    uo, sto = orc.register(p["dims"], p["spacing"], p["R"], p["T"], ocfg)
+    du = np.abs(u.astype(np.float64) - uo)
+    mean_vox = float(np.sqrt((du ** 2).sum(axis=0)).mean()) / min(p["spacing"])
+    assert st["status"] == 0 and sto["status"] == 0
+    assert mean_vox <= 0.1, (mean_vox, st, sto)
+    assert abs(st["J"][0] - sto["J"][0]) <= 1e-3 * abs(sto["J"][0]), (st, sto)
+    r.close()
+
+
+def test_register_fixed_iterations_trajectory(reg_mod, orc):
+    """Three levels, a fixed number of accepted steps: step-for-step trajectory parity."""
+    dims, h = (48, 40, 32), (1.5, 1.5, 1.5)
+    R = random_image(dims, 11)
+    T = random_image(dims, 11)
+    T = np.roll(T, shift=(1, 2, -1), axis=(0, 1, 2))
+    kw = dict(levels=3, tau=0.05, alpha=5.0, mem=5, max_iter=[8, 8, 8], fixed_iters=True)
+    cfg, ocfg = reg_mod.make_config(**kw), orc.make_config(**kw)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    u, st = r.register(out="numpy")
+    uo, sto = orc.register(dims, h, R, T, ocfg)
+    assert st["iters"] == sto["iters"] == [8, 8, 8]
+    du = np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0))
+    assert du.mean() / min(h) <= 0.02, (du.mean(), st, sto)
+    for lv in range(3):
+        assert abs(st["J"][lv] - sto["J"][lv]) <= 1e-4 * abs(sto["J"][lv]), (lv, st["J"], sto["J"])
+    r.close()
+
+
+def test_register_host_and_device_buffers_agree(reg_mod):
+    dims, h = (32, 32, 32), (1.0, 1.0, 1.0)
+    R, T = random_image(dims, 21), random_image(dims, 22)
+    cfg = reg_mod.make_config(levels=2, tau=0.05, alpha=2.0, max_iter=[10, 10], fixed_iters=True)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    u1, s1 = r.register(out="numpy")
+    r2 = reg_mod.Registration(cfg).set_images(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda(), h)
+    u2, s2 = r2.register(out="torch")
+    np.testing.assert_array_equal(u1, u2.cpu().numpy())   # deterministic reductions: bit-identical
+    assert s1["evals"] == s2["evals"]
+    r.close()
+    r2.close()
+
+
+def test_register_warm_start(reg_mod):
+    """A registration resumed from its own result at the finest level stays put."""
+    dims, h = (32, 32, 32), (1.0, 1.0, 1.0)
+    p = make_pair(0, dims=dims)
+    cfg = reg_mod.make_config(levels=1, tau=0.01, alpha=10.0, max_iter=30)
+    r = reg_mod.Registration(cfg).set_images(p["R"], p["T"], h)
+    u, st = r.register(out="torch")
+    u2, st2 = r.register(out="torch", u_init=u)
+    assert st2["J"][0] <= st["J"][0] * (1 + 1e-9)
+    assert float((u2 - u).abs().max()) < 0.5
+    r.close()
+
+
+@pytest.mark.slow
+def test_register_128_ct_three_levels(reg_mod, orc):
+    """CT-like 128^3, three levels (limited iterations): device and oracle agree."""
+    c = CONFIGS[1]
+    p = make_pair(1)
+    cfg, ocfg = _cfgs(reg_mod, orc, c, max_iter=[20, 20, 20], fixed_iters=True)
+    r = reg_mod.Registration(cfg).set_images(p["R"], p["T"], p["spacing"])
+    u, st = r.register(out="numpy")
+    uo, sto = orc.register(p["dims"], p["spacing"], p["R"], p["T"], ocfg)
+    du = np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0))
+    assert du.mean() / min(p["spacing"]) <= 0.1, (du.mean(), st, sto)
+    r.close()
