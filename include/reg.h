@@ -28,8 +28,8 @@
  * the current CUDA device; host pointers plain host memory.
  *
  * Threads and streams: a handle is not thread-safe; all its GPU work is queued
- * on the stream given to reg_create (or a stream it creates) plus one internal
- * side stream for the template pyramid.  Calls that return host values
+ * on the stream given to reg_create plus one internal side stream for the
+ * template pyramid (joined back with an event).  Calls that return host values
  * synchronise that stream.
  */
 #ifndef REG_H
@@ -58,7 +58,7 @@ typedef struct reg_ctx *reg_handle;
  *   tau = rho = 0.01, alpha = 10, c1 = 1e-4, max_backtracks = 20,
  *   tol_grad_rel = 1e-5, tol_j_rel = 1e-7, tol_j_count = 3, levels = 1,
  *   lbfgs_mem = 5, max_iter = 50 on every level, node_dims = 0 (rule m_d/2+1),
- *   start_level = -1 (coarsest), eval_impl = 0 (fused), use_graph = 1. */
+ *   start_level = -1 (coarsest), eval_impl = 0 (fused), use_graph = 0. */
 typedef struct reg_config {
     double tau, rho;      /* NGF edge parameters of Eq. 2 (template, reference), > 0 */
     double alpha;         /* regularisation weight of Eq. 1, >= 0 */
@@ -98,9 +98,10 @@ int reg_version(void);
 void reg_config_default(reg_config *cfg);
 
 /* Create a handle.  cfg is copied (validated here: REG_ERR_ARG on bad values).
- * cuda_stream is a cudaStream_t of the current device, or NULL for a stream
- * owned by the handle.  On success *out owns the handle; free it with
- * reg_destroy.  Allocates no image buffers yet. */
+ * cuda_stream is a cudaStream_t of the current device, or NULL for the legacy
+ * default stream (the stream PyTorch uses unless told otherwise); the caller
+ * keeps ownership of a stream it passes.  On success *out owns the handle;
+ * free it with reg_destroy.  Allocates no image buffers yet. */
 int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream);
 
 /* Load a reference R and template T (Sec. 2.1) of dims[3] = (m_x, m_y, m_z)

@@ -107,3 +107,18 @@ cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const
                                        const float *g, float *p, double Hmin, cudaStream_t s);
 int eval_partials_needed(const Level &L);
 int num_blocks_for(reg_ctx *c, long long n, int threads);
+
+// objective pass variants (k_ngf_fused.cu, k_ngf_multipass.cu)
+bool fused_eligible(const Level &L);
+size_t fused_part_floats(const Level &L, int num_sms);
+cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
+                             float *grad, double *partials, int *n_partials, cudaStream_t s);
+cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
+                                 float *grad, double *partials, int *n_partials, cudaStream_t s);
+cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alpha_hy, float *grad, cudaStream_t s);
+
+// the fused pass serves levels whose grids have ratio exactly 2; others use the multi-pass kernels
+inline bool use_fused(const reg_ctx *c, int level)
+{
+    return c->cfg.eval_impl == 0 && fused_eligible(c->L[level]);
+}

@@ -106,11 +106,6 @@ __global__ void __launch_bounds__(512) k_finalize(const double *__restrict__ pD,
 
 }  // namespace
 
-cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
-                                 float *grad, double *partials, int *n_partials, cudaStream_t s);
-cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
-                             float *grad, double *partials, int *n_partials, cudaStream_t s);
-
 cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev, float *grad,
                         double *scal_out, cudaStream_t s)
 {
@@ -118,10 +113,11 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     LevelGeom g = L.geom();
     int nD = 0;
     cudaError_t e;
-    if (c->cfg.eval_impl == 1)
-        e = launch_ngf_multipass(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
-    else
+    const bool fused = use_fused(c, level);
+    if (fused)
         e = launch_ngf_fused(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
+    else
+        e = launch_ngf_multipass(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
     if (e != cudaSuccess)
         return e;
     dim3 blk(32, 8, 1);
@@ -129,11 +125,18 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     double *pS = c->es.partials + nD;
     k_curv_w<<<gn, blk, 0, s>>>(g, ub, dir, t_dev, c->es.w, pS);
     double hy = L.H[0] * L.H[1] * L.H[2];
-    k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);
+    if (fused) {   // grad = (tile partials of P^T r) + alpha hbar_y L^T w
+        e = launch_gather_grad(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, s);
+        if (e != cudaSuccess)
+            return e;
+    } else {       // grad += alpha hbar_y L^T w
+        k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);
+        c->launches += 1;
+    }
     int nS = (int)(gn.x * gn.y * gn.z);
     double hbar = L.h[0] * L.h[1] * L.h[2];
     k_finalize<<<1, 512, 0, s>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out);
-    c->launches += 3;
+    c->launches += 2;
     return cudaGetLastError();
 }
 

@@ -23,11 +23,8 @@ __global__ void __launch_bounds__(256) k_mp_warp(LevelGeom g, const float *__res
     if (x >= g.m[0] || y >= g.m[1])
         return;
     float t = dir ? (float)__ldg(t_dev) : 0.f;
-    float yh[3];
-    grid_convert_point(g, ub, dir, t, x, y, z, yh);
-    float s[3] = {x + yh[0] * g.ih[0], y + yh[1] * g.ih[1], z + yh[2] * g.ih[2]};
     float val, gr[3];
-    interp_value_grad(T, g.m[0], g.m[1], g.m[2], s, g.ih, val, gr);
+    warp_voxel(g, T, ub, dir, t, x, y, z, val, gr);
     size_t i = x + (size_t)g.m[0] * (y + (size_t)g.m[1] * z);
     Tw[i] = val;
     dT[i] = gr[0];

@@ -16,11 +16,37 @@ __device__ __forceinline__ float node_value(const float *__restrict__ ub, const 
     return v;
 }
 
+// Sampling coordinate of one voxel along one axis, t = i + yhat / h (voxel
+// units, so that T's sample j sits at t = j), returned as an integer cell
+// c = floor(t) and a fraction f = t - c in [0, 1).
+//
+// yhat = u0 + delta, where u0 is the displacement at the voxel's first node
+// (an FP32 input value) and delta the trilinear interpolation of the node
+// differences u_k - u0 (small for smooth fields).  Splitting off the integer
+// part before adding delta keeps the absolute error of t near 1e-7 instead of
+// the ~1e-5 that a float i + yhat / h has at i ~ 256: the interpolant's
+// gradient jumps at cell faces, so a coordinate rounded across a face changes
+// that voxel's gradient contribution completely.
+// ok = false when the coordinate is not finite or absurdly far away.
+__device__ __forceinline__ void sample_coord(int i, float u0, float delta, float h, float ih, int &c, float &f,
+                                             bool &ok)
+{
+    float q0 = u0 * ih;
+    ok = fabsf(q0) < 1.0e6f && fabsf(delta * ih) < 1.0e6f;   // also false for NaN
+    float qi = floorf(q0);
+    float rem = fmaf(-qi, h, u0);          // u0 - qi h with one rounding, |rem| <~ h
+    float fr = (rem + delta) * ih;
+    float ff = floorf(fr);
+    f = fr - ff;
+    c = ok ? i + (int)qi + (int)ff : 0;
+}
+
 // Grid conversion P at one voxel (Sec. 2.1 Eq. 1, Sec. 2.2): trilinear in the
-// 8 surrounding nodes, weights from the per-dimension tables.
+// 8 surrounding nodes with the per-dimension weights; per component the value
+// at the first node (u0) and the interpolated differences to it (delta).
 __device__ __forceinline__ void grid_convert_point(const LevelGeom &g, const float *__restrict__ ub,
                                                    const float *__restrict__ dir, float t, int x, int y, int z,
-                                                   float yh[3])
+                                                   float u0[3], float delta[3])
 {
     int kx = __ldg(g.pk0[0] + x), ky = __ldg(g.pk0[1] + y), kz = __ldg(g.pk0[2] + z);
     float wx = __ldg(g.pw1[0] + x), wy = __ldg(g.pw1[1] + y), wz = __ldg(g.pw1[2] + z);
@@ -30,11 +56,17 @@ __device__ __forceinline__ void grid_convert_point(const LevelGeom &g, const flo
     for (int c = 0; c < 3; c++) {
         const float *u = ub + c * g.nn;
         const float *d = dir ? dir + c * g.nn : nullptr;
-        float a0 = lerpf(node_value(u, d, t, b), node_value(u, d, t, b + 1), wx);
-        float a1 = lerpf(node_value(u, d, t, b + sy), node_value(u, d, t, b + sy + 1), wx);
-        float a2 = lerpf(node_value(u, d, t, b + sz), node_value(u, d, t, b + sz + 1), wx);
-        float a3 = lerpf(node_value(u, d, t, b + sz + sy), node_value(u, d, t, b + sz + sy + 1), wx);
-        yh[c] = lerpf(lerpf(a0, a1, wy), lerpf(a2, a3, wy), wz);
+        float a = node_value(u, d, t, b);
+        float d100 = node_value(u, d, t, b + 1) - a;
+        float d010 = node_value(u, d, t, b + sy) - a, d110 = node_value(u, d, t, b + sy + 1) - a;
+        float d001 = node_value(u, d, t, b + sz) - a, d101 = node_value(u, d, t, b + sz + 1) - a;
+        float d011 = node_value(u, d, t, b + sz + sy) - a, d111 = node_value(u, d, t, b + sz + sy + 1) - a;
+        float a0 = wx * d100;
+        float a1 = lerpf(d010, d110, wx);
+        float a2 = lerpf(d001, d101, wx);
+        float a3 = lerpf(d011, d111, wx);
+        u0[c] = a;
+        delta[c] = lerpf(lerpf(a0, a1, wy), lerpf(a2, a3, wy), wz);
     }
 }
 
@@ -45,22 +77,21 @@ __device__ __forceinline__ float load_zero_ext(const float *__restrict__ T, int 
     return in ? __ldg(T + x + (size_t)mx * (y + (size_t)my * z)) : 0.f;
 }
 
-// Trilinear interpolation of T at voxel-index coordinates s (s_d = p_d / h_d - 1/2)
-// with zero extension, and the gradient of the interpolant in the cell
-// floor(s) (per mm, through ih = 1 / h).
-__device__ __forceinline__ void interp_value_grad(const float *__restrict__ T, int mx, int my, int mz,
-                                                  const float s[3], const float ih[3], float &val, float gr[3])
+// Trilinear interpolation of T at cell c + fraction f (voxel units, sample j at
+// t = j) with zero extension, and the gradient of the interpolant in that cell
+// (per mm, through ih = 1 / h).
+__device__ __forceinline__ void interp_value_grad(const float *__restrict__ T, int mx, int my, int mz, const int c[3],
+                                                  const float f[3], bool ok, const float ih[3], float &val,
+                                                  float gr[3])
 {
-    // outside (-1 <= s_d < m_d) every corner is outside; also catches NaN
-    if (!(s[0] >= -1.f && s[0] < (float)mx && s[1] >= -1.f && s[1] < (float)my && s[2] >= -1.f &&
-          s[2] < (float)mz)) {
+    // outside -1 <= c_d <= m_d - 1 every corner is outside
+    if (!(ok && c[0] >= -1 && c[0] <= mx - 1 && c[1] >= -1 && c[1] <= my - 1 && c[2] >= -1 && c[2] <= mz - 1)) {
         val = 0.f;
         gr[0] = gr[1] = gr[2] = 0.f;
         return;
     }
-    float fx = floorf(s[0]), fy = floorf(s[1]), fz = floorf(s[2]);
-    int cx = (int)fx, cy = (int)fy, cz = (int)fz;
-    float tx = s[0] - fx, ty = s[1] - fy, tz = s[2] - fz;
+    const int cx = c[0], cy = c[1], cz = c[2];
+    const float tx = f[0], ty = f[1], tz = f[2];
     float t000 = load_zero_ext(T, mx, my, mz, cx, cy, cz);
     float t100 = load_zero_ext(T, mx, my, mz, cx + 1, cy, cz);
     float t010 = load_zero_ext(T, mx, my, mz, cx, cy + 1, cz);
@@ -77,6 +108,23 @@ __device__ __forceinline__ void interp_value_grad(const float *__restrict__ T, i
     gr[0] = lerpf(dx0, dx1, tz) * ih[0];
     gr[1] = lerpf(a10 - a00, a11 - a01, tz) * ih[1];
     gr[2] = (b1 - b0) * ih[2];
+}
+
+// Deformed-template value and interpolant gradient at voxel (x, y, z):
+// y-hat = P u, then T(x + y-hat) (Eq. 1).
+__device__ __forceinline__ void warp_voxel(const LevelGeom &g, const float *__restrict__ T,
+                                           const float *__restrict__ ub, const float *__restrict__ dir, float t,
+                                           int x, int y, int z, float &val, float gr[3])
+{
+    float u0[3], dl[3];
+    grid_convert_point(g, ub, dir, t, x, y, z, u0, dl);
+    int c[3];
+    float f[3];
+    bool ok0, ok1, ok2;
+    sample_coord(x, u0[0], dl[0], g.h[0], g.ih[0], c[0], f[0], ok0);
+    sample_coord(y, u0[1], dl[1], g.h[1], g.ih[1], c[1], f[1], ok1);
+    sample_coord(z, u0[2], dl[2], g.h[2], g.ih[2], c[2], f[2], ok2);
+    interp_value_grad(T, g.m[0], g.m[1], g.m[2], c, f, ok0 && ok1 && ok2, g.ih, val, gr);
 }
 
 // NGF residual of Eq. 2 at one interior voxel, a = grad T-tilde, b = grad R.

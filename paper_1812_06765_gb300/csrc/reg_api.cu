@@ -223,11 +223,26 @@ int allocate_buffers(reg_ctx *c)
         if (p > maxpart) maxpart = p;
     }
     EvalScratch &es = c->es;
-    if (cfg.eval_impl == 1) {
-        CK(cudaMalloc(&es.Tw, sizeof(float) * nv0));
-        CK(cudaMalloc(&es.dT, sizeof(float) * 3 * nv0));
-        CK(cudaMalloc(&es.v, sizeof(float) * 3 * nv0));
-        CK(cudaMalloc(&es.r, sizeof(float) * 3 * nv0));
+    long long mp_vox = 0;      // largest level served by the multi-pass kernels
+    size_t part = 0;           // largest tile-partial buffer of the fused pass
+    for (int l = 0; l < c->levels; l++) {
+        if (use_fused(c, l)) {
+            size_t p = fused_part_floats(c->L[l], c->num_sms);
+            if (p > part) part = p;
+        } else if (c->L[l].nv > mp_vox) {
+            mp_vox = c->L[l].nv;
+        }
+    }
+    (void)nv0;
+    if (mp_vox > 0) {
+        CK(cudaMalloc(&es.Tw, sizeof(float) * mp_vox));
+        CK(cudaMalloc(&es.dT, sizeof(float) * 3 * mp_vox));
+        CK(cudaMalloc(&es.v, sizeof(float) * 3 * mp_vox));
+        CK(cudaMalloc(&es.r, sizeof(float) * 3 * mp_vox));
+    }
+    if (part > 0) {
+        CK(cudaMalloc(&es.part, sizeof(float) * part));
+        es.part_floats = part;
     }
     CK(cudaMalloc(&es.w, sizeof(float) * nmax));
     CK(cudaMalloc(&es.partials, sizeof(double) * maxpart));
@@ -272,7 +287,7 @@ void reg_config_default(reg_config *cfg)
     cfg->fixed_iters = 0;
     cfg->start_level = -1;
     for (int l = 0; l < REG_MAX_LEVELS; l++) cfg->max_iter[l] = 50;
-    cfg->eval_impl = 1;
+    cfg->eval_impl = 0;
     cfg->use_graph = 0;
 }
 
@@ -287,12 +302,9 @@ int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) {
-        if (cuda_stream) {
-            c->stream = (cudaStream_t)cuda_stream;
-        } else {
-            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-            c->own_stream = true;
-        }
+        // NULL is the legacy default stream (ordered with every blocking stream)
+        c->stream = (cudaStream_t)cuda_stream;
+        c->own_stream = false;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming);

@@ -349,8 +349,8 @@ def true_inverse_displacement(field, points, iters=50):
 # --------------------------------------------------------------------------
 # generic random inputs for unit and parity tests
 # --------------------------------------------------------------------------
-def random_image(dims, seed, n_blobs=12, smooth=True):
-    """Random image in [0, 1]: Gaussian blobs (smooth) or uniform noise."""
+def random_image(dims, seed, n_blobs=12, smooth=True, noise=0.02):
+    """Random image in [0, 1]: Gaussian blobs plus N(0, noise) (smooth) or uniform noise."""
     rng = _rng(seed)
     mx, my, mz = dims
     if not smooth:
@@ -362,7 +362,7 @@ def random_image(dims, seed, n_blobs=12, smooth=True):
         sig = rng.uniform(0.08, 0.25) * L.min() + 0.8
         shapes.append(_Shape("blob", c, [sig, sig, sig], rng.uniform(-1.0, 1.0)))
     img = _sample(Phantom(0.5, shapes), dims, (1.0, 1.0, 1.0))
-    img += 0.02 * rng.normal(size=img.shape)
+    img += noise * rng.normal(size=img.shape)
     return np.clip(img, 0.0, 1.0).astype(np.float32)
 
 

@@ -22,10 +22,14 @@ def reg_mod():
     return reg
 
 
-EVAL_IMPLS = [1]
+EVAL_IMPLS = [0, 1]   # 0: fused pass (ratio-2 grids), 1: multi-pass
 
 # (dims, spacing, nodes or None, tau, rho, alpha, amplitude of u in mm)
 CASES = [
+    ((30, 26, 22), (1.0, 1.0, 1.0), None, 0.05, 0.05, 1.0, 1.5),          # ragged tiles (28 x 12 x 8)
+    ((58, 38, 70), (1.2, 0.8, 1.0), None, 0.05, 0.03, 2.0, 2.5),          # several tiles and z segments
+    ((28, 12, 8), (1.0, 1.0, 1.0), None, 0.1, 0.1, 1.0, 0.8),             # exactly one tile
+    ((4, 6, 4), (1.0, 1.0, 1.0), None, 0.1, 0.1, 1.0, 0.3),               # smallest even grid
     ((16, 16, 16), (1.0, 1.0, 1.0), None, 0.05, 0.05, 1.0, 1.0),          # one tile
     ((37, 29, 23), (1.0, 1.1, 0.9), None, 0.05, 0.02, 3.0, 1.5),          # ragged, non-integer ratio
     ((40, 36, 20), (0.97, 0.97, 2.5), None, 0.1, 0.1, 50.0, 3.0),         # anisotropic spacing
@@ -192,25 +196,34 @@ def test_errors_are_reported(reg_mod):
         reg_mod.Registration(reg_mod.make_config(levels=0))
 
 
-def test_autograd_function(reg_mod):
+def test_autograd_function(reg_mod, orc):
+    """RegObjective: backward = the hand-written adjoint gradient (= oracle gradient),
+    and a directional finite difference of the forward agrees with it."""
     from paper_1812_06765_gb300 import RegObjective
     dims, h = (32, 28, 24), (1.0, 1.0, 1.0)
-    R, T = random_image(dims, 91), random_image(dims, 92)
-    r = reg_mod.Registration(reg_mod.make_config(levels=1, tau=0.05, alpha=2.0)).set_images(R, T, h)
-    u = torch.from_numpy(random_field(r.level_info(0)["nodes"], 93, 1.0)).cuda().requires_grad_(True)
+    # noise-free smooth images: the trilinear interpolant is only C0 across cell
+    # faces, so difference quotients need a step that averages over few kinks
+    R, T = random_image(dims, 91, noise=0.0), random_image(dims, 92, noise=0.0)
+    tau, alpha = 0.05, 2.0
+    r = reg_mod.Registration(reg_mod.make_config(levels=1, tau=tau, alpha=alpha)).set_images(R, T, h)
+    nodes = r.level_info(0)["nodes"]
+    u = torch.from_numpy(random_field(nodes, 93, 1.0)).cuda().requires_grad_(True)
     J = RegObjective.apply(u, r, 0)
     loss = 2.0 * J + (u.double() ** 2).sum()
     loss.backward()
     _, _, _, g = r.eval(u.detach())
     np.testing.assert_allclose(u.grad.cpu().numpy(), (2.0 * g + 2.0 * u.detach()).cpu().numpy(), rtol=1e-6,
                                atol=1e-6)
+    Jo, _, _, go = orc.objective(dims, h, R, T, nodes, u.detach().cpu().numpy(), tau, tau, alpha)
+    assert rel_l2(g.cpu().numpy(), go) <= GRAD_RTOL
+    assert abs(J.item() - Jo) <= J_RTOL * abs(Jo)
     # directional finite difference of the forward against the backward
-    d = torch.from_numpy(random_field(r.level_info(0)["nodes"], 94, 1.0)).cuda()
-    eps = 1e-2
+    d = torch.from_numpy(random_field(nodes, 94, 1.0)).cuda()
+    eps = 5e-2
     with torch.no_grad():
         Jp = RegObjective.apply(u + eps * d, r, 0).item()
         Jm = RegObjective.apply(u - eps * d, r, 0).item()
     fd = (Jp - Jm) / (2 * eps)
     an = float((g.double() * d.double()).sum())
-    assert abs(fd - an) <= 2e-3 * abs(an), (fd, an)
+    assert abs(fd - an) <= 1e-2 * abs(an), (fd, an)
     r.close()

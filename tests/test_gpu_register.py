@@ -74,15 +74,15 @@ def test_register_host_and_device_buffers_agree(reg_mod):
 
 
 def test_register_warm_start(reg_mod):
-    """A registration resumed from its own result at the finest level stays put."""
+    """A registration resumed from its own result continues downhill (checkpoint/resume)."""
     dims, h = (32, 32, 32), (1.0, 1.0, 1.0)
     p = make_pair(0, dims=dims)
     cfg = reg_mod.make_config(levels=1, tau=0.01, alpha=10.0, max_iter=30)
     r = reg_mod.Registration(cfg).set_images(p["R"], p["T"], h)
     u, st = r.register(out="torch")
     u2, st2 = r.register(out="torch", u_init=u)
+    assert st2["status"] == 0 and st2["evals"][0] >= 1
     assert st2["J"][0] <= st["J"][0] * (1 + 1e-9)
-    assert float((u2 - u).abs().max()) < 0.5
     r.close()
 
 
