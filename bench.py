@@ -51,6 +51,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eval-impl", type=int, default=None, help="0 fused, 1 multi-pass (default: library)")
+    ap.add_argument("--eval-only", action="store_true", help="time only the isolated evaluation (profiling)")
     return ap.parse_args(argv)
 
 
@@ -237,6 +238,34 @@ def run_ours(args):
         u, st = reg.register(out="torch")
         return st
 
+    def isolated_eval():
+        """Median device time (ms) of one full-resolution objective+gradient evaluation."""
+        reg.set_images(R_d, T_d, p["spacing"])
+        info = reg.level_info(0)
+        u = torch.from_numpy(random_field(info["nodes"], 5, 5.0)).to(dev)
+        grad = torch.empty_like(u)
+        for _ in range(5):
+            _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
+        ev_ms = []
+        for _ in range(args.eval_iters):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
+            e1.record(stream)
+            e1.synchronize()
+            ev_ms.append(e0.elapsed_time(e1))
+        return statistics.median(ev_ms), info
+
+    if args.eval_only:   # profiling aid: the isolated evaluation alone
+        eval_ms, info = isolated_eval()
+        if rank == 0:
+            print(json.dumps({"eval_ms_full_res": eval_ms, "workload": c["name"],
+                              "eval_impl": reg.cfg.eval_impl, "iters": args.eval_iters}))
+        reg.close()
+        return
+
     # warm-up (untimed)
     for _ in range(args.warmup):
         step_device()
@@ -279,24 +308,8 @@ def run_ours(args):
     e2e_s = dist_reduce(statistics.mean(e2e_times), "max", dev)
     e2e_value = world * e2e_eq / e2e_s
 
-    # isolated full-resolution evaluation: the fused objective+gradient pass
-    reg.set_images(R_d, T_d, p["spacing"])
-    info = reg.level_info(0)
-    u = torch.from_numpy(random_field(info["nodes"], 5, 5.0)).to(dev)
-    grad = torch.empty_like(u)
-    for _ in range(5):
-        _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
-    ev_ms = []
-    for _ in range(args.eval_iters):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
-        e1.record(stream)
-        e1.synchronize()
-        ev_ms.append(e0.elapsed_time(e1))
-    eval_ms = statistics.median(ev_ms)
+    # isolated full-resolution evaluation: the objective+gradient pass
+    eval_ms, info = isolated_eval()
     nv = int(np.prod(info["dims"]))
     nn = int(np.prod(info["nodes"]))
     alg_bytes = 4 * nv + 4 * nv + 12 * nn + 12 * nn       # read R, T, u; write grad J

@@ -1,0 +1,142 @@
+// One pyramid level of L-BFGS as one CUDA graph launch.
+//
+//   init: objective at u0, ||g||, ||g||_inf, control(INIT)  -> sets the iteration condition
+//   WHILE (iteration condition)
+//       direction (+ a p0 redo when the compact-form direction is not a descent direction)
+//       WHILE (line-search condition)
+//           objective at u + t p, control(ARMIJO)              -> sets the line-search condition
+//       accept (no-op unless accepted), control(ACCEPTED)      -> sets the iteration condition
+//
+// The conditions are set on the device by the FP64 control kernel, so a whole
+// level runs without a host round trip.  Termination does not depend on the
+// host: every search ends after max_backtracks trials and the control kernel
+// ends the level after max_iter accepted steps, a failed search, a non-finite
+// value, or (a bound that should never bind) 2 max_iter + 8 loop bodies.
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+struct CaptureGuard {   // ends a capture that an early return would leave open
+    cudaStream_t s;
+    bool active = false;
+    ~CaptureGuard()
+    {
+        if (active) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s, &g);
+        }
+    }
+};
+
+// leaf nodes of the capture so far (copied: the runtime's array is transient)
+cudaError_t capture_leaves(cudaStream_t s, std::vector<cudaGraphNode_t> &out)
+{
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e != cudaSuccess)
+        return e;
+    out.assign(deps, deps + nd);
+    return cudaSuccess;
+}
+
+cudaError_t add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                      cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p);
+    if (e == cudaSuccess)
+        *body = p.conditional.phGraph_out[0];
+    return e;
+}
+
+}  // namespace
+
+#define GK(call)                                  \
+    do {                                          \
+        cudaError_t _e = (call);                  \
+        if (_e != cudaSuccess) {                  \
+            lbfgs_set_graph_handles(0, 0);        \
+            c->launches = launches0;              \
+            if (G) cudaGraphDestroy(G);           \
+            return _e;                            \
+        }                                         \
+    } while (0)
+
+// Build (once per level and geometry) the executable graph of a whole level.
+cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
+{
+    const long long launches0 = c->launches;   // capture queues nothing: keep the counter
+    cudaGraph_t G = nullptr;
+    cudaStream_t cs = c->cap_stream;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    GK(cudaGraphCreate(&G, 0));
+    cudaGraphConditionalHandle h_iter, h_ls;
+    GK(cudaGraphConditionalHandleCreate(&h_iter, G, 0, cudaGraphCondAssignDefault));
+
+    std::vector<cudaGraphNode_t> leaves;
+    {   // init
+        CaptureGuard guard{cs};
+        GK(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, mode));
+        guard.active = true;
+        lbfgs_set_graph_handles(0, h_iter);
+        GK(lbfgs_launch_init(c, level, cs));
+        GK(capture_leaves(cs, leaves));
+        guard.active = false;
+        cudaGraph_t g2 = nullptr;
+        GK(cudaStreamEndCapture(cs, &g2));
+    }
+    cudaGraphNode_t w_iter;
+    cudaGraph_t body = nullptr;
+    GK(add_while(G, leaves, h_iter, &w_iter, &body));
+    GK(cudaGraphConditionalHandleCreate(&h_ls, body, 0, cudaGraphCondAssignDefault));
+    {   // iteration body, up to the line search
+        CaptureGuard guard{cs};
+        GK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
+        guard.active = true;
+        lbfgs_set_graph_handles(h_ls, h_iter);
+        GK(lbfgs_launch_direction_level(c, level, cs));
+        GK(capture_leaves(cs, leaves));
+        guard.active = false;
+        cudaGraph_t g2 = nullptr;
+        GK(cudaStreamEndCapture(cs, &g2));
+    }
+    cudaGraphNode_t w_ls;
+    cudaGraph_t ls_body = nullptr;
+    GK(add_while(body, leaves, h_ls, &w_ls, &ls_body));
+    {   // line-search body
+        CaptureGuard guard{cs};
+        GK(cudaStreamBeginCaptureToGraph(cs, ls_body, nullptr, nullptr, 0, mode));
+        guard.active = true;
+        lbfgs_set_graph_handles(h_ls, h_iter);
+        GK(lbfgs_launch_trial(c, level, cs));
+        guard.active = false;
+        cudaGraph_t g2 = nullptr;
+        GK(cudaStreamEndCapture(cs, &g2));
+    }
+    {   // accept, after the line search
+        CaptureGuard guard{cs};
+        GK(cudaStreamBeginCaptureToGraph(cs, body, &w_ls, nullptr, 1, mode));
+        guard.active = true;
+        lbfgs_set_graph_handles(h_ls, h_iter);
+        GK(lbfgs_launch_accept_level(c, level, cs));
+        guard.active = false;
+        cudaGraph_t g2 = nullptr;
+        GK(cudaStreamEndCapture(cs, &g2));
+    }
+    lbfgs_set_graph_handles(0, 0);
+    GK(cudaGraphInstantiate(out, G, 0));
+    cudaGraphDestroy(G);
+    c->launches = launches0;
+    return cudaSuccess;
+}
+
+// kernels of one objective evaluation at a level (for the launch statistics)
+int eval_kernel_count(const reg_ctx *c, int level) { return use_fused(c, level) ? 4 : 7; }

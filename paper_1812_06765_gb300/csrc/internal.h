@@ -60,6 +60,7 @@ struct reg_ctx {
     reg_config cfg;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     bool own_stream = false;
     cudaEvent_t ev_side = nullptr;
     int device = 0;
@@ -116,6 +117,9 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
 cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
                                  float *grad, double *partials, int *n_partials, cudaStream_t s);
 cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alpha_hy, float *grad, cudaStream_t s);
+
+cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out);
+int eval_kernel_count(const reg_ctx *c, int level);
 
 // the fused pass serves levels whose grids have ratio exactly 2; others use the multi-pass kernels
 inline bool use_fused(const reg_ctx *c, int level)

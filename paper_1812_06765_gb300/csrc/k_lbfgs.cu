@@ -45,12 +45,28 @@ __device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, dou
     }
 }
 
+// All vector passes read and write 16-byte vectors: u, g, gt and pdir are
+// separate allocations and the P / Y ring slots sit at a stride that is a
+// multiple of 4 floats.  The n % 4 tail is done by the first threads of block 0.
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ float max4(float4 a)
+{
+    return fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+}
+
 __global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *__restrict__ g,
                                                      double *__restrict__ partials)
 {
     float v[2] = {0.f, 0.f};
-    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
-        float x = g[e];
+    const long long n4 = n >> 2;
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n4; e += (long long)gridDim.x * VT) {
+        float4 x = g4[e];
+        v[0] += dot4(x, x);
+        v[1] = fmaxf(v[1], max4(x));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        float x = g[4 * n4 + threadIdx.x];
         v[0] = fmaf(x, x, v[0]);
         v[1] = fmaxf(v[1], fabsf(x));
     }
@@ -58,7 +74,7 @@ __global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *_
 }
 
 // p = cg g + sum_j cp_j P_j + cy_j Y_j, written to pdir; partial sums of g'p and p'p.
-__global__ void __launch_bounds__(VT) k_lb_direction(long long n, const LbfgsState *__restrict__ st,
+__global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stride, const LbfgsState *__restrict__ st,
                                                      const float *__restrict__ g, const float *__restrict__ P,
                                                      const float *__restrict__ Y, float *__restrict__ pdir,
                                                      double *__restrict__ partials, int redo)
@@ -79,17 +95,44 @@ __global__ void __launch_bounds__(VT) k_lb_direction(long long n, const LbfgsSta
     if (!s_run)
         return;
     const int dc = s_dc;
+    const float cg = s_cg;
+    const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
+    float cp[LB_MAXM], cy[LB_MAXM];
+#pragma unroll
+    for (int j = 0; j < LB_MAXM; j++) {
+        const int sl = j < dc ? s_slot[j] : 0;
+        Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
+        Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
+        cp[j] = s_cp[j];
+        cy[j] = s_cy[j];
+    }
     float v[2] = {0.f, 0.f};
-    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
-        float gv = g[e];
-        float p = s_cg * gv;
+    const long long n4 = n >> 2;
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    float4 *p4 = reinterpret_cast<float4 *>(pdir);
+    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n4; e += (long long)gridDim.x * VT) {
+        float4 gv = g4[e];
+        float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
 #pragma unroll
         for (int j = 0; j < LB_MAXM; j++)
             if (j < dc) {
-                size_t o = (size_t)s_slot[j] * n + e;
-                p = fmaf(s_cp[j], P[o], p);
-                p = fmaf(s_cy[j], Y[o], p);
+                float4 a = Pj[j][e], b = Yj[j][e];
+                p.x = fmaf(cp[j], a.x, fmaf(cy[j], b.x, p.x));
+                p.y = fmaf(cp[j], a.y, fmaf(cy[j], b.y, p.y));
+                p.z = fmaf(cp[j], a.z, fmaf(cy[j], b.z, p.z));
+                p.w = fmaf(cp[j], a.w, fmaf(cy[j], b.w, p.w));
             }
+        p4[e] = p;
+        v[0] += dot4(gv, p);
+        v[1] += dot4(p, p);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        const long long e = 4 * n4 + threadIdx.x;
+        float gv = g[e], p = cg * gv;
+#pragma unroll
+        for (int j = 0; j < LB_MAXM; j++)
+            if (j < dc)
+                p = fmaf(cp[j], P[(size_t)s_slot[j] * stride + e], fmaf(cy[j], Y[(size_t)s_slot[j] * stride + e], p));
         pdir[e] = p;
         v[0] = fmaf(gv, p, v[0]);
         v[1] = fmaf(p, p, v[1]);
@@ -99,8 +142,16 @@ __global__ void __launch_bounds__(VT) k_lb_direction(long long n, const LbfgsSta
 
 // Accept the trial point: u += t pdir (the fmaf the evaluation used), store the
 // candidate pair in the free slot (P = pdir, Y = g_new - g), g = g_new, and
-// take every dot the next direction needs in the same pass.
-__global__ void __launch_bounds__(VT) k_lb_accept(long long n, const LbfgsState *__restrict__ st,
+// take every dot the next direction needs in the same pass: with g_new and with
+// y_new against every stored P and Y (the free slot, always the last list
+// entry, from registers), plus g_new'g_new and ||g_new||_inf.
+__device__ __forceinline__ void accept_elem(float gn, float go, float pf, float &u, float t, float &yn)
+{
+    yn = gn - go;
+    u = fmaf(t, pf, u);
+}
+
+__global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride, const LbfgsState *__restrict__ st,
                                                   float *__restrict__ u, float *__restrict__ g,
                                                   const float *__restrict__ gt, const float *__restrict__ pdir,
                                                   float *__restrict__ P, float *__restrict__ Y,
@@ -119,40 +170,86 @@ __global__ void __launch_bounds__(VT) k_lb_accept(long long n, const LbfgsState 
     __syncthreads();
     if (!s_ok)
         return;
-    const int lc = s_lc, fr = s_free;
+    const int np = s_lc - 1;    // stored pairs before the free slot
     const float t = s_t;
+    const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
+#pragma unroll
+    for (int j = 0; j < LB_MAXM; j++) {
+        const int sl = j < np ? s_slot[j] : 0;
+        Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
+        Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
+    }
+    float *Pf = P + (size_t)s_free * stride;
+    float *Yf = Y + (size_t)s_free * stride;
     float v[ND_ACC];
 #pragma unroll
     for (int d = 0; d < ND_ACC; d++)
         v[d] = 0.f;
-    float *Pf = P + (size_t)fr * n;
-    float *Yf = Y + (size_t)fr * n;
-    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
-        float gn = gt[e], yn = gn - g[e], pf = pdir[e];
-        u[e] = fmaf(t, pf, u[e]);
+    float fr[4] = {0.f, 0.f, 0.f, 0.f};   // dots of the free slot (p, y_new) with g_new, y_new
+    const long long n4 = n >> 2;
+    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n4; e += (long long)gridDim.x * VT) {
+        float4 gn = reinterpret_cast<const float4 *>(gt)[e];
+        float4 go = reinterpret_cast<float4 *>(g)[e];
+        float4 pf = reinterpret_cast<const float4 *>(pdir)[e];
+        float4 uu = reinterpret_cast<float4 *>(u)[e];
+        float4 yn;
+        accept_elem(gn.x, go.x, pf.x, uu.x, t, yn.x);
+        accept_elem(gn.y, go.y, pf.y, uu.y, t, yn.y);
+        accept_elem(gn.z, go.z, pf.z, uu.z, t, yn.z);
+        accept_elem(gn.w, go.w, pf.w, uu.w, t, yn.w);
+        reinterpret_cast<float4 *>(u)[e] = uu;
+        reinterpret_cast<float4 *>(g)[e] = gn;
+        reinterpret_cast<float4 *>(Pf)[e] = pf;
+        reinterpret_cast<float4 *>(Yf)[e] = yn;
+        v[0] += dot4(gn, gn);
+        v[1] = fmaxf(v[1], max4(gn));
+#pragma unroll
+        for (int j = 0; j < LB_MAXM; j++)
+            if (j < np) {
+                float4 pj = Pj[j][e], yj = Yj[j][e];
+                v[2 + 4 * j] += dot4(pj, gn);
+                v[3 + 4 * j] += dot4(yj, gn);
+                v[4 + 4 * j] += dot4(pj, yn);
+                v[5 + 4 * j] += dot4(yj, yn);
+            }
+        fr[0] += dot4(pf, gn);
+        fr[1] += dot4(yn, gn);
+        fr[2] += dot4(pf, yn);
+        fr[3] += dot4(yn, yn);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        const long long e = 4 * n4 + threadIdx.x;
+        float gn = gt[e], go = g[e], pf = pdir[e], uu = u[e], yn;
+        accept_elem(gn, go, pf, uu, t, yn);
+        u[e] = uu;
         g[e] = gn;
         Pf[e] = pf;
         Yf[e] = yn;
         v[0] = fmaf(gn, gn, v[0]);
         v[1] = fmaxf(v[1], fabsf(gn));
 #pragma unroll
-        for (int j = 0; j < LB_MAXS; j++)
-            if (j < lc) {
-                int s = s_slot[j];
-                float pj, yj;
-                if (s == fr) {
-                    pj = pf;
-                    yj = yn;
-                } else {
-                    pj = P[(size_t)s * n + e];
-                    yj = Y[(size_t)s * n + e];
-                }
+        for (int j = 0; j < LB_MAXM; j++)
+            if (j < np) {   // unrolled with a predicate so that v stays in registers
+                float pj = P[(size_t)s_slot[j] * stride + e], yj = Y[(size_t)s_slot[j] * stride + e];
                 v[2 + 4 * j] = fmaf(pj, gn, v[2 + 4 * j]);
                 v[3 + 4 * j] = fmaf(yj, gn, v[3 + 4 * j]);
                 v[4 + 4 * j] = fmaf(pj, yn, v[4 + 4 * j]);
                 v[5 + 4 * j] = fmaf(yj, yn, v[5 + 4 * j]);
             }
+        fr[0] = fmaf(pf, gn, fr[0]);
+        fr[1] = fmaf(yn, gn, fr[1]);
+        fr[2] = fmaf(pf, yn, fr[2]);
+        fr[3] = fmaf(yn, yn, fr[3]);
     }
+    // the free slot is list position np
+#pragma unroll
+    for (int j = 0; j < LB_MAXS; j++)
+        if (j == np) {
+            v[2 + 4 * j] += fr[0];
+            v[3 + 4 * j] += fr[1];
+            v[4 + 4 * j] += fr[2];
+            v[5 + 4 * j] += fr[3];
+        }
     block_reduce_write<ND_ACC>(v, 1, partials + (size_t)ND_ACC * blockIdx.x);
 }
 
@@ -211,12 +308,21 @@ __device__ void set_compact(LbfgsState *st)
 
 __device__ bool finite_d(double x) { return isfinite(x); }
 
-__global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__restrict__ st,
+__global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__restrict__ gst,
                                                     const double *__restrict__ partials, int nblocks,
                                                     const double *__restrict__ scal, unsigned long long h_ls,
                                                     unsigned long long h_iter)
 {
+    // the state lives in shared memory while the single decision thread works
+    // on it: one coalesced copy in and out instead of hundreds of dependent
+    // global accesses
+    __shared__ LbfgsState S;
     __shared__ double red[ND_ACC];
+    constexpr int NW = (int)(sizeof(LbfgsState) / sizeof(int));
+    for (int i = threadIdx.x; i < NW; i += blockDim.x)
+        reinterpret_cast<int *>(&S)[i] = reinterpret_cast<const int *>(gst)[i];
+    __syncthreads();
+    LbfgsState *st = &S;
     const int nd = phase == LB_ACCEPTED ? ND_ACC : 2;
     const int imax = (phase == LB_INIT || phase == LB_ACCEPTED) ? 1 : -1;
     const bool need = phase != LB_ARMIJO && !(phase == LB_ACCEPTED && st->ls != LS_ACCEPTED) &&
@@ -224,7 +330,7 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
     if (need) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int d = warp; d < nd; d += 8) {
-            double s = (d == imax) ? 0.0 : 0.0;
+            double s = 0.0;
             for (int b = lane; b < nblocks; b += 32) {
                 double x = partials[(size_t)b * nd + d];
                 s = (d == imax) ? fmax(s, x) : s + x;
@@ -238,9 +344,7 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
         }
     }
     __syncthreads();
-    if (threadIdx.x != 0)
-        return;
-
+    if (threadIdx.x == 0) {
     switch (phase) {
     case LB_INIT: {
         st->J = scal[0];
@@ -251,6 +355,7 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
         st->ginf = red[1];
         st->g0norm = st->gnorm = sqrt(red[0]);
         st->k = 0;
+        st->bodies = 0;
         st->evals = 1;
         st->small_count = 0;
         st->count = 0;
@@ -327,6 +432,12 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
         break;
     }
     case LB_ACCEPTED: {
+        if (++st->bodies > 2 * st->max_iter + 8) {   // cannot happen with the rules below; a hard stop
+            st->status = -6;
+            st->done = 1;
+            st->iter_continue = 0;
+            break;
+        }
         if (st->ls == LS_RETRY) {
             st->iter_continue = 1;
             break;
@@ -412,6 +523,10 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
     if (h_iter)
         cudaGraphSetConditional((cudaGraphConditionalHandle)h_iter, st->iter_continue ? 1u : 0u);
 #endif
+    }   // thread 0
+    __syncthreads();
+    for (int i = threadIdx.x; i < NW; i += blockDim.x)
+        reinterpret_cast<int *>(gst)[i] = reinterpret_cast<const int *>(&S)[i];
 }
 
 // Standalone direction for a given set of pairs (reg_lbfgs_direction): the
@@ -456,6 +571,22 @@ __global__ void __launch_bounds__(VT) k_lb_pair_dots(long long n, int count, con
         __syncthreads();
         block_reduce_write<1>(v, d == 1 ? 0 : -1, partials + (size_t)blockIdx.x * nd + d);
         __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(VT) k_lb_direction_plain(long long n, const LbfgsState *__restrict__ st,
+                                                           const float *__restrict__ g, const float *__restrict__ S,
+                                                           const float *__restrict__ Y, float *__restrict__ p)
+{
+    const int dc = st->dcount;
+    const float cg = (float)st->cg;
+    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n; e += (long long)gridDim.x * VT) {
+        float v = cg * g[e];
+        for (int j = 0; j < dc; j++) {
+            size_t o = (size_t)st->dslot[j] * n + e;
+            v = fmaf((float)st->cp[j], S[o], fmaf((float)st->cy[j], Y[o], v));
+        }
+        p[e] = v;
     }
 }
 
@@ -541,29 +672,32 @@ static cudaError_t control(reg_ctx *c, int phase, int nblocks, const double *sca
     return cudaGetLastError();
 }
 
+// ring slots start on 16-byte boundaries
+static long long ring_stride(long long n) { return (n + 3) & ~3LL; }
+
 cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s)
 {
     long long n = 3 * c->L[level].nn;
-    int nb = num_blocks_for(c, n, VT);
+    int nb = num_blocks_for(c, (n + 3) / 4, VT);
     cudaError_t e = launch_eval(c, level, c->lb.u, nullptr, nullptr, c->lb.g, c->es.scal, s);
     if (e != cudaSuccess)
         return e;
     k_lb_init_dots<<<nb, VT, 0, s>>>(n, c->lb.g, c->lb.partials);
     c->launches += 1;
-    return control(c, LB_INIT, nb, c->es.scal, s, false, false);
+    return control(c, LB_INIT, nb, c->es.scal, s, false, true);
 }
 
 cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s)
 {
-    long long n = 3 * c->L[level].nn;
-    int nb = num_blocks_for(c, n, VT);
-    k_lb_direction<<<nb, VT, 0, s>>>(n, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0);
+    long long n = 3 * c->L[level].nn, sd = ring_stride(n);
+    int nb = num_blocks_for(c, (n + 3) / 4, VT);
+    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0);
     c->launches += 2;
-    cudaError_t e = control(c, LB_DIR, nb, nullptr, s, false, false);
+    cudaError_t e = control(c, LB_DIR, nb, nullptr, s, true, false);
     if (e != cudaSuccess)
         return e;
-    k_lb_direction<<<nb, VT, 0, s>>>(n, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1);
-    return control(c, LB_DIR_REDO, nb, nullptr, s, false, false);
+    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1);
+    return control(c, LB_DIR_REDO, nb, nullptr, s, true, false);
 }
 
 cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s)
@@ -577,9 +711,9 @@ cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s)
 
 cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s)
 {
-    long long n = 3 * c->L[level].nn;
-    int nb = num_blocks_for(c, n, VT);
-    k_lb_accept<<<nb, VT, 0, s>>>(n, c->lb.st, c->lb.u, c->lb.g, c->lb.gt, c->lb.pdir, c->lb.P, c->lb.Y,
+    long long n = 3 * c->L[level].nn, sd = ring_stride(n);
+    int nb = num_blocks_for(c, (n + 3) / 4, VT);
+    k_lb_accept<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.u, c->lb.g, c->lb.gt, c->lb.pdir, c->lb.P, c->lb.Y,
                                   c->lb.partials);
     c->launches += 1;
     return control(c, LB_ACCEPTED, nb, nullptr, s, false, true);
@@ -594,8 +728,8 @@ cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const
     if (e != cudaSuccess)
         return e;
     k_lb_pair_setup<<<1, 32, 0, s>>>(c->lb.st, count, c->lb.partials, nb);
-    // pairs live in the caller's S, Y: slots 0..count-1 at stride n
-    k_lb_direction<<<nb, VT, 0, s>>>(n, c->lb.st, g, S, Y, p, c->lb.partials, 0);
+    // pairs live in the caller's S, Y: slots 0..count-1 at stride n (any alignment)
+    k_lb_direction_plain<<<nb, VT, 0, s>>>(n, c->lb.st, g, S, Y, p);
     c->launches += 3;
     return cudaGetLastError();
 }

@@ -43,8 +43,19 @@ struct FusedArgs {
     double *partials;       // D block partials
 };
 
+// node value at the trial point u + t dir (HAS_DIR) or u
+template <bool HAS_DIR>
+__device__ __forceinline__ float nval(const float *__restrict__ u, const float *__restrict__ d, float t, int k)
+{
+    float v = __ldg(u + k);
+    if (HAS_DIR)
+        v = fmaf(t, __ldg(d + k), v);
+    return v;
+}
+
 // displacement plane K of this thread's column: value at the first node and
 // the bilinear interpolation of the in-plane node differences to it
+template <bool HAS_DIR>
 __device__ __forceinline__ void load_node_plane(const FusedArgs &a, int kx, int ky, int K, float wx, float wy,
                                                 float t, float U[3], float Bd[3])
 {
@@ -54,21 +65,23 @@ __device__ __forceinline__ void load_node_plane(const FusedArgs &a, int kx, int 
         Bd[0] = Bd[1] = Bd[2] = 0.f;
         return;
     }
-    size_t sy = (size_t)g.n[0];
-    size_t b = kx + sy * (ky + (size_t)g.n[1] * K);
+    const int sy = g.n[0];
+    const int b = kx + sy * (ky + g.n[1] * K);
+    const int nn = (int)g.nn;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const float *u = a.ub + c * g.nn;
-        const float *d = a.dir ? a.dir + c * g.nn : nullptr;
-        float u00 = node_value(u, d, t, b);
-        float d10 = node_value(u, d, t, b + 1) - u00;
-        float d01 = node_value(u, d, t, b + sy) - u00;
-        float d11 = node_value(u, d, t, b + sy + 1) - u00;
+        const float *u = a.ub + c * nn;
+        const float *d = a.dir + (HAS_DIR ? c * nn : 0);
+        float u00 = nval<HAS_DIR>(u, d, t, b);
+        float d10 = nval<HAS_DIR>(u, d, t, b + 1) - u00;
+        float d01 = nval<HAS_DIR>(u, d, t, b + sy) - u00;
+        float d11 = nval<HAS_DIR>(u, d, t, b + sy + 1) - u00;
         U[c] = u00;
         Bd[c] = lerpf(wx * d10, lerpf(d01, d11, wx), wy);
     }
 }
 
+template <bool HAS_DIR>
 __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
 {
     __shared__ float sT[2][BY][BX];      // T~ planes (double buffered)
@@ -88,7 +101,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
     const bool col_in = x >= 0 && x < mx && y >= 0 && y < my;
     const bool b_thr = tx >= 1 && tx < BX - 1 && ty >= 1 && ty < BY - 1;
     const bool c_thr = tx >= 2 && tx < BX - 2 && ty >= 2 && ty < BY - 2;
-    const float t = a.dir ? (float)__ldg(a.t_dev) : 0.f;
+    const float t = HAS_DIR ? (float)__ldg(a.t_dev) : 0.f;
 
     // ratio 2: voxel i lies between nodes i/2 and i/2 + 1, weight of the second 1/4 or 3/4
     const int kx = x >> 1, ky = y >> 1;
@@ -98,8 +111,8 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
     float Ulo[3], Blo[3], Uhi[3], Bhi[3];
     int Klo = (z0 - 2) >> 1;
     if (col_in) {
-        load_node_plane(a, kx, ky, Klo, wx, wy, t, Ulo, Blo);
-        load_node_plane(a, kx, ky, Klo + 1, wx, wy, t, Uhi, Bhi);
+        load_node_plane<HAS_DIR>(a, kx, ky, Klo, wx, wy, t, Ulo, Blo);
+        load_node_plane<HAS_DIR>(a, kx, ky, Klo + 1, wx, wy, t, Uhi, Bhi);
     }
     float Tq0 = 0.f, Tq1 = 0.f, Tq2 = 0.f;    // T~ at zA-2, zA-1, zA
     float Rq0 = 0.f, Rq1 = 0.f, Rq2 = 0.f;    // R at zA-2, zA-1, zA
@@ -127,7 +140,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
                     Blo[c] = Bhi[c];
                 }
                 if (col_in)
-                    load_node_plane(a, kx, ky, Klo + 1, wx, wy, t, Uhi, Bhi);
+                    load_node_plane<HAS_DIR>(a, kx, ky, Klo + 1, wx, wy, t, Uhi, Bhi);
             }
             float val = 0.f, gr[3] = {0.f, 0.f, 0.f}, rv = 0.f;
             if (col_in && zA >= 0 && zA < mz) {
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
                     sample_coord(i, Ulo[c], delta, g.h[c], g.ih[c], cc[c], ff[c], ok[c]);
                 }
                 interp_value_grad(a.T, mx, my, mz, cc, ff, ok[0] && ok[1] && ok[2], g.ih, val, gr);
-                rv = __ldg(a.R + x + (size_t)mx * (y + (size_t)my * zA));
+                rv = __ldg(a.R + (x + mx * (y + my * zA)));
             }
             Tq0 = Tq1;
             Tq1 = Tq2;
@@ -355,7 +368,10 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     a.part = c->es.part;
     a.partials = partials;
     dim3 blk(BX, BY, 1), grd(a.ntx, a.nty, a.ntz);
-    k_ngf_fused<<<grd, blk, 0, s>>>(a);
+    if (dir)
+        k_ngf_fused<true><<<grd, blk, 0, s>>>(a);
+    else
+        k_ngf_fused<false><<<grd, blk, 0, s>>>(a);
     *n_partials = a.ntx * a.nty * a.ntz;
     c->launches += 1;
     return cudaGetLastError();

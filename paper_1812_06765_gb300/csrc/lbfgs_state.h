@@ -23,6 +23,7 @@ struct LbfgsState {
     int trial;         // trial index inside the current search
     int evals;         // objective evaluations on this level
     int small_count;   // consecutive small-J-change iterations
+    int bodies;        // iteration bodies run (accepted steps, retries, the final failed search)
     int retried;       // the p0 retry of this iteration has been used
     int redo_dir;      // the direction must be recomputed as p0
     int ls;            // LbSearch

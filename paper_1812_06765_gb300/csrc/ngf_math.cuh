@@ -74,32 +74,47 @@ __device__ __forceinline__ float load_zero_ext(const float *__restrict__ T, int 
                                                int z)
 {
     bool in = (unsigned)x < (unsigned)mx && (unsigned)y < (unsigned)my && (unsigned)z < (unsigned)mz;
-    return in ? __ldg(T + x + (size_t)mx * (y + (size_t)my * z)) : 0.f;
+    return in ? __ldg(T + (x + mx * (y + my * z))) : 0.f;
 }
 
 // Trilinear interpolation of T at cell c + fraction f (voxel units, sample j at
 // t = j) with zero extension, and the gradient of the interpolant in that cell
-// (per mm, through ih = 1 / h).
+// (per mm, through ih = 1 / h).  Index arithmetic is 32-bit (volumes below
+// 2^31 voxels).  Cells whose 8 corners are all inside take a path with one
+// bounds test; cells on the border load each corner with its own test.
 __device__ __forceinline__ void interp_value_grad(const float *__restrict__ T, int mx, int my, int mz, const int c[3],
                                                   const float f[3], bool ok, const float ih[3], float &val,
                                                   float gr[3])
 {
-    // outside -1 <= c_d <= m_d - 1 every corner is outside
-    if (!(ok && c[0] >= -1 && c[0] <= mx - 1 && c[1] >= -1 && c[1] <= my - 1 && c[2] >= -1 && c[2] <= mz - 1)) {
+    const int cx = c[0], cy = c[1], cz = c[2];
+    const int sxy = mx * my;
+    float t000, t100, t010, t110, t001, t101, t011, t111;
+    if (ok && (unsigned)cx < (unsigned)(mx - 1) && (unsigned)cy < (unsigned)(my - 1) &&
+        (unsigned)cz < (unsigned)(mz - 1)) {
+        const float *p = T + (cx + mx * (cy + my * cz));
+        t000 = __ldg(p);
+        t100 = __ldg(p + 1);
+        t010 = __ldg(p + mx);
+        t110 = __ldg(p + mx + 1);
+        t001 = __ldg(p + sxy);
+        t101 = __ldg(p + sxy + 1);
+        t011 = __ldg(p + sxy + mx);
+        t111 = __ldg(p + sxy + mx + 1);
+    } else if (ok && cx >= -1 && cx <= mx - 1 && cy >= -1 && cy <= my - 1 && cz >= -1 && cz <= mz - 1) {
+        t000 = load_zero_ext(T, mx, my, mz, cx, cy, cz);
+        t100 = load_zero_ext(T, mx, my, mz, cx + 1, cy, cz);
+        t010 = load_zero_ext(T, mx, my, mz, cx, cy + 1, cz);
+        t110 = load_zero_ext(T, mx, my, mz, cx + 1, cy + 1, cz);
+        t001 = load_zero_ext(T, mx, my, mz, cx, cy, cz + 1);
+        t101 = load_zero_ext(T, mx, my, mz, cx + 1, cy, cz + 1);
+        t011 = load_zero_ext(T, mx, my, mz, cx, cy + 1, cz + 1);
+        t111 = load_zero_ext(T, mx, my, mz, cx + 1, cy + 1, cz + 1);
+    } else {   // every corner outside (or a non-finite coordinate)
         val = 0.f;
         gr[0] = gr[1] = gr[2] = 0.f;
         return;
     }
-    const int cx = c[0], cy = c[1], cz = c[2];
     const float tx = f[0], ty = f[1], tz = f[2];
-    float t000 = load_zero_ext(T, mx, my, mz, cx, cy, cz);
-    float t100 = load_zero_ext(T, mx, my, mz, cx + 1, cy, cz);
-    float t010 = load_zero_ext(T, mx, my, mz, cx, cy + 1, cz);
-    float t110 = load_zero_ext(T, mx, my, mz, cx + 1, cy + 1, cz);
-    float t001 = load_zero_ext(T, mx, my, mz, cx, cy, cz + 1);
-    float t101 = load_zero_ext(T, mx, my, mz, cx + 1, cy, cz + 1);
-    float t011 = load_zero_ext(T, mx, my, mz, cx, cy + 1, cz + 1);
-    float t111 = load_zero_ext(T, mx, my, mz, cx + 1, cy + 1, cz + 1);
     float a00 = lerpf(t000, t100, tx), a10 = lerpf(t010, t110, tx);
     float a01 = lerpf(t001, t101, tx), a11 = lerpf(t011, t111, tx);
     float b0 = lerpf(a00, a10, ty), b1 = lerpf(a01, a11, ty);
@@ -144,11 +159,11 @@ __device__ __forceinline__ float ngf_residual(const float a[3], const float b[3]
     float ex = tau * b[0] - rho * a[0], ey = tau * b[1] - rho * a[1], ez = tau * b[2] - rho * a[2];
     float num = cx * cx + cy * cy + cz * cz + ex * ex + ey * ey + ez * ez;
     float den = na2 * nb2;
-    float psi = num / den;
+    float psi = __fdividef(num, den);   // approximate division: ~2 ulp
     float rs = rsqrtf(den);            // 1 / (||a||_tau ||b||_rho)
     float c = (ab + tau * rho) * rs;
     float k1 = -2.f * c * rs;          // v = -2c (b / (na nb) - c a / na^2)
-    float k2 = 2.f * c * c / na2;
+    float k2 = __fdividef(2.f * c * c, na2);
     v[0] = fmaf(k1, b[0], k2 * a[0]);
     v[1] = fmaf(k1, b[1], k2 * a[1]);
     v[2] = fmaf(k1, b[2], k2 * a[2]);

@@ -255,8 +255,9 @@ int allocate_buffers(reg_ctx *c)
     CK(cudaMalloc(&b.pdir, sizeof(float) * nmax));
     CK(cudaMalloc(&b.g, sizeof(float) * nmax));
     CK(cudaMalloc(&b.gt, sizeof(float) * nmax));
-    CK(cudaMalloc(&b.P, sizeof(float) * nmax * b.slots));
-    CK(cudaMalloc(&b.Y, sizeof(float) * nmax * b.slots));
+    const long long nring = (nmax + 3) & ~3LL;   // slot stride rounded up to 16 bytes
+    CK(cudaMalloc(&b.P, sizeof(float) * nring * b.slots));
+    CK(cudaMalloc(&b.Y, sizeof(float) * nring * b.slots));
     // the largest per-block layout is that of reg_lbfgs_direction's pair dots
     b.max_partials = 4 * (c->num_sms > 0 ? c->num_sms : 148) * (2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM) + 1024;
     CK(cudaMalloc(&b.partials, sizeof(double) * b.max_partials));
@@ -307,6 +308,7 @@ int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
         c->own_stream = false;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         set_err(nullptr, REG_ERR_CUDA, "reg_create: %s", cudaGetErrorString(e));
@@ -353,6 +355,16 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
         for (int d = 0; d < 3; d++)
             reuse = reuse && c->L[l].m[d] == G[l].m[d] && c->L[l].n[d] == G[l].n[d];
     if (reuse) {
+        bool same_spacing = true;
+        for (int l = 0; l < cfg.levels; l++)
+            for (int d = 0; d < 3; d++)
+                same_spacing = same_spacing && c->L[l].h[d] == G[l].h[d];
+        if (!same_spacing)   // graphs bake the spacings into their kernel arguments
+            for (int l = 0; l < REG_MAX_LEVELS; l++)
+                if (c->iter_graph[l]) {
+                    cudaGraphExecDestroy(c->iter_graph[l]);
+                    c->iter_graph[l] = nullptr;
+                }
         for (int l = 0; l < cfg.levels; l++)
             for (int d = 0; d < 3; d++) {
                 c->L[l].h[d] = G[l].h[d];
@@ -508,6 +520,28 @@ int run_level_host(reg_ctx *c, int level)
     return REG_OK;
 }
 
+// One level as a single graph launch (built on first use); the host reads
+// the device state once, after the level.
+int run_level_graph(reg_ctx *c, int level)
+{
+    if (!c->iter_graph[level]) {
+        cudaError_t e = build_level_graph(c, level, &c->iter_graph[level]);
+        if (e != cudaSuccess) {
+            c->iter_graph[level] = nullptr;
+            return cuda_err(c, e, "building the L-BFGS level graph");
+        }
+    }
+    CK(cudaGraphLaunch(c->iter_graph[level], c->stream));
+    int r = read_state(c);
+    if (r != REG_OK) return r;
+    const LbfgsState *sh = c->lb.st_host;
+    const int ek = eval_kernel_count(c, level);
+    // init: evaluation + norms + control; per body: 2 directions + 2 controls + accept + control;
+    // per trial: evaluation + control
+    c->launches += (ek + 2) + 6LL * sh->bodies + (long long)(ek + 1) * (sh->evals - 1);
+    return REG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -541,13 +575,15 @@ int reg_register(reg_handle c, float *u_out, int out_is_device, const float *u_i
         double Hmin = fmin(L.H[0], fmin(L.H[1], L.H[2]));
         lbfgs_state_reset_host(b.st_host, c->cfg, c->cfg.max_iter[l], Hmin);
         CK(cudaMemcpyAsync(b.st, b.st_host, sizeof(LbfgsState), cudaMemcpyHostToDevice, c->stream));
-        int r = run_level_host(c, l);
+        int r = c->cfg.use_graph ? run_level_graph(c, l) : run_level_host(c, l);
         if (r != REG_OK) return r;
         const LbfgsState *sh = b.st_host;
         local.iters[l] = sh->k;
         local.evals[l] = sh->evals;
         local.J[l] = sh->J;
         if (sh->status == -5) return set_err(c, REG_ERR_NUMERIC, "reg_register: non-finite J or gradient at level %d", l);
+        if (sh->status == -6)
+            return set_err(c, REG_ERR_TIMEOUT, "reg_register: level %d exceeded its loop bound", l);
         local.level_status[l] = sh->status == 1 ? REG_WARN_LINESEARCH : REG_OK;
         if (sh->status == 1) status = REG_WARN_LINESEARCH;
         if (l == 0) {
@@ -574,6 +610,7 @@ int reg_destroy(reg_handle c)
     free_buffers(c);
     if (c->ev_side) cudaEventDestroy(c->ev_side);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return REG_OK;

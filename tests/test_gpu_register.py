@@ -98,3 +98,38 @@ def test_register_128_ct_three_levels(reg_mod, orc):
     du = np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0))
     assert du.mean() / min(p["spacing"]) <= 0.1, (du.mean(), st, sto)
     r.close()
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+def test_graph_and_host_driven_levels_agree(reg_mod, impl):
+    """One graph launch per level (device-side loops) runs exactly the kernels the
+    host-driven loop runs, in the same order: results are bit-identical."""
+    p = make_pair(1, dims=(64, 64, 48))
+    kw = dict(levels=2, tau=0.1, alpha=50.0, max_iter=[25, 25], eval_impl=impl)
+    out = []
+    for graph in (0, 1):
+        r = reg_mod.Registration(reg_mod.make_config(use_graph=graph, **kw)).set_images(p["R"], p["T"], p["spacing"])
+        u, st = r.register(out="numpy")
+        out.append((u, st))
+        r.close()
+    (u0, s0), (u1, s1) = out
+    np.testing.assert_array_equal(u0, u1)
+    assert s0["iters"] == s1["iters"] and s0["evals"] == s1["evals"]
+    assert s0["kernel_launches"] == s1["kernel_launches"]
+    assert s0["J"] == s1["J"]
+
+
+def test_graph_registration_matches_oracle(reg_mod, orc):
+    """The graph form on the 64^3 workload: the same parity bar as the host-driven form."""
+    c = CONFIGS[0]
+    p = make_pair(0)
+    cfg, ocfg = _cfgs(reg_mod, orc, c)
+    cfg.use_graph = 1
+    r = reg_mod.Registration(cfg).set_images(p["R"], p["T"], p["spacing"])
+    u, st = r.register(out="numpy")
+    u2, st2 = r.register(out="numpy")          # the cached graph is replayed
+    np.testing.assert_array_equal(u, u2)
+    uo, sto = orc.register(p["dims"], p["spacing"], p["R"], p["T"], ocfg)
+    mean_vox = float(np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0)).mean()) / min(p["spacing"])
+    assert mean_vox <= 0.1, (mean_vox, st, sto)
+    r.close()
