@@ -58,7 +58,7 @@ typedef struct reg_ctx *reg_handle;
  *   tau = rho = 0.01, alpha = 10, c1 = 1e-4, max_backtracks = 20,
  *   tol_grad_rel = 1e-5, tol_j_rel = 1e-7, tol_j_count = 3, levels = 1,
  *   lbfgs_mem = 5, max_iter = 50 on every level, node_dims = 0 (rule m_d/2+1),
- *   start_level = -1 (coarsest), eval_impl = 0 (fused), use_graph = 0. */
+ *   start_level = -1 (coarsest), eval_impl = 0 (fused), use_graph = 1. */
 typedef struct reg_config {
     double tau, rho;      /* NGF edge parameters of Eq. 2 (template, reference), > 0 */
     double alpha;         /* regularisation weight of Eq. 1, >= 0 */

@@ -9,28 +9,43 @@
 //
 // Tiling.  A CTA of 32 x 16 threads owns the voxel columns of a 28 x 12 output
 // tile plus a 2-voxel halo (the stencil chain T~ -> a -> v -> g reaches two
-// voxels), and marches along z through a segment of TZ output planes.  Step s
-// computes, in order,
-//   A: T~ and grad T at plane zA = z0 - 2 + s   (every thread of the 32 x 16 plane)
-//   B: v at plane zA - 1                         (the 30 x 14 inner threads)
-//   C: r at plane zA - 2                         (the 28 x 12 output threads)
-//   D: P^T of that r plane into node sums        (shuffles in x, shared memory in y,
-//                                                  registers in z)
-// Neighbours along z live in per-thread registers; along x and y in
-// double-buffered shared-memory planes.  With ratio 2 the P weights are 1/4
-// and 3/4 and a node gathers voxels 2k-2 .. 2k+1 with weights 1/4, 3/4, 3/4,
-// 1/4 per dimension, so an output tile of 28 x 12 x TZ voxels feeds
-// 15 x 7 x (TZ/2 + 1) nodes; neighbouring tiles share one node plane per
-// dimension and the gather kernel sums them.
+// voxels), and marches along z through a segment of TZ output planes.  With
+// ratio 2 the P weights are 1/4 and 3/4 and a node gathers voxels 2k-2 .. 2k+1
+// with weights 1/4, 3/4, 3/4, 1/4 per dimension, so an output tile of
+// 28 x 12 x TZ voxels feeds 15 x 7 x (TZ/2 + 1) nodes; neighbouring tiles share
+// one node plane per dimension and the gather kernel sums them.
+//
+// Pipeline.  Step s (zA = z0 - 2 + s) runs, between two barriers,
+//   A-finish zA  : interpolate T at plane zA from the 8 corners staged last step
+//   A-issue zA+1 : coordinates of plane zA+1, cp.async of its 8 corners and of
+//                  R(zA+1) into shared rings (node planes two intervals ahead)
+//   B  zA-2      : v from T~ and R planes zA-3 .. zA-1
+//   C  zA-4      : r from v planes zA-5 .. zA-3; x reduction by warp shuffles
+//   D  zA-5      : y reduction of last step's rows, accumulation along z
+// Every phase reads only what earlier steps wrote, so one barrier per step
+// suffices, and the global loads of a plane overlap a whole step of compute.
 #include "internal.h"
 #include "ngf_math.cuh"
 
 namespace {
 
-constexpr int BX = 32, BY = 16;            // threads (voxel columns incl. halo)
-constexpr int OX = 28, OY = 12;            // output voxels per tile
+constexpr int BX = 32, BY = 16;                   // threads (voxel columns incl. halo)
+constexpr int OX = 28, OY = 12;                   // output voxels per tile
 constexpr int NX = OX / 2 + 1, NY = OY / 2 + 1;   // 15 x 7 node columns per tile
-constexpr int NE = 3 * NX * NY;            // partial entries per node plane (315)
+constexpr int NE = 3 * NX * NY;                   // partial entries per node plane (315)
+constexpr int PLANE = BX * BY;                    // floats of one shared plane
+constexpr int TNX = BX / 2 + 1, TNY = BY / 2 + 1; // node tile of the columns: 17 x 9
+constexpr int TNP = 3 * TNY * TNX;                // floats of one node plane tile per array
+
+// shared layout (floats)
+constexpr int OFF_T = 0;                          // T~ ring [4][PLANE]
+constexpr int OFF_R = OFF_T + 4 * PLANE;          // R ring [4][PLANE]
+constexpr int OFF_V = OFF_R + 4 * PLANE;          // v ring [4][3][PLANE]
+constexpr int OFF_G = OFF_V + 12 * PLANE;         // grad T ring [8][3][PLANE]
+constexpr int OFF_RED = OFF_G + 24 * PLANE;       // x-reduced rows [2][BY][NX][3]
+constexpr int OFF_N = OFF_RED + 2 * BY * NX * 3;  // node planes [4][2][TNP] (u, dir)
+constexpr int SMEM_FLOATS = OFF_N + 4 * 2 * TNP;
+constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 
 struct FusedArgs {
     LevelGeom g;
@@ -43,182 +58,258 @@ struct FusedArgs {
     double *partials;       // D block partials
 };
 
-// node value at the trial point u + t dir (HAS_DIR) or u
-template <bool HAS_DIR>
-__device__ __forceinline__ float nval(const float *__restrict__ u, const float *__restrict__ d, float t, int k)
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc, bool valid)
 {
-    float v = __ldg(u + k);
-    if (HAS_DIR)
-        v = fmaf(t, __ldg(d + k), v);
-    return v;
+    unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+    int src_size = valid ? 4 : 0;   // 0: no bytes read, the word is zero-filled
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(gsrc), "r"(src_size)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// displacement plane K of this thread's column: value at the first node and
-// the bilinear interpolation of the in-plane node differences to it
+// One thread's share of the cooperative copy of a node plane (u and, with a
+// direction, dir) of the CTA's 17 x 9 node tile: entries tid and tid + PLANE.
+// The in-plane offsets do not change along z, so they are computed once.
+struct NodeCopy {
+    const float *src[2];   // node (kx, ky, plane 0) of the entry's component and array
+    int dst[2];            // offset inside a ring slot
+    bool in[2];            // node column inside the grid
+};
+
 template <bool HAS_DIR>
-__device__ __forceinline__ void load_node_plane(const FusedArgs &a, int kx, int ky, int K, float wx, float wy,
-                                                float t, float U[3], float Bd[3])
+__device__ __forceinline__ NodeCopy node_copy_setup(const FusedArgs &a, int kx0, int ky0, int tid)
 {
     const LevelGeom &g = a.g;
-    if (K < 0 || K >= g.n[2]) {
-        U[0] = U[1] = U[2] = 0.f;
-        Bd[0] = Bd[1] = Bd[2] = 0.f;
-        return;
+    const int nn = (int)g.nn, total = (HAS_DIR ? 2 : 1) * TNP;
+    NodeCopy nc;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int e = tid + q * PLANE;
+        const int arr = e / TNP, r = e - arr * TNP;
+        const int c = r / (TNY * TNX), r2 = r - c * (TNY * TNX);
+        const int ly = r2 / TNX, lx = r2 - ly * TNX;
+        const int kx = kx0 + lx, ky = ky0 + ly;
+        nc.in[q] = e < total && kx >= 0 && kx < g.n[0] && ky >= 0 && ky < g.n[1];
+        nc.dst[q] = e < total ? e : -1;
+        nc.src[q] = nc.in[q] ? (arr ? a.dir : a.ub) + c * nn + (kx + g.n[0] * ky) : a.ub;
     }
-    const int sy = g.n[0];
-    const int b = kx + sy * (ky + g.n[1] * K);
-    const int nn = (int)g.nn;
+    return nc;
+}
+
+// copy node plane K into ring slot K % 4; nodes outside the grid read as zero
+__device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, float *sm, int K, int nz, int plane_stride)
+{
+    float *dst = sm + OFF_N + (K & 3) * 2 * TNP;
+    const bool kin = K >= 0 && K < nz;
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+        if (nc.dst[q] >= 0) {
+            const bool in = kin && nc.in[q];
+            cp_async4(dst + nc.dst[q], in ? nc.src[q] + (size_t)plane_stride * K : nc.src[q], in);
+        }
+}
+
+// displacement plane K of a column from the shared node tile: the value at the
+// first node (U) and the bilinear interpolation of the in-plane differences (Bd)
+template <bool HAS_DIR>
+__device__ __forceinline__ void column_plane(const float *sm, int K, int lkx, int lky, float wx, float wy, float t,
+                                             float U[3], float Bd[3])
+{
+    const float *nu = sm + OFF_N + (K & 3) * 2 * TNP;
+    const float *np = nu + TNP;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const float *u = a.ub + c * nn;
-        const float *d = a.dir + (HAS_DIR ? c * nn : 0);
-        float u00 = nval<HAS_DIR>(u, d, t, b);
-        float d10 = nval<HAS_DIR>(u, d, t, b + 1) - u00;
-        float d01 = nval<HAS_DIR>(u, d, t, b + sy) - u00;
-        float d11 = nval<HAS_DIR>(u, d, t, b + sy + 1) - u00;
+        const int o = c * (TNY * TNX) + lky * TNX + lkx;
+        float u00 = nu[o], u10 = nu[o + 1], u01 = nu[o + TNX], u11 = nu[o + TNX + 1];
+        if (HAS_DIR) {   // trial point u + t dir, the same fmaf as the accepted update
+            u00 = fmaf(t, np[o], u00);
+            u10 = fmaf(t, np[o + 1], u10);
+            u01 = fmaf(t, np[o + TNX], u01);
+            u11 = fmaf(t, np[o + TNX + 1], u11);
+        }
         U[c] = u00;
-        Bd[c] = lerpf(wx * d10, lerpf(d01, d11, wx), wy);
+        Bd[c] = lerpf(wx * (u10 - u00), lerpf(u01 - u00, u11 - u00, wx), wy);
     }
 }
 
 template <bool HAS_DIR>
 __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
 {
-    __shared__ float sT[2][BY][BX];      // T~ planes (double buffered)
-    __shared__ float sR[2][BY][BX];      // R planes
-    __shared__ float sVx[2][BY][BX];     // v_x planes
-    __shared__ float sVy[2][BY][BX];     // v_y planes
-    __shared__ float sRed[BY][NX][3];    // x-reduced r rows
-    __shared__ double sm[BX * BY / 32];
-
+    extern __shared__ float sm[];
     const LevelGeom &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
-    const int tile_x = blockIdx.x, tile_y = blockIdx.y, tile_z = blockIdx.z;
-    const int x = tile_x * OX - 2 + tx;
-    const int y = tile_y * OY - 2 + ty;
-    const int z0 = tile_z * a.tz;
+    const int x0 = blockIdx.x * OX, y0 = blockIdx.y * OY, z0 = blockIdx.z * a.tz;
+    const int x = x0 - 2 + tx, y = y0 - 2 + ty;
     const int mx = g.m[0], my = g.m[1], mz = g.m[2];
+    const int sxy = mx * my;
     const bool col_in = x >= 0 && x < mx && y >= 0 && y < my;
-    const bool b_thr = tx >= 1 && tx < BX - 1 && ty >= 1 && ty < BY - 1;
-    const bool c_thr = tx >= 2 && tx < BX - 2 && ty >= 2 && ty < BY - 2;
     const float t = HAS_DIR ? (float)__ldg(a.t_dev) : 0.f;
-
     // ratio 2: voxel i lies between nodes i/2 and i/2 + 1, weight of the second 1/4 or 3/4
-    const int kx = x >> 1, ky = y >> 1;
+    const int lkx = tx >> 1, lky = ty >> 1;           // node of the column inside the tile
+    const int kx0 = (x0 >> 1) - 1, ky0 = (y0 >> 1) - 1;
     const float wx = (x & 1) ? 0.75f : 0.25f, wy = (y & 1) ? 0.75f : 0.25f;
-
-    // per-column state
-    float Ulo[3], Blo[3], Uhi[3], Bhi[3];
-    int Klo = (z0 - 2) >> 1;
-    if (col_in) {
-        load_node_plane<HAS_DIR>(a, kx, ky, Klo, wx, wy, t, Ulo, Blo);
-        load_node_plane<HAS_DIR>(a, kx, ky, Klo + 1, wx, wy, t, Uhi, Bhi);
-    }
-    float Tq0 = 0.f, Tq1 = 0.f, Tq2 = 0.f;    // T~ at zA-2, zA-1, zA
-    float Rq0 = 0.f, Rq1 = 0.f, Rq2 = 0.f;    // R at zA-2, zA-1, zA
-    float vz0 = 0.f, vz1 = 0.f, vz2 = 0.f;    // v_z at zA-3, zA-2, zA-1
-    float gq[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // grad T at zA-2, zA-1, zA
-    float acc_lo = 0.f, acc_hi = 0.f;         // z accumulation of partial entry `tid`
-    KahanF psi_sum;
     const float hx = 0.5f * g.ih[0], hy = 0.5f * g.ih[1], hz = 0.5f * g.ih[2];
     const float half_hbar = 0.5f * g.hbar;
-    const size_t tile_lin = (size_t)tile_x + (size_t)a.ntx * (tile_y + (size_t)a.nty * tile_z);
+    const int zlast = z0 + a.tz + 1;                  // last T~ plane needed
+    const size_t tile_lin = (size_t)blockIdx.x + (size_t)a.ntx * (blockIdx.y + (size_t)a.nty * blockIdx.z);
     float *part_tile = a.part + tile_lin * (size_t)(a.tz / 2 + 1) * NE;
+    const NodeCopy nc = node_copy_setup<HAS_DIR>(a, kx0, ky0, tid);
+    const int node_plane = g.n[0] * g.n[1];
+    const float *Rcol = a.R + (col_in ? x + mx * y : 0);
 
-    const int nsteps = a.tz + 4;
-    for (int s = 0; s < nsteps; s++) {
-        const int zA = z0 - 2 + s;
-        const int buf = s & 1;
-        // ---- A: T~ and grad T at (x, y, zA); R at (x, y, zA)
-        {
-            // advance the node planes when zA enters a new node interval
-            if (s > 0 && !(zA & 1)) {
-                Klo++;
+    float Ulo[3], Blo[3], Uhi[3], Bhi[3];             // node planes floor(z/2) and +1 of this column
+    float pc[8];                                      // corners of the next plane, loaded a step ahead
+    float fr0 = 0.f, fr1 = 0.f, fr2 = 0.f;            // its fractions
+    float rnext = 0.f;                                // R of the next plane
+    float acc_lo = 0.f, acc_hi = 0.f;                 // z accumulation of partial entry `tid`
+    KahanF psi_sum;
+
+    // rows of the x-reduction buffer that no output row writes stay zero
+    for (int e = tid; e < 2 * BY * NX * 3; e += PLANE)
+        sm[OFF_RED + e] = 0.f;
+
+    // ---- A-issue: coordinates of plane z1 and loads of its 8 corners and of R(z1)
+    // into registers; they are first used one step later
+    auto a_issue = [&](int z1, bool first) {
+        const int K1 = z1 >> 1;
+        if (!(z1 & 1)) {   // a new node interval [K1, K1 + 1]
+            if (col_in) {
+                if (first) {
+                    column_plane<HAS_DIR>(sm, K1, lkx, lky, wx, wy, t, Ulo, Blo);
+                } else {
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    Ulo[c] = Uhi[c];
-                    Blo[c] = Bhi[c];
+                    for (int c = 0; c < 3; c++) {
+                        Ulo[c] = Uhi[c];
+                        Blo[c] = Bhi[c];
+                    }
                 }
-                if (col_in)
-                    load_node_plane<HAS_DIR>(a, kx, ky, Klo + 1, wx, wy, t, Uhi, Bhi);
+                column_plane<HAS_DIR>(sm, K1 + 1, lkx, lky, wx, wy, t, Uhi, Bhi);
             }
-            float val = 0.f, gr[3] = {0.f, 0.f, 0.f}, rv = 0.f;
-            if (col_in && zA >= 0 && zA < mz) {
-                const float wz = (zA & 1) ? 0.75f : 0.25f;
-                int cc[3];
-                float ff[3];
-                bool ok[3];
+            issue_node_plane(nc, sm, K1 + 2, g.n[2], node_plane);
+            cp_async_commit();
+        }
+        const bool zin = col_in && z1 >= 0 && z1 < mz;
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz)
-                    float delta = lerpf(Blo[c], (Uhi[c] - Ulo[c]) + Bhi[c], wz);
-                    int i = c == 0 ? x : (c == 1 ? y : zA);
-                    sample_coord(i, Ulo[c], delta, g.h[c], g.ih[c], cc[c], ff[c], ok[c]);
-                }
-                interp_value_grad(a.T, mx, my, mz, cc, ff, ok[0] && ok[1] && ok[2], g.ih, val, gr);
-                rv = __ldg(a.R + (x + mx * (y + my * zA)));
-            }
-            Tq0 = Tq1;
-            Tq1 = Tq2;
-            Tq2 = val;
-            Rq0 = Rq1;
-            Rq1 = Rq2;
-            Rq2 = rv;
+        for (int k = 0; k < 8; k++)
+            pc[k] = 0.f;
+        if (zin) {
+            const float wz = (z1 & 1) ? 0.75f : 0.25f;
+            int cc[3];
+            float ff[3];
+            bool ok[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                gq[0][c] = gq[1][c];
-                gq[1][c] = gq[2][c];
-                gq[2][c] = gr[c];
+                // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz)
+                float delta = lerpf(Blo[c], (Uhi[c] - Ulo[c]) + Bhi[c], wz);
+                const int i = c == 0 ? x : (c == 1 ? y : z1);
+                sample_coord(i, Ulo[c], delta, g.h[c], g.ih[c], cc[c], ff[c], ok[c]);
             }
-            sT[buf][ty][tx] = val;
-            sR[buf][ty][tx] = rv;
-        }
-        __syncthreads();
-        // ---- B: v at (x, y, zB = zA - 1)
-        const int zB = zA - 1;
-        {
-            float v[3] = {0.f, 0.f, 0.f};
-            if (b_thr && s >= 1) {
-                const int bb = buf ^ 1;   // plane zB was written at step s - 1
-                bool interior = col_in && x >= 1 && x <= mx - 2 && y >= 1 && y <= my - 2 && zB >= 1 && zB <= mz - 2;
-                if (interior) {
-                    float av[3], bv[3];
-                    av[0] = (sT[bb][ty][tx + 1] - sT[bb][ty][tx - 1]) * hx;
-                    av[1] = (sT[bb][ty + 1][tx] - sT[bb][ty - 1][tx]) * hy;
-                    av[2] = (Tq2 - Tq0) * hz;
-                    bv[0] = (sR[bb][ty][tx + 1] - sR[bb][ty][tx - 1]) * hx;
-                    bv[1] = (sR[bb][ty + 1][tx] - sR[bb][ty - 1][tx]) * hy;
-                    bv[2] = (Rq2 - Rq0) * hz;
-                    float psi = ngf_residual(av, bv, a.tau, a.rho, v);
-                    if (c_thr && zB >= z0 && zB < z0 + a.tz)
-                        psi_sum.add(psi);
+            fr0 = ff[0];
+            fr1 = ff[1];
+            fr2 = ff[2];
+            const int cx = cc[0], cy = cc[1], cz = cc[2];
+            if (ok[0] && ok[1] && ok[2]) {
+                if ((unsigned)cx < (unsigned)(mx - 1) && (unsigned)cy < (unsigned)(my - 1) &&
+                    (unsigned)cz < (unsigned)(mz - 1)) {   // all 8 corners inside
+                    const float *p = a.T + (cx + mx * (cy + my * cz));
+                    pc[0] = __ldg(p);
+                    pc[1] = __ldg(p + 1);
+                    pc[2] = __ldg(p + mx);
+                    pc[3] = __ldg(p + mx + 1);
+                    pc[4] = __ldg(p + sxy);
+                    pc[5] = __ldg(p + sxy + 1);
+                    pc[6] = __ldg(p + sxy + mx);
+                    pc[7] = __ldg(p + sxy + mx + 1);
+                } else {   // zero extension corner by corner
+#pragma unroll
+                    for (int k = 0; k < 8; k++)
+                        pc[k] = load_zero_ext(a.T, mx, my, mz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
                 }
             }
-            if (b_thr) {
-                sVx[buf][ty][tx] = v[0];
-                sVy[buf][ty][tx] = v[1];
-            }
-            vz0 = vz1;
-            vz1 = vz2;
-            vz2 = v[2];
         }
+        rnext = zin ? __ldg(Rcol + sxy * z1) : 0.f;
+    };
+
+    // prologue: node planes of the first interval, then the loads of plane z0 - 2
+    {
+        const int K0 = (z0 - 2) >> 1;
+        issue_node_plane(nc, sm, K0, g.n[2], node_plane);
+        issue_node_plane(nc, sm, K0 + 1, g.n[2], node_plane);
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
-        // ---- C: r at (x, y, zC = zA - 2); D: x reduction of the r row
-        const int zC = zA - 2;
-        const int lz = zC - z0;          // output plane index inside the segment
-        const bool c_plane = lz >= 0 && lz < a.tz;
-        if (c_plane) {
-            float r[3] = {0.f, 0.f, 0.f};
-            if (c_thr && col_in && zC < mz) {
-                const int vb = buf ^ 1;   // v of plane zC was written at step s - 1
-                float gs = (sVx[vb][ty][tx - 1] - sVx[vb][ty][tx + 1]) * hx +
-                           (sVy[vb][ty - 1][tx] - sVy[vb][ty + 1][tx]) * hy + (vz0 - vz2) * hz;
-                float gj = half_hbar * gs;
-                r[0] = gj * gq[0][0];
-                r[1] = gj * gq[0][1];
-                r[2] = gj * gq[0][2];
+        a_issue(z0 - 2, true);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+
+    const int nsteps = a.tz + 7;
+    for (int s = 0; s < nsteps; s++) {
+        const int zA = z0 - 2 + s;
+        // ---- A-finish: T~ and grad T at plane zA from the corners loaded last step
+        if (zA <= zlast) {
+            const float t000 = pc[0], t100 = pc[1], t010 = pc[2], t110 = pc[3];
+            const float t001 = pc[4], t101 = pc[5], t011 = pc[6], t111 = pc[7];
+            float a00 = lerpf(t000, t100, fr0), a10 = lerpf(t010, t110, fr0);
+            float a01 = lerpf(t001, t101, fr0), a11 = lerpf(t011, t111, fr0);
+            float b0 = lerpf(a00, a10, fr1), b1 = lerpf(a01, a11, fr1);
+            const float val = lerpf(b0, b1, fr2);
+            float dx0 = lerpf(t100 - t000, t110 - t010, fr1), dx1 = lerpf(t101 - t001, t111 - t011, fr1);
+            sm[OFF_T + (zA & 3) * PLANE + tid] = val;
+            sm[OFF_R + (zA & 3) * PLANE + tid] = rnext;
+            float *gq = sm + OFF_G + (zA & 7) * 3 * PLANE + tid;
+            gq[0] = lerpf(dx0, dx1, fr2) * g.ih[0];
+            gq[PLANE] = lerpf(a10 - a00, a11 - a01, fr2) * g.ih[1];
+            gq[2 * PLANE] = (b1 - b0) * g.ih[2];
+        }
+        // ---- A-issue for plane zA + 1
+        if (zA + 1 <= zlast)
+            a_issue(zA + 1, false);
+        // ---- B: v at plane zB = zA - 2 (warps 1 .. 14, lanes 1 .. 30)
+        const int zB = zA - 2;
+        if (ty >= 1 && ty < BY - 1 && zB >= z0 - 1 && zB <= z0 + a.tz) {
+            float v[3] = {0.f, 0.f, 0.f};
+            if (tx >= 1 && tx < BX - 1) {
+                const bool interior = col_in && x >= 1 && x <= mx - 2 && y >= 1 && y <= my - 2 && zB >= 1 &&
+                                      zB <= mz - 2;
+                if (interior) {
+                    const float *T0 = sm + OFF_T + (zB & 3) * PLANE + tid;
+                    const float *R0 = sm + OFF_R + (zB & 3) * PLANE + tid;
+                    float av[3], bv[3];
+                    av[0] = (T0[1] - T0[-1]) * hx;
+                    av[1] = (T0[BX] - T0[-BX]) * hy;
+                    av[2] = (sm[OFF_T + ((zB + 1) & 3) * PLANE + tid] - sm[OFF_T + ((zB - 1) & 3) * PLANE + tid]) * hz;
+                    bv[0] = (R0[1] - R0[-1]) * hx;
+                    bv[1] = (R0[BX] - R0[-BX]) * hy;
+                    bv[2] = (sm[OFF_R + ((zB + 1) & 3) * PLANE + tid] - sm[OFF_R + ((zB - 1) & 3) * PLANE + tid]) * hz;
+                    float psi = ngf_residual(av, bv, a.tau, a.rho, v);
+                    if (tx >= 2 && tx < BX - 2 && ty >= 2 && ty < BY - 2 && zB >= z0 && zB < z0 + a.tz)
+                        psi_sum.add(psi);
+                }
+                float *vq = sm + OFF_V + (zB & 3) * 3 * PLANE + tid;
+                vq[0] = v[0];
+                vq[PLANE] = v[1];
+                vq[2 * PLANE] = v[2];
             }
-            // node column j (0..14) of this row gathers threads 2j .. 2j+3 with 1/4, 3/4, 3/4, 1/4
+        }
+        // ---- C: r at plane zC = zA - 4 (warps 2 .. 13), x reduction into node columns
+        const int zC = zA - 4;
+        if (ty >= 2 && ty < BY - 2 && zC >= z0 && zC < z0 + a.tz) {
+            float r[3] = {0.f, 0.f, 0.f};
+            if (tx >= 2 && tx < BX - 2 && col_in && zC < mz) {
+                const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + tid;
+                float gs = (V0[-1] - V0[1]) * hx + (V0[PLANE - BX] - V0[PLANE + BX]) * hy +
+                           (sm[OFF_V + ((zC - 1) & 3) * 3 * PLANE + 2 * PLANE + tid] -
+                            sm[OFF_V + ((zC + 1) & 3) * 3 * PLANE + 2 * PLANE + tid]) * hz;
+                const float gj = half_hbar * gs;
+                const float *gq = sm + OFF_G + (zC & 7) * 3 * PLANE + tid;
+                r[0] = gj * gq[0];
+                r[1] = gj * gq[PLANE];
+                r[2] = gj * gq[2 * PLANE];
+            }
+            // node column j (0..14) gathers lanes 2j .. 2j+3 with weights 1/4, 3/4, 3/4, 1/4
+            float *red = sm + OFF_RED + (s & 1) * BY * NX * 3 + ty * NX * 3;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 float r1 = __shfl_down_sync(0xffffffffu, r[c], 1);
@@ -226,35 +317,36 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
                 float r3 = __shfl_down_sync(0xffffffffu, r[c], 3);
                 // written nodes have tx = 2j <= 28, so lanes tx + 1 .. tx + 3 exist
                 if (!(tx & 1) && (tx >> 1) < NX)
-                    sRed[ty][tx >> 1][c] = 0.25f * (r[c] + r3) + 0.75f * (r1 + r2);
+                    red[(tx >> 1) * 3 + c] = 0.25f * (r[c] + r3) + 0.75f * (r1 + r2);
             }
         }
+        // ---- D: y reduction of plane zD = zA - 5 and accumulation along z
+        const int zD = zA - 5;
+        if (tid < NE && zD >= z0 && zD < z0 + a.tz) {
+            const int lz = zD - z0;
+            const int c = tid / (NX * NY), rem = tid - c * (NX * NY), jy = rem / NX, jx = rem - jy * NX;
+            const float *red = sm + OFF_RED + ((s - 1) & 1) * BY * NX * 3;
+            const int r0 = 2 * jy;
+            float v = 0.25f * red[(r0 * NX + jx) * 3 + c] + 0.75f * red[((r0 + 1) * NX + jx) * 3 + c] +
+                      0.75f * red[((r0 + 2) * NX + jx) * 3 + c] + 0.25f * red[((r0 + 3) * NX + jx) * 3 + c];
+            if (!(lz & 1)) {
+                acc_lo = fmaf(0.75f, v, acc_lo);
+                acc_hi = fmaf(0.25f, v, acc_hi);
+            } else {
+                acc_lo = fmaf(0.25f, v, acc_lo);
+                acc_hi = fmaf(0.75f, v, acc_hi);
+                // node plane lz / 2 of the segment is complete
+                part_tile[(size_t)(lz >> 1) * NE + tid] = acc_lo;
+                acc_lo = acc_hi;
+                acc_hi = 0.f;
+            }
+            if (lz == a.tz - 1)
+                part_tile[(size_t)(a.tz >> 1) * NE + tid] = acc_lo;
+        }
+        cp_async_wait_all();
         __syncthreads();
-        if (c_plane) {
-            // y reduction of entry tid = (c, jy, jx) and accumulation along z
-            if (tid < NE) {
-                const int c = tid / (NX * NY), rem = tid % (NX * NY), jy = rem / NX, jx = rem % NX;
-                const int r0 = 2 * jy;
-                float v = 0.25f * sRed[r0][jx][c] + 0.75f * (sRed[r0 + 1][jx][c] + sRed[r0 + 2][jx][c]) +
-                          0.25f * sRed[r0 + 3][jx][c];
-                if (!(lz & 1)) {
-                    acc_lo = fmaf(0.75f, v, acc_lo);
-                    acc_hi = fmaf(0.25f, v, acc_hi);
-                } else {
-                    acc_lo = fmaf(0.25f, v, acc_lo);
-                    acc_hi = fmaf(0.75f, v, acc_hi);
-                    // node plane lz / 2 of the segment is complete
-                    part_tile[(size_t)(lz >> 1) * NE + tid] = acc_lo;
-                    acc_lo = acc_hi;
-                    acc_hi = 0.f;
-                }
-                if (lz == a.tz - 1)
-                    part_tile[(size_t)(a.tz >> 1) * NE + tid] = acc_lo;
-            }
-        }
-        // the next step's writes to sRed follow two more barriers
     }
-    double ssum = block_sum_to_f64(psi_sum.s, sm);
+    double ssum = block_sum_to_f64(psi_sum.s, reinterpret_cast<double *>(sm + OFF_RED));
     if (tid == 0)
         a.partials[(size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = ssum;
 }
@@ -368,10 +460,21 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     a.part = c->es.part;
     a.partials = partials;
     dim3 blk(BX, BY, 1), grd(a.ntx, a.nty, a.ntz);
+    static bool attr_set = false;   // the shared rings exceed the 48 KB default
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_ngf_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ngf_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_BYTES);
+        if (e != cudaSuccess)
+            return e;
+        attr_set = true;
+    }
     if (dir)
-        k_ngf_fused<true><<<grd, blk, 0, s>>>(a);
+        k_ngf_fused<true><<<grd, blk, SMEM_BYTES, s>>>(a);
     else
-        k_ngf_fused<false><<<grd, blk, 0, s>>>(a);
+        k_ngf_fused<false><<<grd, blk, SMEM_BYTES, s>>>(a);
     *n_partials = a.ntx * a.nty * a.ntz;
     c->launches += 1;
     return cudaGetLastError();

@@ -289,7 +289,7 @@ void reg_config_default(reg_config *cfg)
     cfg->start_level = -1;
     for (int l = 0; l < REG_MAX_LEVELS; l++) cfg->max_iter[l] = 50;
     cfg->eval_impl = 0;
-    cfg->use_graph = 0;
+    cfg->use_graph = 1;
 }
 
 int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
