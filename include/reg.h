@@ -132,6 +132,34 @@ int reg_get_level_image(reg_handle h, int level, int which, float *out, int out_
 int reg_eval_objective_grad(reg_handle h, int level, const float *u_dev, float *grad_dev,
                             double *J, double *D, double *S);
 
+/* Allocation-free evaluation: the same J, D_NGF, S and grad_u J as
+ * reg_eval_objective_grad computes at one resolution, for callers that must not
+ * allocate device memory while they run - code hosted by a framework that owns
+ * all device memory through its own pool and budget, or a latency-bound loop
+ * that cannot go through cudaMalloc / cudaFree (which may synchronise the
+ * device).  The paper has no counterpart: it is an interface of this library.
+ *   R, T: device images, dims[3] = (m_x, m_y, m_z), each even and >= 4 (the
+ *     deformation grid is m_d / 2 + 1 nodes per dimension), spacing_mm[3] > 0;
+ *   u, grad: device, 3 planes of the node count (grad is overwritten);
+ *   tau, rho > 0, alpha >= 0: the parameters of Eq. 1-2;
+ *   jds: device, 3 doubles receiving J, D and S;
+ *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * Every buffer is the caller's.  The working memory is one fixed 12.5 MiB array
+ * in the library's device image, held by every GPU that loads the library until
+ * the process exits; it fits images up to about 136^3 voxels (a 128^3 pair
+ * needs 8.3 MiB), and larger sizes are rejected with REG_ERR_ARG before
+ * anything is launched.  No call allocates memory.  The first call on each
+ * device looks up the array's device address and sets a kernel attribute for
+ * that device: make that first call before any stream capture.  All calls share
+ * the array and every call overwrites what it reads, so calls that may overlap
+ * on the GPU (different streams or threads) race and must be serialised by the
+ * caller.  Returns REG_OK, REG_ERR_ARG or REG_ERR_CUDA; reg_last_error(NULL)
+ * describes a failure.  Nothing is synchronised. */
+int reg_eval_objective_grad_noalloc(const float *R, const float *T, const int dims[3],
+                                    const double spacing_mm[3], const float *u, float *grad,
+                                    double tau, double rho, double alpha, double *jds,
+                                    void *cuda_stream);
+
 /* Nodal trilinear prolongation (Sec. 2.1 multilevel) of a displacement from
  * level `level_coarse` to level_coarse - 1.  Device pointers, 3 planes each. */
 int reg_prolong(reg_handle h, int level_coarse, const float *uc_dev, float *uf_dev);

@@ -77,6 +77,9 @@ def lib():
         L.reg_destroy.argtypes = [vp]
         L.reg_last_error.argtypes = [vp]
         L.reg_last_error.restype = ctypes.c_char_p
+        L.reg_eval_objective_grad_noalloc.argtypes = [fp, fp, ip, dp, fp, fp, ctypes.c_double, ctypes.c_double,
+                                                      ctypes.c_double, fp, vp]
+        L.reg_eval_objective_grad_noalloc.restype = ctypes.c_int
         for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_get_level_image",
                      "reg_eval_objective_grad", "reg_prolong", "reg_lbfgs_direction", "reg_register",
                      "reg_destroy"):
@@ -151,6 +154,16 @@ def reg_eval_objective_grad(h, level, u_ptr, grad_ptr, want_scalars=True):
     check(h, lib().reg_eval_objective_grad(h, int(level), ctypes.c_void_p(u_ptr), ctypes.c_void_p(grad_ptr),
                                            None, None, None))
     return None
+
+
+def reg_eval_objective_grad_noalloc(R_ptr, T_ptr, dims, spacing, u_ptr, grad_ptr, tau, rho, alpha, jds_ptr,
+                                    stream=None):
+    """The allocation-free evaluation (no handle); J, D, S land in the device array at jds_ptr."""
+    d = (ctypes.c_int * 3)(*[int(v) for v in dims])
+    s = (ctypes.c_double * 3)(*[float(v) for v in spacing])
+    return check(None, lib().reg_eval_objective_grad_noalloc(
+        ctypes.c_void_p(R_ptr), ctypes.c_void_p(T_ptr), d, s, ctypes.c_void_p(u_ptr), ctypes.c_void_p(grad_ptr),
+        float(tau), float(rho), float(alpha), ctypes.c_void_p(jds_ptr), ctypes.c_void_p(stream or 0)))
 
 
 def reg_prolong(h, level_coarse, uc_ptr, uf_ptr):

@@ -147,3 +147,22 @@ int eval_partials_needed(const Level &L)
     long long node_blocks = (long long)((L.n[0] + 31) / 32) * ((L.n[1] + 7) / 8) * L.n[2];
     return (int)(vox_blocks + node_blocks + 1024);
 }
+
+// Explicit-buffer launches of the curvature Laplacian and of the final
+// reduction, for callers that own every buffer (the allocation-free entry point).
+int curv_blocks(const LevelGeom &g) { return ((g.n[0] + 31) / 32) * ((g.n[1] + 7) / 8) * g.n[2]; }
+
+cudaError_t launch_curv_w_raw(const LevelGeom &g, const float *u, float *w, double *partials, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]);
+    k_curv_w<<<gn, blk, 0, s>>>(g, u, nullptr, nullptr, w, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_raw(const double *pD, int nD, const double *pS, int nS, double hbar_half, double alpha,
+                                double hy_half, double *scal, cudaStream_t s)
+{
+    k_finalize<<<1, 512, 0, s>>>(pD, nD, pS, nS, hbar_half, alpha, hy_half, scal);
+    return cudaGetLastError();
+}

@@ -491,3 +491,69 @@ cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alph
     c->launches += 1;
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Explicit-buffer launches of the fused pass and its gather, for callers that
+// own every buffer themselves (the allocation-free entry point).  Geometry
+// comes in as a LevelGeom of a ratio-2 grid; no per-dimension tables are used.
+// ---------------------------------------------------------------------------
+static int fused_tz_dims(const int m[3], int num_sms)
+{
+    long long cols = (long long)((m[0] + OX - 1) / OX) * ((m[1] + OY - 1) / OY);
+    int tz = 64;
+    while (tz > 8 && cols * ((m[2] + tz - 1) / tz) < 2LL * num_sms)
+        tz /= 2;
+    return tz;
+}
+
+void fused_layout_dims(const int m[3], int num_sms, int *tz, int *tiles, size_t *part_floats)
+{
+    const int z = fused_tz_dims(m, num_sms);
+    const int nt = ((m[0] + OX - 1) / OX) * ((m[1] + OY - 1) / OY) * ((m[2] + z - 1) / z);
+    *tz = z;
+    *tiles = nt;
+    *part_floats = (size_t)nt * (z / 2 + 1) * NE;
+}
+
+cudaError_t fused_set_smem_limit()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_ngf_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ngf_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    return e;
+}
+
+cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float *R, const float *u, float tau,
+                                 float rho, int num_sms, float *part, double *partials, cudaStream_t s)
+{
+    FusedArgs a;
+    a.g = g;
+    a.T = T;
+    a.R = R;
+    a.ub = u;
+    a.dir = nullptr;
+    a.t_dev = nullptr;
+    a.tau = tau;
+    a.rho = rho;
+    a.tz = fused_tz_dims(g.m, num_sms);
+    a.ntx = (g.m[0] + OX - 1) / OX;
+    a.nty = (g.m[1] + OY - 1) / OY;
+    a.ntz = (g.m[2] + a.tz - 1) / a.tz;
+    a.part = part;
+    a.partials = partials;
+    dim3 blk(BX, BY, 1), grd(a.ntx, a.nty, a.ntz);
+    k_ngf_fused<false><<<grd, blk, SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_grad_raw(const LevelGeom &g, const float *part, int num_sms, const float *w,
+                                   float alpha_hy, float *grad, cudaStream_t s)
+{
+    const int tz = fused_tz_dims(g.m, num_sms);
+    const int ntx = (g.m[0] + OX - 1) / OX, nty = (g.m[1] + OY - 1) / OY, ntz = (g.m[2] + tz - 1) / tz;
+    dim3 blk(32, 8, 1);
+    dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]);
+    k_gather_grad<<<gn, blk, 0, s>>>(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad);
+    return cudaGetLastError();
+}
