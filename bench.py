@@ -52,6 +52,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eval-impl", type=int, default=None, help="0 fused, 1 multi-pass (default: library)")
     ap.add_argument("--eval-only", action="store_true", help="time only the isolated evaluation (profiling)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="queue every L-BFGS step from the host instead of one graph per level (the same kernels "
+                         "in the same order; ncu cannot list kernels inside graphs with conditional nodes)")
     return ap.parse_args(argv)
 
 
@@ -223,6 +226,8 @@ def run_ours(args):
     kw = dict(levels=c["levels"], tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"], c1=c["c1"])
     if args.eval_impl is not None:
         kw["eval_impl"] = args.eval_impl
+    if args.host_loop:
+        kw["use_graph"] = False
     cfg = reg_pkg.make_config(**kw)
     stream = torch.cuda.current_stream(dev)
     reg = reg_pkg.Registration(cfg, stream=stream)
@@ -238,31 +243,42 @@ def run_ours(args):
         u, st = reg.register(out="torch")
         return st
 
-    def isolated_eval():
+    def isolated_eval(r=None):
         """Median device time (ms) of one full-resolution objective+gradient evaluation."""
-        reg.set_images(R_d, T_d, p["spacing"])
-        info = reg.level_info(0)
+        r = reg if r is None else r
+        r.set_images(R_d, T_d, p["spacing"])
+        info = r.level_info(0)
         u = torch.from_numpy(random_field(info["nodes"], 5, 5.0)).to(dev)
         grad = torch.empty_like(u)
         for _ in range(5):
-            _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
+            _lib.reg_eval_objective_grad(r.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
         ev_ms = []
         for _ in range(args.eval_iters):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _lib.reg_eval_objective_grad(reg.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
+            _lib.reg_eval_objective_grad(r.h, 0, u.data_ptr(), grad.data_ptr(), want_scalars=False)
             e1.record(stream)
             e1.synchronize()
             ev_ms.append(e0.elapsed_time(e1))
         return statistics.median(ev_ms), info
 
+    def isolated_eval_bf16():
+        """The same evaluation with BF16 image storage (FP32 arithmetic)."""
+        cfg_b = reg_pkg.make_config(image_dtype="bf16", **kw)
+        rb = reg_pkg.Registration(cfg_b, stream=stream)
+        try:
+            return isolated_eval(rb)[0]
+        finally:
+            rb.close()
+
     if args.eval_only:   # profiling aid: the isolated evaluation alone
         eval_ms, info = isolated_eval()
+        eval_ms_bf16 = isolated_eval_bf16()
         if rank == 0:
-            print(json.dumps({"eval_ms_full_res": eval_ms, "workload": c["name"],
-                              "eval_impl": reg.cfg.eval_impl, "iters": args.eval_iters}))
+            print(json.dumps({"eval_ms_full_res": eval_ms, "eval_ms_full_res_bf16_images": eval_ms_bf16,
+                              "workload": c["name"], "eval_impl": reg.cfg.eval_impl, "iters": args.eval_iters}))
         reg.close()
         return
 
@@ -310,6 +326,7 @@ def run_ours(args):
 
     # isolated full-resolution evaluation: the objective+gradient pass
     eval_ms, info = isolated_eval()
+    eval_ms_bf16 = isolated_eval_bf16()
     nv = int(np.prod(info["dims"]))
     nn = int(np.prod(info["nodes"]))
     alg_bytes = 4 * nv + 4 * nv + 12 * nn + 12 * nn       # read R, T, u; write grad J
@@ -339,11 +356,13 @@ def run_ours(args):
                        "alpha": c["alpha"], "lbfgs_mem": c["mem"], "max_iter_per_level": c["max_iter"],
                        "evals_per_level": evals_per_level, "iters_per_level": iters_per_level,
                        "eval_impl": "fused" if impl == 0 else "multi-pass",
+                       "lbfgs_loop": "one CUDA graph per level" if reg.cfg.use_graph else "host-driven",
                        "l2": "flushed between steps (2x L2 buffer written, untimed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "image_shape_zyx": list(mz)},
             "registration_s": total_ms / args.steps / 1000.0,
             "eval_ms_full_res": eval_ms,
+            "eval_ms_full_res_bf16_images": eval_ms_bf16,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                          "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind},

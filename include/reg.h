@@ -74,8 +74,10 @@ typedef struct reg_config {
     int max_iter[REG_MAX_LEVELS];       /* accepted iterations per level (index = level) */
     int node_dims[REG_MAX_LEVELS][3];   /* deformation grid per level; 0 = m_d / 2 + 1 */
     int eval_impl;        /* 0 fused objective pass, 1 multi-pass (intermediates in HBM) */
-    int use_graph;        /* 1: each L-BFGS iteration runs as one CUDA graph launch */
-    int reserved[6];
+    int use_graph;        /* 1: each pyramid level runs as one CUDA graph launch */
+    int image_dtype;      /* 0: FP32 images; 1: the fused pass reads BF16 copies of R and T
+                             (arithmetic stays FP32; levels without the fused pass use FP32) */
+    int reserved[5];
 } reg_config;
 
 /* Per-registration statistics (filled by reg_register). */

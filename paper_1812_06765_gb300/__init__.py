@@ -22,8 +22,9 @@ __all__ = ["make_config", "Registration", "RegObjective", "register", "RegError"
 
 def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1=1e-4, max_backtracks=20,
                 tol_grad_rel=1e-5, tol_j_rel=1e-7, tol_j_count=3, fixed_iters=False, start_level=-1,
-                node_dims=None, eval_impl=None, use_graph=None):
-    """A reg_config; max_iter is one value for every level or a per-level list (index 0 = finest)."""
+                node_dims=None, eval_impl=None, use_graph=None, image_dtype=None):
+    """A reg_config; max_iter is one value for every level or a per-level list (index 0 = finest).
+    image_dtype: "f32" (default) or "bf16" (the fused pass reads BF16 copies of the images)."""
     cfg = _lib.reg_config_default()
     cfg.tau = float(tau)
     cfg.rho = float(tau if rho is None else rho)
@@ -46,6 +47,10 @@ def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1
         cfg.eval_impl = int(eval_impl)
     if use_graph is not None:
         cfg.use_graph = int(bool(use_graph))
+    if image_dtype is not None:
+        if image_dtype not in ("f32", "bf16"):
+            raise ValueError("image_dtype must be 'f32' or 'bf16'")
+        cfg.image_dtype = 1 if image_dtype == "bf16" else 0
     return cfg
 
 

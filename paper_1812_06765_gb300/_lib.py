@@ -32,7 +32,8 @@ class RegConfig(ctypes.Structure):
         ("tol_j_count", ctypes.c_int), ("levels", ctypes.c_int), ("lbfgs_mem", ctypes.c_int),
         ("max_backtracks", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("start_level", ctypes.c_int),
         ("max_iter", ctypes.c_int * MAX_LEVELS), ("node_dims", (ctypes.c_int * 3) * MAX_LEVELS),
-        ("eval_impl", ctypes.c_int), ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6),
+        ("eval_impl", ctypes.c_int), ("use_graph", ctypes.c_int), ("image_dtype", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 

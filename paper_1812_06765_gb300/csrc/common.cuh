@@ -1,6 +1,7 @@
 // Shared device-side definitions of the CUDA path (sm_103a).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -17,6 +17,7 @@ struct Level {
     double H[3];
     long long nv, nn;
     float *R = nullptr, *T = nullptr;        // device images
+    __nv_bfloat16 *Rb = nullptr, *Tb = nullptr;   // BF16 copies read by the fused pass (image_dtype 1)
     int *pk0[3] = {nullptr, nullptr, nullptr};
     float *pw1[3] = {nullptr, nullptr, nullptr};
     int *tfirst[3] = {nullptr, nullptr, nullptr};
@@ -89,6 +90,7 @@ int cuda_err(reg_ctx *c, cudaError_t e, const char *what);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_restrict(const float *src, const int m[3], float *dst, cudaStream_t s);
+cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s);
 cudaError_t launch_prolong(const Level &coarse, const Level &fine, const float *uc, float *uf, cudaStream_t s);
 
 // objective + gradient at u_base + t_scale * dir (dir may be NULL: plain u_base);

@@ -16,9 +16,10 @@
 // one node plane per dimension and the gather kernel sums them.
 //
 // Pipeline.  Step s (zA = z0 - 2 + s) runs, between two barriers,
-//   A-finish zA  : interpolate T at plane zA from the 8 corners staged last step
-//   A-issue zA+1 : coordinates of plane zA+1, cp.async of its 8 corners and of
-//                  R(zA+1) into shared rings (node planes two intervals ahead)
+//   A-finish zA  : interpolate T at plane zA from the 8 corners loaded last step
+//   A-issue zA+1 : coordinates of plane zA+1, loads of its 8 corners and of
+//                  R(zA+1) into registers (used one step later); cp.async of
+//                  the node-plane tile two intervals ahead
 //   B  zA-2      : v from T~ and R planes zA-3 .. zA-1
 //   C  zA-4      : r from v planes zA-5 .. zA-3; x reduction by warp shuffles
 //   D  zA-5      : y reduction of last step's rows, accumulation along z
@@ -49,7 +50,8 @@ constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 
 struct FusedArgs {
     LevelGeom g;
-    const float *T, *R, *ub, *dir;
+    const void *T, *R;      // images, elements of the kernel's IMG type (float or bf16)
+    const float *ub, *dir;
     const double *t_dev;
     float tau, rho;
     int tz;                 // output planes per z segment (even)
@@ -133,7 +135,18 @@ __device__ __forceinline__ void column_plane(const float *sm, int K, int lkx, in
     }
 }
 
-template <bool HAS_DIR>
+// image element loads: FP32, or BF16 widened to FP32 (all arithmetic is FP32)
+__device__ __forceinline__ float ldimg(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldimg(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+template <typename IMG>
+__device__ __forceinline__ float ldimg_zero_ext(const IMG *T, int mx, int my, int mz, int x, int y, int z)
+{
+    bool in = (unsigned)x < (unsigned)mx && (unsigned)y < (unsigned)my && (unsigned)z < (unsigned)mz;
+    return in ? ldimg(T + (x + mx * (y + my * z))) : 0.f;
+}
+
+template <bool HAS_DIR, typename IMG = float>
 __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
 {
     extern __shared__ float sm[];
@@ -156,9 +169,15 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
     float *part_tile = a.part + tile_lin * (size_t)(a.tz / 2 + 1) * NE;
     const NodeCopy nc = node_copy_setup<HAS_DIR>(a, kx0, ky0, tid);
     const int node_plane = g.n[0] * g.n[1];
-    const float *Rcol = a.R + (col_in ? x + mx * y : 0);
+    const IMG *Tim = static_cast<const IMG *>(a.T);
+    const IMG *Rcol = static_cast<const IMG *>(a.R) + (col_in ? x + mx * y : 0);
 
-    float Ulo[3], Blo[3], Uhi[3], Bhi[3];             // node planes floor(z/2) and +1 of this column
+    float Uhi[3], Bhi[3];                             // node plane floor(z/2) + 1 of this column
+    // per node interval and component: integer part of the sampling coordinate
+    // (without the voxel index) and its fractional remainder for even and odd z
+    int qb[3] = {0, 0, 0};
+    float fe[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};
+    bool iv_ok = false;
     float pc[8];                                      // corners of the next plane, loaded a step ahead
     float fr0 = 0.f, fr1 = 0.f, fr2 = 0.f;            // its fractions
     float rnext = 0.f;                                // R of the next plane
@@ -175,6 +194,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
         const int K1 = z1 >> 1;
         if (!(z1 & 1)) {   // a new node interval [K1, K1 + 1]
             if (col_in) {
+                float Ulo[3], Blo[3];
                 if (first) {
                     column_plane<HAS_DIR>(sm, K1, lkx, lky, wx, wy, t, Ulo, Blo);
                 } else {
@@ -185,6 +205,30 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
                     }
                 }
                 column_plane<HAS_DIR>(sm, K1 + 1, lkx, lky, wx, wy, t, Uhi, Bhi);
+                // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz) with wz = 1/4 (even z) or
+                // 3/4 (odd z).  The sampling coordinate i + y-hat / h is kept as an integer
+                // part plus a small fraction (see sample_coord); both depend only on the
+                // interval and the parity of z, so they are formed here once.
+                iv_ok = true;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float ih = g.ih[c];
+                    const float q0 = Ulo[c] * ih;
+                    const float d1 = (Uhi[c] - Ulo[c]) + Bhi[c];
+                    iv_ok = iv_ok && fabsf(q0) < 1.0e6f && fabsf(Blo[c] * ih) < 1.0e6f && fabsf(d1 * ih) < 1.0e6f;
+                    const float qi = floorf(q0);
+                    const float rem = fmaf(-qi, g.h[c], Ulo[c]);   // |rem| <~ h
+                    fe[c] = (rem + lerpf(Blo[c], d1, 0.25f)) * ih;
+                    fo[c] = (rem + lerpf(Blo[c], d1, 0.75f)) * ih;
+                    qb[c] = (int)qi;
+                }
+                if (!iv_ok) {   // non-finite or absurd displacement: nothing is sampled
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        fe[c] = fo[c] = 0.f;
+                        qb[c] = 0;
+                    }
+                }
             }
             issue_node_plane(nc, sm, K1 + 2, g.n[2], node_plane);
             cp_async_commit();
@@ -194,41 +238,40 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
         for (int k = 0; k < 8; k++)
             pc[k] = 0.f;
         if (zin) {
-            const float wz = (z1 & 1) ? 0.75f : 0.25f;
+            const bool odd = z1 & 1;
             int cc[3];
             float ff[3];
-            bool ok[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz)
-                float delta = lerpf(Blo[c], (Uhi[c] - Ulo[c]) + Bhi[c], wz);
-                const int i = c == 0 ? x : (c == 1 ? y : z1);
-                sample_coord(i, Ulo[c], delta, g.h[c], g.ih[c], cc[c], ff[c], ok[c]);
+                const float fr = odd ? fo[c] : fe[c];
+                const float fl = floorf(fr);
+                ff[c] = fr - fl;
+                cc[c] = qb[c] + (int)fl;
             }
             fr0 = ff[0];
             fr1 = ff[1];
             fr2 = ff[2];
-            const int cx = cc[0], cy = cc[1], cz = cc[2];
-            if (ok[0] && ok[1] && ok[2]) {
+            const int cx = cc[0] + x, cy = cc[1] + y, cz = cc[2] + z1;
+            if (iv_ok) {
                 if ((unsigned)cx < (unsigned)(mx - 1) && (unsigned)cy < (unsigned)(my - 1) &&
                     (unsigned)cz < (unsigned)(mz - 1)) {   // all 8 corners inside
-                    const float *p = a.T + (cx + mx * (cy + my * cz));
-                    pc[0] = __ldg(p);
-                    pc[1] = __ldg(p + 1);
-                    pc[2] = __ldg(p + mx);
-                    pc[3] = __ldg(p + mx + 1);
-                    pc[4] = __ldg(p + sxy);
-                    pc[5] = __ldg(p + sxy + 1);
-                    pc[6] = __ldg(p + sxy + mx);
-                    pc[7] = __ldg(p + sxy + mx + 1);
+                    const IMG *p = Tim + (cx + mx * (cy + my * cz));
+                    pc[0] = ldimg(p);
+                    pc[1] = ldimg(p + 1);
+                    pc[2] = ldimg(p + mx);
+                    pc[3] = ldimg(p + mx + 1);
+                    pc[4] = ldimg(p + sxy);
+                    pc[5] = ldimg(p + sxy + 1);
+                    pc[6] = ldimg(p + sxy + mx);
+                    pc[7] = ldimg(p + sxy + mx + 1);
                 } else {   // zero extension corner by corner
 #pragma unroll
                     for (int k = 0; k < 8; k++)
-                        pc[k] = load_zero_ext(a.T, mx, my, mz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
+                        pc[k] = ldimg_zero_ext(Tim, mx, my, mz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
                 }
             }
         }
-        rnext = zin ? __ldg(Rcol + sxy * z1) : 0.f;
+        rnext = zin ? ldimg(Rcol + sxy * z1) : 0.f;
     };
 
     // prologue: node planes of the first interval, then the loads of plane z0 - 2
@@ -417,11 +460,12 @@ bool fused_eligible(const Level &L)
     return true;
 }
 
-// z segment length: even, 8 .. 64, aiming at >= 2 CTAs per SM
+// z segment length: even, 8 .. 128, the longest that still gives >= 2 CTAs per
+// SM (each segment pays 7 pipeline-fill steps)
 int fused_tz(const Level &L, int num_sms)
 {
     long long cols = (long long)((L.m[0] + OX - 1) / OX) * ((L.m[1] + OY - 1) / OY);
-    int tz = 64;
+    int tz = 128;
     while (tz > 8 && cols * ((L.m[2] + tz - 1) / tz) < 2LL * num_sms)
         tz /= 2;
     return tz;
@@ -448,8 +492,9 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     const Level &L = c->L[level];
     FusedArgs a;
     a.g = L.geom();
-    a.T = L.T;
-    a.R = L.R;
+    const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
+    a.T = bf16 ? L.Tb : static_cast<const void *>(L.T);
+    a.R = bf16 ? L.Rb : static_cast<const void *>(L.R);
     a.ub = ub;
     a.dir = dir;
     a.t_dev = t_dev;
@@ -460,21 +505,33 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     a.part = c->es.part;
     a.partials = partials;
     dim3 blk(BX, BY, 1), grd(a.ntx, a.nty, a.ntz);
-    static bool attr_set = false;   // the shared rings exceed the 48 KB default
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_ngf_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SMEM_BYTES);
+    // the shared rings exceed the 48 KB default; the limit is set once per device
+    static bool attr_set[64] = {};
+    const int dev = c->device >= 0 && c->device < 64 ? c->device : 0;
+    if (!attr_set[dev]) {
+        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(k_ngf_fused<true, float>, at, (int)SMEM_BYTES);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ngf_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES);
+            e = cudaFuncSetAttribute(k_ngf_fused<false, float>, at, (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ngf_fused<true, __nv_bfloat16>, at, (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ngf_fused<false, __nv_bfloat16>, at, (int)SMEM_BYTES);
         if (e != cudaSuccess)
             return e;
-        attr_set = true;
+        attr_set[dev] = true;
     }
-    if (dir)
-        k_ngf_fused<true><<<grd, blk, SMEM_BYTES, s>>>(a);
-    else
-        k_ngf_fused<false><<<grd, blk, SMEM_BYTES, s>>>(a);
+    if (bf16) {
+        if (dir)
+            k_ngf_fused<true, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a);
+        else
+            k_ngf_fused<false, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a);
+    } else {
+        if (dir)
+            k_ngf_fused<true, float><<<grd, blk, SMEM_BYTES, s>>>(a);
+        else
+            k_ngf_fused<false, float><<<grd, blk, SMEM_BYTES, s>>>(a);
+    }
     *n_partials = a.ntx * a.nty * a.ntz;
     c->launches += 1;
     return cudaGetLastError();

@@ -59,7 +59,31 @@ __global__ void k_prolong(const float *__restrict__ uc, int cx, int cy, int cz, 
     }
 }
 
+// FP32 -> BF16 (round to nearest even) image copy, float4 reads.
+__global__ void __launch_bounds__(256) k_to_bf16(const float *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
+                                                 long long n)
+{
+    const long long n4 = n >> 2;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n4; e += (long long)gridDim.x * 256) {
+        float4 v = reinterpret_cast<const float4 *>(src)[e];
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        reinterpret_cast<__nv_bfloat162 *>(dst)[2 * e] = a;
+        reinterpret_cast<__nv_bfloat162 *>(dst)[2 * e + 1] = b;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3))
+        dst[4 * n4 + threadIdx.x] = __float2bfloat16_rn(src[4 * n4 + threadIdx.x]);
+}
+
 }  // namespace
+
+cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s)
+{
+    long long blocks = ((n >> 2) + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 4096) blocks = 4096;
+    k_to_bf16<<<(int)blocks, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_restrict(const float *src, const int m[3], float *dst, cudaStream_t s)
 {

@@ -17,6 +17,8 @@ void free_level(Level &L)
 {
     cudaFree(L.R);
     cudaFree(L.T);
+    cudaFree(L.Rb);
+    cudaFree(L.Tb);
     for (int d = 0; d < 3; d++) {
         cudaFree(L.pk0[d]);
         cudaFree(L.pw1[d]);
@@ -78,6 +80,7 @@ int validate_config(const reg_config *cfg, std::string &msg)
     } else if (cfg->max_backtracks < 1) msg = "max_backtracks must be >= 1";
     else if (cfg->start_level >= cfg->levels) msg = "start_level must be < levels";
     else if (cfg->eval_impl != 0 && cfg->eval_impl != 1) msg = "eval_impl must be 0 or 1";
+    else if (cfg->image_dtype != 0 && cfg->image_dtype != 1) msg = "image_dtype must be 0 (FP32) or 1 (BF16)";
     else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
     else return REG_OK;
     return REG_ERR_ARG;
@@ -244,6 +247,12 @@ int allocate_buffers(reg_ctx *c)
         CK(cudaMalloc(&es.part, sizeof(float) * part));
         es.part_floats = part;
     }
+    if (cfg.image_dtype == 1)   // BF16 copies for the levels the fused pass serves
+        for (int l = 0; l < c->levels; l++)
+            if (use_fused(c, l)) {
+                CK(cudaMalloc(&c->L[l].Rb, sizeof(__nv_bfloat16) * c->L[l].nv));
+                CK(cudaMalloc(&c->L[l].Tb, sizeof(__nv_bfloat16) * c->L[l].nv));
+            }
     CK(cudaMalloc(&es.w, sizeof(float) * nmax));
     CK(cudaMalloc(&es.partials, sizeof(double) * maxpart));
     CK(cudaMalloc(&es.scal, sizeof(double) * 4));
@@ -403,6 +412,12 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
     }
     CK(cudaEventRecord(c->ev_side, c->side));
     CK(cudaStreamWaitEvent(c->stream, c->ev_side, 0));
+    for (int l = 0; l < c->levels; l++)   // BF16 copies (image_dtype 1), rounded to nearest even
+        if (c->L[l].Rb) {
+            CK(launch_to_bf16(c->L[l].R, c->L[l].Rb, c->L[l].nv, c->stream));
+            CK(launch_to_bf16(c->L[l].T, c->L[l].Tb, c->L[l].nv, c->stream));
+            c->launches += 2;
+        }
     if (!ptr_is_device) CK(cudaStreamSynchronize(c->stream));  // host arrays may be released on return
     c->have_images = true;
     return REG_OK;

@@ -227,3 +227,35 @@ def test_autograd_function(reg_mod, orc):
     an = float((g.double() * d.double()).sum())
     assert abs(fd - an) <= 1e-2 * abs(an), (fd, an)
     r.close()
+
+
+def _bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).bfloat16().float().numpy()
+
+
+@pytest.mark.parametrize("config_id", [None, 2])
+def test_bf16_image_storage(reg_mod, orc, config_id):
+    """BF16 image storage, FP32 arithmetic: against the oracle fed the BF16-rounded
+    images the kernel error meets the FP32 bar; against the FP32-image oracle the
+    storage error is reported (and bounded loosely)."""
+    from synth import CONFIGS
+    if config_id is None:
+        dims, h, tau, alpha = (58, 38, 70), (1.2, 0.8, 1.0), 0.05, 2.0
+        R, T = random_image(dims, 601), random_image(dims, 602)
+        amp, levels = 2.0, 1
+    else:
+        p = make_pair(config_id)
+        c = CONFIGS[config_id]
+        dims, h, tau, alpha, R, T = p["dims"], p["spacing"], c["eta"], c["alpha"], p["R"], p["T"]
+        amp, levels = 5.0, c["levels"]
+    cfg = reg_mod.make_config(levels=levels, tau=tau, alpha=alpha, image_dtype="bf16")
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    u = random_field(r.level_info(0)["nodes"], 603, amp)
+    Rb, Tb = _bf16_round(R), _bf16_round(T)
+    e_kernel = compare_eval(r, orc, Rb, Tb, dims, h, u, tau, tau, alpha)
+    e_store = compare_eval(r, orc, R, T, dims, h, u, tau, tau, alpha)
+    print("bf16 kernel error J %.2e grad %.2e; storage error J %.2e grad %.2e"
+          % (e_kernel["eJ"], e_kernel["eg"], e_store["eJ"], e_store["eg"]))
+    assert e_kernel["eJ"] <= J_RTOL and e_kernel["eg"] <= GRAD_RTOL, e_kernel
+    assert e_store["eJ"] <= 1e-2 and e_store["eg"] <= 0.2, e_store
+    r.close()
