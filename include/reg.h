@@ -183,6 +183,23 @@ int reg_lbfgs_direction(reg_handle h, long long n, int count, const float *S_dev
  * statistics.  Returns REG_OK, REG_WARN_LINESEARCH, or an error. */
 int reg_register(reg_handle h, float *u_out, int out_is_device, const float *u_init, reg_stats *st);
 
+/* Register n pairs together (many pairs of uneven size, Sec. 2.1-2.2 per
+ * pair): each hs[i] is a handle with its images set; all share the number of
+ * levels, the start level, image_dtype and the device, and every level must be a
+ * ratio-2 grid served by the fused pass (even dims, default node counts,
+ * eval_impl 0).  Per pyramid level the pairs iterate in lock step inside one
+ * CUDA graph launch: each kernel of an iteration runs once for the whole batch
+ * over a work list of (pair, tile / block) items, and pairs that have finished
+ * their level or their line search skip their items.  Every pair runs exactly
+ * the computation of reg_register with its own configuration, so its result is
+ * the one reg_register gives.  u_out[i]: the finest displacement of pair i
+ * (device pointers if out_is_device, else host); stats (nullable) receives n
+ * entries (kernel_launches counts the launches of the whole batch).  Work runs
+ * on hs[0]'s stream; the call synchronises it.  Returns REG_OK,
+ * REG_WARN_LINESEARCH (some pair), or an error (argument errors are described
+ * by reg_last_error(NULL), CUDA errors by reg_last_error(hs[0])). */
+int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_is_device, reg_stats *stats);
+
 /* Release all device memory, streams and graphs of the handle.  NULL-safe.
  * Returns REG_OK. */
 int reg_destroy(reg_handle h);

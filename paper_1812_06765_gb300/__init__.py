@@ -203,6 +203,26 @@ class RegObjective(torch.autograd.Function):
         return (gJ.to(grad.dtype) * grad).reshape(grad.shape), None, None
 
 
+def _stats_dict(rc, st):
+    L = st.levels
+    return dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L], level_status=list(st.level_status)[:L],
+                J=list(st.J)[:L], J_final=st.J_final, D_final=st.D_final, S_final=st.S_final,
+                kernel_launches=st.kernel_launches)
+
+
+def register_batch(regs, out="torch"):
+    """Register the pairs of several Registration handles together (one graph
+    launch per pyramid level for all of them); returns a list of (u, stats)."""
+    outs = []
+    for r in regs:
+        shape = r.node_shape(0)
+        outs.append(torch.empty(shape, dtype=torch.float32, device="cuda") if out == "torch"
+                    else np.empty(shape, dtype=np.float32))
+    ptrs = [o.data_ptr() if out == "torch" else o.ctypes.data for o in outs]
+    rc, stats = _lib.reg_register_batch([r.h for r in regs], ptrs, out == "torch")
+    return [(o, _stats_dict(rc, s)) for o, s in zip(outs, stats)]
+
+
 def register(R, T, spacing, out="torch", u_init=None, **cfg_kw):
     """Convenience: one registration of (R, T); returns (u, stats)."""
     reg = Registration(make_config(**cfg_kw))

@@ -81,6 +81,9 @@ def lib():
         L.reg_eval_objective_grad_noalloc.argtypes = [fp, fp, ip, dp, fp, fp, ctypes.c_double, ctypes.c_double,
                                                       ctypes.c_double, fp, vp]
         L.reg_eval_objective_grad_noalloc.restype = ctypes.c_int
+        L.reg_register_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(fp), ctypes.c_int,
+                                         ctypes.POINTER(RegStats)]
+        L.reg_register_batch.restype = ctypes.c_int
         for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_get_level_image",
                      "reg_eval_objective_grad", "reg_prolong", "reg_lbfgs_direction", "reg_register",
                      "reg_destroy"):
@@ -182,6 +185,18 @@ def reg_register(h, u_out_ptr, out_is_device, u_init_ptr=None):
     rc = check(h, lib().reg_register(h, ctypes.c_void_p(u_out_ptr), int(bool(out_is_device)),
                                      ctypes.c_void_p(u_init_ptr or 0), ctypes.byref(st)))
     return rc, st
+
+
+def reg_register_batch(handles, u_out_ptrs, out_is_device):
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    outs = (ctypes.c_void_p * n)(*u_out_ptrs)
+    stats = (RegStats * n)()
+    rc = lib().reg_register_batch(hs, n, outs, int(bool(out_is_device)), stats)
+    if rc < 0:
+        msg = last_error(None) or last_error(handles[0])
+        raise RegError(rc, msg)
+    return rc, list(stats)
 
 
 def reg_destroy(h):

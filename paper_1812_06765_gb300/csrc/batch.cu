@@ -1,0 +1,364 @@
+// Batched registration of many pairs of uneven size (reg_register_batch).
+//
+// Per pyramid level, all pairs run their L-BFGS iterations in lock step inside
+// one CUDA graph: every kernel of an iteration is launched once for the whole
+// batch and walks a work list of (pair, item) over all pairs - fused-pass
+// tiles, node blocks, vector blocks - with a persistent grid.  Each item runs
+// the same per-pair code as a single registration with that pair's own
+// buffers, tiling and block counts, so every pair gets exactly the result it
+// gets alone.  Pairs that have finished their level, or their line search,
+// skip their items; the loops run while any pair still iterates / searches.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "batch.h"
+
+namespace {
+
+long long ring_stride(long long n) { return (n + 3) & ~3LL; }
+
+void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
+{
+    const Level &L = c->L[level];
+    memset(&P, 0, sizeof P);
+    P.geom = L.geom();
+    int tz, ntx, nty, ntz;
+    fused_tiling(L, c->num_sms, &tz, &ntx, &nty, &ntz);
+    const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
+    FusedArgs a;
+    memset(&a, 0, sizeof a);
+    a.g = P.geom;
+    a.T = bf16 ? static_cast<const void *>(L.Tb) : static_cast<const void *>(L.T);
+    a.R = bf16 ? static_cast<const void *>(L.Rb) : static_cast<const void *>(L.R);
+    a.ub = c->lb.u;
+    a.dir = nullptr;
+    a.t_dev = nullptr;
+    a.tau = (float)c->cfg.tau;
+    a.rho = (float)c->cfg.rho;
+    a.tz = tz;
+    a.ntx = ntx;
+    a.nty = nty;
+    a.ntz = ntz;
+    a.part = c->es.part;
+    a.partials = c->es.partials;
+    P.fa_init = a;
+    a.dir = c->lb.pdir;
+    a.t_dev = &c->lb.st->t;
+    P.fa_trial = a;
+    P.tz = tz;
+    P.ntx = ntx;
+    P.nty = nty;
+    P.ncx = (L.n[0] + 31) / 32;
+    P.ncy = (L.n[1] + 7) / 8;
+    P.nD = ntx * nty * ntz;
+    P.nS = P.ncx * P.ncy * L.n[2];
+    P.w = c->es.w;
+    P.pS = c->es.partials + P.nD;
+    const double hy = L.H[0] * L.H[1] * L.H[2];
+    P.hbar_half = 0.5 * L.h[0] * L.h[1] * L.h[2];
+    P.alpha = c->cfg.alpha;
+    P.hy_half = 0.5 * hy;
+    P.alpha_hy = (float)(c->cfg.alpha * hy);
+    P.scal = c->es.scal;
+    P.scal_t = c->lb.scal_t;
+    P.st = c->lb.st;
+    P.n = 3 * L.nn;
+    P.stride = ring_stride(P.n);
+    P.u = c->lb.u;
+    P.g = c->lb.g;
+    P.gt = c->lb.gt;
+    P.pdir = c->lb.pdir;
+    P.P = c->lb.P;
+    P.Y = c->lb.Y;
+    P.lpart = c->lb.partials;
+    P.nchunks = num_blocks_for(c, (P.n + 3) / 4, 256);
+}
+
+struct BatchDev {
+    PairLevel *pl = nullptr;
+    int *off = nullptr;      // [3][npairs + 1]: tiles, node blocks, vector blocks
+    int *counters = nullptr; // [2]: runs of the iteration and search conditions
+};
+
+struct CaptureGuard {
+    cudaStream_t s;
+    bool active = false;
+    ~CaptureGuard()
+    {
+        if (active) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s, &g);
+            if (g)
+                cudaGraphDestroy(g);
+        }
+    }
+};
+
+cudaError_t leaves_of(cudaStream_t s, std::vector<cudaGraphNode_t> &out)
+{
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e == cudaSuccess)
+        out.assign(deps, deps + nd);
+    return e;
+}
+
+cudaError_t while_node(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                       cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p);
+    if (e == cudaSuccess)
+        *body = p.conditional.phGraph_out[0];
+    return e;
+}
+
+struct BatchLaunch {
+    const BatchDev *d;
+    int npairs, tiles, nodes, chunks;
+    int g_fused, g_nodes, g_chunks;
+    bool bf16;
+    int device;
+
+    cudaError_t eval(int mode, cudaStream_t s) const
+    {
+        cudaError_t e = launch_fused_batch(d->pl, d->off, npairs, tiles, mode, bf16, g_fused, device, s);
+        if (e == cudaSuccess)
+            e = launch_curv_w_batch(d->pl, d->off + (npairs + 1), npairs, nodes, mode, g_nodes, s);
+        if (e == cudaSuccess)
+            e = launch_gather_batch(d->pl, d->off + (npairs + 1), npairs, nodes, mode, g_nodes, s);
+        if (e == cudaSuccess)
+            e = launch_finalize_batch(d->pl, npairs, mode, s);
+        return e;
+    }
+    cudaError_t vec(int step, cudaStream_t s) const
+    {
+        return launch_lb_vector_batch(d->pl, d->off + 2 * (npairs + 1), npairs, chunks, step, g_chunks, s);
+    }
+    cudaError_t ctl(int phase, cudaStream_t s) const { return launch_lb_control_batch(d->pl, npairs, phase, s); }
+    cudaError_t cond(int which, cudaGraphConditionalHandle h, cudaStream_t s) const
+    {
+        return launch_batch_condition(d->pl, npairs, which, h, d->counters, s);
+    }
+};
+
+#define BK(call)                                  \
+    do {                                          \
+        cudaError_t _e = (call);                  \
+        if (_e != cudaSuccess) {                  \
+            if (G) cudaGraphDestroy(G);           \
+            return _e;                            \
+        }                                         \
+    } while (0)
+
+// The whole level for all pairs: init, then WHILE any pair iterates
+// { direction; WHILE any pair searches { objective at the trial points; Armijo }; accept }.
+cudaError_t build_batch_graph(const BatchLaunch &B, cudaStream_t cs, cudaGraphExec_t *out)
+{
+    cudaGraph_t G = nullptr;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    BK(cudaGraphCreate(&G, 0));
+    cudaGraphConditionalHandle h_iter, h_ls;
+    BK(cudaGraphConditionalHandleCreate(&h_iter, G, 0, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> leaves;
+    cudaGraph_t g2 = nullptr;
+    {
+        CaptureGuard guard{cs};
+        BK(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, mode));
+        guard.active = true;
+        BK(B.eval(0, cs));
+        BK(B.vec(0, cs));
+        BK(B.ctl(LB_INIT, cs));
+        BK(B.cond(0, h_iter, cs));
+        BK(leaves_of(cs, leaves));
+        guard.active = false;
+        BK(cudaStreamEndCapture(cs, &g2));
+    }
+    cudaGraphNode_t w_iter, w_ls;
+    cudaGraph_t body = nullptr, ls_body = nullptr;
+    BK(while_node(G, leaves, h_iter, &w_iter, &body));
+    BK(cudaGraphConditionalHandleCreate(&h_ls, body, 0, cudaGraphCondAssignDefault));
+    {
+        CaptureGuard guard{cs};
+        BK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
+        guard.active = true;
+        BK(B.vec(1, cs));
+        BK(B.ctl(LB_DIR, cs));
+        BK(B.vec(2, cs));
+        BK(B.ctl(LB_DIR_REDO, cs));
+        BK(B.cond(1, h_ls, cs));
+        BK(leaves_of(cs, leaves));
+        guard.active = false;
+        BK(cudaStreamEndCapture(cs, &g2));
+    }
+    BK(while_node(body, leaves, h_ls, &w_ls, &ls_body));
+    {
+        CaptureGuard guard{cs};
+        BK(cudaStreamBeginCaptureToGraph(cs, ls_body, nullptr, nullptr, 0, mode));
+        guard.active = true;
+        BK(B.eval(1, cs));
+        BK(B.ctl(LB_ARMIJO, cs));
+        BK(B.cond(1, h_ls, cs));
+        guard.active = false;
+        BK(cudaStreamEndCapture(cs, &g2));
+    }
+    {
+        CaptureGuard guard{cs};
+        BK(cudaStreamBeginCaptureToGraph(cs, body, &w_ls, nullptr, 1, mode));
+        guard.active = true;
+        BK(B.vec(3, cs));
+        BK(B.ctl(LB_ACCEPTED, cs));
+        BK(B.cond(0, h_iter, cs));
+        guard.active = false;
+        BK(cudaStreamEndCapture(cs, &g2));
+    }
+    BK(cudaGraphInstantiate(out, G, 0));
+    cudaGraphDestroy(G);
+    return cudaSuccess;
+}
+
+int cap(long long v, long long hi) { return (int)(v < 1 ? 1 : (v > hi ? hi : v)); }
+
+}  // namespace
+
+extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_is_device, reg_stats *stats)
+{
+    if (!hs || n < 1 || !u_out)
+        return set_err(nullptr, REG_ERR_ARG, "reg_register_batch: NULL argument or n < 1");
+    reg_ctx *c0 = hs[0];
+    for (int i = 0; i < n; i++) {
+        reg_ctx *c = hs[i];
+        if (!c || !u_out[i])
+            return set_err(nullptr, REG_ERR_ARG, "reg_register_batch: NULL handle or output %d", i);
+        if (!c->have_images)
+            return set_err(nullptr, REG_ERR_STATE, "reg_register_batch: pair %d has no images", i);
+        if (c->levels != c0->levels || c->cfg.image_dtype != c0->cfg.image_dtype || c->device != c0->device ||
+            (c->cfg.start_level < 0 ? c->levels - 1 : c->cfg.start_level) !=
+                (c0->cfg.start_level < 0 ? c0->levels - 1 : c0->cfg.start_level))
+            return set_err(nullptr, REG_ERR_ARG,
+                           "reg_register_batch: pairs must share levels, start level, image type and device (pair %d)", i);
+        for (int l = 0; l < c->levels; l++)
+            if (!use_fused(c, l))
+                return set_err(nullptr, REG_ERR_ARG,
+                               "reg_register_batch: pair %d level %d is not a ratio-2 grid (even dims, default "
+                               "node counts, eval_impl 0)", i, l);
+        for (int j = 0; j < i; j++)
+            if (hs[j] == c)
+                return set_err(nullptr, REG_ERR_ARG, "reg_register_batch: handle %d repeats handle %d", i, j);
+    }
+    cudaStream_t s = c0->stream;
+    reg_ctx *c = c0;   // for CK
+    const int levels = c0->levels;
+    const int start = c0->cfg.start_level < 0 ? levels - 1 : c0->cfg.start_level;
+    const bool bf16 = c0->cfg.image_dtype == 1;
+    std::vector<reg_stats> st(n);
+    for (int i = 0; i < n; i++) {
+        memset(&st[i], 0, sizeof(reg_stats));
+        st[i].levels = levels;
+    }
+    BatchDev d;
+    CK(cudaMallocAsync((void **)&d.pl, sizeof(PairLevel) * n, s));
+    CK(cudaMallocAsync((void **)&d.off, sizeof(int) * 3 * (n + 1), s));
+    CK(cudaMallocAsync((void **)&d.counters, sizeof(int) * 2, s));
+    // every pair's own stream work (prolongations, state uploads) is ordered on c0's stream
+    for (int i = 0; i < n; i++)
+        CK(cudaMemsetAsync(hs[i]->lb.u, 0, sizeof(float) * 3 * hs[i]->L[start].nn, s));
+    long long launches = 0;
+    int status = REG_OK;
+    std::vector<PairLevel> hpl(n);
+    std::vector<int> hoff(3 * (n + 1));
+    for (int l = start; l >= 0 && status >= 0; l--) {
+        int tiles = 0, nodes = 0, chunks = 0;
+        for (int i = 0; i < n; i++) {
+            reg_ctx *ci = hs[i];
+            const Level &L = ci->L[l];
+            if (l < start) {
+                CK(launch_prolong(ci->L[l + 1], L, ci->lb.u, ci->lb.g, s));
+                CK(cudaMemcpyAsync(ci->lb.u, ci->lb.g, sizeof(float) * 3 * L.nn, cudaMemcpyDeviceToDevice, s));
+                launches++;
+            }
+            double Hmin = fmin(L.H[0], fmin(L.H[1], L.H[2]));
+            lbfgs_state_reset_host(ci->lb.st_host, ci->cfg, ci->cfg.max_iter[l], Hmin);
+            CK(cudaMemcpyAsync(ci->lb.st, ci->lb.st_host, sizeof(LbfgsState), cudaMemcpyHostToDevice, s));
+            fill_pair_level(ci, l, hpl[i]);
+            hoff[i] = tiles;
+            hoff[(n + 1) + i] = nodes;
+            hoff[2 * (n + 1) + i] = chunks;
+            tiles += hpl[i].nD;
+            nodes += hpl[i].nS;
+            chunks += hpl[i].nchunks;
+        }
+        hoff[n] = tiles;
+        hoff[(n + 1) + n] = nodes;
+        hoff[2 * (n + 1) + n] = chunks;
+        CK(cudaMemcpyAsync(d.pl, hpl.data(), sizeof(PairLevel) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d.off, hoff.data(), sizeof(int) * hoff.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(d.counters, 0, sizeof(int) * 2, s));
+        BatchLaunch B{&d, n, tiles, nodes, chunks, cap(tiles, c0->num_sms), cap(nodes, 8LL * c0->num_sms),
+                      cap(chunks, 8LL * c0->num_sms), bf16, c0->device};
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = build_batch_graph(B, c0->cap_stream, &exec);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(d.pl, s);
+            cudaFreeAsync(d.off, s);
+            cudaFreeAsync(d.counters, s);
+            return cuda_err(c0, e, "reg_register_batch: building the level graph");
+        }
+        e = cudaGraphLaunch(exec, s);
+        int cnt[2] = {0, 0};
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cnt, d.counters, sizeof cnt, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(exec);
+        CK(e);
+        // launches: init 7; per iteration body 8; per search round 6
+        const long long bodies = cnt[0] - 1, rounds = cnt[1] - bodies;
+        launches += 7 + 8 * bodies + 6 * rounds;
+        for (int i = 0; i < n; i++) {
+            reg_ctx *ci = hs[i];
+            CK(cudaMemcpyAsync(ci->lb.st_host, ci->lb.st, sizeof(LbfgsState), cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; i++) {
+            const LbfgsState *sh = hs[i]->lb.st_host;
+            st[i].iters[l] = sh->k;
+            st[i].evals[l] = sh->evals;
+            st[i].J[l] = sh->J;
+            st[i].level_status[l] = sh->status == 1 ? REG_WARN_LINESEARCH : REG_OK;
+            if (sh->status == -5 || sh->status == -6)
+                status = sh->status == -5 ? REG_ERR_NUMERIC : REG_ERR_TIMEOUT;
+            else if (sh->status == 1 && status == REG_OK)
+                status = REG_WARN_LINESEARCH;
+            if (l == 0) {
+                st[i].J_final = sh->J;
+                st[i].D_final = sh->D;
+                st[i].S_final = sh->S;
+            }
+        }
+    }
+    for (int i = 0; i < n; i++)
+        CK(cudaMemcpyAsync(u_out[i], hs[i]->lb.u, sizeof(float) * 3 * hs[i]->L[0].nn,
+                           out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaFreeAsync(d.pl, s));
+    CK(cudaFreeAsync(d.off, s));
+    CK(cudaFreeAsync(d.counters, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; i++) {
+        st[i].status = status;
+        st[i].kernel_launches = launches;
+        if (stats)
+            stats[i] = st[i];
+    }
+    if (status < 0)
+        return set_err(nullptr, status, "reg_register_batch: a pair ended with a numeric or loop-bound error");
+    return status;
+}

@@ -1,0 +1,79 @@
+// Batched registration: one descriptor per pair and pyramid level, read by
+// the batched kernels, which walk prefix-sum work lists over all pairs.
+#pragma once
+
+#include "internal.h"
+
+// Arguments of the fused objective pass over one pair (k_ngf_fused.cu).
+struct FusedArgs {
+    LevelGeom g;
+    const void *T, *R;      // images, elements of the kernel's IMG type (float or bf16)
+    const float *ub, *dir;
+    const double *t_dev;
+    float tau, rho;
+    int tz;                 // output planes per z segment (even)
+    int ntx, nty, ntz;      // tiles
+    float *part;            // [tile][TZ/2 + 1][NE]
+    double *partials;       // D block partials
+};
+
+struct PairLevel {
+    // objective evaluation
+    FusedArgs fa_init;      // at u (level start)
+    FusedArgs fa_trial;     // at u + t pdir, t read from the pair's state
+    LevelGeom geom;
+    float *w;               // curvature Laplacian scratch
+    double *pS;             // curvature block partials (after the fused-pass partials)
+    int nD, nS;             // block partials of D and of S
+    double hbar_half, alpha, hy_half;
+    float alpha_hy;
+    double *scal, *scal_t;  // [J, D, S] at u and at the trial point
+    // L-BFGS
+    LbfgsState *st;
+    long long n, stride;    // vector length, ring slot stride
+    float *u, *g, *gt, *pdir, *P, *Y;
+    double *lpart;          // vector-pass block partials
+    int nchunks;            // blocks of the vector passes
+    int tz, ntx, nty;       // fused tiling (also inside fa_*)
+    int ncx, ncy;           // curvature / gather blocks along x and y (32 x 8 nodes each)
+};
+
+// prefix sums of per-pair item counts: item i belongs to pair p with
+// off[p] <= i < off[p + 1]
+struct WorkLists {
+    int *tiles;             // fused-pass tiles
+    int *nodes;             // curvature / gather blocks
+    int *chunks;            // vector-pass blocks
+    int total_tiles, total_nodes, total_chunks;
+};
+
+__device__ __forceinline__ int find_pair(const int *__restrict__ off, int npairs, int item)
+{
+    int lo = 0, hi = npairs;   // off[lo] <= item < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= item)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// batched launchers (mode 0: objective at u, 1: at the trial point of pairs still searching)
+cudaError_t launch_fused_batch(const PairLevel *pl, const int *tile_off, int npairs, int total, int mode, bool bf16,
+                               int grid, int device, cudaStream_t s);
+cudaError_t launch_curv_w_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
+                                cudaStream_t s);
+cudaError_t launch_gather_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
+                                cudaStream_t s);
+cudaError_t launch_finalize_batch(const PairLevel *pl, int npairs, int mode, cudaStream_t s);
+// step 0: norms of g, 1: direction, 2: its p0 redo, 3: accept
+cudaError_t launch_lb_vector_batch(const PairLevel *pl, const int *chunk_off, int npairs, int total, int step,
+                                   int grid, cudaStream_t s);
+cudaError_t launch_lb_control_batch(const PairLevel *pl, int npairs, int phase, cudaStream_t s);
+// sets handle h to "any pair iterates" (which 0) or "any pair searches" (which 1);
+// counts its runs in counters[which]
+cudaError_t launch_batch_condition(const PairLevel *pl, int npairs, int which, unsigned long long h, int *counters,
+                                   cudaStream_t s);
+void fused_tiling(const Level &L, int num_sms, int *tz, int *ntx, int *nty, int *ntz);

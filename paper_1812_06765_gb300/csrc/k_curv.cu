@@ -6,19 +6,22 @@
 //   grad_c J += alpha hbar_y L^T w_c     (the symmetric stencil gathered over
 //                                         the zero-extended w)
 // Both passes are node-parallel, one thread per node and all 3 components.
+#include "batch.h"
 #include "internal.h"
 #include "ngf_math.cuh"
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_curv_w(LevelGeom g, const float *__restrict__ ub,
-                                                const float *__restrict__ dir, const double *__restrict__ t_dev,
-                                                float *__restrict__ w, double *__restrict__ partials)
+// block (bx, by, bz) of 32 x 8 nodes; its S partial goes to partials[lin]
+__device__ __forceinline__ void curv_w_body(const LevelGeom &g, const float *__restrict__ ub,
+                                            const float *__restrict__ dir, const double *__restrict__ t_dev,
+                                            float *__restrict__ w, double *__restrict__ partials, int bx, int by,
+                                            int bz, int lin)
 {
     __shared__ double sm[8];
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
-    int z = blockIdx.z;
+    int x = bx * blockDim.x + threadIdx.x;
+    int y = by * blockDim.y + threadIdx.y;
+    int z = bz;
     bool in = x < g.n[0] && y < g.n[1];
     float t = dir ? (float)__ldg(t_dev) : 0.f;
     float acc = 0.f;
@@ -44,7 +47,14 @@ __global__ void __launch_bounds__(256) k_curv_w(LevelGeom g, const float *__rest
     }
     double s = block_sum_to_f64(acc, sm);
     if (linear_tid() == 0)
-        partials[linear_bid()] = s;
+        partials[lin] = s;
+}
+
+__global__ void __launch_bounds__(256) k_curv_w(LevelGeom g, const float *__restrict__ ub,
+                                                const float *__restrict__ dir, const double *__restrict__ t_dev,
+                                                float *__restrict__ w, double *__restrict__ partials)
+{
+    curv_w_body(g, ub, dir, t_dev, w, partials, blockIdx.x, blockIdx.y, blockIdx.z, linear_bid());
 }
 
 __global__ void __launch_bounds__(256) k_curv_grad(LevelGeom g, const float *__restrict__ w, float alpha_hy,
@@ -75,9 +85,9 @@ __global__ void __launch_bounds__(256) k_curv_grad(LevelGeom g, const float *__r
 
 // Deterministic FP64 sum of block partials (fixed thread-to-partial
 // assignment, fixed tree): scal = [J, D, S].
-__global__ void __launch_bounds__(512) k_finalize(const double *__restrict__ pD, int nD,
-                                                  const double *__restrict__ pS, int nS, double hbar_half,
-                                                  double alpha, double hy_half, double *__restrict__ scal)
+__device__ __forceinline__ void finalize_body(const double *__restrict__ pD, int nD, const double *__restrict__ pS,
+                                              int nS, double hbar_half, double alpha, double hy_half,
+                                              double *__restrict__ scal)
 {
     __shared__ double sd[512], ss[512];
     int t = threadIdx.x;
@@ -104,7 +114,58 @@ __global__ void __launch_bounds__(512) k_finalize(const double *__restrict__ pD,
     }
 }
 
+__global__ void __launch_bounds__(512) k_finalize(const double *__restrict__ pD, int nD,
+                                                  const double *__restrict__ pS, int nS, double hbar_half,
+                                                  double alpha, double hy_half, double *__restrict__ scal)
+{
+    finalize_body(pD, nD, pS, nS, hbar_half, alpha, hy_half, scal);
+}
+
+// Batched forms over all pairs of a level.  Mode 0: at u; mode 1: at the trial
+// point, only for pairs still searching.
+__device__ __forceinline__ bool batch_skip(const PairLevel &P, int mode)
+{
+    return mode == 1 && !(P.st->active && P.st->ls_continue);
+}
+
+__global__ void __launch_bounds__(256) k_curv_w_batch(const PairLevel *__restrict__ pl, const int *__restrict__ off,
+                                                      int npairs, int total, int mode)
+{
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int p = find_pair(off, npairs, item);
+        const PairLevel &P = pl[p];
+        if (batch_skip(P, mode))
+            continue;
+        const int lin = item - __ldg(off + p);
+        const int bx = lin % P.ncx, r = lin / P.ncx;
+        curv_w_body(P.geom, P.u, mode ? P.pdir : nullptr, mode ? &P.st->t : nullptr, P.w, P.pS, bx, r % P.ncy,
+                    r / P.ncy, lin);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(512) k_finalize_batch(const PairLevel *__restrict__ pl, int mode)
+{
+    const PairLevel &P = pl[blockIdx.x];
+    if (batch_skip(P, mode))
+        return;
+    finalize_body(P.fa_init.partials, P.nD, P.pS, P.nS, P.hbar_half, P.alpha, P.hy_half, mode ? P.scal_t : P.scal);
+}
+
 }  // namespace
+
+cudaError_t launch_curv_w_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
+                                cudaStream_t s)
+{
+    k_curv_w_batch<<<grid, dim3(32, 8, 1), 0, s>>>(pl, off, npairs, total, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const PairLevel *pl, int npairs, int mode, cudaStream_t s)
+{
+    k_finalize_batch<<<npairs, 512, 0, s>>>(pl, mode);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev, float *grad,
                         double *scal_out, cudaStream_t s)

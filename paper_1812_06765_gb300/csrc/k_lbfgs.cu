@@ -14,6 +14,7 @@
 // pdir (current direction), P and Y rings of m + 1 slots each (s_j = t_j P_j).
 #include <math.h>
 
+#include "batch.h"
 #include "internal.h"
 
 namespace {
@@ -54,30 +55,36 @@ __device__ __forceinline__ float max4(float4 a)
     return fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
 }
 
-__global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *__restrict__ g,
-                                                     double *__restrict__ partials)
+__device__ __forceinline__ void lb_init_dots_body(long long n, const float *__restrict__ g,
+                                                     double *__restrict__ partials, int bx, int gdx)
 {
     float v[2] = {0.f, 0.f};
     const long long n4 = n >> 2;
     const float4 *g4 = reinterpret_cast<const float4 *>(g);
-    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n4; e += (long long)gridDim.x * VT) {
+    for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
         float4 x = g4[e];
         v[0] += dot4(x, x);
         v[1] = fmaxf(v[1], max4(x));
     }
-    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+    if (bx == 0 && threadIdx.x < (n & 3)) {
         float x = g[4 * n4 + threadIdx.x];
         v[0] = fmaf(x, x, v[0]);
         v[1] = fmaxf(v[1], fabsf(x));
     }
-    block_reduce_write<2>(v, 1, partials + 2 * blockIdx.x);
+    block_reduce_write<2>(v, 1, partials + 2 * bx);
+}
+
+__global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *__restrict__ g,
+                                                     double *__restrict__ partials)
+{
+    lb_init_dots_body(n, g, partials, blockIdx.x, gridDim.x);
 }
 
 // p = cg g + sum_j cp_j P_j + cy_j Y_j, written to pdir; partial sums of g'p and p'p.
-__global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stride, const LbfgsState *__restrict__ st,
+__device__ __forceinline__ void lb_direction_body(long long n, long long stride, const LbfgsState *__restrict__ st,
                                                      const float *__restrict__ g, const float *__restrict__ P,
                                                      const float *__restrict__ Y, float *__restrict__ pdir,
-                                                     double *__restrict__ partials, int redo)
+                                                     double *__restrict__ partials, int redo, int bx, int gdx)
 {
     __shared__ int s_run, s_dc, s_slot[LB_MAXM];
     __shared__ float s_cg, s_cp[LB_MAXM], s_cy[LB_MAXM];
@@ -110,7 +117,7 @@ __global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stri
     const long long n4 = n >> 2;
     const float4 *g4 = reinterpret_cast<const float4 *>(g);
     float4 *p4 = reinterpret_cast<float4 *>(pdir);
-    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n4; e += (long long)gridDim.x * VT) {
+    for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
         float4 gv = g4[e];
         float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
 #pragma unroll
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stri
         v[0] += dot4(gv, p);
         v[1] += dot4(p, p);
     }
-    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+    if (bx == 0 && threadIdx.x < (n & 3)) {
         const long long e = 4 * n4 + threadIdx.x;
         float gv = g[e], p = cg * gv;
 #pragma unroll
@@ -137,7 +144,15 @@ __global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stri
         v[0] = fmaf(gv, p, v[0]);
         v[1] = fmaf(p, p, v[1]);
     }
-    block_reduce_write<2>(v, -1, partials + 2 * blockIdx.x);
+    block_reduce_write<2>(v, -1, partials + 2 * bx);
+}
+
+__global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stride, const LbfgsState *__restrict__ st,
+                                                     const float *__restrict__ g, const float *__restrict__ P,
+                                                     const float *__restrict__ Y, float *__restrict__ pdir,
+                                                     double *__restrict__ partials, int redo)
+{
+    lb_direction_body(n, stride, st, g, P, Y, pdir, partials, redo, blockIdx.x, gridDim.x);
 }
 
 // Accept the trial point: u += t pdir (the fmaf the evaluation used), store the
@@ -151,16 +166,16 @@ __device__ __forceinline__ void accept_elem(float gn, float go, float pf, float 
     u = fmaf(t, pf, u);
 }
 
-__global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride, const LbfgsState *__restrict__ st,
+__device__ __forceinline__ void lb_accept_body(long long n, long long stride, const LbfgsState *__restrict__ st,
                                                   float *__restrict__ u, float *__restrict__ g,
                                                   const float *__restrict__ gt, const float *__restrict__ pdir,
                                                   float *__restrict__ P, float *__restrict__ Y,
-                                                  double *__restrict__ partials)
+                                                  double *__restrict__ partials, int bx, int gdx)
 {
     __shared__ int s_ok, s_lc, s_free, s_slot[LB_MAXS];
     __shared__ float s_t;
     if (threadIdx.x == 0) {
-        s_ok = st->ls == LS_ACCEPTED;
+        s_ok = st->active && st->ls == LS_ACCEPTED;
         s_lc = st->lcount;
         s_free = st->free_slot;
         s_t = (float)st->t;
@@ -187,7 +202,7 @@ __global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride,
         v[d] = 0.f;
     float fr[4] = {0.f, 0.f, 0.f, 0.f};   // dots of the free slot (p, y_new) with g_new, y_new
     const long long n4 = n >> 2;
-    for (long long e = blockIdx.x * (long long)VT + threadIdx.x; e < n4; e += (long long)gridDim.x * VT) {
+    for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
         float4 gn = reinterpret_cast<const float4 *>(gt)[e];
         float4 go = reinterpret_cast<float4 *>(g)[e];
         float4 pf = reinterpret_cast<const float4 *>(pdir)[e];
@@ -217,7 +232,7 @@ __global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride,
         fr[2] += dot4(pf, yn);
         fr[3] += dot4(yn, yn);
     }
-    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+    if (bx == 0 && threadIdx.x < (n & 3)) {
         const long long e = 4 * n4 + threadIdx.x;
         float gn = gt[e], go = g[e], pf = pdir[e], uu = u[e], yn;
         accept_elem(gn, go, pf, uu, t, yn);
@@ -250,7 +265,16 @@ __global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride,
             v[4 + 4 * j] += fr[2];
             v[5 + 4 * j] += fr[3];
         }
-    block_reduce_write<ND_ACC>(v, 1, partials + (size_t)ND_ACC * blockIdx.x);
+    block_reduce_write<ND_ACC>(v, 1, partials + (size_t)ND_ACC * bx);
+}
+
+__global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride, const LbfgsState *__restrict__ st,
+                                                  float *__restrict__ u, float *__restrict__ g,
+                                                  const float *__restrict__ gt, const float *__restrict__ pdir,
+                                                  float *__restrict__ P, float *__restrict__ Y,
+                                                  double *__restrict__ partials)
+{
+    lb_accept_body(n, stride, st, u, g, gt, pdir, P, Y, partials, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -308,7 +332,7 @@ __device__ void set_compact(LbfgsState *st)
 
 __device__ bool finite_d(double x) { return isfinite(x); }
 
-__global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__restrict__ gst,
+__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restrict__ gst,
                                                     const double *__restrict__ partials, int nblocks,
                                                     const double *__restrict__ scal, unsigned long long h_ls,
                                                     unsigned long long h_iter)
@@ -325,7 +349,7 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
     LbfgsState *st = &S;
     const int nd = phase == LB_ACCEPTED ? ND_ACC : 2;
     const int imax = (phase == LB_INIT || phase == LB_ACCEPTED) ? 1 : -1;
-    const bool need = phase != LB_ARMIJO && !(phase == LB_ACCEPTED && st->ls != LS_ACCEPTED) &&
+    const bool need = phase != LB_ARMIJO && !(phase == LB_ACCEPTED && (!st->active || st->ls != LS_ACCEPTED)) &&
                       !(phase == LB_DIR_REDO && !st->redo_dir) && !(phase == LB_DIR && !st->iter_continue);
     if (need) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -372,9 +396,12 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
             st->done = 1;
         set_p0(st);
         st->iter_continue = !st->done;
+        st->active = 0;
+        st->ls_continue = 0;
         break;
     }
     case LB_DIR: {
+        st->active = st->iter_continue;
         if (!st->iter_continue)
             break;
         st->gtp = red[0];
@@ -400,6 +427,8 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
         break;
     }
     case LB_ARMIJO: {
+        if (!st->active || !st->ls_continue)   // this pair is not searching (batched levels)
+            break;
         st->Jt = scal[0];
         st->Dt = scal[1];
         st->St = scal[2];
@@ -432,6 +461,8 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
         break;
     }
     case LB_ACCEPTED: {
+        if (!st->active)   // this pair did not run the iteration (batched levels)
+            break;
         if (++st->bodies > 2 * st->max_iter + 8) {   // cannot happen with the rules below; a hard stop
             st->status = -6;
             st->done = 1;
@@ -527,6 +558,64 @@ __global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__res
     __syncthreads();
     for (int i = threadIdx.x; i < NW; i += blockDim.x)
         reinterpret_cast<int *>(gst)[i] = reinterpret_cast<const int *>(&S)[i];
+}
+
+__global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__restrict__ gst,
+                                                    const double *__restrict__ partials, int nblocks,
+                                                    const double *__restrict__ scal, unsigned long long h_ls,
+                                                    unsigned long long h_iter)
+{
+    lb_control_body(phase, gst, partials, nblocks, scal, h_ls, h_iter);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: one launch covers the vectors (or the states) of all pairs.
+// A vector item is (pair, block) and runs the per-pair body with that pair's
+// block count, so every pair gets exactly the partial sums it gets alone.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(VT) k_lb_vector_batch(const PairLevel *__restrict__ pl,
+                                                        const int *__restrict__ chunk_off, int npairs, int total,
+                                                        int step)
+{
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int p = find_pair(chunk_off, npairs, item);
+        const PairLevel &P = pl[p];
+        const int b = item - __ldg(chunk_off + p);
+        if (step == 0)
+            lb_init_dots_body(P.n, P.g, P.lpart, b, P.nchunks);
+        else if (step == 1 || step == 2)
+            lb_direction_body(P.n, P.stride, P.st, P.g, P.P, P.Y, P.pdir, P.lpart, step == 2, b, P.nchunks);
+        else
+            lb_accept_body(P.n, P.stride, P.st, P.u, P.g, P.gt, P.pdir, P.P, P.Y, P.lpart, b, P.nchunks);
+        __syncthreads();   // the next item reuses the block's shared staging
+    }
+}
+
+// one block per pair; phase as in k_lb_control, scalars of the objective at u
+// (INIT) or at the trial point (ARMIJO)
+__global__ void __launch_bounds__(256) k_lb_control_batch(const PairLevel *__restrict__ pl, int phase)
+{
+    const PairLevel &P = pl[blockIdx.x];
+    lb_control_body(phase, P.st, P.lpart, P.nchunks, phase == LB_INIT ? P.scal : P.scal_t, 0ULL, 0ULL);
+}
+
+// condition of a batched loop: 1 while any pair still iterates (which = 0) or
+// still searches (which = 1)
+__global__ void k_batch_condition(const PairLevel *__restrict__ pl, int npairs, int which, unsigned long long h,
+                                  int *__restrict__ counters)
+{
+    if (threadIdx.x == 0 && counters)
+        counters[which]++;
+    int any = 0;
+    for (int p = threadIdx.x; p < npairs; p += 32) {
+        const LbfgsState *st = pl[p].st;
+        any |= which == 0 ? st->iter_continue : (st->active && st->ls_continue);
+    }
+    any = __any_sync(0xffffffffu, any);
+#if CUDART_VERSION >= 12040
+    if (threadIdx.x == 0 && h)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)h, any ? 1u : 0u);
+#endif
 }
 
 // Standalone direction for a given set of pairs (reg_lbfgs_direction): the
@@ -731,5 +820,26 @@ cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const
     // pairs live in the caller's S, Y: slots 0..count-1 at stride n (any alignment)
     k_lb_direction_plain<<<nb, VT, 0, s>>>(n, c->lb.st, g, S, Y, p);
     c->launches += 3;
+    return cudaGetLastError();
+}
+
+// batched launchers (batch.cu): step 0 norms of g, 1 direction, 2 its p0 redo, 3 accept
+cudaError_t launch_lb_vector_batch(const PairLevel *pl, const int *chunk_off, int npairs, int total, int step,
+                                   int grid, cudaStream_t s)
+{
+    k_lb_vector_batch<<<grid, VT, 0, s>>>(pl, chunk_off, npairs, total, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lb_control_batch(const PairLevel *pl, int npairs, int phase, cudaStream_t s)
+{
+    k_lb_control_batch<<<npairs, 256, 0, s>>>(pl, phase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_condition(const PairLevel *pl, int npairs, int which, unsigned long long h, int *counters,
+                                   cudaStream_t s)
+{
+    k_batch_condition<<<1, 32, 0, s>>>(pl, npairs, which, h, counters);
     return cudaGetLastError();
 }

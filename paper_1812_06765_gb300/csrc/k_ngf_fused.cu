@@ -25,6 +25,7 @@
 //   D  zA-5      : y reduction of last step's rows, accumulation along z
 // Every phase reads only what earlier steps wrote, so one barrier per step
 // suffices, and the global loads of a plane overlap a whole step of compute.
+#include "batch.h"
 #include "internal.h"
 #include "ngf_math.cuh"
 
@@ -48,17 +49,6 @@ constexpr int OFF_N = OFF_RED + 2 * BY * NX * 3;  // node planes [4][2][TNP] (u,
 constexpr int SMEM_FLOATS = OFF_N + 4 * 2 * TNP;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 
-struct FusedArgs {
-    LevelGeom g;
-    const void *T, *R;      // images, elements of the kernel's IMG type (float or bf16)
-    const float *ub, *dir;
-    const double *t_dev;
-    float tau, rho;
-    int tz;                 // output planes per z segment (even)
-    int ntx, nty, ntz;      // tiles
-    float *part;            // [tile][TZ/2 + 1][NE]
-    double *partials;       // D block partials
-};
 
 __device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc, bool valid)
 {
@@ -146,13 +136,14 @@ __device__ __forceinline__ float ldimg_zero_ext(const IMG *T, int mx, int my, in
     return in ? ldimg(T + (x + mx * (y + my * z))) : 0.f;
 }
 
-template <bool HAS_DIR, typename IMG = float>
-__global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
+// One output tile (tile_x, tile_y, tile_z) of the fused pass; sm is the CTA's
+// dynamic shared memory (SMEM_BYTES).
+template <bool HAS_DIR, typename IMG>
+__device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int tile_y, int tile_z, float *sm)
 {
-    extern __shared__ float sm[];
     const LevelGeom &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
-    const int x0 = blockIdx.x * OX, y0 = blockIdx.y * OY, z0 = blockIdx.z * a.tz;
+    const int x0 = tile_x * OX, y0 = tile_y * OY, z0 = tile_z * a.tz;
     const int x = x0 - 2 + tx, y = y0 - 2 + ty;
     const int mx = g.m[0], my = g.m[1], mz = g.m[2];
     const int sxy = mx * my;
@@ -165,7 +156,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
     const float hx = 0.5f * g.ih[0], hy = 0.5f * g.ih[1], hz = 0.5f * g.ih[2];
     const float half_hbar = 0.5f * g.hbar;
     const int zlast = z0 + a.tz + 1;                  // last T~ plane needed
-    const size_t tile_lin = (size_t)blockIdx.x + (size_t)a.ntx * (blockIdx.y + (size_t)a.nty * blockIdx.z);
+    const size_t tile_lin = (size_t)tile_x + (size_t)a.ntx * (tile_y + (size_t)a.nty * tile_z);
     float *part_tile = a.part + tile_lin * (size_t)(a.tz / 2 + 1) * NE;
     const NodeCopy nc = node_copy_setup<HAS_DIR>(a, kx0, ky0, tid);
     const int node_plane = g.n[0] * g.n[1];
@@ -391,18 +382,46 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
     }
     double ssum = block_sum_to_f64(psi_sum.s, reinterpret_cast<double *>(sm + OFF_RED));
     if (tid == 0)
-        a.partials[(size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = ssum;
+        a.partials[tile_lin] = ssum;
+}
+
+template <bool HAS_DIR, typename IMG = float>
+__global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
+{
+    extern __shared__ float sm[];
+    fused_tile<HAS_DIR, IMG>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+}
+
+// Batched fused pass: a persistent grid walks the tiles of all pairs.  Mode 0
+// evaluates at u; mode 1 at the trial point, for the pairs still searching.
+template <bool HAS_DIR, typename IMG>
+__global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused_batch(const PairLevel *__restrict__ pl,
+                                                                const int *__restrict__ tile_off, int npairs,
+                                                                int total)
+{
+    extern __shared__ float sm[];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int p = find_pair(tile_off, npairs, item);
+        const PairLevel &P = pl[p];
+        if (HAS_DIR && !(P.st->active && P.st->ls_continue))
+            continue;   // uniform over the CTA
+        const FusedArgs &a = HAS_DIR ? P.fa_trial : P.fa_init;
+        const int local = item - __ldg(tile_off + p);
+        const int tx = local % a.ntx, rest = local / a.ntx;
+        fused_tile<HAS_DIR, IMG>(a, tx, rest % a.nty, rest / a.nty, sm);
+        __syncthreads();   // the next tile reuses the shared rings
+    }
 }
 
 // grad J at node k = sum of the tile partials that contain k (P^T r) plus
 // alpha hbar_y L^T w (curvature), one thread per node, 3 components.
-__global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *__restrict__ part, int tz, int ntx,
-                                                     int nty, int ntz, const float *__restrict__ w, float alpha_hy,
-                                                     float *__restrict__ grad)
+__device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float *__restrict__ part, int tz, int ntx,
+                                                 int nty, int ntz, const float *__restrict__ w, float alpha_hy,
+                                                 float *__restrict__ grad, int bx, int by, int bz)
 {
-    int kx = blockIdx.x * blockDim.x + threadIdx.x;
-    int ky = blockIdx.y * blockDim.y + threadIdx.y;
-    int kz = blockIdx.z;
+    int kx = bx * blockDim.x + threadIdx.x;
+    int ky = by * blockDim.y + threadIdx.y;
+    int kz = bz;
     if (kx >= g.n[0] || ky >= g.n[1])
         return;
     const int hz = tz / 2;
@@ -448,6 +467,13 @@ __global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *_
         }
         grad[c * g.nn + k] = fmaf(alpha_hy, l, s[c]);
     }
+}
+
+__global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *__restrict__ part, int tz, int ntx,
+                                                     int nty, int ntz, const float *__restrict__ w, float alpha_hy,
+                                                     float *__restrict__ grad)
+{
+    gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace
@@ -613,4 +639,75 @@ cudaError_t launch_gather_grad_raw(const LevelGeom &g, const float *part, int nu
     dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]);
     k_gather_grad<<<gn, blk, 0, s>>>(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched fused pass and gather over all pairs of a level (batch.cu)
+// ---------------------------------------------------------------------------
+static bool g_batch_attr_set[64] = {};
+
+cudaError_t launch_fused_batch(const PairLevel *pl, const int *tile_off, int npairs, int total, int mode, bool bf16,
+                               int grid, int device, cudaStream_t s)
+{
+    const int dev = device >= 0 && device < 64 ? device : 0;
+    if (!g_batch_attr_set[dev]) {
+        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(k_ngf_fused_batch<true, float>, at, (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ngf_fused_batch<false, float>, at, (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ngf_fused_batch<true, __nv_bfloat16>, at, (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ngf_fused_batch<false, __nv_bfloat16>, at, (int)SMEM_BYTES);
+        if (e != cudaSuccess)
+            return e;
+        g_batch_attr_set[dev] = true;
+    }
+    dim3 blk(BX, BY, 1);
+    if (bf16) {
+        if (mode)
+            k_ngf_fused_batch<true, __nv_bfloat16><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+        else
+            k_ngf_fused_batch<false, __nv_bfloat16><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+    } else {
+        if (mode)
+            k_ngf_fused_batch<true, float><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+        else
+            k_ngf_fused_batch<false, float><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_gather_batch(const PairLevel *__restrict__ pl, const int *__restrict__ off,
+                                                      int npairs, int total, int mode)
+{
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int p = find_pair(off, npairs, item);
+        const PairLevel &P = pl[p];
+        if (mode == 1 && !(P.st->active && P.st->ls_continue))
+            continue;
+        const int lin = item - __ldg(off + p);
+        const int bx = lin % P.ncx, r = lin / P.ncx;
+        const FusedArgs &a = P.fa_init;
+        gather_grad_body(P.geom, a.part, a.tz, a.ntx, a.nty, a.ntz, P.w, P.alpha_hy, mode ? P.gt : P.g, bx,
+                         r % P.ncy, r / P.ncy);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
+                                cudaStream_t s)
+{
+    k_gather_batch<<<grid, dim3(32, 8, 1), 0, s>>>(pl, off, npairs, total, mode);
+    return cudaGetLastError();
+}
+
+// tiling of a level of the fused pass, for the batch descriptors
+void fused_tiling(const Level &L, int num_sms, int *tz, int *ntx, int *nty, int *ntz)
+{
+    *tz = fused_tz(L, num_sms);
+    fused_grid(L, *tz, *ntx, *nty, *ntz);
 }

@@ -29,6 +29,8 @@ struct LbfgsState {
     int ls;            // LbSearch
     int ls_continue;   // 1 while the line search needs another trial
     int iter_continue; // 1 while the level needs another iteration
+    int active;        // this pair runs the current iteration body (set by the direction
+                       // control; in a batch, finished pairs skip every later phase)
     int done;
     int status;        // 0, 1 (line search warning) or -5 (numeric)
     // pair memory: order[0..count-1] are slots oldest..newest, free_slot holds p
