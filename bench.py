@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--host-loop", action="store_true",
                     help="queue every L-BFGS step from the host instead of one graph per level (the same kernels "
                          "in the same order; ncu cannot list kernels inside graphs with conditional nodes)")
+    ap.add_argument("--pairs", type=int, default=None, help="pairs of the uneven batch (workload 4; default 64)")
+    ap.add_argument("--gen-procs", type=int, default=None, help="processes that generate the batch's pairs")
     return ap.parse_args(argv)
 
 
@@ -179,9 +181,10 @@ def committed_traffic(kernel, digest):
 
 
 def workload(config_id, rank):
-    from synth import CONFIGS, make_pair
+    from synth import CONFIGS, make_pair, batch_sizes
     c = CONFIGS[config_id]
-    p = make_pair(config_id, pair=rank)
+    dims = batch_sizes(rank + 1)[rank] if c["dims"] is None else None
+    p = make_pair(config_id, pair=rank, dims=dims)
     return c, p
 
 
@@ -377,6 +380,194 @@ def run_ours(args):
 
 
 # ----------------------------------------------------------------------------
+# the uneven batch: batched, graph-captured form against the per-pair loop
+# ----------------------------------------------------------------------------
+def _batch_pair(job):
+    """One pair of the uneven batch (runs in a generator process)."""
+    i, dims = job
+    from synth import make_pair
+    p = make_pair(4, pair=i, dims=dims)
+    return p["R"], p["T"], tuple(p["dims"]), tuple(p["spacing"])
+
+
+def batch_inputs(n_pairs, first_pair, procs):
+    """The pairs of the batch, generated in a spawn pool (before any CUDA call)."""
+    import multiprocessing as mp
+    from synth import batch_sizes
+    jobs = [(first_pair + i, d) for i, d in enumerate(batch_sizes(n_pairs))]
+    procs = procs or min(len(jobs), os.cpu_count() or 1, 16)
+    if procs <= 1:
+        return [_batch_pair(j) for j in jobs]
+    order = sorted(range(len(jobs)), key=lambda k: -int(np.prod(jobs[k][1])))   # largest first
+    with mp.get_context("spawn").Pool(procs) as pool:
+        made = pool.map(_batch_pair, [jobs[k] for k in order], chunksize=1)
+    out = [None] * len(jobs)
+    for k, v in zip(order, made):
+        out[k] = v
+    return out
+
+
+def percentile_ms(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+def run_batch(args):
+    """Workload 4: 64 pairs of uneven size, registered (a) together, one graph
+    launch per pyramid level for the whole batch, and (b) one after another
+    through reg_register.  Both start from device-resident images and include
+    the pyramid; pairs/s and per-pair completion times (from the step start to
+    the moment the pair's result is in memory) are reported for both."""
+    from synth import CONFIGS
+    rank, world = dist_init("nccl")
+    _, _, local = dist_env()
+    c = CONFIGS[4]
+    n = args.pairs or c["pairs"]
+    pairs = batch_inputs(n, rank * n, args.gen_procs)
+    import torch
+    import paper_1812_06765_gb300 as reg_pkg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    levels = c["levels"]
+    kw = dict(levels=levels, tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"], c1=c["c1"])
+    regs = [reg_pkg.Registration(reg_pkg.make_config(**kw), stream=stream) for _ in range(n)]
+    Rd = [torch.from_numpy(p[0]).to(dev) for p in pairs]
+    Td = [torch.from_numpy(p[1]).to(dev) for p in pairs]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    restrict_launches = 2 * (levels - 1)
+
+    def load_all():
+        for i in range(n):
+            regs[i].set_images(Rd[i], Td[i], pairs[i][3])
+
+    def step_batch():
+        load_all()
+        return reg_pkg.register_batch(regs, out="torch")
+
+    def step_loop(marks=None):
+        res = []
+        for i in range(n):
+            regs[i].set_images(Rd[i], Td[i], pairs[i][3])
+            res.append(regs[i].register(out="torch"))
+            if marks is not None:
+                marks[i].record(stream)
+        return res
+
+    for _ in range(args.warmup):
+        step_batch()
+        step_loop()
+    torch.cuda.synchronize(dev)
+
+    dist_barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local).start()
+    t_batch, done_batch, launches_batch = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res_b = step_batch()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        t_batch.append(ms)
+        done_batch += [ms] * n                      # every result lands when the batch returns
+        launches_batch += res_b[0][1]["kernel_launches"] + restrict_launches * n
+    t_loop, done_loop, own_loop, launches_loop = [], [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        e0.record(stream)
+        res_l = step_loop(marks)
+        marks[-1].synchronize()
+        t = [e0.elapsed_time(m) for m in marks]
+        t_loop.append(t[-1])
+        done_loop += t
+        own_loop += [t[0]] + [b - a for a, b in zip(t[:-1], t[1:])]
+        launches_loop += sum(s["kernel_launches"] for _, s in res_l) + restrict_launches * n
+    torch.cuda.synchronize(dev)
+    dist_barrier()
+    clk = clocks.stop()
+    tb = dist_reduce(sum(t_batch), "max", dev)
+    tl = dist_reduce(sum(t_loop), "max", dev)
+    pairs_all = world * n * args.steps
+    pairs_s_batch = pairs_all / (tb / 1000.0)
+    pairs_s_loop = pairs_all / (tl / 1000.0)
+
+    # equal accuracy: the batch gives each pair the result of its own registration
+    max_diff = max(float((ub - ul).abs().max()) for (ub, _), (ul, _) in zip(res_b, res_l))
+    same_counts = all(sb["iters"] == sl["iters"] and sb["evals"] == sl["evals"]
+                      for (_, sb), (_, sl) in zip(res_b, res_l))
+    d_ratio = []
+    for i in range(n):
+        z = torch.zeros(regs[i].node_shape(0), dtype=torch.float32, device=dev)
+        J0, D0, _, _ = regs[i].eval(z, 0)
+        d_ratio.append(res_b[i][1]["D_final"] / D0)
+
+    # algorithmic evaluation bytes (images, u and grad J at every evaluation) over the batch's step time
+    eval_bytes = 0
+    for i in range(n):
+        for lv in range(levels):
+            info = regs[i].level_info(lv)
+            eval_bytes += res_b[i][1]["evals"][lv] * (8 * int(np.prod(info["dims"])) + 24 * int(np.prod(info["nodes"])))
+    eff_gbs = eval_bytes / (statistics.mean(t_batch) * 1e-3) / 1e9
+
+    # end to end from pinned host images, results back into pinned host memory
+    Rh = [torch.from_numpy(p[0]).pin_memory() for p in pairs]
+    Th = [torch.from_numpy(p[1]).pin_memory() for p in pairs]
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(n):
+            regs[i].set_images(Rh[i], Th[i], pairs[i][3])
+        reg_pkg.register_batch(regs, out="pinned")
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = dist_reduce(statistics.mean(e2e), "max", dev)
+    h2d = sum(8 * int(np.prod(p[2])) for p in pairs)
+    d2h = sum(12 * int(np.prod(r.level_info(0)["nodes"])) for r in regs)
+
+    if rank == 0:
+        vox = [int(np.prod(p[2])) for p in pairs]
+        line = {
+            "metric": "registration pairs/s of a batch of 64 uneven CT-like pairs (batched, graph-captured) "
+                      "against the per-pair loop; p50/p99 per-pair completion time",
+            "value": pairs_s_batch, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tb / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": c["name"], "pairs": n, "sizes": sorted({p[2] for p in pairs}),
+                       "voxels_total": sum(vox), "spacing_mm": list(c["spacing"]), "levels": levels,
+                       "eta": c["eta"], "alpha": c["alpha"], "lbfgs_mem": c["mem"],
+                       "max_iter_per_level": c["max_iter"],
+                       "l2": "flushed between steps (2x L2 buffer written, untimed); inputs exceed L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "batched": {"pairs_s": pairs_s_batch, "p50_ms": percentile_ms(done_batch, 50),
+                        "p99_ms": percentile_ms(done_batch, 99), "step_ms": statistics.mean(t_batch),
+                        "gpu_launches_per_step": launches_batch // max(1, args.steps)},
+            "per_pair_loop": {"pairs_s": pairs_s_loop, "p50_ms": percentile_ms(done_loop, 50),
+                              "p99_ms": percentile_ms(done_loop, 99), "step_ms": statistics.mean(t_loop),
+                              "own_time_p50_ms": percentile_ms(own_loop, 50),
+                              "own_time_p99_ms": percentile_ms(own_loop, 99),
+                              "gpu_launches_per_step": launches_loop // max(1, args.steps)},
+            "batched_over_loop": pairs_s_batch / pairs_s_loop,
+            "equal_accuracy": {"max_abs_u_diff_mm": max_diff, "same_iterations_and_evaluations": same_counts,
+                               "D_final_over_D0_median": float(np.median(d_ratio)),
+                               "D_final_over_D0_max": float(np.max(d_ratio))},
+            "effective_eval_gbs": eff_gbs,
+            "roofline": None,
+            "e2e": {"value": world * n / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "batch_s": e2e_s},
+            "gpu_launches": launches_batch + launches_loop,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    for r in regs:
+        r.close()
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ----------------------------------------------------------------------------
 def run_reference(args):
@@ -420,6 +611,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 4:
+        run_batch(args)
     else:
         run_ours(args)
 

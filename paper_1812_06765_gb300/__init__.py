@@ -17,7 +17,7 @@ import torch
 from . import _lib
 from ._lib import RegConfig, RegError, RegStats  # noqa: F401
 
-__all__ = ["make_config", "Registration", "RegObjective", "register", "RegError"]
+__all__ = ["make_config", "Registration", "RegObjective", "register", "register_batch", "RegError"]
 
 
 def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1=1e-4, max_backtracks=20,
@@ -212,13 +212,20 @@ def _stats_dict(rc, st):
 
 def register_batch(regs, out="torch"):
     """Register the pairs of several Registration handles together (one graph
-    launch per pyramid level for all of them); returns a list of (u, stats)."""
+    launch per pyramid level for all of them); returns a list of (u, stats).
+    out: "torch" (CUDA tensors), "pinned" (page-locked host tensors) or "numpy"."""
+    if out not in ("torch", "pinned", "numpy"):
+        raise ValueError("out must be 'torch', 'pinned' or 'numpy'")
     outs = []
     for r in regs:
         shape = r.node_shape(0)
-        outs.append(torch.empty(shape, dtype=torch.float32, device="cuda") if out == "torch"
-                    else np.empty(shape, dtype=np.float32))
-    ptrs = [o.data_ptr() if out == "torch" else o.ctypes.data for o in outs]
+        if out == "torch":
+            outs.append(torch.empty(shape, dtype=torch.float32, device="cuda"))
+        elif out == "pinned":
+            outs.append(torch.empty(shape, dtype=torch.float32, pin_memory=True))
+        else:
+            outs.append(np.empty(shape, dtype=np.float32))
+    ptrs = [o.ctypes.data if out == "numpy" else o.data_ptr() for o in outs]
     rc, stats = _lib.reg_register_batch([r.h for r in regs], ptrs, out == "torch")
     return [(o, _stats_dict(rc, s)) for o, s in zip(outs, stats)]
 

@@ -56,3 +56,19 @@ def test_single_process_reductions_are_identity():
     import bench
     assert bench.dist_reduce(4.5, "max") == 4.5
     assert bench.dist_reduce(4.5, "sum") == 4.5
+
+
+def test_batch_inputs_pool_matches_serial():
+    """The uneven batch generated in a spawn pool equals the serial generation,
+    and ranks draw disjoint pair seeds (rank r starts at pair r * n)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    serial = bench.batch_inputs(3, 0, 1)
+    pooled = bench.batch_inputs(3, 0, 2)
+    for a, b in zip(serial, pooled):
+        assert a[2] == b[2] and a[3] == b[3]
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+    other = bench.batch_inputs(1, 3, 1)[0]
+    assert other[2] == serial[0][2] and not np.array_equal(other[0], serial[0][0])
