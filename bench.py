@@ -294,7 +294,7 @@ def run_ours(args):
     dist_barrier()
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local).start()
-    times, eq_evals, launches, evals_per_level, iters_per_level = [], 0.0, 0, None, None
+    times, eq_evals, launches, evals_per_level, iters_per_level, level_s = [], 0.0, 0, None, None, None
     for _ in range(args.steps):
         flush.zero_()                       # evict the previous step from L2 (not timed)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -306,7 +306,7 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1))
         eq_evals += full_res_equivalent(st, reg, levels)
         launches += st["kernel_launches"] + 2 * (levels - 1)
-        evals_per_level, iters_per_level = st["evals"], st["iters"]
+        evals_per_level, iters_per_level, level_s = st["evals"], st["iters"], st["level_seconds"]
     torch.cuda.synchronize(dev)
     dist_barrier()
     clk = clocks.stop()
@@ -358,7 +358,10 @@ def run_ours(args):
                        "levels": levels, "finest_nodes": list(info["nodes"]), "eta": c["eta"],
                        "alpha": c["alpha"], "lbfgs_mem": c["mem"], "max_iter_per_level": c["max_iter"],
                        "evals_per_level": evals_per_level, "iters_per_level": iters_per_level,
+                       "level_device_s": level_s,
                        "eval_impl": "fused" if impl == 0 else "multi-pass",
+                       "fused_tz_per_level": [reg.level_tiling(lv)[0] for lv in range(levels)],
+                       "tiling": "autotuned (z segment length timed per level)" if reg.cfg.autotune else "fixed rule",
                        "lbfgs_loop": "one CUDA graph per level" if reg.cfg.use_graph else "host-driven",
                        "l2": "flushed between steps (2x L2 buffer written, untimed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
@@ -545,6 +548,7 @@ def run_batch(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "batched": {"pairs_s": pairs_s_batch, "p50_ms": percentile_ms(done_batch, 50),
                         "p99_ms": percentile_ms(done_batch, 99), "step_ms": statistics.mean(t_batch),
+                        "level_device_s": res_b[0][1]["level_seconds"],
                         "gpu_launches_per_step": launches_batch // max(1, args.steps)},
             "per_pair_loop": {"pairs_s": pairs_s_loop, "p50_ms": percentile_ms(done_loop, 50),
                               "p99_ms": percentile_ms(done_loop, 99), "step_ms": statistics.mean(t_loop),

@@ -58,7 +58,8 @@ typedef struct reg_ctx *reg_handle;
  *   tau = rho = 0.01, alpha = 10, c1 = 1e-4, max_backtracks = 20,
  *   tol_grad_rel = 1e-5, tol_j_rel = 1e-7, tol_j_count = 3, levels = 1,
  *   lbfgs_mem = 5, max_iter = 50 on every level, node_dims = 0 (rule m_d/2+1),
- *   start_level = -1 (coarsest), eval_impl = 0 (fused), use_graph = 1. */
+ *   start_level = -1 (coarsest), eval_impl = 0 (fused), use_graph = 1, image_dtype = 0,
+ *   autotune = 1, fused_tz = 0. */
 typedef struct reg_config {
     double tau, rho;      /* NGF edge parameters of Eq. 2 (template, reference), > 0 */
     double alpha;         /* regularisation weight of Eq. 1, >= 0 */
@@ -77,7 +78,13 @@ typedef struct reg_config {
     int use_graph;        /* 1: each pyramid level runs as one CUDA graph launch */
     int image_dtype;      /* 0: FP32 images; 1: the fused pass reads BF16 copies of R and T
                              (arithmetic stays FP32; levels without the fused pass use FP32) */
-    int reserved[5];
+    int autotune;         /* 1: reg_set_images times every z segment length of the fused pass
+                             on each level and keeps the fastest (cached per geometry for the
+                             process; the first call of a geometry synchronises the stream);
+                             0: a fixed rule */
+    int fused_tz;         /* 0: autotune / rule; else this z segment length on every level
+                             (one of 2, 4, 8, 16, 32, 64, 128) */
+    int reserved[3];
 } reg_config;
 
 /* Per-registration statistics (filled by reg_register). */
@@ -91,6 +98,8 @@ typedef struct reg_stats {
     double seconds;                   /* host wall time of the call */
     long long kernel_launches;        /* kernels this call ran on the GPU (graph nodes included) */
     int status;
+    double level_seconds[REG_MAX_LEVELS]; /* device time of each level, its prolongation included
+                                             (CUDA events on the handle's stream) */
 } reg_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -119,6 +128,13 @@ int reg_set_images(reg_handle h, const float *R, const float *T, const int dims[
  * node spacing (mm).  Any output pointer may be NULL. */
 int reg_level_info(reg_handle h, int level, int img_dims[3], int node_dims[3],
                    double spacing_mm[3], double node_spacing_mm[3]);
+
+/* Tiling of the fused objective pass on a level (no counterpart in the paper,
+ * which uses separate kernels): *tz = the z segment length (output planes per
+ * CTA, chosen by the autotuner, cfg.fused_tz or the fixed rule), *tiles = CTAs
+ * per evaluation.  Both 0 on levels the multi-pass kernels serve.  Any output
+ * pointer may be NULL. */
+int reg_level_tiling(reg_handle h, int level, int *tz, int *tiles);
 
 /* Copy pyramid image `which` (0 = R, 1 = T) of a level into out
  * (m_x m_y m_z floats; device pointer if out_is_device). */

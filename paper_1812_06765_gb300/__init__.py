@@ -22,9 +22,10 @@ __all__ = ["make_config", "Registration", "RegObjective", "register", "register_
 
 def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1=1e-4, max_backtracks=20,
                 tol_grad_rel=1e-5, tol_j_rel=1e-7, tol_j_count=3, fixed_iters=False, start_level=-1,
-                node_dims=None, eval_impl=None, use_graph=None, image_dtype=None):
+                node_dims=None, eval_impl=None, use_graph=None, image_dtype=None, autotune=None, fused_tz=None):
     """A reg_config; max_iter is one value for every level or a per-level list (index 0 = finest).
-    image_dtype: "f32" (default) or "bf16" (the fused pass reads BF16 copies of the images)."""
+    image_dtype: "f32" (default) or "bf16" (the fused pass reads BF16 copies of the images).
+    autotune: time the fused pass's z segment lengths per level (default on); fused_tz: force one."""
     cfg = _lib.reg_config_default()
     cfg.tau = float(tau)
     cfg.rho = float(tau if rho is None else rho)
@@ -51,6 +52,10 @@ def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1
         if image_dtype not in ("f32", "bf16"):
             raise ValueError("image_dtype must be 'f32' or 'bf16'")
         cfg.image_dtype = 1 if image_dtype == "bf16" else 0
+    if autotune is not None:
+        cfg.autotune = int(bool(autotune))
+    if fused_tz is not None:
+        cfg.fused_tz = int(fused_tz)
     return cfg
 
 
@@ -95,6 +100,10 @@ class Registration:
     def level_info(self, level=0):
         m, n, h, H = _lib.reg_level_info(self.h, level)
         return dict(dims=m, nodes=n, spacing=h, node_spacing=H)
+
+    def level_tiling(self, level=0):
+        """(z segment length, CTAs) of the fused pass on a level; (0, 0) for multi-pass levels."""
+        return _lib.reg_level_tiling(self.h, level)
 
     def node_shape(self, level=0):
         n = self.level_info(level)["nodes"]
@@ -163,7 +172,7 @@ class Registration:
         stats = dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L],
                      level_status=list(st.level_status)[:L], J=list(st.J)[:L], J_final=st.J_final,
                      D_final=st.D_final, S_final=st.S_final, seconds=st.seconds,
-                     kernel_launches=st.kernel_launches)
+                     kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L])
         return u, stats
 
     def _node_tensor(self, u, level):
@@ -207,7 +216,7 @@ def _stats_dict(rc, st):
     L = st.levels
     return dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L], level_status=list(st.level_status)[:L],
                 J=list(st.J)[:L], J_final=st.J_final, D_final=st.D_final, S_final=st.S_final,
-                kernel_launches=st.kernel_launches)
+                kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L])
 
 
 def register_batch(regs, out="torch"):

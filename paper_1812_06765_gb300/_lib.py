@@ -33,7 +33,7 @@ class RegConfig(ctypes.Structure):
         ("max_backtracks", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("start_level", ctypes.c_int),
         ("max_iter", ctypes.c_int * MAX_LEVELS), ("node_dims", (ctypes.c_int * 3) * MAX_LEVELS),
         ("eval_impl", ctypes.c_int), ("use_graph", ctypes.c_int), ("image_dtype", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("autotune", ctypes.c_int), ("fused_tz", ctypes.c_int), ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -43,6 +43,7 @@ class RegStats(ctypes.Structure):
         ("level_status", ctypes.c_int * MAX_LEVELS), ("J", ctypes.c_double * MAX_LEVELS),
         ("J_final", ctypes.c_double), ("D_final", ctypes.c_double), ("S_final", ctypes.c_double),
         ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong), ("status", ctypes.c_int),
+        ("level_seconds", ctypes.c_double * MAX_LEVELS),
     ]
 
 
@@ -70,6 +71,7 @@ def lib():
         L.reg_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(RegConfig), vp]
         L.reg_set_images.argtypes = [vp, fp, fp, ip, dp, ctypes.c_int]
         L.reg_level_info.argtypes = [vp, ctypes.c_int, ip, ip, dp, dp]
+        L.reg_level_tiling.argtypes = [vp, ctypes.c_int, ip, ip]
         L.reg_get_level_image.argtypes = [vp, ctypes.c_int, ctypes.c_int, fp, ctypes.c_int]
         L.reg_eval_objective_grad.argtypes = [vp, ctypes.c_int, fp, fp, dp, dp, dp]
         L.reg_prolong.argtypes = [vp, ctypes.c_int, fp, fp]
@@ -84,7 +86,7 @@ def lib():
         L.reg_register_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(fp), ctypes.c_int,
                                          ctypes.POINTER(RegStats)]
         L.reg_register_batch.restype = ctypes.c_int
-        for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_get_level_image",
+        for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_level_tiling", "reg_get_level_image",
                      "reg_eval_objective_grad", "reg_prolong", "reg_lbfgs_direction", "reg_register",
                      "reg_destroy"):
             getattr(L, name).restype = ctypes.c_int
@@ -142,6 +144,12 @@ def reg_level_info(h, level):
     sp, H = (ctypes.c_double * 3)(), (ctypes.c_double * 3)()
     check(h, lib().reg_level_info(h, int(level), m, n, sp, H))
     return tuple(m), tuple(n), tuple(sp), tuple(H)
+
+
+def reg_level_tiling(h, level):
+    tz, tiles = ctypes.c_int(), ctypes.c_int()
+    check(h, lib().reg_level_tiling(h, int(level), ctypes.byref(tz), ctypes.byref(tiles)))
+    return tz.value, tiles.value
 
 
 def reg_get_level_image(h, level, which, out_ptr, out_is_device):

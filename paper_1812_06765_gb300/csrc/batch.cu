@@ -53,7 +53,8 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     P.ncx = (L.n[0] + 31) / 32;
     P.ncy = (L.n[1] + 7) / 8;
     P.nD = ntx * nty * ntz;
-    P.nS = P.ncx * P.ncy * L.n[2];
+    P.nS = P.ncx * P.ncy * curv_zchunks(L.n[2]);
+    P.ngather = P.ncx * P.ncy * L.n[2];
     P.w = c->es.w;
     P.pS = c->es.partials + P.nD;
     const double hy = L.H[0] * L.H[1] * L.H[2];
@@ -73,12 +74,12 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     P.P = c->lb.P;
     P.Y = c->lb.Y;
     P.lpart = c->lb.partials;
-    P.nchunks = num_blocks_for(c, (P.n + 3) / 4, 256);
+    P.nchunks = num_blocks_for(c, (P.n + 3) / 4, LB_VT);
 }
 
 struct BatchDev {
     PairLevel *pl = nullptr;
-    int *off = nullptr;      // [3][npairs + 1]: tiles, node blocks, vector blocks
+    int *off = nullptr;      // [4][npairs + 1]: tiles, gather blocks, vector blocks, curvature blocks
     int *counters = nullptr; // [2]: runs of the iteration and search conditions
 };
 
@@ -123,16 +124,26 @@ cudaError_t while_node(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, 
 
 struct BatchLaunch {
     const BatchDev *d;
-    int npairs, tiles, nodes, chunks;
-    int g_fused, g_nodes, g_chunks;
+    int npairs, tiles, nodes, chunks, curv;
+    int g_fused, g_nodes, g_chunks, g_curv;
     bool bf16;
     int device;
+    cudaStream_t side;             // the curvature pass runs beside the fused pass
+    cudaEvent_t ev_fork, ev_join;
 
     cudaError_t eval(int mode, cudaStream_t s) const
     {
-        cudaError_t e = launch_fused_batch(d->pl, d->off, npairs, tiles, mode, bf16, g_fused, device, s);
+        cudaError_t e = cudaEventRecord(ev_fork, s);
         if (e == cudaSuccess)
-            e = launch_curv_w_batch(d->pl, d->off + (npairs + 1), npairs, nodes, mode, g_nodes, s);
+            e = cudaStreamWaitEvent(side, ev_fork, 0);
+        if (e == cudaSuccess)
+            e = launch_fused_batch(d->pl, d->off, npairs, tiles, mode, bf16, g_fused, device, s);
+        if (e == cudaSuccess)
+            e = launch_curv_w_batch(d->pl, d->off + 3 * (npairs + 1), npairs, curv, mode, g_curv, side);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_join, side);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, ev_join, 0);
         if (e == cudaSuccess)
             e = launch_gather_batch(d->pl, d->off + (npairs + 1), npairs, nodes, mode, g_nodes, s);
         if (e == cudaSuccess)
@@ -266,7 +277,7 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     }
     BatchDev d;
     CK(cudaMallocAsync((void **)&d.pl, sizeof(PairLevel) * n, s));
-    CK(cudaMallocAsync((void **)&d.off, sizeof(int) * 3 * (n + 1), s));
+    CK(cudaMallocAsync((void **)&d.off, sizeof(int) * 4 * (n + 1), s));
     CK(cudaMallocAsync((void **)&d.counters, sizeof(int) * 2, s));
     // every pair's own stream work (prolongations, state uploads) is ordered on c0's stream
     for (int i = 0; i < n; i++)
@@ -274,9 +285,13 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     long long launches = 0;
     int status = REG_OK;
     std::vector<PairLevel> hpl(n);
-    std::vector<int> hoff(3 * (n + 1));
+    std::vector<int> hoff(4 * (n + 1));
+    if (!c0->lev_ev[0])
+        for (int i = 0; i <= REG_MAX_LEVELS; i++)
+            CK(cudaEventCreate(&c0->lev_ev[i]));
     for (int l = start; l >= 0 && status >= 0; l--) {
-        int tiles = 0, nodes = 0, chunks = 0;
+        CK(cudaEventRecord(c0->lev_ev[l + 1], s));
+        int tiles = 0, nodes = 0, chunks = 0, curv = 0;
         for (int i = 0; i < n; i++) {
             reg_ctx *ci = hs[i];
             const Level &L = ci->L[l];
@@ -292,18 +307,22 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
             hoff[i] = tiles;
             hoff[(n + 1) + i] = nodes;
             hoff[2 * (n + 1) + i] = chunks;
+            hoff[3 * (n + 1) + i] = curv;
             tiles += hpl[i].nD;
-            nodes += hpl[i].nS;
+            nodes += hpl[i].ngather;
             chunks += hpl[i].nchunks;
+            curv += hpl[i].nS;
         }
         hoff[n] = tiles;
         hoff[(n + 1) + n] = nodes;
         hoff[2 * (n + 1) + n] = chunks;
+        hoff[3 * (n + 1) + n] = curv;
         CK(cudaMemcpyAsync(d.pl, hpl.data(), sizeof(PairLevel) * n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d.off, hoff.data(), sizeof(int) * hoff.size(), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(d.counters, 0, sizeof(int) * 2, s));
-        BatchLaunch B{&d, n, tiles, nodes, chunks, cap(tiles, c0->num_sms), cap(nodes, 8LL * c0->num_sms),
-                      cap(chunks, 8LL * c0->num_sms), bf16, c0->device};
+        BatchLaunch B{&d, n, tiles, nodes, chunks, curv, cap(tiles, c0->num_sms), cap(nodes, 8LL * c0->num_sms),
+                      cap(chunks, 4LL * c0->num_sms), cap(curv, 8LL * c0->num_sms), bf16, c0->device,
+                      c0->side, c0->ev_fork, c0->ev_join};
         cudaGraphExec_t exec = nullptr;
         cudaError_t e = build_batch_graph(B, c0->cap_stream, &exec);
         if (e != cudaSuccess) {
@@ -345,6 +364,7 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
             }
         }
     }
+    CK(cudaEventRecord(c0->lev_ev[0], s));
     for (int i = 0; i < n; i++)
         CK(cudaMemcpyAsync(u_out[i], hs[i]->lb.u, sizeof(float) * 3 * hs[i]->L[0].nn,
                            out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -352,7 +372,16 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     CK(cudaFreeAsync(d.off, s));
     CK(cudaFreeAsync(d.counters, s));
     CK(cudaStreamSynchronize(s));
+    double lsec[REG_MAX_LEVELS] = {};
+    if (status >= 0)
+        for (int l = start; l >= 0; l--) {   // level l ran from event l + 1 to event l
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c0->lev_ev[l + 1], c0->lev_ev[l]));
+            lsec[l] = 1e-3 * ms;
+        }
     for (int i = 0; i < n; i++) {
+        for (int l = 0; l < REG_MAX_LEVELS; l++)
+            st[i].level_seconds[l] = lsec[l];
         st[i].status = status;
         st[i].kernel_launches = launches;
         if (stats)

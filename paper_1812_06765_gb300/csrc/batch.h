@@ -24,7 +24,8 @@ struct PairLevel {
     LevelGeom geom;
     float *w;               // curvature Laplacian scratch
     double *pS;             // curvature block partials (after the fused-pass partials)
-    int nD, nS;             // block partials of D and of S
+    int nD, nS;             // block partials of D and of S (= curvature blocks)
+    int ngather;            // gather blocks (32 x 8 nodes of one plane)
     double hbar_half, alpha, hy_half;
     float alpha_hy;
     double *scal, *scal_t;  // [J, D, S] at u and at the trial point
@@ -42,9 +43,10 @@ struct PairLevel {
 // off[p] <= i < off[p + 1]
 struct WorkLists {
     int *tiles;             // fused-pass tiles
-    int *nodes;             // curvature / gather blocks
+    int *nodes;             // gather blocks
     int *chunks;            // vector-pass blocks
-    int total_tiles, total_nodes, total_chunks;
+    int *curv;              // curvature blocks
+    int total_tiles, total_nodes, total_chunks, total_curv;
 };
 
 __device__ __forceinline__ int find_pair(const int *__restrict__ off, int npairs, int item)

@@ -59,20 +59,27 @@ __device__ __forceinline__ int linear_bid()
     return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 }
 
-// Block sum of one float per thread: FP32 within each warp (32 terms), FP64
-// across warps.  The result is valid in thread 0.  sm holds >= nwarps doubles.
+// Block sum of one float per thread, returned as FP64 in thread 0 (other
+// threads: 0).  sm holds >= nwarps floats (declared double for callers).
 __device__ __forceinline__ double block_sum_to_f64(float v, double *sm)
 {
+    // FP32 inside the block (warp sums, then the warp totals by one warp, in a
+    // fixed order); the block total goes to FP64 for the cross-block sum.  FP64
+    // arithmetic costs ~64 cycles per warp instruction on this GPU, so it is
+    // kept to the cross-block step.
+    float *smf = reinterpret_cast<float *>(sm);
     const int tid = linear_tid();
-    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) / 32;
     v = warp_sum(v);
     if ((tid & 31) == 0)
-        sm[tid >> 5] = (double)v;
+        smf[tid >> 5] = v;
     __syncthreads();
     double s = 0.0;
-    if (tid == 0)
-        for (int w = 0; w < (nthreads + 31) / 32; w++)
-            s += sm[w];
+    if (tid < 32) {
+        float x = warp_sum(tid < nw ? smf[tid] : 0.f);
+        if (tid == 0)
+            s = (double)x;
+    }
     __syncthreads();
     return s;
 }

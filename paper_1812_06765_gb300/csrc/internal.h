@@ -27,6 +27,7 @@ struct Level {
     // prolongation from level + 1 onto this level's nodes
     int *qk0[3] = {nullptr, nullptr, nullptr};
     float *qw1[3] = {nullptr, nullptr, nullptr};
+    int tz = 0;   // z segment length of the fused pass (0: the default rule)
     LevelGeom geom() const;
 };
 
@@ -64,6 +65,7 @@ struct reg_ctx {
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     bool own_stream = false;
     cudaEvent_t ev_side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // curvature pass beside the NGF pass
     int device = 0;
     int num_sms = 0;
     int levels = 0;
@@ -76,6 +78,8 @@ struct reg_ctx {
     // CUDA graph of one L-BFGS iteration per level (built lazily)
     cudaGraphExec_t iter_graph[REG_MAX_LEVELS] = {};
     cudaGraphExec_t init_graph[REG_MAX_LEVELS] = {};
+    // events at the level boundaries of reg_register (created on first use)
+    cudaEvent_t lev_ev[REG_MAX_LEVELS + 1] = {};
 };
 
 // status helpers
@@ -87,6 +91,11 @@ int cuda_err(reg_ctx *c, cudaError_t e, const char *what);
         cudaError_t _e = (call);                                          \
         if (_e != cudaSuccess) return cuda_err(c, _e, #call);             \
     } while (0)
+
+// The curvature Laplacian pass: blocks of 32 x 8 nodes over CURV_ZB node
+// planes, one FP64 partial of S per block.
+#define CURV_ZB 1
+inline int curv_zchunks(int nz) { return (nz + CURV_ZB - 1) / CURV_ZB; }
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_restrict(const float *src, const int m[3], float *dst, cudaStream_t s);
@@ -114,6 +123,11 @@ int num_blocks_for(reg_ctx *c, long long n, int threads);
 // objective pass variants (k_ngf_fused.cu, k_ngf_multipass.cu)
 bool fused_eligible(const Level &L);
 size_t fused_part_floats(const Level &L, int num_sms);
+int fused_tz(const Level &L, int num_sms);
+bool fused_tz_valid(int tz);
+// times every z segment length on the level's images at u_zero (3 node planes
+// of zeros) and keeps the fastest in L.tz; cached per geometry
+cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStream_t s);
 cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
                              float *grad, double *partials, int *n_partials, cudaStream_t s);
 cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,

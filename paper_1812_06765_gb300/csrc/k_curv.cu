@@ -12,39 +12,42 @@
 
 namespace {
 
-// block (bx, by, bz) of 32 x 8 nodes; its S partial goes to partials[lin]
+// block (bx, by, bzc) of 32 x 8 nodes over the CURV_ZB node planes from
+// bzc * CURV_ZB; its S partial goes to partials[lin]
 __device__ __forceinline__ void curv_w_body(const LevelGeom &g, const float *__restrict__ ub,
                                             const float *__restrict__ dir, const double *__restrict__ t_dev,
                                             float *__restrict__ w, double *__restrict__ partials, int bx, int by,
-                                            int bz, int lin)
+                                            int bzc, int lin)
 {
     __shared__ double sm[8];
-    int x = bx * blockDim.x + threadIdx.x;
-    int y = by * blockDim.y + threadIdx.y;
-    int z = bz;
-    bool in = x < g.n[0] && y < g.n[1];
-    float t = dir ? (float)__ldg(t_dev) : 0.f;
+    const int x = bx * blockDim.x + threadIdx.x;
+    const int y = by * blockDim.y + threadIdx.y;
+    const bool in = x < g.n[0] && y < g.n[1];
+    const float t = dir ? (float)__ldg(t_dev) : 0.f;
+    const size_t st[3] = {1, (size_t)g.n[0], (size_t)g.n[0] * g.n[1]};
+    const bool inxy = x >= 1 && y >= 1 && x <= g.n[0] - 2 && y <= g.n[1] - 2;
+    const int z1 = min(g.n[2], (bzc + 1) * CURV_ZB);
     float acc = 0.f;
-    if (in) {
-        size_t k = x + (size_t)g.n[0] * (y + (size_t)g.n[1] * z);
-        bool interior = x >= 1 && y >= 1 && z >= 1 && x <= g.n[0] - 2 && y <= g.n[1] - 2 && z <= g.n[2] - 2;
-        size_t st[3] = {1, (size_t)g.n[0], (size_t)g.n[0] * g.n[1]};
+    if (in)
+        for (int z = bzc * CURV_ZB; z < z1; z++) {
+            const size_t k = x + (size_t)g.n[0] * (y + (size_t)g.n[1] * z);
+            const bool interior = inxy && z >= 1 && z <= g.n[2] - 2;
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            float lap = 0.f;
-            if (interior) {
-                const float *u = ub + c * g.nn;
-                const float *d = dir ? dir + c * g.nn : nullptr;
-                float u0 = node_value(u, d, t, k);
+            for (int c = 0; c < 3; c++) {
+                float lap = 0.f;
+                if (interior) {
+                    const float *u = ub + c * g.nn;
+                    const float *d = dir ? dir + c * g.nn : nullptr;
+                    float u0 = node_value(u, d, t, k);
 #pragma unroll
-                for (int e = 0; e < 3; e++)
-                    lap = fmaf(node_value(u, d, t, k + st[e]) - 2.f * u0 + node_value(u, d, t, k - st[e]),
-                               g.iH2[e], lap);
+                    for (int e = 0; e < 3; e++)
+                        lap = fmaf(node_value(u, d, t, k + st[e]) - 2.f * u0 + node_value(u, d, t, k - st[e]),
+                                   g.iH2[e], lap);
+                }
+                w[c * g.nn + k] = lap;
+                acc = fmaf(lap, lap, acc);
             }
-            w[c * g.nn + k] = lap;
-            acc = fmaf(lap, lap, acc);
         }
-    }
     double s = block_sum_to_f64(acc, sm);
     if (linear_tid() == 0)
         partials[lin] = s;
@@ -175,6 +178,15 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     int nD = 0;
     cudaError_t e;
     const bool fused = use_fused(c, level);
+    // The curvature Laplacian (node pass, HBM-light) runs on the side stream
+    // beside the NGF pass (issue-bound, one CTA per SM): fork before, join
+    // before the gradient assembly.  Captured, the two become parallel graph
+    // branches.
+    e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (e != cudaSuccess)
+        return e;
     if (fused)
         e = launch_ngf_fused(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
     else
@@ -183,8 +195,16 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
         return e;
     dim3 blk(32, 8, 1);
     dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
+    dim3 gw(gn.x, gn.y, curv_zchunks(L.n[2]));
     double *pS = c->es.partials + nD;
-    k_curv_w<<<gn, blk, 0, s>>>(g, ub, dir, t_dev, c->es.w, pS);
+    k_curv_w<<<gw, blk, 0, c->side>>>(g, ub, dir, t_dev, c->es.w, pS);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c->ev_join, c->side);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(s, c->ev_join, 0);
+    if (e != cudaSuccess)
+        return e;
     double hy = L.H[0] * L.H[1] * L.H[2];
     if (fused) {   // grad = (tile partials of P^T r) + alpha hbar_y L^T w
         e = launch_gather_grad(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, s);
@@ -194,7 +214,7 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
         k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);
         c->launches += 1;
     }
-    int nS = (int)(gn.x * gn.y * gn.z);
+    int nS = (int)(gw.x * gw.y * gw.z);
     double hbar = L.h[0] * L.h[1] * L.h[2];
     k_finalize<<<1, 512, 0, s>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out);
     c->launches += 2;
@@ -211,12 +231,12 @@ int eval_partials_needed(const Level &L)
 
 // Explicit-buffer launches of the curvature Laplacian and of the final
 // reduction, for callers that own every buffer (the allocation-free entry point).
-int curv_blocks(const LevelGeom &g) { return ((g.n[0] + 31) / 32) * ((g.n[1] + 7) / 8) * g.n[2]; }
+int curv_blocks(const LevelGeom &g) { return ((g.n[0] + 31) / 32) * ((g.n[1] + 7) / 8) * curv_zchunks(g.n[2]); }
 
 cudaError_t launch_curv_w_raw(const LevelGeom &g, const float *u, float *w, double *partials, cudaStream_t s)
 {
     dim3 blk(32, 8, 1);
-    dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]);
+    dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, curv_zchunks(g.n[2]));
     k_curv_w<<<gn, blk, 0, s>>>(g, u, nullptr, nullptr, w, partials);
     return cudaGetLastError();
 }

@@ -19,30 +19,32 @@
 
 namespace {
 
-constexpr int VT = 256;             // threads of the vector kernels
+constexpr int VT = LB_VT;           // threads of the vector kernels
+constexpr int CT = 256;             // threads of the control kernel
 constexpr int ND_ACC = 2 + 4 * LB_MAXS;
 
 // Reduce ND per-thread values over the block; entry `imax` (if >= 0) by max,
-// the others by sum (FP32 in the warp, FP64 across warps); write the block
-// totals to out[0 .. ND).
+// the others by sum, in FP32 and a fixed order (warp shuffles, then the warp
+// totals by one thread per entry); write the block totals as FP64 to
+// out[0 .. ND) for the cross-block FP64 sum.
 template <int ND>
 __device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, double *out)
 {
-    __shared__ double sm[VT / 32][ND];
+    __shared__ float sm[VT / 32][ND];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 0; d < ND; d++) {
         float x = (d == imax) ? warp_max(v[d]) : warp_sum(v[d]);
         if (lane == 0)
-            sm[warp][d] = (double)x;
+            sm[warp][d] = x;
     }
     __syncthreads();
     if (threadIdx.x < ND) {
         int d = threadIdx.x;
-        double s = sm[0][d];
+        float s = sm[0][d];
         for (int w = 1; w < VT / 32; w++)
-            s = (d == imax) ? fmax(s, sm[w][d]) : s + sm[w][d];
-        out[d] = s;
+            s = (d == imax) ? fmaxf(s, sm[w][d]) : s + sm[w][d];
+        out[d] = (double)s;
     }
 }
 
@@ -291,46 +293,92 @@ __device__ void set_p0(LbfgsState *st)
 // gamma = s'y / y'y of the newest pair, q = R^{-1} S'g and
 // w = R^{-T} ((D + gamma Y'Y) q - gamma Y'g):
 //   H g = gamma g + S w - gamma Y q,   p = -H g.
-__device__ void set_compact(LbfgsState *st)
+// Run by one full warp, lane i holding row i: the triangular solves go column
+// by column (q_i, then every remaining row updated at once), so the FP64
+// dependency chain is about 3 count operations long.  1 / R_ii and gamma are
+// taken once, when the pair is stored (FP64 divides cost ~640 cycles here).
+__device__ void set_compact_warp(LbfgsState *st)
 {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int c = st->count;
-    double Sg[LB_MAXM], Yg[LB_MAXM], q[LB_MAXM], z[LB_MAXM], w[LB_MAXM];
-    int o[LB_MAXM];
-    for (int i = 0; i < c; i++) {
-        o[i] = st->order[i];
-        Sg[i] = st->tscale[o[i]] * st->Pg[o[i]];
-        Yg[i] = st->Yg[o[i]];
+    const bool row = lane < c;
+    const int oi = row ? st->order[lane] : 0;
+    const double gamma = st->gamma;
+    const double Rii = row ? st->SY[oi][oi] : 0.0;
+    const double iR = row ? st->iSY[oi] : 0.0;
+    const double Yg = row ? st->Yg[oi] : 0.0;
+    double r = row ? st->tscale[oi] * st->Pg[oi] : 0.0;   // S'g
+    double q = 0.0;
+    for (int i = c - 1; i >= 0; i--) {   // R q = S'g, upper triangular
+        const double qi = __shfl_sync(FULL, r * iR, i);
+        if (lane == i)
+            q = qi;
+        if (lane < i)
+            r = fma(-st->SY[oi][st->order[i]], qi, r);
     }
-    const int nw = o[c - 1];
-    double gamma = st->SY[nw][nw] / st->YY[nw][nw];
-    for (int i = c - 1; i >= 0; i--) {
-        double s = Sg[i];
-        for (int j = i + 1; j < c; j++)
-            s -= st->SY[o[i]][o[j]] * q[j];
-        q[i] = s / st->SY[o[i]][o[i]];
+    double acc = 0.0;                     // (Y'Y q)_i
+    for (int j = 0; j < c; j++) {
+        const double qj = __shfl_sync(FULL, q, j);
+        if (row)
+            acc = fma(st->YY[oi][st->order[j]], qj, acc);
     }
-    for (int i = 0; i < c; i++) {
-        double s = st->SY[o[i]][o[i]] * q[i] - gamma * Yg[i];
-        for (int j = 0; j < c; j++)
-            s += gamma * st->YY[o[i]][o[j]] * q[j];
-        z[i] = s;
+    r = fma(Rii, q, gamma * (acc - Yg));  // (D + gamma Y'Y) q - gamma Y'g
+    double w = 0.0;
+    for (int i = 0; i < c; i++) {        // R^T w = r, lower triangular
+        const double wi = __shfl_sync(FULL, r * iR, i);
+        if (lane == i)
+            w = wi;
+        if (lane > i && row)
+            r = fma(-st->SY[st->order[i]][oi], wi, r);
     }
-    for (int i = 0; i < c; i++) {
-        double s = z[i];
-        for (int j = 0; j < i; j++)
-            s -= st->SY[o[j]][o[i]] * w[j];
-        w[i] = s / st->SY[o[i]][o[i]];
+    if (lane == 0) {
+        st->dcount = c;
+        st->cg = -gamma;
     }
-    st->dcount = c;
-    st->cg = -gamma;
-    for (int i = 0; i < c; i++) {
-        st->dslot[i] = o[i];
-        st->cp[i] = -w[i] * st->tscale[o[i]];
-        st->cy[i] = gamma * q[i];
+    if (row) {
+        st->dslot[lane] = oi;
+        st->cp[lane] = -w * st->tscale[oi];
+        st->cy[lane] = gamma * q;
     }
 }
 
 __device__ bool finite_d(double x) { return isfinite(x); }
+
+// Cross-block FP64 sum (entry imax: max) of nd values over nblocks block
+// partials (partials[b * nd + d]) in a fixed order.  FP64 instructions cost
+// ~64 cycles per warp instruction whatever the active lanes, so the adds are
+// packed: thread (d, j) sums blocks j, j + J, ... for J groups per value (J
+// about sqrt(nblocks), at most CT / nd), then thread d adds its J group sums.
+__device__ __forceinline__ void control_reduce(const double *__restrict__ partials, int nblocks, int nd, int imax,
+                                               double *red, double *scratch)
+{
+    const int t = threadIdx.x;
+    int J = 1;
+    while (J * J < nblocks)
+        J++;
+    if (J > CT / nd)
+        J = CT / nd;
+    if (t < nd * J) {
+        const int d = t % nd, j = t / nd;
+        double s = 0.0;   // the max entry is a max of absolute values: 0 is its identity
+        for (int b = j; b < nblocks; b += J) {
+            const double x = __ldcg(partials + (size_t)b * nd + d);
+            s = (d == imax) ? fmax(s, x) : s + x;
+        }
+        scratch[t] = s;
+    }
+    __syncthreads();
+    if (t < nd) {
+        double s = scratch[t];
+        for (int j = 1; j < J; j++) {
+            const double x = scratch[j * nd + t];
+            s = (t == imax) ? fmax(s, x) : s + x;
+        }
+        red[t] = s;
+    }
+    __syncthreads();
+}
 
 __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restrict__ gst,
                                                     const double *__restrict__ partials, int nblocks,
@@ -342,6 +390,8 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
     // global accesses
     __shared__ LbfgsState S;
     __shared__ double red[ND_ACC];
+    __shared__ double scratch[CT];
+    __shared__ int s_store, s_compact;
     constexpr int NW = (int)(sizeof(LbfgsState) / sizeof(int));
     for (int i = threadIdx.x; i < NW; i += blockDim.x)
         reinterpret_cast<int *>(&S)[i] = reinterpret_cast<const int *>(gst)[i];
@@ -351,24 +401,12 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
     const int imax = (phase == LB_INIT || phase == LB_ACCEPTED) ? 1 : -1;
     const bool need = phase != LB_ARMIJO && !(phase == LB_ACCEPTED && (!st->active || st->ls != LS_ACCEPTED)) &&
                       !(phase == LB_DIR_REDO && !st->redo_dir) && !(phase == LB_DIR && !st->iter_continue);
-    if (need) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int d = warp; d < nd; d += 8) {
-            double s = 0.0;
-            for (int b = lane; b < nblocks; b += 32) {
-                double x = partials[(size_t)b * nd + d];
-                s = (d == imax) ? fmax(s, x) : s + x;
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-                double y = __shfl_xor_sync(0xffffffffu, s, off);
-                s = (d == imax) ? fmax(s, y) : s + y;
-            }
-            if (lane == 0)
-                red[d] = s;
-        }
-    }
+    if (need)
+        control_reduce(partials, nblocks, nd, imax, red, scratch);
     __syncthreads();
     if (threadIdx.x == 0) {
+    s_store = 0;
+    s_compact = 0;
     switch (phase) {
     case LB_INIT: {
         st->J = scal[0];
@@ -377,7 +415,8 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
         st->J0 = st->J;
         st->gg = red[0];
         st->ginf = red[1];
-        st->g0norm = st->gnorm = sqrt(red[0]);
+        st->g0norm = sqrt(red[0]);
+        st->gtol2 = st->tol_grad_rel * st->tol_grad_rel * red[0];
         st->k = 0;
         st->bodies = 0;
         st->evals = 1;
@@ -491,12 +530,13 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
         st->k++;
         st->gg = red[0];
         st->ginf = red[1];
-        st->gnorm = sqrt(red[0]);
         const int f = st->free_slot;
         const double tn = st->t;
         double sy = tn * st->Py[f], ss = tn * tn * st->pp, yy = st->Yy[f];
-        if (sy > 1e-10 * sqrt(ss) * sqrt(yy)) { // curvature test: keep the pair
+        // curvature test s'y > 1e-10 ||s|| ||y||, compared as squares (sy > 0)
+        if (sy > 0.0 && sy * sy > 1e-20 * ss * yy) {   // keep the pair
             st->tscale[f] = tn;
+            s_store = 1;   // 1 / s'y and gamma are formed by the warp below
             for (int j = 0; j < st->lcount; j++) {
                 int s = st->lslot[j];
                 st->SY[s][f] = st->tscale[s] * st->Py[s];
@@ -527,7 +567,7 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
         } else if (st->k >= st->max_iter) {
             st->done = 1;
         } else if (!st->fixed_iters) {
-            if (st->gnorm <= st->tol_grad_rel * st->g0norm) {
+            if (st->gg <= st->gtol2) {   // ||g|| <= tol_grad_rel ||g0||
                 st->done = 1;
             } else if (fabs(Jprev - st->J) <= st->tol_j_rel * (1.0 + fabs(st->J0))) {
                 if (++st->small_count >= st->tol_j_count)
@@ -538,7 +578,7 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
         }
         if (!st->done) {
             if (st->count > 0)
-                set_compact(st);
+                s_compact = 1;
             else
                 set_p0(st);
         }
@@ -548,19 +588,39 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
     default:
         break;
     }
-#if CUDART_VERSION >= 12040
-    if (h_ls)
-        cudaGraphSetConditional((cudaGraphConditionalHandle)h_ls, st->ls_continue ? 1u : 0u);
-    if (h_iter)
-        cudaGraphSetConditional((cudaGraphConditionalHandle)h_iter, st->iter_continue ? 1u : 0u);
-#endif
     }   // thread 0
+    __syncthreads();
+    if (threadIdx.x < 32 && (s_store || s_compact)) {
+        const int lane = threadIdx.x;
+        if (s_store) {   // the pair in the free slot's predecessor position was stored
+            const int f = st->order[st->count - 1];
+            const double num = lane == 1 ? st->SY[f][f] : 1.0;
+            const double den = lane == 1 ? st->YY[f][f] : st->SY[f][f];
+            const double x = num / den;   // lanes 0 and 1 divide at once
+            const double gm = __shfl_sync(0xffffffffu, x, 1);
+            if (lane == 0) {
+                st->iSY[f] = x;
+                st->gamma = gm;
+            }
+            __syncwarp();
+        }
+        if (s_compact)
+            set_compact_warp(st);
+    }
+#if CUDART_VERSION >= 12040
+    if (threadIdx.x == 0) {
+        if (h_ls)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)h_ls, st->ls_continue ? 1u : 0u);
+        if (h_iter)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)h_iter, st->iter_continue ? 1u : 0u);
+    }
+#endif
     __syncthreads();
     for (int i = threadIdx.x; i < NW; i += blockDim.x)
         reinterpret_cast<int *>(gst)[i] = reinterpret_cast<const int *>(&S)[i];
 }
 
-__global__ void __launch_bounds__(256) k_lb_control(int phase, LbfgsState *__restrict__ gst,
+__global__ void __launch_bounds__(CT) k_lb_control(int phase, LbfgsState *__restrict__ gst,
                                                     const double *__restrict__ partials, int nblocks,
                                                     const double *__restrict__ scal, unsigned long long h_ls,
                                                     unsigned long long h_iter)
@@ -593,7 +653,7 @@ __global__ void __launch_bounds__(VT) k_lb_vector_batch(const PairLevel *__restr
 
 // one block per pair; phase as in k_lb_control, scalars of the objective at u
 // (INIT) or at the trial point (ARMIJO)
-__global__ void __launch_bounds__(256) k_lb_control_batch(const PairLevel *__restrict__ pl, int phase)
+__global__ void __launch_bounds__(CT) k_lb_control_batch(const PairLevel *__restrict__ pl, int phase)
 {
     const PairLevel &P = pl[blockIdx.x];
     lb_control_body(phase, P.st, P.lpart, P.nchunks, phase == LB_INIT ? P.scal : P.scal_t, 0ULL, 0ULL);
@@ -683,37 +743,41 @@ __global__ void k_lb_pair_setup(LbfgsState *__restrict__ st, int count, const do
                                 int nblocks)
 {
     const int nd = 2 + 2 * count + 2 * count * count;
-    if (threadIdx.x != 0)
-        return;
-    double red[2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM];
-    for (int d = 0; d < nd; d++) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; b++) {
-            double x = partials[(size_t)b * nd + d];
-            s = (d == 1) ? fmax(s, x) : s + x;
+    if (threadIdx.x == 0) {
+        double red[2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM];
+        for (int d = 0; d < nd; d++) {
+            double s = 0.0;
+            for (int b = 0; b < nblocks; b++) {
+                double x = partials[(size_t)b * nd + d];
+                s = (d == 1) ? fmax(s, x) : s + x;
+            }
+            red[d] = s;
         }
-        red[d] = s;
-    }
-    st->gg = red[0];
-    st->ginf = red[1];
-    st->count = count;
-    for (int i = 0; i < count; i++) {
-        st->order[i] = i;
-        st->tscale[i] = 1.0;
-        st->Pg[i] = red[2 + 2 * i];
-        st->Yg[i] = red[3 + 2 * i];
-        for (int j = 0; j < count; j++) {
-            int q = 2 + 2 * count + 2 * (i * count + j);
-            st->SY[i][j] = red[q];
-            st->YY[i][j] = red[q + 1];
+        st->gg = red[0];
+        st->ginf = red[1];
+        st->count = count;
+        for (int i = 0; i < count; i++) {
+            st->order[i] = i;
+            st->tscale[i] = 1.0;
+            st->Pg[i] = red[2 + 2 * i];
+            st->Yg[i] = red[3 + 2 * i];
+            for (int j = 0; j < count; j++) {
+                int q = 2 + 2 * count + 2 * (i * count + j);
+                st->SY[i][j] = red[q];
+                st->YY[i][j] = red[q + 1];
+            }
+            st->iSY[i] = 1.0 / st->SY[i][i];
         }
+        if (count > 0)
+            st->gamma = st->SY[count - 1][count - 1] / st->YY[count - 1][count - 1];
+        else
+            set_p0(st);
+        st->iter_continue = 1;
+        st->done = 0;
     }
+    __syncwarp();
     if (count > 0)
-        set_compact(st);
-    else
-        set_p0(st);
-    st->iter_continue = 1;
-    st->done = 0;
+        set_compact_warp(st);
 }
 
 }  // namespace
@@ -755,7 +819,7 @@ void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter)
 static cudaError_t control(reg_ctx *c, int phase, int nblocks, const double *scal, cudaStream_t s,
                            bool use_ls_handle, bool use_iter_handle)
 {
-    k_lb_control<<<1, 256, 0, s>>>(phase, c->lb.st, c->lb.partials, nblocks, scal, use_ls_handle ? g_h_ls : 0ULL,
+    k_lb_control<<<1, CT, 0, s>>>(phase, c->lb.st, c->lb.partials, nblocks, scal, use_ls_handle ? g_h_ls : 0ULL,
                                    use_iter_handle ? g_h_iter : 0ULL);
     c->launches += 1;
     return cudaGetLastError();
@@ -833,7 +897,7 @@ cudaError_t launch_lb_vector_batch(const PairLevel *pl, const int *chunk_off, in
 
 cudaError_t launch_lb_control_batch(const PairLevel *pl, int npairs, int phase, cudaStream_t s)
 {
-    k_lb_control_batch<<<npairs, 256, 0, s>>>(pl, phase);
+    k_lb_control_batch<<<npairs, CT, 0, s>>>(pl, phase);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,10 @@
 //   D  zA-5      : y reduction of last step's rows, accumulation along z
 // Every phase reads only what earlier steps wrote, so one barrier per step
 // suffices, and the global loads of a plane overlap a whole step of compute.
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "batch.h"
 #include "internal.h"
 #include "ngf_math.cuh"
@@ -486,15 +490,28 @@ bool fused_eligible(const Level &L)
     return true;
 }
 
-// z segment length: even, 8 .. 128, the longest that still gives >= 2 CTAs per
-// SM (each segment pays 7 pipeline-fill steps)
-int fused_tz(const Level &L, int num_sms)
+// z segment lengths the autotuner tries (even: a segment covers whole node intervals)
+constexpr int TZ_CAND[] = {2, 4, 8, 16, 32, 64, 128};
+
+// Default z segment length when the level was not tuned: the longest of 8 ..
+// 128 that still gives >= 2 CTAs per SM (each segment pays 7 pipeline-fill steps).
+static int fused_tz_default(const Level &L, int num_sms)
 {
     long long cols = (long long)((L.m[0] + OX - 1) / OX) * ((L.m[1] + OY - 1) / OY);
     int tz = 128;
     while (tz > 8 && cols * ((L.m[2] + tz - 1) / tz) < 2LL * num_sms)
         tz /= 2;
     return tz;
+}
+
+int fused_tz(const Level &L, int num_sms) { return L.tz > 0 ? L.tz : fused_tz_default(L, num_sms); }
+
+bool fused_tz_valid(int tz)
+{
+    for (int t : TZ_CAND)
+        if (t == tz)
+            return true;
+    return false;
 }
 
 void fused_grid(const Level &L, int tz, int &ntx, int &nty, int &ntz)
@@ -504,11 +521,20 @@ void fused_grid(const Level &L, int tz, int &ntx, int &nty, int &ntz)
     ntz = (L.m[2] + tz - 1) / tz;
 }
 
+// tile-partial floats of the level: the largest over every z segment length
+// the autotuner may pick
 size_t fused_part_floats(const Level &L, int num_sms)
 {
-    int tz = fused_tz(L, num_sms), ntx, nty, ntz;
-    fused_grid(L, tz, ntx, nty, ntz);
-    return (size_t)ntx * nty * ntz * (tz / 2 + 1) * NE;
+    (void)num_sms;
+    size_t best = 0;
+    for (int tz : TZ_CAND) {
+        int ntx, nty, ntz;
+        fused_grid(L, tz, ntx, nty, ntz);
+        size_t p = (size_t)ntx * nty * ntz * (tz / 2 + 1) * NE;
+        if (p > best)
+            best = p;
+    }
+    return best;
 }
 
 cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
@@ -573,6 +599,82 @@ cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alph
     k_gather_grad<<<gn, blk, 0, s>>>(L.geom(), c->es.part, tz, ntx, nty, ntz, w, alpha_hy, grad);
     c->launches += 1;
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the z segment length (the tile depth of the fused pass).  For
+// every candidate the pass runs on the level's own images at u = u_zero (one
+// warm launch, then the median of three CUDA-event timings); the fastest wins.
+// Short segments start more CTAs (small levels fill the GPU) but pay the 7
+// pipeline-fill steps and the shared node planes more often, so the best
+// depth depends on the level and the GPU.  Choices are cached per (image
+// dims, SM count, image type, device) for the life of the process: handles of
+// the same geometry tune once and pick the same tiling.
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, int> g_tune;
+}
+
+cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStream_t s)
+{
+    Level &L = c->L[level];
+    const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
+    const std::array<int, 6> key{L.m[0], L.m[1], L.m[2], c->num_sms, bf16 ? 1 : 0, c->device};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            L.tz = it->second;
+            return cudaSuccess;
+        }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 0.f;
+    for (int tz : TZ_CAND) {
+        if (e != cudaSuccess)
+            break;
+        if (tz > 2 && tz / 2 >= L.m[2])   // the previous candidate already spans the whole depth
+            break;
+        L.tz = tz;
+        int nD = 0;
+        float t[3];
+        for (int r = -1; r < 3 && e == cudaSuccess; r++) {   // r = -1: warm launch
+            if (r >= 0)
+                e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess)
+                e = launch_ngf_fused(c, level, u_zero, nullptr, nullptr, nullptr, c->es.partials, &nD, s);
+            if (e == cudaSuccess && r >= 0)
+                e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess && r >= 0)
+                e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && r >= 0)
+                e = cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        if (e != cudaSuccess)
+            break;
+        const float med = fmaxf(fminf(t[0], t[1]), fminf(fmaxf(t[0], t[1]), t[2]));
+        if (best == 0 || med < best_ms) {
+            best = tz;
+            best_ms = med;
+        }
+    }
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        L.tz = 0;
+        return e;
+    }
+    L.tz = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

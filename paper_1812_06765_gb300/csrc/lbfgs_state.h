@@ -5,6 +5,7 @@
 
 #define LB_MAXM 8
 #define LB_MAXS (LB_MAXM + 1)   // m pairs + one free slot for the next direction
+#define LB_VT 256               // threads of the vector passes (up to 4 blocks per SM)
 
 enum LbPhase { LB_INIT = 0, LB_DIR = 1, LB_DIR_REDO = 2, LB_ARMIJO = 3, LB_ACCEPTED = 4 };
 enum LbSearch { LS_RUNNING = 0, LS_ACCEPTED = 1, LS_FAILED = 2, LS_RETRY = 3 };
@@ -14,7 +15,8 @@ struct LbfgsState {
     int m, max_iter, max_bt, fixed_iters, tol_j_count;
     double c1, tol_grad_rel, tol_j_rel, Hmin;
     // accepted iterate
-    double J, D, S, J0, g0norm, gnorm, ginf;
+    double J, D, S, J0, g0norm, ginf;
+    double gtol2;      // (tol_grad_rel * ||g0||)^2: the gradient test compares squares
     // trial point
     double Jt, Dt, St;
     double t;          // current step length
@@ -37,6 +39,8 @@ struct LbfgsState {
     int count, free_slot;
     int order[LB_MAXM];
     double tscale[LB_MAXS];          // s_slot = tscale * P_slot
+    double iSY[LB_MAXS];             // 1 / (s'y) of the pair in the slot
+    double gamma;                    // s'y / y'y of the newest stored pair
     double SY[LB_MAXS][LB_MAXS];     // s_i' y_j by slot (upper triangle by age)
     double YY[LB_MAXS][LB_MAXS];     // y_i' y_j by slot
     // direction p = cg g + sum_j cp[j] P[dslot[j]] + cy[j] Y[dslot[j]]

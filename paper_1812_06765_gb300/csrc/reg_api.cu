@@ -82,6 +82,9 @@ int validate_config(const reg_config *cfg, std::string &msg)
     else if (cfg->eval_impl != 0 && cfg->eval_impl != 1) msg = "eval_impl must be 0 or 1";
     else if (cfg->image_dtype != 0 && cfg->image_dtype != 1) msg = "image_dtype must be 0 (FP32) or 1 (BF16)";
     else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
+    else if (cfg->autotune != 0 && cfg->autotune != 1) msg = "autotune must be 0 or 1";
+    else if (cfg->fused_tz != 0 && !fused_tz_valid(cfg->fused_tz))
+        msg = "fused_tz must be 0 or one of 2, 4, 8, 16, 32, 64, 128";
     else return REG_OK;
     return REG_ERR_ARG;
 }
@@ -299,6 +302,8 @@ void reg_config_default(reg_config *cfg)
     for (int l = 0; l < REG_MAX_LEVELS; l++) cfg->max_iter[l] = 50;
     cfg->eval_impl = 0;
     cfg->use_graph = 1;
+    cfg->autotune = 1;
+    cfg->fused_tz = 0;
 }
 
 int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
@@ -319,6 +324,8 @@ int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         set_err(nullptr, REG_ERR_CUDA, "reg_create: %s", cudaGetErrorString(e));
         reg_destroy(c);
@@ -418,8 +425,37 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
             CK(launch_to_bf16(c->L[l].T, c->L[l].Tb, c->L[l].nv, c->stream));
             c->launches += 2;
         }
+    // tiling of the fused pass per level: forced, autotuned (at u = 0, with the
+    // direction buffer as the zero field) or the default rule
+    for (int l = 0; l < c->levels; l++) {
+        if (!use_fused(c, l) || c->L[l].tz > 0)
+            continue;
+        if (cfg.fused_tz > 0) {
+            c->L[l].tz = cfg.fused_tz;
+        } else if (cfg.autotune) {
+            CK(cudaMemsetAsync(c->lb.pdir, 0, sizeof(float) * 3 * c->L[l].nn, c->stream));
+            CK(fused_autotune(c, l, c->lb.pdir, c->stream));
+        }
+    }
     if (!ptr_is_device) CK(cudaStreamSynchronize(c->stream));  // host arrays may be released on return
     c->have_images = true;
+    return REG_OK;
+}
+
+int reg_level_tiling(reg_handle c, int level, int *tz, int *tiles)
+{
+    if (!c) return set_err(nullptr, REG_ERR_ARG, "reg_level_tiling: NULL handle");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_level_tiling: no images set");
+    if (level < 0 || level >= c->levels)
+        return set_err(c, REG_ERR_ARG, "reg_level_tiling: level %d out of range", level);
+    int z = 0, n = 0;
+    if (use_fused(c, level)) {
+        const Level &L = c->L[level];
+        z = fused_tz(L, c->num_sms);
+        n = ((L.m[0] + 27) / 28) * ((L.m[1] + 11) / 12) * ((L.m[2] + z - 1) / z);
+    }
+    if (tz) *tz = z;
+    if (tiles) *tiles = n;
     return REG_OK;
 }
 
@@ -580,8 +616,12 @@ int reg_register(reg_handle c, float *u_out, int out_is_device, const float *u_i
         CK(cudaMemsetAsync(b.u, 0, sizeof(float) * n0, c->stream));
     int status = REG_OK;
     const long long launches0 = c->launches;
+    if (!c->lev_ev[0])
+        for (int i = 0; i <= REG_MAX_LEVELS; i++)
+            CK(cudaEventCreate(&c->lev_ev[i]));
     for (int l = start; l >= 0; l--) {
         const Level &L = c->L[l];
+        CK(cudaEventRecord(c->lev_ev[l + 1], c->stream));
         if (l < start) {
             CK(launch_prolong(c->L[l + 1], L, b.u, b.g, c->stream));
             c->launches += 1;
@@ -607,9 +647,15 @@ int reg_register(reg_handle c, float *u_out, int out_is_device, const float *u_i
             local.S_final = sh->S;
         }
     }
+    CK(cudaEventRecord(c->lev_ev[0], c->stream));
     CK(cudaMemcpyAsync(u_out, b.u, sizeof(float) * 3 * c->L[0].nn,
                        out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    for (int l = start; l >= 0; l--) {   // level l ran from event l + 1 to event l
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->lev_ev[l + 1], c->lev_ev[l]));
+        local.level_seconds[l] = 1e-3 * ms;
+    }
     local.status = status;
     local.kernel_launches = c->launches - launches0;
     local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -623,7 +669,11 @@ int reg_destroy(reg_handle c)
     if (!c) return REG_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_buffers(c);
+    for (int i = 0; i <= REG_MAX_LEVELS; i++)
+        if (c->lev_ev[i]) cudaEventDestroy(c->lev_ev[i]);
     if (c->ev_side) cudaEventDestroy(c->ev_side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

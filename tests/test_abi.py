@@ -36,13 +36,15 @@ def test_config_default_and_version(libreg):
     assert cfg.tau == 0.01 and cfg.rho == 0.01 and cfg.alpha == 10.0
     assert cfg.lbfgs_mem == 5 and cfg.max_backtracks == 20 and cfg.levels == 1
     assert list(cfg.max_iter) == [50] * 8 and cfg.start_level == -1
+    assert cfg.autotune == 1 and cfg.fused_tz == 0 and cfg.use_graph == 1 and cfg.image_dtype == 0
     assert libreg.reg_version() >= 10000
     assert ctypes.sizeof(libreg.RegConfig) == 8 * 6 + 4 * 6 + 4 * 8 + 4 * 24 + 4 * 8
 
 
 def test_create_rejects_bad_config_before_touching_the_gpu(libreg):
     for field, value in (("levels", 0), ("levels", 9), ("lbfgs_mem", 0), ("tau", 0.0), ("c1", 1.5),
-                         ("max_backtracks", 0), ("eval_impl", 7)):
+                         ("max_backtracks", 0), ("eval_impl", 7), ("autotune", 2), ("fused_tz", 6),
+                         ("fused_tz", 256), ("fused_tz", -2)):
         cfg = libreg.reg_config_default()
         setattr(cfg, field, value)
         with pytest.raises(libreg.RegError) as ei:

@@ -259,3 +259,39 @@ def test_bf16_image_storage(reg_mod, orc, config_id):
     assert e_kernel["eJ"] <= J_RTOL and e_kernel["eg"] <= GRAD_RTOL, e_kernel
     assert e_store["eJ"] <= 1e-2 and e_store["eg"] <= 0.2, e_store
     r.close()
+
+
+TZ_CANDIDATES = [2, 4, 8, 16, 32, 64, 128]
+
+
+@pytest.mark.parametrize("tz", TZ_CANDIDATES)
+def test_every_fused_tile_depth_matches_oracle(reg_mod, orc, tz):
+    # every z segment length the autotuner may pick: ragged segments, segments
+    # longer than the image, tiles sharing node planes in z
+    dims, h, tau, rho, alpha = (58, 38, 70), (1.2, 0.8, 1.0), 0.05, 0.03, 2.0
+    R = random_image(dims, 71)
+    T = random_image(dims, 72)
+    cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=tz)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    z, tiles = r.level_tiling(0)
+    assert z == tz and tiles == 3 * 4 * -(-dims[2] // tz)
+    u = random_field(r.level_info(0)["nodes"], 73, 2.5)
+    e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
+    assert e["eJ"] <= J_RTOL and e["eg"] <= GRAD_RTOL, e
+    r.close()
+
+
+def test_autotuned_tiling_is_cached_per_geometry(reg_mod):
+    dims, h = (96, 80, 64), (1.0, 1.0, 1.0)
+    R = random_image(dims, 81)
+    cfg = reg_mod.make_config(levels=3, tau=0.05, alpha=1.0)
+    r1 = reg_mod.Registration(cfg).set_images(R, R, h)
+    r2 = reg_mod.Registration(cfg).set_images(R, R, h)
+    for lv in range(3):
+        t1, t2 = r1.level_tiling(lv), r2.level_tiling(lv)
+        assert t1 == t2 and t1[0] in TZ_CANDIDATES and t1[1] > 0
+    off = reg_mod.Registration(reg_mod.make_config(levels=3, tau=0.05, alpha=1.0, autotune=False))
+    off.set_images(R, R, h)
+    assert all(off.level_tiling(lv)[0] in (8, 16, 32, 64, 128) for lv in range(3))
+    for r in (r1, r2, off):
+        r.close()
