@@ -28,8 +28,9 @@
  * the current CUDA device; host pointers plain host memory.
  *
  * Threads and streams: a handle is not thread-safe; all its GPU work is queued
- * on the stream given to reg_create plus one internal side stream for the
- * template pyramid (joined back with an event).  Calls that return host values
+ * on the stream given to reg_create plus one internal side stream (the template
+ * pyramid, and the curvature pass that runs beside the NGF pass), forked from
+ * and joined back to that stream with events.  Calls that return host values
  * synchronise that stream.
  */
 #ifndef REG_H
