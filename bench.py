@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--host-loop", action="store_true",
                     help="queue every L-BFGS step from the host instead of one graph per level (the same kernels "
                          "in the same order; ncu cannot list kernels inside graphs with conditional nodes)")
+    ap.add_argument("--fused-tz", type=int, default=None,
+                    help="force the fused pass's z segment length (no autotuning launches; for profiling)")
     ap.add_argument("--pairs", type=int, default=None, help="pairs of the uneven batch (workload 4; default 64)")
     ap.add_argument("--gen-procs", type=int, default=None, help="processes that generate the batch's pairs")
     return ap.parse_args(argv)
@@ -231,6 +233,8 @@ def run_ours(args):
         kw["eval_impl"] = args.eval_impl
     if args.host_loop:
         kw["use_graph"] = False
+    if args.fused_tz is not None:
+        kw["fused_tz"] = args.fused_tz
     cfg = reg_pkg.make_config(**kw)
     stream = torch.cuda.current_stream(dev)
     reg = reg_pkg.Registration(cfg, stream=stream)

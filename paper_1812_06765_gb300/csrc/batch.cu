@@ -74,6 +74,8 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     P.P = c->lb.P;
     P.Y = c->lb.Y;
     P.lpart = c->lb.partials;
+    P.lgpart = c->lb.gpart;
+    P.lcnt = c->lb.cnt;
     P.nchunks = num_blocks_for(c, (P.n + 3) / 4, LB_VT);
 }
 
@@ -280,8 +282,10 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     CK(cudaMallocAsync((void **)&d.off, sizeof(int) * 4 * (n + 1), s));
     CK(cudaMallocAsync((void **)&d.counters, sizeof(int) * 2, s));
     // every pair's own stream work (prolongations, state uploads) is ordered on c0's stream
-    for (int i = 0; i < n; i++)
+    for (int i = 0; i < n; i++) {
         CK(cudaMemsetAsync(hs[i]->lb.u, 0, sizeof(float) * 3 * hs[i]->L[start].nn, s));
+        CK(cudaMemsetAsync(hs[i]->lb.cnt, 0, sizeof(unsigned) * hs[i]->lb.cnt_len, s));
+    }
     long long launches = 0;
     int status = REG_OK;
     std::vector<PairLevel> hpl(n);

@@ -34,6 +34,8 @@ struct PairLevel {
     long long n, stride;    // vector length, ring slot stride
     float *u, *g, *gt, *pdir, *P, *Y;
     double *lpart;          // vector-pass block partials
+    double *lgpart;         // their group sums
+    unsigned *lcnt;         // arrival counters of the groups
     int nchunks;            // blocks of the vector passes
     int tz, ntx, nty;       // fused tiling (also inside fa_*)
     int ncx, ncy;           // curvature / gather blocks along x and y (32 x 8 nodes each)

@@ -96,3 +96,34 @@ struct KahanF {
         s = t;
     }
 };
+
+// Deterministic FP64 sum of block partials (fixed thread-to-partial
+// assignment, fixed tree): scal = [J, D, S].
+__device__ __forceinline__ void finalize_body(const double *__restrict__ pD, int nD, const double *__restrict__ pS,
+                                              int nS, double hbar_half, double alpha, double hy_half,
+                                              double *__restrict__ scal)
+{
+    __shared__ double sd[512], ss[512];
+    int t = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = t; i < nD; i += 512)
+        a += pD[i];
+    for (int i = t; i < nS; i += 512)
+        b += pS[i];
+    sd[t] = a;
+    ss[t] = b;
+    __syncthreads();
+    for (int o = 256; o > 0; o >>= 1) {
+        if (t < o) {
+            sd[t] += sd[t + o];
+            ss[t] += ss[t + o];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double D = hbar_half * sd[0], S = hy_half * ss[0];
+        scal[0] = D + alpha * S;
+        scal[1] = D;
+        scal[2] = S;
+    }
+}

@@ -1,14 +1,15 @@
 // One pyramid level of L-BFGS as one CUDA graph launch.
 //
-//   init: objective at u0, ||g||, ||g||_inf, control(INIT)  -> sets the iteration condition
+//   init: objective at u0; ||g||, ||g||_inf + control(INIT)      -> sets the iteration condition
 //   WHILE (iteration condition)
-//       direction (+ a p0 redo when the compact-form direction is not a descent direction)
+//       direction + control(DIR); p0 redo + control(DIR_REDO)      -> set the line-search condition
 //       WHILE (line-search condition)
-//           objective at u + t p, control(ARMIJO)              -> sets the line-search condition
-//       accept (no-op unless accepted), control(ACCEPTED)      -> sets the iteration condition
+//           objective at u + t p; its final reduction + control(ARMIJO)
+//       accept (no-op unless accepted) + control(ACCEPTED)        -> sets the iteration condition
 //
-// The conditions are set on the device by the FP64 control kernel, so a whole
-// level runs without a host round trip.  Termination does not depend on the
+// Each control phase runs in FP64 in the last block of the kernel before it
+// (the block that completes that kernel's cross-block reduction), so a level
+// runs without a host round trip and without separate control launches.  Termination does not depend on the
 // host: every search ends after max_backtracks trials and the control kernel
 // ends the level after max_iter accepted steps, a failed search, a non-finite
 // value, or (a bound that should never bind) 2 max_iter + 8 loop bodies.

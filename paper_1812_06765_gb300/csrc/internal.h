@@ -53,6 +53,9 @@ struct LbfgsBuffers {
     float *P = nullptr, *Y = nullptr;   // slots * n each
     double *partials = nullptr;
     int max_partials = 0;
+    double *gpart = nullptr;            // group sums of the vector passes' block partials
+    unsigned *cnt = nullptr;            // their arrival counters
+    int cnt_len = 0;
     LbfgsState *st = nullptr;           // device
     LbfgsState *st_host = nullptr;      // pinned mirror
     double *scal_t = nullptr;           // [J, D, S] of the trial point
@@ -105,8 +108,11 @@ cudaError_t launch_prolong(const Level &coarse, const Level &fine, const float *
 // objective + gradient at u_base + t_scale * dir (dir may be NULL: plain u_base);
 // t_scale is read on the device from *t_dev when dir != NULL.
 // Writes grad (3 node planes) and scal_out[0..2] = J, D, S (device).
+// ctl_phase >= 0: the final reduction also runs that L-BFGS control phase.
 cudaError_t launch_eval(reg_ctx *c, int level, const float *u_base, const float *dir, const double *t_dev,
-                        float *grad, double *scal_out, cudaStream_t s);
+                        float *grad, double *scal_out, int ctl_phase, cudaStream_t s);
+cudaError_t launch_finalize_ctl(reg_ctx *c, const double *pD, int nD, const double *pS, int nS, double hbar_half,
+                                double alpha, double hy_half, double *scal, int phase, cudaStream_t s);
 
 // L-BFGS device steps (k_lbfgs.cu)
 cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s);

@@ -86,37 +86,6 @@ __global__ void __launch_bounds__(256) k_curv_grad(LevelGeom g, const float *__r
     }
 }
 
-// Deterministic FP64 sum of block partials (fixed thread-to-partial
-// assignment, fixed tree): scal = [J, D, S].
-__device__ __forceinline__ void finalize_body(const double *__restrict__ pD, int nD, const double *__restrict__ pS,
-                                              int nS, double hbar_half, double alpha, double hy_half,
-                                              double *__restrict__ scal)
-{
-    __shared__ double sd[512], ss[512];
-    int t = threadIdx.x;
-    double a = 0.0, b = 0.0;
-    for (int i = t; i < nD; i += 512)
-        a += pD[i];
-    for (int i = t; i < nS; i += 512)
-        b += pS[i];
-    sd[t] = a;
-    ss[t] = b;
-    __syncthreads();
-    for (int o = 256; o > 0; o >>= 1) {
-        if (t < o) {
-            sd[t] += sd[t + o];
-            ss[t] += ss[t + o];
-        }
-        __syncthreads();
-    }
-    if (t == 0) {
-        double D = hbar_half * sd[0], S = hy_half * ss[0];
-        scal[0] = D + alpha * S;
-        scal[1] = D;
-        scal[2] = S;
-    }
-}
-
 __global__ void __launch_bounds__(512) k_finalize(const double *__restrict__ pD, int nD,
                                                   const double *__restrict__ pS, int nS, double hbar_half,
                                                   double alpha, double hy_half, double *__restrict__ scal)
@@ -171,7 +140,7 @@ cudaError_t launch_finalize_batch(const PairLevel *pl, int npairs, int mode, cud
 }
 
 cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev, float *grad,
-                        double *scal_out, cudaStream_t s)
+                        double *scal_out, int ctl_phase, cudaStream_t s)
 {
     const Level &L = c->L[level];
     LevelGeom g = L.geom();
@@ -216,8 +185,11 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     }
     int nS = (int)(gw.x * gw.y * gw.z);
     double hbar = L.h[0] * L.h[1] * L.h[2];
-    k_finalize<<<1, 512, 0, s>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out);
     c->launches += 2;
+    if (ctl_phase >= 0)   // the reduction block also takes the line-search decision
+        return launch_finalize_ctl(c, c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out,
+                                   ctl_phase, s);
+    k_finalize<<<1, 512, 0, s>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out);
     return cudaGetLastError();
 }
 

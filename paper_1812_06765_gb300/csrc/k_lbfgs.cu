@@ -48,6 +48,49 @@ __device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, dou
     }
 }
 
+__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
+                                                const double *__restrict__ partials, int nblocks,
+                                                const double *__restrict__ scal, unsigned long long h_ls,
+                                                unsigned long long h_iter);
+
+// Called by every block of a vector pass after block_reduce_write (see VecTail).
+__device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restrict__ partials, int nd, int imax,
+                                         int bx, int nblocks)
+{
+    __shared__ int s_last;
+    __threadfence();   // this block's partials, before its arrival is counted
+    __syncthreads();
+    const int g = bx / LB_RG, g0 = g * LB_RG, gs = min(LB_RG, nblocks - g0);
+    const int ng = (nblocks + LB_RG - 1) / LB_RG;
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(&t.cnt[g], 1u) == (unsigned)(gs - 1);
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        double s = 0.0;   // the max entry is a max of absolute values: 0 is its identity
+        for (int k = 0; k < gs; k++) {
+            const double x = __ldcg(partials + (size_t)(g0 + k) * nd + d);
+            s = (d == imax) ? fmax(s, x) : s + x;
+        }
+        t.gpart[(size_t)g * nd + d] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t.cnt[g] = 0;
+        s_last = atomicAdd(&t.cnt[ng], 1u) == (unsigned)(ng - 1);
+        if (s_last)
+            t.cnt[ng] = 0;
+    }
+    __syncthreads();
+    if (!s_last || t.phase < 0)
+        return;
+    __threadfence();
+    lb_control_body(t.phase, t.st, t.gpart, ng, t.scal, t.h_ls, t.h_iter);
+}
+
 // All vector passes read and write 16-byte vectors: u, g, gt and pdir are
 // separate allocations and the P / Y ring slots sit at a stride that is a
 // multiple of 4 floats.  The n % 4 tail is done by the first threads of block 0.
@@ -58,7 +101,8 @@ __device__ __forceinline__ float max4(float4 a)
 }
 
 __device__ __forceinline__ void lb_init_dots_body(long long n, const float *__restrict__ g,
-                                                     double *__restrict__ partials, int bx, int gdx)
+                                                     double *__restrict__ partials, const VecTail &tail, int bx,
+                                                     int gdx)
 {
     float v[2] = {0.f, 0.f};
     const long long n4 = n >> 2;
@@ -74,19 +118,21 @@ __device__ __forceinline__ void lb_init_dots_body(long long n, const float *__re
         v[1] = fmaxf(v[1], fabsf(x));
     }
     block_reduce_write<2>(v, 1, partials + 2 * bx);
+    vec_tail(tail, partials, 2, 1, bx, gdx);
 }
 
 __global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *__restrict__ g,
-                                                     double *__restrict__ partials)
+                                                     double *__restrict__ partials, VecTail tail)
 {
-    lb_init_dots_body(n, g, partials, blockIdx.x, gridDim.x);
+    lb_init_dots_body(n, g, partials, tail, blockIdx.x, gridDim.x);
 }
 
 // p = cg g + sum_j cp_j P_j + cy_j Y_j, written to pdir; partial sums of g'p and p'p.
-__device__ __forceinline__ void lb_direction_body(long long n, long long stride, const LbfgsState *__restrict__ st,
+__device__ __forceinline__ void lb_direction_body(long long n, long long stride, const LbfgsState *st,
                                                      const float *__restrict__ g, const float *__restrict__ P,
                                                      const float *__restrict__ Y, float *__restrict__ pdir,
-                                                     double *__restrict__ partials, int redo, int bx, int gdx)
+                                                     double *__restrict__ partials, int redo, const VecTail &tail,
+                                                     int bx, int gdx)
 {
     __shared__ int s_run, s_dc, s_slot[LB_MAXM];
     __shared__ float s_cg, s_cp[LB_MAXM], s_cy[LB_MAXM];
@@ -101,60 +147,61 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
         }
     }
     __syncthreads();
-    if (!s_run)
-        return;
-    const int dc = s_dc;
-    const float cg = s_cg;
-    const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
-    float cp[LB_MAXM], cy[LB_MAXM];
-#pragma unroll
-    for (int j = 0; j < LB_MAXM; j++) {
-        const int sl = j < dc ? s_slot[j] : 0;
-        Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
-        Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
-        cp[j] = s_cp[j];
-        cy[j] = s_cy[j];
-    }
     float v[2] = {0.f, 0.f};
-    const long long n4 = n >> 2;
-    const float4 *g4 = reinterpret_cast<const float4 *>(g);
-    float4 *p4 = reinterpret_cast<float4 *>(pdir);
-    for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
-        float4 gv = g4[e];
-        float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
+    if (s_run) {   // otherwise only the arrival below (partials unused)
+        const int dc = s_dc;
+        const float cg = s_cg;
+        const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
+        float cp[LB_MAXM], cy[LB_MAXM];
 #pragma unroll
-        for (int j = 0; j < LB_MAXM; j++)
-            if (j < dc) {
-                float4 a = Pj[j][e], b = Yj[j][e];
-                p.x = fmaf(cp[j], a.x, fmaf(cy[j], b.x, p.x));
-                p.y = fmaf(cp[j], a.y, fmaf(cy[j], b.y, p.y));
-                p.z = fmaf(cp[j], a.z, fmaf(cy[j], b.z, p.z));
-                p.w = fmaf(cp[j], a.w, fmaf(cy[j], b.w, p.w));
-            }
-        p4[e] = p;
-        v[0] += dot4(gv, p);
-        v[1] += dot4(p, p);
-    }
-    if (bx == 0 && threadIdx.x < (n & 3)) {
-        const long long e = 4 * n4 + threadIdx.x;
-        float gv = g[e], p = cg * gv;
+        for (int j = 0; j < LB_MAXM; j++) {
+            const int sl = j < dc ? s_slot[j] : 0;
+            Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
+            Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
+            cp[j] = s_cp[j];
+            cy[j] = s_cy[j];
+        }
+        const long long n4 = n >> 2;
+        const float4 *g4 = reinterpret_cast<const float4 *>(g);
+        float4 *p4 = reinterpret_cast<float4 *>(pdir);
+        for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
+            float4 gv = g4[e];
+            float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
 #pragma unroll
-        for (int j = 0; j < LB_MAXM; j++)
-            if (j < dc)
-                p = fmaf(cp[j], P[(size_t)s_slot[j] * stride + e], fmaf(cy[j], Y[(size_t)s_slot[j] * stride + e], p));
-        pdir[e] = p;
-        v[0] = fmaf(gv, p, v[0]);
-        v[1] = fmaf(p, p, v[1]);
+            for (int j = 0; j < LB_MAXM; j++)
+                if (j < dc) {
+                    float4 a = Pj[j][e], b = Yj[j][e];
+                    p.x = fmaf(cp[j], a.x, fmaf(cy[j], b.x, p.x));
+                    p.y = fmaf(cp[j], a.y, fmaf(cy[j], b.y, p.y));
+                    p.z = fmaf(cp[j], a.z, fmaf(cy[j], b.z, p.z));
+                    p.w = fmaf(cp[j], a.w, fmaf(cy[j], b.w, p.w));
+                }
+            p4[e] = p;
+            v[0] += dot4(gv, p);
+            v[1] += dot4(p, p);
+        }
+        if (bx == 0 && threadIdx.x < (n & 3)) {
+            const long long e = 4 * n4 + threadIdx.x;
+            float gv = g[e], p = cg * gv;
+#pragma unroll
+            for (int j = 0; j < LB_MAXM; j++)
+                if (j < dc)
+                    p = fmaf(cp[j], P[(size_t)s_slot[j] * stride + e], fmaf(cy[j], Y[(size_t)s_slot[j] * stride + e], p));
+            pdir[e] = p;
+            v[0] = fmaf(gv, p, v[0]);
+            v[1] = fmaf(p, p, v[1]);
+        }
     }
     block_reduce_write<2>(v, -1, partials + 2 * bx);
+    vec_tail(tail, partials, 2, -1, bx, gdx);
 }
 
-__global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stride, const LbfgsState *__restrict__ st,
+__global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stride, const LbfgsState *st,
                                                      const float *__restrict__ g, const float *__restrict__ P,
                                                      const float *__restrict__ Y, float *__restrict__ pdir,
-                                                     double *__restrict__ partials, int redo)
+                                                     double *__restrict__ partials, int redo, VecTail tail)
 {
-    lb_direction_body(n, stride, st, g, P, Y, pdir, partials, redo, blockIdx.x, gridDim.x);
+    lb_direction_body(n, stride, st, g, P, Y, pdir, partials, redo, tail, blockIdx.x, gridDim.x);
 }
 
 // Accept the trial point: u += t pdir (the fmaf the evaluation used), store the
@@ -168,11 +215,12 @@ __device__ __forceinline__ void accept_elem(float gn, float go, float pf, float 
     u = fmaf(t, pf, u);
 }
 
-__device__ __forceinline__ void lb_accept_body(long long n, long long stride, const LbfgsState *__restrict__ st,
+__device__ __forceinline__ void lb_accept_body(long long n, long long stride, const LbfgsState *st,
                                                   float *__restrict__ u, float *__restrict__ g,
                                                   const float *__restrict__ gt, const float *__restrict__ pdir,
                                                   float *__restrict__ P, float *__restrict__ Y,
-                                                  double *__restrict__ partials, int bx, int gdx)
+                                                  double *__restrict__ partials, const VecTail &tail, int bx,
+                                                  int gdx)
 {
     __shared__ int s_ok, s_lc, s_free, s_slot[LB_MAXS];
     __shared__ float s_t;
@@ -185,98 +233,99 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
             s_slot[j] = st->lslot[j];
     }
     __syncthreads();
-    if (!s_ok)
-        return;
-    const int np = s_lc - 1;    // stored pairs before the free slot
-    const float t = s_t;
-    const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
-#pragma unroll
-    for (int j = 0; j < LB_MAXM; j++) {
-        const int sl = j < np ? s_slot[j] : 0;
-        Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
-        Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
-    }
-    float *Pf = P + (size_t)s_free * stride;
-    float *Yf = Y + (size_t)s_free * stride;
     float v[ND_ACC];
 #pragma unroll
     for (int d = 0; d < ND_ACC; d++)
         v[d] = 0.f;
-    float fr[4] = {0.f, 0.f, 0.f, 0.f};   // dots of the free slot (p, y_new) with g_new, y_new
-    const long long n4 = n >> 2;
-    for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
-        float4 gn = reinterpret_cast<const float4 *>(gt)[e];
-        float4 go = reinterpret_cast<float4 *>(g)[e];
-        float4 pf = reinterpret_cast<const float4 *>(pdir)[e];
-        float4 uu = reinterpret_cast<float4 *>(u)[e];
-        float4 yn;
-        accept_elem(gn.x, go.x, pf.x, uu.x, t, yn.x);
-        accept_elem(gn.y, go.y, pf.y, uu.y, t, yn.y);
-        accept_elem(gn.z, go.z, pf.z, uu.z, t, yn.z);
-        accept_elem(gn.w, go.w, pf.w, uu.w, t, yn.w);
-        reinterpret_cast<float4 *>(u)[e] = uu;
-        reinterpret_cast<float4 *>(g)[e] = gn;
-        reinterpret_cast<float4 *>(Pf)[e] = pf;
-        reinterpret_cast<float4 *>(Yf)[e] = yn;
-        v[0] += dot4(gn, gn);
-        v[1] = fmaxf(v[1], max4(gn));
+    if (s_ok) {   // otherwise only the arrival below (partials unused)
+        const int np = s_lc - 1;    // stored pairs before the free slot
+        const float t = s_t;
+        const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
 #pragma unroll
-        for (int j = 0; j < LB_MAXM; j++)
-            if (j < np) {
-                float4 pj = Pj[j][e], yj = Yj[j][e];
-                v[2 + 4 * j] += dot4(pj, gn);
-                v[3 + 4 * j] += dot4(yj, gn);
-                v[4 + 4 * j] += dot4(pj, yn);
-                v[5 + 4 * j] += dot4(yj, yn);
-            }
-        fr[0] += dot4(pf, gn);
-        fr[1] += dot4(yn, gn);
-        fr[2] += dot4(pf, yn);
-        fr[3] += dot4(yn, yn);
-    }
-    if (bx == 0 && threadIdx.x < (n & 3)) {
-        const long long e = 4 * n4 + threadIdx.x;
-        float gn = gt[e], go = g[e], pf = pdir[e], uu = u[e], yn;
-        accept_elem(gn, go, pf, uu, t, yn);
-        u[e] = uu;
-        g[e] = gn;
-        Pf[e] = pf;
-        Yf[e] = yn;
-        v[0] = fmaf(gn, gn, v[0]);
-        v[1] = fmaxf(v[1], fabsf(gn));
-#pragma unroll
-        for (int j = 0; j < LB_MAXM; j++)
-            if (j < np) {   // unrolled with a predicate so that v stays in registers
-                float pj = P[(size_t)s_slot[j] * stride + e], yj = Y[(size_t)s_slot[j] * stride + e];
-                v[2 + 4 * j] = fmaf(pj, gn, v[2 + 4 * j]);
-                v[3 + 4 * j] = fmaf(yj, gn, v[3 + 4 * j]);
-                v[4 + 4 * j] = fmaf(pj, yn, v[4 + 4 * j]);
-                v[5 + 4 * j] = fmaf(yj, yn, v[5 + 4 * j]);
-            }
-        fr[0] = fmaf(pf, gn, fr[0]);
-        fr[1] = fmaf(yn, gn, fr[1]);
-        fr[2] = fmaf(pf, yn, fr[2]);
-        fr[3] = fmaf(yn, yn, fr[3]);
-    }
-    // the free slot is list position np
-#pragma unroll
-    for (int j = 0; j < LB_MAXS; j++)
-        if (j == np) {
-            v[2 + 4 * j] += fr[0];
-            v[3 + 4 * j] += fr[1];
-            v[4 + 4 * j] += fr[2];
-            v[5 + 4 * j] += fr[3];
+        for (int j = 0; j < LB_MAXM; j++) {
+            const int sl = j < np ? s_slot[j] : 0;
+            Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
+            Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
         }
+        float *Pf = P + (size_t)s_free * stride;
+        float *Yf = Y + (size_t)s_free * stride;
+        float fr[4] = {0.f, 0.f, 0.f, 0.f};   // dots of the free slot (p, y_new) with g_new, y_new
+        const long long n4 = n >> 2;
+        for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
+            float4 gn = reinterpret_cast<const float4 *>(gt)[e];
+            float4 go = reinterpret_cast<float4 *>(g)[e];
+            float4 pf = reinterpret_cast<const float4 *>(pdir)[e];
+            float4 uu = reinterpret_cast<float4 *>(u)[e];
+            float4 yn;
+            accept_elem(gn.x, go.x, pf.x, uu.x, t, yn.x);
+            accept_elem(gn.y, go.y, pf.y, uu.y, t, yn.y);
+            accept_elem(gn.z, go.z, pf.z, uu.z, t, yn.z);
+            accept_elem(gn.w, go.w, pf.w, uu.w, t, yn.w);
+            reinterpret_cast<float4 *>(u)[e] = uu;
+            reinterpret_cast<float4 *>(g)[e] = gn;
+            reinterpret_cast<float4 *>(Pf)[e] = pf;
+            reinterpret_cast<float4 *>(Yf)[e] = yn;
+            v[0] += dot4(gn, gn);
+            v[1] = fmaxf(v[1], max4(gn));
+#pragma unroll
+            for (int j = 0; j < LB_MAXM; j++)
+                if (j < np) {
+                    float4 pj = Pj[j][e], yj = Yj[j][e];
+                    v[2 + 4 * j] += dot4(pj, gn);
+                    v[3 + 4 * j] += dot4(yj, gn);
+                    v[4 + 4 * j] += dot4(pj, yn);
+                    v[5 + 4 * j] += dot4(yj, yn);
+                }
+            fr[0] += dot4(pf, gn);
+            fr[1] += dot4(yn, gn);
+            fr[2] += dot4(pf, yn);
+            fr[3] += dot4(yn, yn);
+        }
+        if (bx == 0 && threadIdx.x < (n & 3)) {
+            const long long e = 4 * n4 + threadIdx.x;
+            float gn = gt[e], go = g[e], pf = pdir[e], uu = u[e], yn;
+            accept_elem(gn, go, pf, uu, t, yn);
+            u[e] = uu;
+            g[e] = gn;
+            Pf[e] = pf;
+            Yf[e] = yn;
+            v[0] = fmaf(gn, gn, v[0]);
+            v[1] = fmaxf(v[1], fabsf(gn));
+#pragma unroll
+            for (int j = 0; j < LB_MAXM; j++)
+                if (j < np) {   // unrolled with a predicate so that v stays in registers
+                    float pj = P[(size_t)s_slot[j] * stride + e], yj = Y[(size_t)s_slot[j] * stride + e];
+                    v[2 + 4 * j] = fmaf(pj, gn, v[2 + 4 * j]);
+                    v[3 + 4 * j] = fmaf(yj, gn, v[3 + 4 * j]);
+                    v[4 + 4 * j] = fmaf(pj, yn, v[4 + 4 * j]);
+                    v[5 + 4 * j] = fmaf(yj, yn, v[5 + 4 * j]);
+                }
+            fr[0] = fmaf(pf, gn, fr[0]);
+            fr[1] = fmaf(yn, gn, fr[1]);
+            fr[2] = fmaf(pf, yn, fr[2]);
+            fr[3] = fmaf(yn, yn, fr[3]);
+        }
+        // the free slot is list position np
+#pragma unroll
+        for (int j = 0; j < LB_MAXS; j++)
+            if (j == np) {
+                v[2 + 4 * j] += fr[0];
+                v[3 + 4 * j] += fr[1];
+                v[4 + 4 * j] += fr[2];
+                v[5 + 4 * j] += fr[3];
+            }
+    }
     block_reduce_write<ND_ACC>(v, 1, partials + (size_t)ND_ACC * bx);
+    vec_tail(tail, partials, ND_ACC, 1, bx, gdx);
 }
 
-__global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride, const LbfgsState *__restrict__ st,
+__global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride, const LbfgsState *st,
                                                   float *__restrict__ u, float *__restrict__ g,
                                                   const float *__restrict__ gt, const float *__restrict__ pdir,
                                                   float *__restrict__ P, float *__restrict__ Y,
-                                                  double *__restrict__ partials)
+                                                  double *__restrict__ partials, VecTail tail)
 {
-    lb_accept_body(n, stride, st, u, g, gt, pdir, P, Y, partials, blockIdx.x, gridDim.x);
+    lb_accept_body(n, stride, st, u, g, gt, pdir, P, Y, partials, tail, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -380,7 +429,7 @@ __device__ __forceinline__ void control_reduce(const double *__restrict__ partia
     __syncthreads();
 }
 
-__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restrict__ gst,
+__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
                                                     const double *__restrict__ partials, int nblocks,
                                                     const double *__restrict__ scal, unsigned long long h_ls,
                                                     unsigned long long h_iter)
@@ -620,12 +669,18 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *__restric
         reinterpret_cast<int *>(gst)[i] = reinterpret_cast<const int *>(&S)[i];
 }
 
-__global__ void __launch_bounds__(CT) k_lb_control(int phase, LbfgsState *__restrict__ gst,
-                                                    const double *__restrict__ partials, int nblocks,
-                                                    const double *__restrict__ scal, unsigned long long h_ls,
-                                                    unsigned long long h_iter)
+// Reduction of an objective evaluation's block partials (J, D, S into scal)
+// followed, in the same block, by a control phase on those scalars (ARMIJO
+// after a trial evaluation).
+__global__ void __launch_bounds__(512) k_finalize_ctl(const double *__restrict__ pD, int nD,
+                                                      const double *__restrict__ pS, int nS, double hbar_half,
+                                                      double alpha, double hy_half, double *scal, int phase,
+                                                      LbfgsState *st, unsigned long long h_ls,
+                                                      unsigned long long h_iter)
 {
-    lb_control_body(phase, gst, partials, nblocks, scal, h_ls, h_iter);
+    finalize_body(pD, nD, pS, nS, hbar_half, alpha, hy_half, scal);
+    __syncthreads();
+    lb_control_body(phase, st, nullptr, 0, scal, h_ls, h_iter);
 }
 
 // ---------------------------------------------------------------------------
@@ -641,12 +696,13 @@ __global__ void __launch_bounds__(VT) k_lb_vector_batch(const PairLevel *__restr
         const int p = find_pair(chunk_off, npairs, item);
         const PairLevel &P = pl[p];
         const int b = item - __ldg(chunk_off + p);
+        const VecTail tail{P.lgpart, P.lcnt, -1, P.st, nullptr, 0ULL, 0ULL};   // control: its own kernel
         if (step == 0)
-            lb_init_dots_body(P.n, P.g, P.lpart, b, P.nchunks);
+            lb_init_dots_body(P.n, P.g, P.lpart, tail, b, P.nchunks);
         else if (step == 1 || step == 2)
-            lb_direction_body(P.n, P.stride, P.st, P.g, P.P, P.Y, P.pdir, P.lpart, step == 2, b, P.nchunks);
+            lb_direction_body(P.n, P.stride, P.st, P.g, P.P, P.Y, P.pdir, P.lpart, step == 2, tail, b, P.nchunks);
         else
-            lb_accept_body(P.n, P.stride, P.st, P.u, P.g, P.gt, P.pdir, P.P, P.Y, P.lpart, b, P.nchunks);
+            lb_accept_body(P.n, P.stride, P.st, P.u, P.g, P.gt, P.pdir, P.P, P.Y, P.lpart, tail, b, P.nchunks);
         __syncthreads();   // the next item reuses the block's shared staging
     }
 }
@@ -656,7 +712,8 @@ __global__ void __launch_bounds__(VT) k_lb_vector_batch(const PairLevel *__restr
 __global__ void __launch_bounds__(CT) k_lb_control_batch(const PairLevel *__restrict__ pl, int phase)
 {
     const PairLevel &P = pl[blockIdx.x];
-    lb_control_body(phase, P.st, P.lpart, P.nchunks, phase == LB_INIT ? P.scal : P.scal_t, 0ULL, 0ULL);
+    lb_control_body(phase, P.st, P.lgpart, (P.nchunks + LB_RG - 1) / LB_RG, phase == LB_INIT ? P.scal : P.scal_t,
+                    0ULL, 0ULL);
 }
 
 // condition of a batched loop: 1 while any pair still iterates (which = 0) or
@@ -816,13 +873,12 @@ void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter)
     g_h_iter = h_iter;
 }
 
-static cudaError_t control(reg_ctx *c, int phase, int nblocks, const double *scal, cudaStream_t s,
-                           bool use_ls_handle, bool use_iter_handle)
+// folded reduction + control of a vector pass (handles: the graph conditions
+// the phase sets while a level graph is captured)
+static VecTail tail_of(reg_ctx *c, int phase, const double *scal, bool use_ls_handle, bool use_iter_handle)
 {
-    k_lb_control<<<1, CT, 0, s>>>(phase, c->lb.st, c->lb.partials, nblocks, scal, use_ls_handle ? g_h_ls : 0ULL,
-                                   use_iter_handle ? g_h_iter : 0ULL);
-    c->launches += 1;
-    return cudaGetLastError();
+    return VecTail{c->lb.gpart, c->lb.cnt, phase, c->lb.st, scal, use_ls_handle ? g_h_ls : 0ULL,
+                   use_iter_handle ? g_h_iter : 0ULL};
 }
 
 // ring slots start on 16-byte boundaries
@@ -832,34 +888,38 @@ cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s)
 {
     long long n = 3 * c->L[level].nn;
     int nb = num_blocks_for(c, (n + 3) / 4, VT);
-    cudaError_t e = launch_eval(c, level, c->lb.u, nullptr, nullptr, c->lb.g, c->es.scal, s);
+    // arrival counters start the level at zero (every launch leaves them so)
+    cudaError_t e = cudaMemsetAsync(c->lb.cnt, 0, sizeof(unsigned) * c->lb.cnt_len, s);
+    if (e == cudaSuccess)
+        e = launch_eval(c, level, c->lb.u, nullptr, nullptr, c->lb.g, c->es.scal, -1, s);
     if (e != cudaSuccess)
         return e;
-    k_lb_init_dots<<<nb, VT, 0, s>>>(n, c->lb.g, c->lb.partials);
+    k_lb_init_dots<<<nb, VT, 0, s>>>(n, c->lb.g, c->lb.partials, tail_of(c, LB_INIT, c->es.scal, false, true));
     c->launches += 1;
-    return control(c, LB_INIT, nb, c->es.scal, s, false, true);
+    return cudaGetLastError();
 }
 
 cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s)
 {
     long long n = 3 * c->L[level].nn, sd = ring_stride(n);
     int nb = num_blocks_for(c, (n + 3) / 4, VT);
-    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0);
-    c->launches += 2;
-    cudaError_t e = control(c, LB_DIR, nb, nullptr, s, true, false);
+    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0,
+                                     tail_of(c, LB_DIR, nullptr, true, false));
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1);
-    return control(c, LB_DIR_REDO, nb, nullptr, s, true, false);
+    // the p0 redo (a no-op pass unless the direction was not a descent direction)
+    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1,
+                                     tail_of(c, LB_DIR_REDO, nullptr, true, false));
+    c->launches += 2;
+    return cudaGetLastError();
 }
 
 cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s)
 {
-    // the trial point u + t pdir is formed inside the evaluation kernels
-    cudaError_t e = launch_eval(c, level, c->lb.u, c->lb.pdir, &c->lb.st->t, c->lb.gt, c->lb.scal_t, s);
-    if (e != cudaSuccess)
-        return e;
-    return control(c, LB_ARMIJO, 0, c->lb.scal_t, s, true, false);
+    // the trial point u + t pdir is formed inside the evaluation kernels; the
+    // Armijo decision runs in the evaluation's final reduction
+    return launch_eval(c, level, c->lb.u, c->lb.pdir, &c->lb.st->t, c->lb.gt, c->lb.scal_t, LB_ARMIJO, s);
 }
 
 cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s)
@@ -867,9 +927,18 @@ cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s)
     long long n = 3 * c->L[level].nn, sd = ring_stride(n);
     int nb = num_blocks_for(c, (n + 3) / 4, VT);
     k_lb_accept<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.u, c->lb.g, c->lb.gt, c->lb.pdir, c->lb.P, c->lb.Y,
-                                  c->lb.partials);
+                                  c->lb.partials, tail_of(c, LB_ACCEPTED, nullptr, false, true));
     c->launches += 1;
-    return control(c, LB_ACCEPTED, nb, nullptr, s, false, true);
+    return cudaGetLastError();
+}
+
+// evaluation reduction with a control phase (k_curv.cu calls this for trial points)
+cudaError_t launch_finalize_ctl(reg_ctx *c, const double *pD, int nD, const double *pS, int nS, double hbar_half,
+                                double alpha, double hy_half, double *scal, int phase, cudaStream_t s)
+{
+    k_finalize_ctl<<<1, 512, 0, s>>>(pD, nD, pS, nS, hbar_half, alpha, hy_half, scal, phase, c->lb.st,
+                                      phase == LB_ARMIJO ? g_h_ls : 0ULL, 0ULL);
+    return cudaGetLastError();
 }
 
 cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const float *S, const float *Y,

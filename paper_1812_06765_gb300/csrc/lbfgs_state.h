@@ -53,3 +53,19 @@ struct LbfgsState {
     double Pg[LB_MAXS], Yg[LB_MAXS], Py[LB_MAXS], Yy[LB_MAXS];
     double gg;
 };
+
+// Cross-block reduction of a vector pass and the control step folded into it.
+// Blocks are grouped LB_RG at a time: the last block of a group (completion
+// order) sums the group's FP64 block partials in block order, and the block
+// that completes the last group runs control phase `phase` on the group sums
+// (-1: none, a separate control kernel follows).  The sums do not depend on
+// the completion order.
+#define LB_RG 16
+struct VecTail {
+    double *gpart;                   // [groups][nd] group sums
+    unsigned *cnt;                   // [groups + 1] arrival counters, zero between launches
+    int phase;
+    LbfgsState *st;
+    const double *scal;              // [J, D, S] the phase reads (INIT)
+    unsigned long long h_ls, h_iter; // graph conditions the phase sets (0: none)
+};

@@ -58,6 +58,8 @@ void free_buffers(reg_ctx *c)
     cudaFree(b.P);
     cudaFree(b.Y);
     cudaFree(b.partials);
+    cudaFree(b.gpart);
+    cudaFree(b.cnt);
     cudaFree(b.st);
     cudaFree(b.scal_t);
     if (b.st_host) cudaFreeHost(b.st_host);
@@ -273,6 +275,13 @@ int allocate_buffers(reg_ctx *c)
     // the largest per-block layout is that of reg_lbfgs_direction's pair dots
     b.max_partials = 4 * (c->num_sms > 0 ? c->num_sms : 148) * (2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM) + 1024;
     CK(cudaMalloc(&b.partials, sizeof(double) * b.max_partials));
+    {   // group sums and arrival counters of the vector passes (<= 4 blocks per SM)
+        const int groups = (4 * (c->num_sms > 0 ? c->num_sms : 148) + LB_RG - 1) / LB_RG;
+        CK(cudaMalloc(&b.gpart, sizeof(double) * groups * (2 + 4 * LB_MAXS)));
+        b.cnt_len = groups + 1;
+        CK(cudaMalloc(&b.cnt, sizeof(unsigned) * b.cnt_len));
+        CK(cudaMemset(b.cnt, 0, sizeof(unsigned) * b.cnt_len));
+    }
     CK(cudaMalloc(&b.st, sizeof(LbfgsState)));
     CK(cudaMalloc(&b.scal_t, sizeof(double) * 4));
     CK(cudaMallocHost(&b.st_host, sizeof(LbfgsState)));
@@ -496,7 +505,7 @@ int reg_eval_objective_grad(reg_handle c, int level, const float *u_dev, float *
     if (level < 0 || level >= c->levels)
         return set_err(c, REG_ERR_ARG, "reg_eval_objective_grad: level %d out of range", level);
     if (!u_dev || !grad_dev) return set_err(c, REG_ERR_ARG, "reg_eval_objective_grad: NULL vector");
-    CK(launch_eval(c, level, u_dev, nullptr, nullptr, grad_dev, c->es.scal, c->stream));
+    CK(launch_eval(c, level, u_dev, nullptr, nullptr, grad_dev, c->es.scal, -1, c->stream));
     if (J || D || S) {
         double h[3];
         CK(cudaMemcpyAsync(h, c->es.scal, sizeof h, cudaMemcpyDeviceToHost, c->stream));
@@ -587,9 +596,9 @@ int run_level_graph(reg_ctx *c, int level)
     if (r != REG_OK) return r;
     const LbfgsState *sh = c->lb.st_host;
     const int ek = eval_kernel_count(c, level);
-    // init: evaluation + norms + control; per body: 2 directions + 2 controls + accept + control;
-    // per trial: evaluation + control
-    c->launches += (ek + 2) + 6LL * sh->bodies + (long long)(ek + 1) * (sh->evals - 1);
+    // init: evaluation + norms (control folded in); per body: 2 directions + accept;
+    // per trial: evaluation (Armijo folded into its final reduction)
+    c->launches += (ek + 1) + 3LL * sh->bodies + (long long)ek * (sh->evals - 1);
     return REG_OK;
 }
 
