@@ -151,6 +151,14 @@ int reg_get_level_image(reg_handle h, int level, int which, float *out, int out_
 int reg_eval_objective_grad(reg_handle h, int level, const float *u_dev, float *grad_dev,
                             double *J, double *D, double *S);
 
+/* Device time (ms) of the NGF pass of the last reg_eval_objective_grad call on
+ * this handle: the fused kernel (or the multi-pass NGF kernels), timed with
+ * CUDA events on the handle's stream around its launch; the curvature and
+ * gradient-assembly kernels are not included.  Synchronises on that event.
+ * REG_ERR_STATE before the first evaluation.  A profiling aid (the paper
+ * reports whole-registration times only). */
+int reg_last_ngf_ms(reg_handle h, double *ms);
+
 /* Allocation-free evaluation: the same J, D_NGF, S and grad_u J as
  * reg_eval_objective_grad computes at one resolution, for callers that must not
  * allocate device memory while they run - code hosted by a framework that owns

@@ -75,6 +75,7 @@ def lib():
         L.reg_get_level_image.argtypes = [vp, ctypes.c_int, ctypes.c_int, fp, ctypes.c_int]
         L.reg_eval_objective_grad.argtypes = [vp, ctypes.c_int, fp, fp, dp, dp, dp]
         L.reg_prolong.argtypes = [vp, ctypes.c_int, fp, fp]
+        L.reg_last_ngf_ms.argtypes = [vp, dp]
         L.reg_lbfgs_direction.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, fp, fp, fp, fp]
         L.reg_register.argtypes = [vp, fp, ctypes.c_int, fp, ctypes.POINTER(RegStats)]
         L.reg_destroy.argtypes = [vp]
@@ -86,7 +87,8 @@ def lib():
         L.reg_register_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(fp), ctypes.c_int,
                                          ctypes.POINTER(RegStats)]
         L.reg_register_batch.restype = ctypes.c_int
-        for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_level_tiling", "reg_get_level_image",
+        for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_level_tiling", "reg_last_ngf_ms",
+                     "reg_get_level_image",
                      "reg_eval_objective_grad", "reg_prolong", "reg_lbfgs_direction", "reg_register",
                      "reg_destroy"):
             getattr(L, name).restype = ctypes.c_int
@@ -176,6 +178,12 @@ def reg_eval_objective_grad_noalloc(R_ptr, T_ptr, dims, spacing, u_ptr, grad_ptr
     return check(None, lib().reg_eval_objective_grad_noalloc(
         ctypes.c_void_p(R_ptr), ctypes.c_void_p(T_ptr), d, s, ctypes.c_void_p(u_ptr), ctypes.c_void_p(grad_ptr),
         float(tau), float(rho), float(alpha), ctypes.c_void_p(jds_ptr), ctypes.c_void_p(stream or 0)))
+
+
+def reg_last_ngf_ms(h):
+    ms = ctypes.c_double()
+    check(h, lib().reg_last_ngf_ms(h, ctypes.byref(ms)))
+    return ms.value
 
 
 def reg_prolong(h, level_coarse, uc_ptr, uf_ptr):

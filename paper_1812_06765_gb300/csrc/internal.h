@@ -69,6 +69,9 @@ struct reg_ctx {
     bool own_stream = false;
     cudaEvent_t ev_side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // curvature pass beside the NGF pass
+    cudaEvent_t kev[2] = {nullptr, nullptr};   // around the NGF pass of reg_eval_objective_grad
+    bool time_ngf = false;                     // record kev in the next launch_eval (never while capturing)
+    bool kev_valid = false;
     int device = 0;
     int num_sms = 0;
     int levels = 0;

@@ -156,10 +156,16 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
         e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     if (e != cudaSuccess)
         return e;
-    if (fused)
-        e = launch_ngf_fused(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
-    else
-        e = launch_ngf_multipass(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
+    if (c->time_ngf)
+        e = cudaEventRecord(c->kev[0], s);
+    if (e == cudaSuccess) {
+        if (fused)
+            e = launch_ngf_fused(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
+        else
+            e = launch_ngf_multipass(c, level, ub, dir, t_dev, grad, c->es.partials, &nD, s);
+    }
+    if (e == cudaSuccess && c->time_ngf)
+        e = cudaEventRecord(c->kev[1], s);
     if (e != cudaSuccess)
         return e;
     dim3 blk(32, 8, 1);

@@ -335,6 +335,8 @@ int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->kev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->kev[1]);
     if (e != cudaSuccess) {
         set_err(nullptr, REG_ERR_CUDA, "reg_create: %s", cudaGetErrorString(e));
         reg_destroy(c);
@@ -505,7 +507,11 @@ int reg_eval_objective_grad(reg_handle c, int level, const float *u_dev, float *
     if (level < 0 || level >= c->levels)
         return set_err(c, REG_ERR_ARG, "reg_eval_objective_grad: level %d out of range", level);
     if (!u_dev || !grad_dev) return set_err(c, REG_ERR_ARG, "reg_eval_objective_grad: NULL vector");
-    CK(launch_eval(c, level, u_dev, nullptr, nullptr, grad_dev, c->es.scal, -1, c->stream));
+    c->time_ngf = true;
+    cudaError_t le = launch_eval(c, level, u_dev, nullptr, nullptr, grad_dev, c->es.scal, -1, c->stream);
+    c->time_ngf = false;
+    c->kev_valid = le == cudaSuccess;
+    CK(le);
     if (J || D || S) {
         double h[3];
         CK(cudaMemcpyAsync(h, c->es.scal, sizeof h, cudaMemcpyDeviceToHost, c->stream));
@@ -515,6 +521,17 @@ int reg_eval_objective_grad(reg_handle c, int level, const float *u_dev, float *
         if (S) *S = h[2];
         if (!isfinite(h[0])) return set_err(c, REG_ERR_NUMERIC, "reg_eval_objective_grad: J is not finite");
     }
+    return REG_OK;
+}
+
+int reg_last_ngf_ms(reg_handle c, double *ms)
+{
+    if (!c || !ms) return set_err(c, REG_ERR_ARG, "reg_last_ngf_ms: NULL argument");
+    if (!c->kev_valid) return set_err(c, REG_ERR_STATE, "reg_last_ngf_ms: no evaluation timed yet");
+    CK(cudaEventSynchronize(c->kev[1]));
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, c->kev[0], c->kev[1]));
+    *ms = f;
     return REG_OK;
 }
 
@@ -683,6 +700,8 @@ int reg_destroy(reg_handle c)
     if (c->ev_side) cudaEventDestroy(c->ev_side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int i = 0; i < 2; i++)
+        if (c->kev[i]) cudaEventDestroy(c->kev[i]);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

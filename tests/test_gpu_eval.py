@@ -295,3 +295,18 @@ def test_autotuned_tiling_is_cached_per_geometry(reg_mod):
     assert all(off.level_tiling(lv)[0] in (8, 16, 32, 64, 128) for lv in range(3))
     for r in (r1, r2, off):
         r.close()
+
+
+def test_ngf_pass_timing_query(reg_mod):
+    from paper_1812_06765_gb300 import _lib
+    dims = (64, 48, 40)
+    R = random_image(dims, 91)
+    r = reg_mod.Registration(reg_mod.make_config(levels=1, tau=0.05)).set_images(R, R, (1.0, 1.0, 1.0))
+    with pytest.raises(_lib.RegError) as ei:
+        _lib.reg_last_ngf_ms(r.h)
+    assert ei.value.code == _lib.REG_ERR_STATE
+    u = torch.zeros(r.node_shape(0), device="cuda")
+    r.eval(u)
+    ms = _lib.reg_last_ngf_ms(r.h)
+    assert 0.0 < ms < 1000.0
+    r.close()
