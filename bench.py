@@ -61,6 +61,9 @@ def parse_args(argv=None):
                          "in the same order; ncu cannot list kernels inside graphs with conditional nodes)")
     ap.add_argument("--fused-tz", type=int, default=None,
                     help="force the fused pass's z segment length (no autotuning launches; for profiling)")
+    ap.add_argument("--report", action="store_true",
+                    help="one JSON line per single-pair workload (64^3, 128^3, 256^3, 4D-CT shape): GPU registration "
+                         "and evaluation times, accuracy, and the FP64 oracle on all host cores and on one core")
     ap.add_argument("--pairs", type=int, default=None, help="pairs of the uneven batch (workload 4; default 64)")
     ap.add_argument("--gen-procs", type=int, default=None, help="processes that generate the batch's pairs")
     return ap.parse_args(argv)
@@ -592,6 +595,169 @@ def run_batch(args):
 
 
 # ----------------------------------------------------------------------------
+# per-workload report: GPU times, accuracy, FP64 oracle on all cores and one core
+# ----------------------------------------------------------------------------
+_ONE_CORE_EVAL = """
+import sys, time, json, numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from synth import CONFIGS, make_pair, random_field
+cid = int(sys.argv[2])
+c = CONFIGS[cid]
+p = make_pair(cid)
+nodes = oracle.default_nodes(p["dims"])
+u = random_field(nodes, 7, 5.0).astype(np.float64)
+R, T = p["R"].astype(np.float64), p["T"].astype(np.float64)
+t0 = time.perf_counter()
+oracle.objective(p["dims"], p["spacing"], R, T, nodes, u, c["eta"], c["eta"], c["alpha"])
+print(json.dumps({"s_per_eval": time.perf_counter() - t0, "threads": oracle.num_threads()}))
+"""
+
+
+def oracle_one_core_eval_s(cid):
+    """Seconds of one FP64 oracle evaluation at full resolution on one core (child process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", _ONE_CORE_EVAL, ROOT, str(cid)], env=env, capture_output=True,
+                         text=True, timeout=600)
+    if out.returncode != 0:
+        return None
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_report(args):
+    import torch
+    import oracle
+    import paper_1812_06765_gb300 as reg_pkg
+    from synth import CONFIGS, random_field, true_inverse_displacement
+    from scipy.ndimage import map_coordinates
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    peak, peak_kind = measured_peaks()
+
+    def u_at(u, points, H):   # nodal trilinear value of u (3, nz, ny, nx) at points (N, 3) in mm
+        idx = (np.asarray(points) / np.asarray(H))[:, ::-1].T
+        return np.stack([map_coordinates(u[cc].astype(np.float64), idx, order=1, mode="nearest")
+                         for cc in range(3)], 1)
+
+    for cid in (0, 1, 2, 3):
+        c, p = workload(cid, 0)
+        kw = dict(levels=c["levels"], tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"],
+                  c1=c["c1"])
+        reg = reg_pkg.Registration(reg_pkg.make_config(**kw), stream=stream)
+        R_d, T_d = torch.from_numpy(p["R"]).to(dev), torch.from_numpy(p["T"]).to(dev)
+        R_h, T_h = torch.from_numpy(p["R"]).pin_memory(), torch.from_numpy(p["T"]).pin_memory()
+        for _ in range(2):   # warm-up (tiling autotuned on the first call)
+            reg.set_images(R_d, T_d, p["spacing"])
+            reg.register(out="torch")
+        dev_ms, host_s = [], []
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reg.set_images(R_d, T_d, p["spacing"])
+            u_dev, st = reg.register(out="torch")
+            e1.record(stream)
+            e1.synchronize()
+            dev_ms.append(e0.elapsed_time(e1))
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            reg.set_images(R_h, T_h, p["spacing"])
+            u_h, st_h = reg.register(out="pinned")
+            host_s.append(time.perf_counter() - t0)
+        u_np = u_h.numpy()
+        # one full-resolution evaluation
+        info = reg.level_info(0)
+        u = torch.from_numpy(random_field(info["nodes"], 5, 5.0)).to(dev)
+        g = torch.empty_like(u)
+        ev = []
+        for i in range(23):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reg.eval(u, 0, grad=g)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                ev.append(e0.elapsed_time(e1))
+        eval_ms = statistics.median(ev)
+        nv, nn = int(np.prod(info["dims"])), int(np.prod(info["nodes"]))
+        eval_gbs = (8 * nv + 24 * nn) / (eval_ms * 1e-3) / 1e9
+        eq = full_res_equivalent(st, reg, c["levels"])
+        line = {"workload": c["name"], "image": list(p["dims"]), "spacing_mm": list(p["spacing"]),
+                "levels": c["levels"], "finest_nodes": list(info["nodes"]),
+                "iters_per_level": st["iters"], "evals_per_level": st["evals"],
+                "fused_tz_per_level": [reg.level_tiling(lv)[0] for lv in range(c["levels"])],
+                "gpu": {"registration_s_device_resident": statistics.median(dev_ms) / 1000.0,
+                        "registration_s_from_host_arrays": statistics.median(host_s),
+                        "level_device_s": st["level_seconds"],
+                        "eval_ms_full_res": eval_ms, "evals_per_s_full_res": 1000.0 / eval_ms,
+                        "eval_hbm_frac": eval_gbs / peak, "peak_kind": peak_kind,
+                        "full_res_equivalent_evals_per_registration": eq,
+                        "l2": "flushed before every timed call"}}
+        acc = {}
+        if cid == 0:   # trajectory parity with the FP64 oracle, and the known warp as a sanity value
+            ocfg = oracle.make_config(**kw)
+            t0 = time.perf_counter()
+            uo, sto = oracle.register(p["dims"], p["spacing"], p["R"], p["T"], ocfg)
+            cpu_reg_s = time.perf_counter() - t0
+            du = np.sqrt(((u_np.astype(np.float64) - uo) ** 2).sum(axis=0))
+            H = info["node_spacing"]
+            nz, ny, nx = u_np.shape[1:]
+            Z, Y, X = np.meshgrid(np.arange(nz) * H[2], np.arange(ny) * H[1], np.arange(nx) * H[0], indexing="ij")
+            pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+            ut = true_inverse_displacement(p["field"], pts)
+            err_true = np.linalg.norm(u_np.reshape(3, -1).T - ut, axis=1)
+            acc = {"mean_abs_u_gpu_minus_oracle_vox": float(du.mean() / min(p["spacing"])),
+                   "J_gpu": st["J_final"], "J_oracle": sto["J"][0],
+                   "mean_abs_u_minus_true_vox_sanity": float(err_true.mean() / min(p["spacing"])),
+                   "cpu_registration_s_measured": cpu_reg_s}
+        elif cid == 1:
+            ocfg = oracle.make_config(**kw)
+            t0 = time.perf_counter()
+            uo, sto = oracle.register(p["dims"], p["spacing"], p["R"], p["T"], ocfg)
+            cpu_reg_s = time.perf_counter() - t0
+            du = np.sqrt(((u_np.astype(np.float64) - uo) ** 2).sum(axis=0))
+            acc = {"mean_abs_u_gpu_minus_oracle_vox": float(du.mean() / min(p["spacing"])),
+                   "J_gpu": st["J_final"], "J_oracle": sto["J"][0], "cpu_registration_s_measured": cpu_reg_s}
+        elif cid == 3:
+            H = info["node_spacing"]
+            before = np.linalg.norm(p["lm_R"] - p["lm_T"], axis=1)
+            after = np.linalg.norm(p["lm_R"] + u_at(u_np, p["lm_R"], H) - p["lm_T"], axis=1)
+            acc = {"landmarks": len(before), "lme_before_mm": [float(before.mean()), float(before.std())],
+                   "lme_after_mm": [float(after.mean()), float(after.std())]}
+        line["accuracy"] = acc
+        # FP64 oracle on the host: all cores, and one core (child process)
+        nodes = oracle.default_nodes(p["dims"])
+        uo64 = random_field(nodes, 7, 5.0).astype(np.float64)
+        R64, T64 = p["R"].astype(np.float64), p["T"].astype(np.float64)
+        n, t0 = 0, time.perf_counter()
+        while n < 20 and (n < 2 or time.perf_counter() - t0 < 4.0):
+            oracle.objective(p["dims"], p["spacing"], R64, T64, nodes, uo64, c["eta"], c["eta"], c["alpha"])
+            n += 1
+        all_s = (time.perf_counter() - t0) / n
+        one = oracle_one_core_eval_s(cid)
+        cpu = {"eval_s_full_res_all_cores": all_s, "cores": oracle.num_threads(),
+               "eval_s_full_res_one_core": one["s_per_eval"] if one else None,
+               "registration_s_estimate_all_cores": all_s * eq,
+               "estimate": "oracle seconds per full-resolution evaluation x the GPU run's full-resolution-"
+                           "equivalent evaluation count (an extrapolation)",
+               "gpu_speedup_eval_vs_all_cores": all_s / (eval_ms * 1e-3)}
+        if "cpu_registration_s_measured" in acc:
+            cpu["registration_s_measured_all_cores"] = acc.pop("cpu_registration_s_measured")
+        line["cpu_oracle"] = cpu
+        print(json.dumps(line), flush=True)
+        reg.close()
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ----------------------------------------------------------------------------
 def run_reference(args):
@@ -635,6 +801,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.report:
+        run_report(args)
     elif args.config == 4:
         run_batch(args)
     else:
