@@ -15,16 +15,21 @@
 // 28 x 12 x TZ voxels feeds 15 x 7 x (TZ/2 + 1) nodes; neighbouring tiles share
 // one node plane per dimension and the gather kernel sums them.
 //
-// Pipeline.  Step s (zA = z0 - 2 + s) runs, between two barriers,
-//   A-finish zA  : interpolate T at plane zA from the 8 corners loaded last step
-//   A-issue zA+1 : coordinates of plane zA+1, loads of its 8 corners and of
-//                  R(zA+1) into registers (used one step later); cp.async of
-//                  the node-plane tile two intervals ahead
-//   B  zA-2      : v from T~ and R planes zA-3 .. zA-1
-//   C  zA-4      : r from v planes zA-5 .. zA-3; x reduction by warp shuffles
-//   D  zA-5      : y reduction of last step's rows, accumulation along z
+// Pipeline.  Step s (zA = z0 - 2 + 2 s, even) handles two planes, exactly one
+// node interval, between two barriers:
+//   A-finish zA, zA+1   : interpolate T on both planes from the corners loaded
+//                         last step
+//   A-issue  zA+2, zA+3 : P on the next node interval, the coordinates of both
+//                         planes, loads of their 2 x 8 corners and of R into
+//                         registers (used one step later); cp.async of the
+//                         node-plane tile two intervals ahead
+//   B  zA-3, zA-2       : v from T~ and R planes zA-4 .. zA-1
+//   C  zA-6, zA-5       : r from v planes zA-7 .. zA-4; x reduction by warp shuffles
+//   D  zA-8, zA-7       : y reduction of last step's rows, accumulation of one
+//                         node interval along z
 // Every phase reads only what earlier steps wrote, so one barrier per step
-// suffices, and the global loads of a plane overlap a whole step of compute.
+// suffices; the global loads of two planes overlap a whole step of compute, and
+// the two planes of each phase are independent work the compiler interleaves.
 #include <array>
 #include <map>
 #include <mutex>
@@ -43,13 +48,14 @@ constexpr int PLANE = BX * BY;                    // floats of one shared plane
 constexpr int TNX = BX / 2 + 1, TNY = BY / 2 + 1; // node tile of the columns: 17 x 9
 constexpr int TNP = 3 * TNY * TNX;                // floats of one node plane tile per array
 
-// shared layout (floats)
-constexpr int OFF_T = 0;                          // T~ ring [4][PLANE]
-constexpr int OFF_R = OFF_T + 4 * PLANE;          // R ring [4][PLANE]
-constexpr int OFF_V = OFF_R + 4 * PLANE;          // v ring [4][3][PLANE]
-constexpr int OFF_G = OFF_V + 12 * PLANE;         // grad T ring [8][3][PLANE]
-constexpr int OFF_RED = OFF_G + 24 * PLANE;       // x-reduced rows [2][BY][NX][3]
-constexpr int OFF_N = OFF_RED + 2 * BY * NX * 3;  // node planes [4][2][TNP] (u, dir)
+// shared layout (floats); the plane rings hold 8 planes (slot z & 7)
+constexpr int OFF_T = 0;                          // T~ ring [8][PLANE]
+constexpr int OFF_R = OFF_T + 8 * PLANE;          // R ring [8][PLANE]
+constexpr int OFF_V = OFF_R + 8 * PLANE;          // v ring [8][3][PLANE]
+constexpr int OFF_G = OFF_V + 24 * PLANE;         // grad T ring [8][3][PLANE]
+constexpr int RED_PLANE = BY * NX * 3;            // x-reduced rows of one plane
+constexpr int OFF_RED = OFF_G + 24 * PLANE;       // x-reduced rows [2 steps][2 planes][BY][NX][3]
+constexpr int OFF_N = OFF_RED + 4 * RED_PLANE;    // node planes [4][2][TNP] (u, dir)
 constexpr int SMEM_FLOATS = OFF_N + 4 * 2 * TNP;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 
@@ -159,117 +165,112 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int t
     const float wx = (x & 1) ? 0.75f : 0.25f, wy = (y & 1) ? 0.75f : 0.25f;
     const float hx = 0.5f * g.ih[0], hy = 0.5f * g.ih[1], hz = 0.5f * g.ih[2];
     const float half_hbar = 0.5f * g.hbar;
-    const int zlast = z0 + a.tz + 1;                  // last T~ plane needed
+    const int zend = z0 + a.tz;                       // first plane after the segment's output planes
     const size_t tile_lin = (size_t)tile_x + (size_t)a.ntx * (tile_y + (size_t)a.nty * tile_z);
     float *part_tile = a.part + tile_lin * (size_t)(a.tz / 2 + 1) * NE;
     const NodeCopy nc = node_copy_setup<HAS_DIR>(a, kx0, ky0, tid);
     const int node_plane = g.n[0] * g.n[1];
     const IMG *Tim = static_cast<const IMG *>(a.T);
     const IMG *Rcol = static_cast<const IMG *>(a.R) + (col_in ? x + mx * y : 0);
+    // output columns and the rows phases B and C run on
+    const bool rowB = ty >= 1 && ty < BY - 1, rowC = ty >= 2 && ty < BY - 2;
+    const bool colB = tx >= 1 && tx < BX - 1, colC = tx >= 2 && tx < BX - 2;
+    const bool intxy = col_in && x >= 1 && x <= mx - 2 && y >= 1 && y <= my - 2;
+    // phase D: partial entry tid = (component, node row jy, node column jx)
+    const bool dD = tid < NE;
+    const int dc = tid / (NX * NY), drem = tid - dc * (NX * NY), djy = drem / NX, djx = drem - djy * NX;
+    const int dofs = ((2 * djy) * NX + djx) * 3 + dc;
 
-    float Uhi[3], Bhi[3];                             // node plane floor(z/2) + 1 of this column
-    // per node interval and component: integer part of the sampling coordinate
-    // (without the voxel index) and its fractional remainder for even and odd z
-    int qb[3] = {0, 0, 0};
-    float fe[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};
-    bool iv_ok = false;
-    float pc[8];                                      // corners of the next plane, loaded a step ahead
-    float fr0 = 0.f, fr1 = 0.f, fr2 = 0.f;            // its fractions
-    float rnext = 0.f;                                // R of the next plane
-    float acc_lo = 0.f, acc_hi = 0.f;                 // z accumulation of partial entry `tid`
+    float Uhi[3], Bhi[3];                             // node plane of the interval's upper end, this column
+    float pc[2][8];                                   // corners of the next two planes, loaded a step ahead
+    float fr[2][3];                                   // their fractions
+    float rnext[2];                                   // R of the next two planes
+    float acc_lo = 0.f;                               // node plane of the interval's lower end (entry tid)
     KahanF psi_sum;
 
-    // rows of the x-reduction buffer that no output row writes stay zero
-    for (int e = tid; e < 2 * BY * NX * 3; e += PLANE)
+    // rows of the x-reduction buffers that no output row writes stay zero
+    for (int e = tid; e < 4 * RED_PLANE; e += PLANE)
         sm[OFF_RED + e] = 0.f;
 
-    // ---- A-issue: coordinates of plane z1 and loads of its 8 corners and of R(z1)
-    // into registers; they are first used one step later
+    // ---- A-issue: P on the node interval of planes z1 (even) and z1 + 1, their
+    // coordinates and the loads of their corners and of R, into registers that
+    // are first used one step later
     auto a_issue = [&](int z1, bool first) {
         const int K1 = z1 >> 1;
-        if (!(z1 & 1)) {   // a new node interval [K1, K1 + 1]
-            if (col_in) {
-                float Ulo[3], Blo[3];
-                if (first) {
-                    column_plane<HAS_DIR>(sm, K1, lkx, lky, wx, wy, t, Ulo, Blo);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        Ulo[c] = Uhi[c];
-                        Blo[c] = Bhi[c];
-                    }
-                }
-                column_plane<HAS_DIR>(sm, K1 + 1, lkx, lky, wx, wy, t, Uhi, Bhi);
-                // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz) with wz = 1/4 (even z) or
-                // 3/4 (odd z).  The sampling coordinate i + y-hat / h is kept as an integer
-                // part plus a small fraction (see sample_coord); both depend only on the
-                // interval and the parity of z, so they are formed here once.
-                iv_ok = true;
+        int qb[3] = {0, 0, 0};
+        float fe[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};
+        bool iv_ok = false;
+        if (col_in) {
+            float Ulo[3], Blo[3];
+            if (first) {
+                column_plane<HAS_DIR>(sm, K1, lkx, lky, wx, wy, t, Ulo, Blo);
+            } else {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    const float ih = g.ih[c];
-                    const float q0 = Ulo[c] * ih;
-                    const float d1 = (Uhi[c] - Ulo[c]) + Bhi[c];
-                    iv_ok = iv_ok && fabsf(q0) < 1.0e6f && fabsf(Blo[c] * ih) < 1.0e6f && fabsf(d1 * ih) < 1.0e6f;
-                    const float qi = floorf(q0);
-                    const float rem = fmaf(-qi, g.h[c], Ulo[c]);   // |rem| <~ h
-                    fe[c] = (rem + lerpf(Blo[c], d1, 0.25f)) * ih;
-                    fo[c] = (rem + lerpf(Blo[c], d1, 0.75f)) * ih;
-                    qb[c] = (int)qi;
-                }
-                if (!iv_ok) {   // non-finite or absurd displacement: nothing is sampled
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        fe[c] = fo[c] = 0.f;
-                        qb[c] = 0;
-                    }
+                    Ulo[c] = Uhi[c];
+                    Blo[c] = Bhi[c];
                 }
             }
-            issue_node_plane(nc, sm, K1 + 2, g.n[2], node_plane);
-            cp_async_commit();
-        }
-        const bool zin = col_in && z1 >= 0 && z1 < mz;
-#pragma unroll
-        for (int k = 0; k < 8; k++)
-            pc[k] = 0.f;
-        if (zin) {
-            const bool odd = z1 & 1;
-            int cc[3];
-            float ff[3];
+            column_plane<HAS_DIR>(sm, K1 + 1, lkx, lky, wx, wy, t, Uhi, Bhi);
+            // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz) with wz = 1/4 (even z) or
+            // 3/4 (odd z).  The sampling coordinate i + y-hat / h is kept as an integer
+            // part plus a small fraction (see sample_coord); both depend only on the
+            // interval and the parity of z, so they are formed here once.
+            iv_ok = true;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const float fr = odd ? fo[c] : fe[c];
-                const float fl = floorf(fr);
-                ff[c] = fr - fl;
+                const float ih = g.ih[c];
+                const float q0 = Ulo[c] * ih;
+                const float d1 = (Uhi[c] - Ulo[c]) + Bhi[c];
+                iv_ok = iv_ok && fabsf(q0) < 1.0e6f && fabsf(Blo[c] * ih) < 1.0e6f && fabsf(d1 * ih) < 1.0e6f;
+                const float qi = floorf(q0);
+                const float rem = fmaf(-qi, g.h[c], Ulo[c]);   // |rem| <~ h
+                fe[c] = (rem + lerpf(Blo[c], d1, 0.25f)) * ih;
+                fo[c] = (rem + lerpf(Blo[c], d1, 0.75f)) * ih;
+                qb[c] = (int)qi;
+            }
+        }
+        issue_node_plane(nc, sm, K1 + 2, g.n[2], node_plane);
+        cp_async_commit();
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int zz = z1 + h;
+            const bool zin = col_in && zz >= 0 && zz < mz;
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                pc[h][k] = 0.f;
+            int cc[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float f = h ? fo[c] : fe[c];
+                const float fl = floorf(f);
+                fr[h][c] = f - fl;
                 cc[c] = qb[c] + (int)fl;
             }
-            fr0 = ff[0];
-            fr1 = ff[1];
-            fr2 = ff[2];
-            const int cx = cc[0] + x, cy = cc[1] + y, cz = cc[2] + z1;
-            if (iv_ok) {
+            const int cx = cc[0] + x, cy = cc[1] + y, cz = cc[2] + zz;
+            if (zin && iv_ok) {
                 if ((unsigned)cx < (unsigned)(mx - 1) && (unsigned)cy < (unsigned)(my - 1) &&
                     (unsigned)cz < (unsigned)(mz - 1)) {   // all 8 corners inside
                     const IMG *p = Tim + (cx + mx * (cy + my * cz));
-                    pc[0] = ldimg(p);
-                    pc[1] = ldimg(p + 1);
-                    pc[2] = ldimg(p + mx);
-                    pc[3] = ldimg(p + mx + 1);
-                    pc[4] = ldimg(p + sxy);
-                    pc[5] = ldimg(p + sxy + 1);
-                    pc[6] = ldimg(p + sxy + mx);
-                    pc[7] = ldimg(p + sxy + mx + 1);
+                    pc[h][0] = ldimg(p);
+                    pc[h][1] = ldimg(p + 1);
+                    pc[h][2] = ldimg(p + mx);
+                    pc[h][3] = ldimg(p + mx + 1);
+                    pc[h][4] = ldimg(p + sxy);
+                    pc[h][5] = ldimg(p + sxy + 1);
+                    pc[h][6] = ldimg(p + sxy + mx);
+                    pc[h][7] = ldimg(p + sxy + mx + 1);
                 } else {   // zero extension corner by corner
 #pragma unroll
                     for (int k = 0; k < 8; k++)
-                        pc[k] = ldimg_zero_ext(Tim, mx, my, mz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
+                        pc[h][k] = ldimg_zero_ext(Tim, mx, my, mz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
                 }
             }
+            rnext[h] = zin ? ldimg(Rcol + sxy * zz) : 0.f;
         }
-        rnext = zin ? ldimg(Rcol + sxy * z1) : 0.f;
     };
 
-    // prologue: node planes of the first interval, then the loads of plane z0 - 2
+    // prologue: node planes of the first interval, then the loads of planes z0 - 2, z0 - 1
     {
         const int K0 = (z0 - 2) >> 1;
         issue_node_plane(nc, sm, K0, g.n[2], node_plane);
@@ -282,103 +283,104 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int t
         __syncthreads();
     }
 
-    const int nsteps = a.tz + 7;
+    const int nsteps = a.tz / 2 + 5;
     for (int s = 0; s < nsteps; s++) {
-        const int zA = z0 - 2 + s;
-        // ---- A-finish: T~ and grad T at plane zA from the corners loaded last step
-        if (zA <= zlast) {
-            const float t000 = pc[0], t100 = pc[1], t010 = pc[2], t110 = pc[3];
-            const float t001 = pc[4], t101 = pc[5], t011 = pc[6], t111 = pc[7];
-            float a00 = lerpf(t000, t100, fr0), a10 = lerpf(t010, t110, fr0);
-            float a01 = lerpf(t001, t101, fr0), a11 = lerpf(t011, t111, fr0);
-            float b0 = lerpf(a00, a10, fr1), b1 = lerpf(a01, a11, fr1);
-            const float val = lerpf(b0, b1, fr2);
-            float dx0 = lerpf(t100 - t000, t110 - t010, fr1), dx1 = lerpf(t101 - t001, t111 - t011, fr1);
-            sm[OFF_T + (zA & 3) * PLANE + tid] = val;
-            sm[OFF_R + (zA & 3) * PLANE + tid] = rnext;
-            float *gq = sm + OFF_G + (zA & 7) * 3 * PLANE + tid;
-            gq[0] = lerpf(dx0, dx1, fr2) * g.ih[0];
-            gq[PLANE] = lerpf(a10 - a00, a11 - a01, fr2) * g.ih[1];
-            gq[2 * PLANE] = (b1 - b0) * g.ih[2];
-        }
-        // ---- A-issue for plane zA + 1
-        if (zA + 1 <= zlast)
-            a_issue(zA + 1, false);
-        // ---- B: v at plane zB = zA - 2 (warps 1 .. 14, lanes 1 .. 30)
-        const int zB = zA - 2;
-        if (ty >= 1 && ty < BY - 1 && zB >= z0 - 1 && zB <= z0 + a.tz) {
-            float v[3] = {0.f, 0.f, 0.f};
-            if (tx >= 1 && tx < BX - 1) {
-                const bool interior = col_in && x >= 1 && x <= mx - 2 && y >= 1 && y <= my - 2 && zB >= 1 &&
-                                      zB <= mz - 2;
-                if (interior) {
-                    const float *T0 = sm + OFF_T + (zB & 3) * PLANE + tid;
-                    const float *R0 = sm + OFF_R + (zB & 3) * PLANE + tid;
-                    float av[3], bv[3];
-                    av[0] = (T0[1] - T0[-1]) * hx;
-                    av[1] = (T0[BX] - T0[-BX]) * hy;
-                    av[2] = (sm[OFF_T + ((zB + 1) & 3) * PLANE + tid] - sm[OFF_T + ((zB - 1) & 3) * PLANE + tid]) * hz;
-                    bv[0] = (R0[1] - R0[-1]) * hx;
-                    bv[1] = (R0[BX] - R0[-BX]) * hy;
-                    bv[2] = (sm[OFF_R + ((zB + 1) & 3) * PLANE + tid] - sm[OFF_R + ((zB - 1) & 3) * PLANE + tid]) * hz;
-                    float psi = ngf_residual(av, bv, a.tau, a.rho, v);
-                    if (tx >= 2 && tx < BX - 2 && ty >= 2 && ty < BY - 2 && zB >= z0 && zB < z0 + a.tz)
-                        psi_sum.add(psi);
-                }
-                float *vq = sm + OFF_V + (zB & 3) * 3 * PLANE + tid;
-                vq[0] = v[0];
-                vq[PLANE] = v[1];
-                vq[2 * PLANE] = v[2];
-            }
-        }
-        // ---- C: r at plane zC = zA - 4 (warps 2 .. 13), x reduction into node columns
-        const int zC = zA - 4;
-        if (ty >= 2 && ty < BY - 2 && zC >= z0 && zC < z0 + a.tz) {
-            float r[3] = {0.f, 0.f, 0.f};
-            if (tx >= 2 && tx < BX - 2 && col_in && zC < mz) {
-                const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + tid;
-                float gs = (V0[-1] - V0[1]) * hx + (V0[PLANE - BX] - V0[PLANE + BX]) * hy +
-                           (sm[OFF_V + ((zC - 1) & 3) * 3 * PLANE + 2 * PLANE + tid] -
-                            sm[OFF_V + ((zC + 1) & 3) * 3 * PLANE + 2 * PLANE + tid]) * hz;
-                const float gj = half_hbar * gs;
-                const float *gq = sm + OFF_G + (zC & 7) * 3 * PLANE + tid;
-                r[0] = gj * gq[0];
-                r[1] = gj * gq[PLANE];
-                r[2] = gj * gq[2 * PLANE];
-            }
-            // node column j (0..14) gathers lanes 2j .. 2j+3 with weights 1/4, 3/4, 3/4, 1/4
-            float *red = sm + OFF_RED + (s & 1) * BY * NX * 3 + ty * NX * 3;
+        const int zA = z0 - 2 + 2 * s;
+        // ---- A-finish: T~ and grad T on planes zA, zA + 1
+        if (zA <= zend) {
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                float r1 = __shfl_down_sync(0xffffffffu, r[c], 1);
-                float r2 = __shfl_down_sync(0xffffffffu, r[c], 2);
-                float r3 = __shfl_down_sync(0xffffffffu, r[c], 3);
-                // written nodes have tx = 2j <= 28, so lanes tx + 1 .. tx + 3 exist
-                if (!(tx & 1) && (tx >> 1) < NX)
-                    red[(tx >> 1) * 3 + c] = 0.25f * (r[c] + r3) + 0.75f * (r1 + r2);
+            for (int h = 0; h < 2; h++) {
+                const float t000 = pc[h][0], t100 = pc[h][1], t010 = pc[h][2], t110 = pc[h][3];
+                const float t001 = pc[h][4], t101 = pc[h][5], t011 = pc[h][6], t111 = pc[h][7];
+                const float f0 = fr[h][0], f1 = fr[h][1], f2 = fr[h][2];
+                const float a00 = lerpf(t000, t100, f0), a10 = lerpf(t010, t110, f0);
+                const float a01 = lerpf(t001, t101, f0), a11 = lerpf(t011, t111, f0);
+                const float b0 = lerpf(a00, a10, f1), b1 = lerpf(a01, a11, f1);
+                const float val = lerpf(b0, b1, f2);
+                const float dx0 = lerpf(t100 - t000, t110 - t010, f1), dx1 = lerpf(t101 - t001, t111 - t011, f1);
+                const int slot = (zA + h) & 7;
+                sm[OFF_T + slot * PLANE + tid] = val;
+                sm[OFF_R + slot * PLANE + tid] = rnext[h];
+                float *gq = sm + OFF_G + slot * 3 * PLANE + tid;
+                gq[0] = lerpf(dx0, dx1, f2) * g.ih[0];
+                gq[PLANE] = lerpf(a10 - a00, a11 - a01, f2) * g.ih[1];
+                gq[2 * PLANE] = (b1 - b0) * g.ih[2];
             }
         }
-        // ---- D: y reduction of plane zD = zA - 5 and accumulation along z
-        const int zD = zA - 5;
-        if (tid < NE && zD >= z0 && zD < z0 + a.tz) {
-            const int lz = zD - z0;
-            const int c = tid / (NX * NY), rem = tid - c * (NX * NY), jy = rem / NX, jx = rem - jy * NX;
-            const float *red = sm + OFF_RED + ((s - 1) & 1) * BY * NX * 3;
-            const int r0 = 2 * jy;
-            float v = 0.25f * red[(r0 * NX + jx) * 3 + c] + 0.75f * red[((r0 + 1) * NX + jx) * 3 + c] +
-                      0.75f * red[((r0 + 2) * NX + jx) * 3 + c] + 0.25f * red[((r0 + 3) * NX + jx) * 3 + c];
-            if (!(lz & 1)) {
-                acc_lo = fmaf(0.75f, v, acc_lo);
-                acc_hi = fmaf(0.25f, v, acc_hi);
-            } else {
-                acc_lo = fmaf(0.25f, v, acc_lo);
-                acc_hi = fmaf(0.75f, v, acc_hi);
-                // node plane lz / 2 of the segment is complete
-                part_tile[(size_t)(lz >> 1) * NE + tid] = acc_lo;
-                acc_lo = acc_hi;
-                acc_hi = 0.f;
+        // ---- A-issue for planes zA + 2, zA + 3
+        if (zA + 2 <= zend)
+            a_issue(zA + 2, false);
+        // ---- B: v on planes zA - 3, zA - 2 (rows 1 .. 14, lanes 1 .. 30)
+        if (rowB && zA - 3 >= z0 - 1 && zA - 3 <= zend) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int zB = zA - 3 + h;
+                float v[3] = {0.f, 0.f, 0.f};
+                if (colB) {
+                    if (intxy && zB >= 1 && zB <= mz - 2) {
+                        const float *T0 = sm + OFF_T + (zB & 7) * PLANE + tid;
+                        const float *R0 = sm + OFF_R + (zB & 7) * PLANE + tid;
+                        float av[3], bv[3];
+                        av[0] = (T0[1] - T0[-1]) * hx;
+                        av[1] = (T0[BX] - T0[-BX]) * hy;
+                        av[2] = (sm[OFF_T + ((zB + 1) & 7) * PLANE + tid] - sm[OFF_T + ((zB - 1) & 7) * PLANE + tid]) * hz;
+                        bv[0] = (R0[1] - R0[-1]) * hx;
+                        bv[1] = (R0[BX] - R0[-BX]) * hy;
+                        bv[2] = (sm[OFF_R + ((zB + 1) & 7) * PLANE + tid] - sm[OFF_R + ((zB - 1) & 7) * PLANE + tid]) * hz;
+                        const float psi = ngf_residual(av, bv, a.tau, a.rho, v);
+                        if (colC && rowC && zB >= z0 && zB < zend)
+                            psi_sum.add(psi);
+                    }
+                    float *vq = sm + OFF_V + (zB & 7) * 3 * PLANE + tid;
+                    vq[0] = v[0];
+                    vq[PLANE] = v[1];
+                    vq[2 * PLANE] = v[2];
+                }
             }
-            if (lz == a.tz - 1)
+        }
+        // ---- C: r on planes zA - 6, zA - 5 (rows 2 .. 13), x reduction into node columns
+        if (rowC && zA - 6 >= z0 && zA - 5 < zend) {
+            float *redb = sm + OFF_RED + (s & 1) * 2 * RED_PLANE + ty * NX * 3;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int zC = zA - 6 + h;
+                float r[3] = {0.f, 0.f, 0.f};
+                if (colC && col_in && zC < mz) {
+                    const float *V0 = sm + OFF_V + (zC & 7) * 3 * PLANE + tid;
+                    const float gs = (V0[-1] - V0[1]) * hx + (V0[PLANE - BX] - V0[PLANE + BX]) * hy +
+                                     (sm[OFF_V + ((zC - 1) & 7) * 3 * PLANE + 2 * PLANE + tid] -
+                                      sm[OFF_V + ((zC + 1) & 7) * 3 * PLANE + 2 * PLANE + tid]) * hz;
+                    const float gj = half_hbar * gs;
+                    const float *gq = sm + OFF_G + (zC & 7) * 3 * PLANE + tid;
+                    r[0] = gj * gq[0];
+                    r[1] = gj * gq[PLANE];
+                    r[2] = gj * gq[2 * PLANE];
+                }
+                // node column j (0..14) gathers lanes 2j .. 2j+3 with weights 1/4, 3/4, 3/4, 1/4
+                float *red = redb + h * RED_PLANE;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float r1 = __shfl_down_sync(0xffffffffu, r[c], 1);
+                    const float r2 = __shfl_down_sync(0xffffffffu, r[c], 2);
+                    const float r3 = __shfl_down_sync(0xffffffffu, r[c], 3);
+                    // written nodes have tx = 2j <= 28, so lanes tx + 1 .. tx + 3 exist
+                    if (!(tx & 1) && (tx >> 1) < NX)
+                        red[(tx >> 1) * 3 + c] = 0.25f * (r[c] + r3) + 0.75f * (r1 + r2);
+                }
+            }
+        }
+        // ---- D: y reduction of planes zA - 8, zA - 7 (one node interval) and
+        // accumulation of its two node planes along z
+        if (dD && zA - 8 >= z0 && zA - 7 < zend) {
+            const int lz = zA - 8 - z0;                   // even
+            const float *red = sm + OFF_RED + ((s - 1) & 1) * 2 * RED_PLANE + dofs;
+            const float v0 = 0.25f * red[0] + 0.75f * red[NX * 3] + 0.75f * red[2 * NX * 3] + 0.25f * red[3 * NX * 3];
+            red += RED_PLANE;
+            const float v1 = 0.25f * red[0] + 0.75f * red[NX * 3] + 0.75f * red[2 * NX * 3] + 0.25f * red[3 * NX * 3];
+            // even plane: 3/4 to the lower node plane, 1/4 to the upper; odd plane: the reverse
+            part_tile[(size_t)(lz >> 1) * NE + tid] = acc_lo + (0.75f * v0 + 0.25f * v1);
+            acc_lo = 0.25f * v0 + 0.75f * v1;
+            if (lz == a.tz - 2)
                 part_tile[(size_t)(a.tz >> 1) * NE + tid] = acc_lo;
         }
         cp_async_wait_all();
