@@ -54,6 +54,8 @@ __device__ __forceinline__ int linear_tid()
     return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
 }
 
+__device__ __forceinline__ int nthreads() { return blockDim.x * blockDim.y * blockDim.z; }
+
 __device__ __forceinline__ int linear_bid()
 {
     return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -97,26 +99,30 @@ struct KahanF {
     }
 };
 
-// Deterministic FP64 sum of block partials (fixed thread-to-partial
-// assignment, fixed tree): scal = [J, D, S].
+// Deterministic FP64 sum of block partials: scal = [J, D, S].  The summation
+// order is a fixed 512-wide layout (strided sums, then a halving tree), the
+// same for any block size, so every kernel that ends an evaluation with it
+// gets bit-identical scalars.
 __device__ __forceinline__ void finalize_body(const double *__restrict__ pD, int nD, const double *__restrict__ pS,
                                               int nS, double hbar_half, double alpha, double hy_half,
                                               double *__restrict__ scal)
 {
     __shared__ double sd[512], ss[512];
-    int t = threadIdx.x;
-    double a = 0.0, b = 0.0;
-    for (int i = t; i < nD; i += 512)
-        a += pD[i];
-    for (int i = t; i < nS; i += 512)
-        b += pS[i];
-    sd[t] = a;
-    ss[t] = b;
+    const int t = linear_tid(), nt = nthreads();
+    for (int v = t; v < 512; v += nt) {
+        double a = 0.0, b = 0.0;
+        for (int i = v; i < nD; i += 512)
+            a += pD[i];
+        for (int i = v; i < nS; i += 512)
+            b += pS[i];
+        sd[v] = a;
+        ss[v] = b;
+    }
     __syncthreads();
     for (int o = 256; o > 0; o >>= 1) {
-        if (t < o) {
-            sd[t] += sd[t + o];
-            ss[t] += ss[t + o];
+        for (int v = t; v < o; v += nt) {
+            sd[v] += sd[v + o];
+            ss[v] += ss[v + o];
         }
         __syncthreads();
     }

@@ -2,7 +2,8 @@
 //
 //   init: objective at u0; ||g||, ||g||_inf + control(INIT)      -> sets the iteration condition
 //   WHILE (iteration condition)
-//       direction + control(DIR); p0 redo + control(DIR_REDO)      -> set the line-search condition
+//       direction + control(DIR)                                    -> sets the redo and line-search conditions
+//       IF (redo condition): p0 direction + control(DIR_REDO)
 //       WHILE (line-search condition)
 //           objective at u + t p; its final reduction + control(ARMIJO)
 //       accept (no-op unless accepted) + control(ACCEPTED)        -> sets the iteration condition
@@ -44,18 +45,24 @@ cudaError_t capture_leaves(cudaStream_t s, std::vector<cudaGraphNode_t> &out)
     return cudaSuccess;
 }
 
-cudaError_t add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
-                      cudaGraphNode_t *node, cudaGraph_t *body)
+cudaError_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                     cudaGraphConditionalNodeType type, cudaGraphNode_t *node, cudaGraph_t *body)
 {
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
     p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.type = type;
     p.conditional.size = 1;
     cudaError_t e = cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p);
     if (e == cudaSuccess)
         *body = p.conditional.phGraph_out[0];
     return e;
+}
+
+cudaError_t add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                      cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    return add_cond(g, deps, h, cudaGraphCondTypeWhile, node, body);
 }
 
 }  // namespace
@@ -64,7 +71,7 @@ cudaError_t add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, c
     do {                                          \
         cudaError_t _e = (call);                  \
         if (_e != cudaSuccess) {                  \
-            lbfgs_set_graph_handles(0, 0);        \
+            lbfgs_set_graph_handles(0, 0, 0);        \
             c->launches = launches0;              \
             if (G) cudaGraphDestroy(G);           \
             return _e;                            \
@@ -87,7 +94,7 @@ cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
         CaptureGuard guard{cs};
         GK(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, mode));
         guard.active = true;
-        lbfgs_set_graph_handles(0, h_iter);
+        lbfgs_set_graph_handles(0, h_iter, 0);
         GK(lbfgs_launch_init(c, level, cs));
         GK(capture_leaves(cs, leaves));
         guard.active = false;
@@ -97,18 +104,34 @@ cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
     cudaGraphNode_t w_iter;
     cudaGraph_t body = nullptr;
     GK(add_while(G, leaves, h_iter, &w_iter, &body));
+    cudaGraphConditionalHandle h_redo;
     GK(cudaGraphConditionalHandleCreate(&h_ls, body, 0, cudaGraphCondAssignDefault));
-    {   // iteration body, up to the line search
+    GK(cudaGraphConditionalHandleCreate(&h_redo, body, 0, cudaGraphCondAssignDefault));
+    {   // iteration body: the direction, whose control sets the redo and line-search conditions
         CaptureGuard guard{cs};
         GK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
         guard.active = true;
-        lbfgs_set_graph_handles(h_ls, h_iter);
-        GK(lbfgs_launch_direction_level(c, level, cs));
+        lbfgs_set_graph_handles(h_ls, h_iter, h_redo);
+        GK(lbfgs_launch_direction(c, level, cs));
         GK(capture_leaves(cs, leaves));
         guard.active = false;
         cudaGraph_t g2 = nullptr;
         GK(cudaStreamEndCapture(cs, &g2));
     }
+    cudaGraphNode_t if_redo;
+    cudaGraph_t redo_body = nullptr;
+    GK(add_cond(body, leaves, h_redo, cudaGraphCondTypeIf, &if_redo, &redo_body));
+    {   // IF (not a descent direction): the p0 direction
+        CaptureGuard guard{cs};
+        GK(cudaStreamBeginCaptureToGraph(cs, redo_body, nullptr, nullptr, 0, mode));
+        guard.active = true;
+        lbfgs_set_graph_handles(h_ls, h_iter, 0);
+        GK(lbfgs_launch_redo(c, level, cs));
+        guard.active = false;
+        cudaGraph_t g2 = nullptr;
+        GK(cudaStreamEndCapture(cs, &g2));
+    }
+    leaves.assign(1, if_redo);
     cudaGraphNode_t w_ls;
     cudaGraph_t ls_body = nullptr;
     GK(add_while(body, leaves, h_ls, &w_ls, &ls_body));
@@ -116,7 +139,7 @@ cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
         CaptureGuard guard{cs};
         GK(cudaStreamBeginCaptureToGraph(cs, ls_body, nullptr, nullptr, 0, mode));
         guard.active = true;
-        lbfgs_set_graph_handles(h_ls, h_iter);
+        lbfgs_set_graph_handles(h_ls, h_iter, 0);
         GK(lbfgs_launch_trial(c, level, cs));
         guard.active = false;
         cudaGraph_t g2 = nullptr;
@@ -126,13 +149,13 @@ cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
         CaptureGuard guard{cs};
         GK(cudaStreamBeginCaptureToGraph(cs, body, &w_ls, nullptr, 1, mode));
         guard.active = true;
-        lbfgs_set_graph_handles(h_ls, h_iter);
+        lbfgs_set_graph_handles(h_ls, h_iter, 0);
         GK(lbfgs_launch_accept_level(c, level, cs));
         guard.active = false;
         cudaGraph_t g2 = nullptr;
         GK(cudaStreamEndCapture(cs, &g2));
     }
-    lbfgs_set_graph_handles(0, 0);
+    lbfgs_set_graph_handles(0, 0, 0);
     GK(cudaGraphInstantiate(out, G, 0));
     cudaGraphDestroy(G);
     c->launches = launches0;
@@ -140,4 +163,4 @@ cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
 }
 
 // kernels of one objective evaluation at a level (for the launch statistics)
-int eval_kernel_count(const reg_ctx *c, int level) { return use_fused(c, level) ? 4 : 7; }
+int eval_kernel_count(const reg_ctx *c, int level) { return use_fused(c, level) ? 3 : 7; }

@@ -42,6 +42,7 @@ struct EvalScratch {
     double *partials = nullptr;   // block partial sums
     int max_partials = 0;
     double *scal = nullptr;       // [J, D, S] on the device
+    unsigned *fin_cnt = nullptr;  // arrival counter of the gather that ends a fused evaluation
     size_t part_floats = 0;
 };
 
@@ -114,6 +115,8 @@ cudaError_t launch_prolong(const Level &coarse, const Level &fine, const float *
 // ctl_phase >= 0: the final reduction also runs that L-BFGS control phase.
 cudaError_t launch_eval(reg_ctx *c, int level, const float *u_base, const float *dir, const double *t_dev,
                         float *grad, double *scal_out, int ctl_phase, cudaStream_t s);
+cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha_hy, float *grad, int nD,
+                              const double *pS, int nS, double *scal, int phase, cudaStream_t s);
 cudaError_t launch_finalize_ctl(reg_ctx *c, const double *pD, int nD, const double *pS, int nS, double hbar_half,
                                 double alpha, double hy_half, double *scal, int phase, cudaStream_t s);
 
@@ -122,7 +125,10 @@ cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s);
 cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s);
 cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s);
 cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s);
-void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter);
+void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter, unsigned long long h_redo);
+unsigned long long lbfgs_graph_handle_ls();
+cudaError_t lbfgs_launch_direction(reg_ctx *c, int level, cudaStream_t s);
+cudaError_t lbfgs_launch_redo(reg_ctx *c, int level, cudaStream_t s);
 void lbfgs_state_reset_host(LbfgsState *st, const reg_config &cfg, int max_iter, double Hmin);
 cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const float *S, const float *Y,
                                        const float *g, float *p, double Hmin, cudaStream_t s);

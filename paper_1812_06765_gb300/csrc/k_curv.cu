@@ -173,6 +173,7 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     dim3 gw(gn.x, gn.y, curv_zchunks(L.n[2]));
     double *pS = c->es.partials + nD;
     k_curv_w<<<gw, blk, 0, c->side>>>(g, ub, dir, t_dev, c->es.w, pS);
+    c->launches += 1;
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaEventRecord(c->ev_join, c->side);
@@ -181,15 +182,12 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     if (e != cudaSuccess)
         return e;
     double hy = L.H[0] * L.H[1] * L.H[2];
-    if (fused) {   // grad = (tile partials of P^T r) + alpha hbar_y L^T w
-        e = launch_gather_grad(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, s);
-        if (e != cudaSuccess)
-            return e;
-    } else {       // grad += alpha hbar_y L^T w
-        k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);
-        c->launches += 1;
-    }
     int nS = (int)(gw.x * gw.y * gw.z);
+    if (fused)   // grad = (tile partials of P^T r) + alpha hbar_y L^T w; then J, D, S (+ control)
+        return launch_gather_fin(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, nD, pS, nS, scal_out,
+                                 ctl_phase, s);
+    // multi-pass: grad += alpha hbar_y L^T w, then the final reduction
+    k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);
     double hbar = L.h[0] * L.h[1] * L.h[2];
     c->launches += 2;
     if (ctl_phase >= 0)   // the reduction block also takes the line-search decision

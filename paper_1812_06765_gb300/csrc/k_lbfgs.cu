@@ -16,12 +16,11 @@
 
 #include "batch.h"
 #include "internal.h"
+#include "lbfgs_control.cuh"
 
 namespace {
 
 constexpr int VT = LB_VT;           // threads of the vector kernels
-constexpr int CT = 256;             // threads of the control kernel
-constexpr int ND_ACC = 2 + 4 * LB_MAXS;
 
 // Reduce ND per-thread values over the block; entry `imax` (if >= 0) by max,
 // the others by sum, in FP32 and a fixed order (warp shuffles, then the warp
@@ -47,11 +46,6 @@ __device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, dou
         out[d] = (double)s;
     }
 }
-
-__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
-                                                const double *__restrict__ partials, int nblocks,
-                                                const double *__restrict__ scal, unsigned long long h_ls,
-                                                unsigned long long h_iter);
 
 // Called by every block of a vector pass after block_reduce_write (see VecTail).
 __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restrict__ partials, int nd, int imax,
@@ -88,7 +82,7 @@ __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restr
     if (!s_last || t.phase < 0)
         return;
     __threadfence();
-    lb_control_body(t.phase, t.st, t.gpart, ng, t.scal, t.h_ls, t.h_iter);
+    lb_control_body(t.phase, t.st, t.gpart, ng, t.scal, t.h_ls, t.h_iter, t.h_redo);
 }
 
 // All vector passes read and write 16-byte vectors: u, g, gt and pdir are
@@ -328,347 +322,6 @@ __global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride,
     lb_accept_body(n, stride, st, u, g, gt, pdir, P, Y, partials, tail, blockIdx.x, gridDim.x);
 }
 
-// ---------------------------------------------------------------------------
-// control kernel (one block): reduce the block partials in FP64 in a fixed
-// order, then thread 0 takes the scalar decisions.
-// ---------------------------------------------------------------------------
-__device__ void set_p0(LbfgsState *st)
-{
-    st->dcount = 0;
-    st->cg = st->ginf > 0.0 ? -st->Hmin / st->ginf : 0.0;
-}
-
-// Compact form: with R = upper triangle of S'Y (by age), D its diagonal,
-// gamma = s'y / y'y of the newest pair, q = R^{-1} S'g and
-// w = R^{-T} ((D + gamma Y'Y) q - gamma Y'g):
-//   H g = gamma g + S w - gamma Y q,   p = -H g.
-// Run by one full warp, lane i holding row i: the triangular solves go column
-// by column (q_i, then every remaining row updated at once), so the FP64
-// dependency chain is about 3 count operations long.  1 / R_ii and gamma are
-// taken once, when the pair is stored (FP64 divides cost ~640 cycles here).
-__device__ void set_compact_warp(LbfgsState *st)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int c = st->count;
-    const bool row = lane < c;
-    const int oi = row ? st->order[lane] : 0;
-    const double gamma = st->gamma;
-    const double Rii = row ? st->SY[oi][oi] : 0.0;
-    const double iR = row ? st->iSY[oi] : 0.0;
-    const double Yg = row ? st->Yg[oi] : 0.0;
-    double r = row ? st->tscale[oi] * st->Pg[oi] : 0.0;   // S'g
-    double q = 0.0;
-    for (int i = c - 1; i >= 0; i--) {   // R q = S'g, upper triangular
-        const double qi = __shfl_sync(FULL, r * iR, i);
-        if (lane == i)
-            q = qi;
-        if (lane < i)
-            r = fma(-st->SY[oi][st->order[i]], qi, r);
-    }
-    double acc = 0.0;                     // (Y'Y q)_i
-    for (int j = 0; j < c; j++) {
-        const double qj = __shfl_sync(FULL, q, j);
-        if (row)
-            acc = fma(st->YY[oi][st->order[j]], qj, acc);
-    }
-    r = fma(Rii, q, gamma * (acc - Yg));  // (D + gamma Y'Y) q - gamma Y'g
-    double w = 0.0;
-    for (int i = 0; i < c; i++) {        // R^T w = r, lower triangular
-        const double wi = __shfl_sync(FULL, r * iR, i);
-        if (lane == i)
-            w = wi;
-        if (lane > i && row)
-            r = fma(-st->SY[st->order[i]][oi], wi, r);
-    }
-    if (lane == 0) {
-        st->dcount = c;
-        st->cg = -gamma;
-    }
-    if (row) {
-        st->dslot[lane] = oi;
-        st->cp[lane] = -w * st->tscale[oi];
-        st->cy[lane] = gamma * q;
-    }
-}
-
-__device__ bool finite_d(double x) { return isfinite(x); }
-
-// Cross-block FP64 sum (entry imax: max) of nd values over nblocks block
-// partials (partials[b * nd + d]) in a fixed order.  FP64 instructions cost
-// ~64 cycles per warp instruction whatever the active lanes, so the adds are
-// packed: thread (d, j) sums blocks j, j + J, ... for J groups per value (J
-// about sqrt(nblocks), at most CT / nd), then thread d adds its J group sums.
-__device__ __forceinline__ void control_reduce(const double *__restrict__ partials, int nblocks, int nd, int imax,
-                                               double *red, double *scratch)
-{
-    const int t = threadIdx.x;
-    int J = 1;
-    while (J * J < nblocks)
-        J++;
-    if (J > CT / nd)
-        J = CT / nd;
-    if (t < nd * J) {
-        const int d = t % nd, j = t / nd;
-        double s = 0.0;   // the max entry is a max of absolute values: 0 is its identity
-        for (int b = j; b < nblocks; b += J) {
-            const double x = __ldcg(partials + (size_t)b * nd + d);
-            s = (d == imax) ? fmax(s, x) : s + x;
-        }
-        scratch[t] = s;
-    }
-    __syncthreads();
-    if (t < nd) {
-        double s = scratch[t];
-        for (int j = 1; j < J; j++) {
-            const double x = scratch[j * nd + t];
-            s = (t == imax) ? fmax(s, x) : s + x;
-        }
-        red[t] = s;
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
-                                                    const double *__restrict__ partials, int nblocks,
-                                                    const double *__restrict__ scal, unsigned long long h_ls,
-                                                    unsigned long long h_iter)
-{
-    // the state lives in shared memory while the single decision thread works
-    // on it: one coalesced copy in and out instead of hundreds of dependent
-    // global accesses
-    __shared__ LbfgsState S;
-    __shared__ double red[ND_ACC];
-    __shared__ double scratch[CT];
-    __shared__ int s_store, s_compact;
-    constexpr int NW = (int)(sizeof(LbfgsState) / sizeof(int));
-    for (int i = threadIdx.x; i < NW; i += blockDim.x)
-        reinterpret_cast<int *>(&S)[i] = reinterpret_cast<const int *>(gst)[i];
-    __syncthreads();
-    LbfgsState *st = &S;
-    const int nd = phase == LB_ACCEPTED ? ND_ACC : 2;
-    const int imax = (phase == LB_INIT || phase == LB_ACCEPTED) ? 1 : -1;
-    const bool need = phase != LB_ARMIJO && !(phase == LB_ACCEPTED && (!st->active || st->ls != LS_ACCEPTED)) &&
-                      !(phase == LB_DIR_REDO && !st->redo_dir) && !(phase == LB_DIR && !st->iter_continue);
-    if (need)
-        control_reduce(partials, nblocks, nd, imax, red, scratch);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-    s_store = 0;
-    s_compact = 0;
-    switch (phase) {
-    case LB_INIT: {
-        st->J = scal[0];
-        st->D = scal[1];
-        st->S = scal[2];
-        st->J0 = st->J;
-        st->gg = red[0];
-        st->ginf = red[1];
-        st->g0norm = sqrt(red[0]);
-        st->gtol2 = st->tol_grad_rel * st->tol_grad_rel * red[0];
-        st->k = 0;
-        st->bodies = 0;
-        st->evals = 1;
-        st->small_count = 0;
-        st->count = 0;
-        st->free_slot = 0;
-        st->status = 0;
-        st->retried = 0;
-        st->redo_dir = 0;
-        st->done = 0;
-        if (!finite_d(st->J) || !finite_d(st->gg)) {
-            st->status = -5;
-            st->done = 1;
-        }
-        if (st->max_iter <= 0 || st->g0norm == 0.0)
-            st->done = 1;
-        set_p0(st);
-        st->iter_continue = !st->done;
-        st->active = 0;
-        st->ls_continue = 0;
-        break;
-    }
-    case LB_DIR: {
-        st->active = st->iter_continue;
-        if (!st->iter_continue)
-            break;
-        st->gtp = red[0];
-        st->pp = red[1];
-        st->redo_dir = 0;
-        if (!(st->gtp < 0.0) && st->dcount > 0) { // not a descent direction: reset the memory
-            st->count = 0;
-            set_p0(st);
-            st->redo_dir = 1;
-        }
-        st->t = 1.0;
-        st->trial = 0;
-        st->ls = LS_RUNNING;
-        st->ls_continue = 1;
-        break;
-    }
-    case LB_DIR_REDO: {
-        if (!st->redo_dir)
-            break;
-        st->gtp = red[0];
-        st->pp = red[1];
-        st->redo_dir = 0;
-        break;
-    }
-    case LB_ARMIJO: {
-        if (!st->active || !st->ls_continue)   // this pair is not searching (batched levels)
-            break;
-        st->Jt = scal[0];
-        st->Dt = scal[1];
-        st->St = scal[2];
-        st->evals++;
-        if (finite_d(st->Jt) && st->Jt <= st->J + st->c1 * st->t * st->gtp) {
-            st->ls = LS_ACCEPTED;
-            st->ls_continue = 0;
-            st->lcount = st->count + 1;
-            for (int j = 0; j < st->count; j++)
-                st->lslot[j] = st->order[j];
-            st->lslot[st->count] = st->free_slot;
-        } else {
-            st->trial++;
-            if (st->trial >= st->max_bt) {
-                st->ls_continue = 0;
-                if (st->dcount > 0 && !st->retried) { // one retry from a fresh memory
-                    st->ls = LS_RETRY;
-                    st->retried = 1;
-                    st->count = 0;
-                    set_p0(st);
-                } else {
-                    st->ls = LS_FAILED;
-                    st->status = 1;
-                    st->done = 1;
-                }
-            } else {
-                st->t *= 0.5;
-            }
-        }
-        break;
-    }
-    case LB_ACCEPTED: {
-        if (!st->active)   // this pair did not run the iteration (batched levels)
-            break;
-        if (++st->bodies > 2 * st->max_iter + 8) {   // cannot happen with the rules below; a hard stop
-            st->status = -6;
-            st->done = 1;
-            st->iter_continue = 0;
-            break;
-        }
-        if (st->ls == LS_RETRY) {
-            st->iter_continue = 1;
-            break;
-        }
-        if (st->ls != LS_ACCEPTED) {
-            st->iter_continue = 0;
-            break;
-        }
-        for (int j = 0; j < st->lcount; j++) {
-            int s = st->lslot[j];
-            st->Pg[s] = red[2 + 4 * j];
-            st->Yg[s] = red[3 + 4 * j];
-            st->Py[s] = red[4 + 4 * j];
-            st->Yy[s] = red[5 + 4 * j];
-        }
-        double Jprev = st->J;
-        st->J = st->Jt;
-        st->D = st->Dt;
-        st->S = st->St;
-        st->k++;
-        st->gg = red[0];
-        st->ginf = red[1];
-        const int f = st->free_slot;
-        const double tn = st->t;
-        double sy = tn * st->Py[f], ss = tn * tn * st->pp, yy = st->Yy[f];
-        // curvature test s'y > 1e-10 ||s|| ||y||, compared as squares (sy > 0)
-        if (sy > 0.0 && sy * sy > 1e-20 * ss * yy) {   // keep the pair
-            st->tscale[f] = tn;
-            s_store = 1;   // 1 / s'y and gamma are formed by the warp below
-            for (int j = 0; j < st->lcount; j++) {
-                int s = st->lslot[j];
-                st->SY[s][f] = st->tscale[s] * st->Py[s];
-                st->YY[s][f] = st->Yy[s];
-                st->YY[f][s] = st->Yy[s];
-            }
-            if (st->count == st->m) {
-                int ev = st->order[0];
-                for (int j = 0; j < st->m - 1; j++)
-                    st->order[j] = st->order[j + 1];
-                st->order[st->m - 1] = f;
-                st->free_slot = ev;
-            } else {
-                st->order[st->count++] = f;
-                unsigned used = 0;
-                for (int j = 0; j < st->count; j++)
-                    used |= 1u << st->order[j];
-                int fs = 0;
-                while (used & (1u << fs))
-                    fs++;
-                st->free_slot = fs;
-            }
-        }
-        st->retried = 0;
-        if (!finite_d(st->J) || !finite_d(st->gg)) {
-            st->status = -5;
-            st->done = 1;
-        } else if (st->k >= st->max_iter) {
-            st->done = 1;
-        } else if (!st->fixed_iters) {
-            if (st->gg <= st->gtol2) {   // ||g|| <= tol_grad_rel ||g0||
-                st->done = 1;
-            } else if (fabs(Jprev - st->J) <= st->tol_j_rel * (1.0 + fabs(st->J0))) {
-                if (++st->small_count >= st->tol_j_count)
-                    st->done = 1;
-            } else {
-                st->small_count = 0;
-            }
-        }
-        if (!st->done) {
-            if (st->count > 0)
-                s_compact = 1;
-            else
-                set_p0(st);
-        }
-        st->iter_continue = !st->done;
-        break;
-    }
-    default:
-        break;
-    }
-    }   // thread 0
-    __syncthreads();
-    if (threadIdx.x < 32 && (s_store || s_compact)) {
-        const int lane = threadIdx.x;
-        if (s_store) {   // the pair in the free slot's predecessor position was stored
-            const int f = st->order[st->count - 1];
-            const double num = lane == 1 ? st->SY[f][f] : 1.0;
-            const double den = lane == 1 ? st->YY[f][f] : st->SY[f][f];
-            const double x = num / den;   // lanes 0 and 1 divide at once
-            const double gm = __shfl_sync(0xffffffffu, x, 1);
-            if (lane == 0) {
-                st->iSY[f] = x;
-                st->gamma = gm;
-            }
-            __syncwarp();
-        }
-        if (s_compact)
-            set_compact_warp(st);
-    }
-#if CUDART_VERSION >= 12040
-    if (threadIdx.x == 0) {
-        if (h_ls)
-            cudaGraphSetConditional((cudaGraphConditionalHandle)h_ls, st->ls_continue ? 1u : 0u);
-        if (h_iter)
-            cudaGraphSetConditional((cudaGraphConditionalHandle)h_iter, st->iter_continue ? 1u : 0u);
-    }
-#endif
-    __syncthreads();
-    for (int i = threadIdx.x; i < NW; i += blockDim.x)
-        reinterpret_cast<int *>(gst)[i] = reinterpret_cast<const int *>(&S)[i];
-}
-
 // Reduction of an objective evaluation's block partials (J, D, S into scal)
 // followed, in the same block, by a control phase on those scalars (ARMIJO
 // after a trial evaluation).
@@ -680,7 +333,7 @@ __global__ void __launch_bounds__(512) k_finalize_ctl(const double *__restrict__
 {
     finalize_body(pD, nD, pS, nS, hbar_half, alpha, hy_half, scal);
     __syncthreads();
-    lb_control_body(phase, st, nullptr, 0, scal, h_ls, h_iter);
+    lb_control_body(phase, st, nullptr, 0, scal, h_ls, h_iter, 0ULL);
 }
 
 // ---------------------------------------------------------------------------
@@ -696,7 +349,7 @@ __global__ void __launch_bounds__(VT) k_lb_vector_batch(const PairLevel *__restr
         const int p = find_pair(chunk_off, npairs, item);
         const PairLevel &P = pl[p];
         const int b = item - __ldg(chunk_off + p);
-        const VecTail tail{P.lgpart, P.lcnt, -1, P.st, nullptr, 0ULL, 0ULL};   // control: its own kernel
+        const VecTail tail{P.lgpart, P.lcnt, -1, P.st, nullptr, 0ULL, 0ULL, 0ULL};   // control: its own kernel
         if (step == 0)
             lb_init_dots_body(P.n, P.g, P.lpart, tail, b, P.nchunks);
         else if (step == 1 || step == 2)
@@ -713,7 +366,7 @@ __global__ void __launch_bounds__(CT) k_lb_control_batch(const PairLevel *__rest
 {
     const PairLevel &P = pl[blockIdx.x];
     lb_control_body(phase, P.st, P.lgpart, (P.nchunks + LB_RG - 1) / LB_RG, phase == LB_INIT ? P.scal : P.scal_t,
-                    0ULL, 0ULL);
+                    0ULL, 0ULL, 0ULL);
 }
 
 // condition of a batched loop: 1 while any pair still iterates (which = 0) or
@@ -865,20 +518,24 @@ void lbfgs_state_reset_host(LbfgsState *st, const reg_config &cfg, int max_iter,
     st->t = 1.0;
 }
 
-static unsigned long long g_h_ls = 0, g_h_iter = 0;  // conditional handles while capturing
+static unsigned long long g_h_ls = 0, g_h_iter = 0, g_h_redo = 0;  // conditional handles while capturing
 
-void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter)
+void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter, unsigned long long h_redo)
 {
     g_h_ls = h_ls;
     g_h_iter = h_iter;
+    g_h_redo = h_redo;
 }
+
+unsigned long long lbfgs_graph_handle_ls() { return g_h_ls; }
 
 // folded reduction + control of a vector pass (handles: the graph conditions
 // the phase sets while a level graph is captured)
-static VecTail tail_of(reg_ctx *c, int phase, const double *scal, bool use_ls_handle, bool use_iter_handle)
+static VecTail tail_of(reg_ctx *c, int phase, const double *scal, bool use_ls_handle, bool use_iter_handle,
+                       bool use_redo_handle = false)
 {
     return VecTail{c->lb.gpart, c->lb.cnt, phase, c->lb.st, scal, use_ls_handle ? g_h_ls : 0ULL,
-                   use_iter_handle ? g_h_iter : 0ULL};
+                   use_iter_handle ? g_h_iter : 0ULL, use_redo_handle ? g_h_redo : 0ULL};
 }
 
 // ring slots start on 16-byte boundaries
@@ -891,6 +548,8 @@ cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s)
     // arrival counters start the level at zero (every launch leaves them so)
     cudaError_t e = cudaMemsetAsync(c->lb.cnt, 0, sizeof(unsigned) * c->lb.cnt_len, s);
     if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->es.fin_cnt, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess)
         e = launch_eval(c, level, c->lb.u, nullptr, nullptr, c->lb.g, c->es.scal, -1, s);
     if (e != cudaSuccess)
         return e;
@@ -899,20 +558,33 @@ cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s)
+cudaError_t lbfgs_launch_direction(reg_ctx *c, int level, cudaStream_t s)
 {
     long long n = 3 * c->L[level].nn, sd = ring_stride(n);
     int nb = num_blocks_for(c, (n + 3) / 4, VT);
     k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0,
-                                     tail_of(c, LB_DIR, nullptr, true, false));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return e;
-    // the p0 redo (a no-op pass unless the direction was not a descent direction)
+                                     tail_of(c, LB_DIR, nullptr, true, false, true));
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// the p0 redo: a direction pass that runs only when the compact-form direction
+// was not a descent direction (a no-op pass otherwise; a graph runs it under an
+// IF node that the direction's control sets)
+cudaError_t lbfgs_launch_redo(reg_ctx *c, int level, cudaStream_t s)
+{
+    long long n = 3 * c->L[level].nn, sd = ring_stride(n);
+    int nb = num_blocks_for(c, (n + 3) / 4, VT);
     k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1,
                                      tail_of(c, LB_DIR_REDO, nullptr, true, false));
-    c->launches += 2;
+    c->launches += 1;
     return cudaGetLastError();
+}
+
+cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s)
+{
+    cudaError_t e = lbfgs_launch_direction(c, level, s);
+    return e == cudaSuccess ? lbfgs_launch_redo(c, level, s) : e;
 }
 
 cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s)

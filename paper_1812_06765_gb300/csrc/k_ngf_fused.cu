@@ -36,6 +36,7 @@
 
 #include "batch.h"
 #include "internal.h"
+#include "lbfgs_control.cuh"
 #include "ngf_math.cuh"
 
 namespace {
@@ -429,7 +430,7 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
     int ky = by * blockDim.y + threadIdx.y;
     int kz = bz;
     if (kx >= g.n[0] || ky >= g.n[1])
-        return;
+        return;   // (only this function: a caller's barrier after it is still reached)
     const int hz = tz / 2;
     const size_t plane_stride = (size_t)(hz + 1) * NE;
     float s[3] = {0.f, 0.f, 0.f};
@@ -480,6 +481,43 @@ __global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *_
                                                      float *__restrict__ grad)
 {
     gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// The end of an evaluation after the gather: the block that completes the
+// launch reduces the D and S block partials into scal = [J, D, S] (the fixed
+// order of finalize_body) and, for phase >= 0, takes that L-BFGS control phase
+// (the Armijo decision of a trial point) in the same block.
+struct FinArgs {
+    const double *pD, *pS;  // block partials of D (fused tiles) and S (curvature blocks)
+    int nD, nS;
+    double hbar_half, alpha, hy_half;
+    double *scal;
+    unsigned *cnt;          // arrival counter, zero between launches
+    int phase;              // -1: no control phase
+    LbfgsState *st;
+    unsigned long long h_ls;
+};
+
+__global__ void __launch_bounds__(256) k_gather_fin(LevelGeom g, const float *__restrict__ part, int tz, int ntx,
+                                                    int nty, int ntz, const float *__restrict__ w, float alpha_hy,
+                                                    float *__restrict__ grad, FinArgs f)
+{
+    gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
+    __shared__ int s_last;
+    __syncthreads();
+    if (linear_tid() == 0)
+        s_last = atomicAdd(f.cnt, 1u) == gridDim.x * gridDim.y * gridDim.z - 1u;
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    finalize_body(f.pD, f.nD, f.pS, f.nS, f.hbar_half, f.alpha, f.hy_half, f.scal);
+    if (linear_tid() == 0)
+        *f.cnt = 0;
+    if (f.phase >= 0) {
+        __syncthreads();
+        lb_control_body(f.phase, f.st, nullptr, 0, f.scal, f.h_ls, 0ULL, 0ULL);
+    }
 }
 
 }  // namespace
@@ -587,6 +625,32 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
             k_ngf_fused<false, float><<<grd, blk, SMEM_BYTES, s>>>(a);
     }
     *n_partials = a.ntx * a.nty * a.ntz;
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha_hy, float *grad, int nD,
+                              const double *pS, int nS, double *scal, int phase, cudaStream_t s)
+{
+    const Level &L = c->L[level];
+    int tz = fused_tz(L, c->num_sms), ntx, nty, ntz;
+    fused_grid(L, tz, ntx, nty, ntz);
+    dim3 blk(32, 8, 1);
+    dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
+    FinArgs f;
+    f.pD = c->es.partials;
+    f.nD = nD;
+    f.pS = pS;
+    f.nS = nS;
+    f.hbar_half = 0.5 * L.h[0] * L.h[1] * L.h[2];
+    f.alpha = c->cfg.alpha;
+    f.hy_half = 0.5 * L.H[0] * L.H[1] * L.H[2];
+    f.scal = scal;
+    f.cnt = c->es.fin_cnt;
+    f.phase = phase;
+    f.st = c->lb.st;
+    f.h_ls = phase >= 0 ? lbfgs_graph_handle_ls() : 0ULL;
+    k_gather_fin<<<gn, blk, 0, s>>>(L.geom(), c->es.part, tz, ntx, nty, ntz, w, alpha_hy, grad, f);
     c->launches += 1;
     return cudaGetLastError();
 }

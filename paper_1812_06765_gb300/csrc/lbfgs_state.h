@@ -28,6 +28,7 @@ struct LbfgsState {
     int bodies;        // iteration bodies run (accepted steps, retries, the final failed search)
     int retried;       // the p0 retry of this iteration has been used
     int redo_dir;      // the direction must be recomputed as p0
+    int redos;         // p0 redos on this level (each one extra direction pass)
     int ls;            // LbSearch
     int ls_continue;   // 1 while the line search needs another trial
     int iter_continue; // 1 while the level needs another iteration
@@ -67,5 +68,5 @@ struct VecTail {
     int phase;
     LbfgsState *st;
     const double *scal;              // [J, D, S] the phase reads (INIT)
-    unsigned long long h_ls, h_iter; // graph conditions the phase sets (0: none)
+    unsigned long long h_ls, h_iter, h_redo; // graph conditions the phase sets (0: none)
 };

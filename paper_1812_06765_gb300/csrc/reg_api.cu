@@ -49,6 +49,7 @@ void free_buffers(reg_ctx *c)
     cudaFree(e.part);
     cudaFree(e.partials);
     cudaFree(e.scal);
+    cudaFree(e.fin_cnt);
     c->es = EvalScratch();
     LbfgsBuffers &b = c->lb;
     cudaFree(b.u);
@@ -261,6 +262,8 @@ int allocate_buffers(reg_ctx *c)
     CK(cudaMalloc(&es.w, sizeof(float) * nmax));
     CK(cudaMalloc(&es.partials, sizeof(double) * maxpart));
     CK(cudaMalloc(&es.scal, sizeof(double) * 4));
+    CK(cudaMalloc(&es.fin_cnt, sizeof(unsigned)));
+    CK(cudaMemset(es.fin_cnt, 0, sizeof(unsigned)));
     es.max_partials = maxpart;
     LbfgsBuffers &b = c->lb;
     b.n = nmax;
@@ -613,9 +616,9 @@ int run_level_graph(reg_ctx *c, int level)
     if (r != REG_OK) return r;
     const LbfgsState *sh = c->lb.st_host;
     const int ek = eval_kernel_count(c, level);
-    // init: evaluation + norms (control folded in); per body: 2 directions + accept;
-    // per trial: evaluation (Armijo folded into its final reduction)
-    c->launches += (ek + 1) + 3LL * sh->bodies + (long long)ek * (sh->evals - 1);
+    // init: evaluation + norms (control folded in); per body: direction + accept, plus
+    // the p0 redos the IF node ran; per trial: evaluation (Armijo in its final reduction)
+    c->launches += (ek + 1) + 2LL * sh->bodies + sh->redos + (long long)ek * (sh->evals - 1);
     return REG_OK;
 }
 

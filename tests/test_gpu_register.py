@@ -102,7 +102,7 @@ def test_register_128_ct_three_levels(reg_mod, orc):
 
 @pytest.mark.parametrize("impl", [0, 1])
 def test_graph_and_host_driven_levels_agree(reg_mod, impl):
-    """One graph launch per level (device-side loops) runs exactly the kernels the
+    """One graph launch per level (device-side loops) runs the kernels the
     host-driven loop runs, in the same order: results are bit-identical."""
     p = make_pair(1, dims=(64, 64, 48))
     kw = dict(levels=2, tau=0.1, alpha=50.0, max_iter=[25, 25], eval_impl=impl)
@@ -115,7 +115,11 @@ def test_graph_and_host_driven_levels_agree(reg_mod, impl):
     (u0, s0), (u1, s1) = out
     np.testing.assert_array_equal(u0, u1)
     assert s0["iters"] == s1["iters"] and s0["evals"] == s1["evals"]
-    assert s0["kernel_launches"] == s1["kernel_launches"]
+    # the host loop queues the p0-redo direction pass every iteration (a no-op
+    # pass unless the direction was not a descent direction); the graph runs it
+    # under an IF node only when needed: at most one launch fewer per iteration
+    skipped = s0["kernel_launches"] - s1["kernel_launches"]
+    assert 0 <= skipped <= sum(s0["evals"]), (s0["kernel_launches"], s1["kernel_launches"])
     assert s0["J"] == s1["J"]
 
 
