@@ -64,6 +64,9 @@ def parse_args(argv=None):
     ap.add_argument("--report", action="store_true",
                     help="one JSON line per single-pair workload (64^3, 128^3, 256^3, 4D-CT shape): GPU registration "
                          "and evaluation times, accuracy, and the FP64 oracle on all host cores and on one core")
+    ap.add_argument("--pt-ab", action="store_true",
+                    help="time one full-resolution evaluation with each P^T design: fused gather, multi-pass "
+                         "gather (Eq. 3), multi-pass atomic scatter, multi-pass 8-colour scatter")
     ap.add_argument("--pairs", type=int, default=None, help="pairs of the uneven batch (workload 4; default 64)")
     ap.add_argument("--gen-procs", type=int, default=None, help="processes that generate the batch's pairs")
     return ap.parse_args(argv)
@@ -755,6 +758,53 @@ def run_report(args):
         reg.close()
 
 
+def run_pt_ab(args):
+    """One full-resolution evaluation of the workload with each P^T design; the
+    multi-pass forms differ only in their last step (gather, atomic, 8 colours)."""
+    import torch
+    import paper_1812_06765_gb300 as reg_pkg
+    from paper_1812_06765_gb300 import _lib
+    from synth import random_field
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    c, p = workload(args.config, 0)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    R_d, T_d = torch.from_numpy(p["R"]).to(dev), torch.from_numpy(p["T"]).to(dev)
+    out = {"workload": c["name"], "image": list(p["dims"]), "evals_timed": args.eval_iters,
+           "l2": "flushed before every timed evaluation"}
+    names = {0: "fused pass (tile partials + node gather)", 1: "multi-pass, P^T gather (Eq. 3)",
+             2: "multi-pass, P^T atomic scatter", 3: "multi-pass, P^T 8-colour scatter"}
+    ref = None
+    for impl in (0, 1, 2, 3):
+        reg = reg_pkg.Registration(reg_pkg.make_config(levels=1, tau=c["eta"], alpha=c["alpha"], eval_impl=impl),
+                                   stream=stream)
+        reg.set_images(R_d, T_d, p["spacing"])
+        u = torch.from_numpy(random_field(reg.level_info(0)["nodes"], 5, 5.0)).to(dev)
+        g = torch.empty_like(u)
+        ms, ngf = [], []
+        for i in range(args.eval_iters + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            J, D, S, _ = reg.eval(u, 0, grad=g)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                ms.append(e0.elapsed_time(e1))
+                ngf.append(_lib.reg_last_ngf_ms(reg.h))
+        if ref is None:
+            ref = (J, g.clone())
+        out[names[impl]] = {"eval_ms": statistics.median(ms), "ngf_pass_ms": statistics.median(ngf),
+                            "J_rel_diff_vs_fused": abs(J - ref[0]) / abs(ref[0]),
+                            "grad_rel_l2_vs_fused": float((g - ref[1]).norm() / ref[1].norm())}
+        reg.close()
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ----------------------------------------------------------------------------
@@ -801,6 +851,8 @@ def main(argv=None):
         run_reference(args)
     elif args.report:
         run_report(args)
+    elif args.pt_ab:
+        run_pt_ab(args)
     elif args.config == 4:
         run_batch(args)
     else:

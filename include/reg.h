@@ -75,7 +75,10 @@ typedef struct reg_config {
     int start_level;      /* coarsest level solved; -1 = levels - 1 */
     int max_iter[REG_MAX_LEVELS];       /* accepted iterations per level (index = level) */
     int node_dims[REG_MAX_LEVELS][3];   /* deformation grid per level; 0 = m_d / 2 + 1 */
-    int eval_impl;        /* 0 fused objective pass, 1 multi-pass (intermediates in HBM) */
+    int eval_impl;        /* 0 fused objective pass; 1 multi-pass (intermediates in HBM,
+                             P^T by the gather of Eq. 3); A/B baselines of P^T: 2 multi-pass
+                             with an atomic scatter (summation order not fixed), 3 multi-pass
+                             with an 8-colour scatter on ratio-2 levels (gather elsewhere) */
     int use_graph;        /* 1: each pyramid level runs as one CUDA graph launch */
     int image_dtype;      /* 0: FP32 images; 1: the fused pass reads BF16 copies of R and T
                              (arithmetic stays FP32; levels without the fused pass use FP32) */

@@ -163,4 +163,10 @@ cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
 }
 
 // kernels of one objective evaluation at a level (for the launch statistics)
-int eval_kernel_count(const reg_ctx *c, int level) { return use_fused(c, level) ? 3 : 7; }
+int eval_kernel_count(const reg_ctx *c, int level)
+{
+    if (use_fused(c, level))
+        return 3;   // fused pass, curvature, gather + final reduction
+    static const int ngf[3] = {4, 3, 10};   // multi-pass NGF kernels per P^T variant
+    return ngf[mp_pt_variant(c, level)] + 3;   // + curvature, its gradient, final reduction
+}

@@ -157,3 +157,15 @@ inline bool use_fused(const reg_ctx *c, int level)
 {
     return c->cfg.eval_impl == 0 && fused_eligible(c->L[level]);
 }
+
+// P^T of the multi-pass path: 0 node-centric gather (Eq. 3; eval_impl 0 and 1),
+// 1 atomic scatter (eval_impl 2), 2 8-colour scatter (eval_impl 3 on ratio-2
+// levels; other levels use the gather)
+inline int mp_pt_variant(const reg_ctx *c, int level)
+{
+    if (c->cfg.eval_impl == 2)
+        return 1;
+    if (c->cfg.eval_impl == 3 && fused_eligible(c->L[level]))
+        return 2;
+    return 0;
+}

@@ -7,6 +7,16 @@
 //   k_mp_resid  : NGF residual on interior voxels (Eq. 2), v = d psi / d grad T
 //   k_mp_adjoint: g = adjoint central difference of v, r = g grad T (chain rule)
 //   k_mp_pt     : grad D = P^T r as the node-centric gather of Eq. 3
+//
+// Two A/B variants of the last two steps measure what the gather form of
+// Eq. 3 buys (Sec. 2.2 names both as slower designs it replaced):
+//   eval_impl 2, k_mp_adjoint_atomic: r per voxel, scattered to its 8 nodes
+//     with atomicAdd (summation order not fixed);
+//   eval_impl 3, k_mp_adjoint_colour: ratio-2 grids only; a thread owns the
+//     2 x 2 x 2 voxels of one node cell (voxels 2k, 2k+1 per dimension lie in
+//     cell [k, k+1]) and writes the cell's 8 nodes without atomics; cells of
+//     equal (k_x, k_y, k_z) parity never share a node, so 8 launches (one per
+//     parity colour) cover the grid in a fixed order.
 #include "internal.h"
 #include "ngf_math.cuh"
 
@@ -121,6 +131,94 @@ __global__ void __launch_bounds__(256) k_mp_pt(LevelGeom g, const float *__restr
     out[2 * g.nn + k] = s2;
 }
 
+// r at voxel (x, y, z): the adjoint central difference of v times grad T
+__device__ __forceinline__ void mp_r(const LevelGeom &g, const float *__restrict__ v, const float *__restrict__ dT,
+                                     int x, int y, int z, float r[3])
+{
+    size_t i = x + (size_t)g.m[0] * (y + (size_t)g.m[1] * z);
+    size_t st[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
+    int j[3] = {x, y, z};
+    float s = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const float *vd = v + d * g.nv;
+        float lo = j[d] > 0 ? __ldg(vd + i - st[d]) : 0.f;
+        float hi = j[d] < g.m[d] - 1 ? __ldg(vd + i + st[d]) : 0.f;
+        s = fmaf(lo - hi, 0.5f * g.ih[d], s);
+    }
+    float gj = 0.5f * g.hbar * s;
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        r[c] = gj * __ldg(dT + c * g.nv + i);
+}
+
+// A/B variant: r scattered to the 8 nodes of the voxel's cell by atomicAdd
+// (P's weights from the per-dimension tables: node k0 weight 1 - w1, k0 + 1 weight w1).
+__global__ void __launch_bounds__(256) k_mp_adjoint_atomic(LevelGeom g, const float *__restrict__ v,
+                                                           const float *__restrict__ dT, float *__restrict__ out)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int z = blockIdx.z;
+    if (x >= g.m[0] || y >= g.m[1])
+        return;
+    float r[3];
+    mp_r(g, v, dT, x, y, z, r);
+    const int kx = g.pk0[0][x], ky = g.pk0[1][y], kz = g.pk0[2][z];
+    const float wx = g.pw1[0][x], wy = g.pw1[1][y], wz = g.pw1[2][z];
+#pragma unroll
+    for (int n = 0; n < 8; n++) {
+        const int a = n & 1, b = (n >> 1) & 1, cz = n >> 2;
+        const float w = (a ? wx : 1.f - wx) * (b ? wy : 1.f - wy) * (cz ? wz : 1.f - wz);
+        const size_t k = (kx + a) + (size_t)g.n[0] * ((ky + b) + (size_t)g.n[1] * (kz + cz));
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            atomicAdd(out + c * g.nn + k, w * r[c]);
+    }
+}
+
+// A/B variant: one thread per node cell of one parity colour, no atomics
+// (ratio-2 grids: voxels 2k, 2k+1 in cell k, weights 3/4, 1/4 of nodes k, k+1
+// for voxel 2k and 1/4, 3/4 for voxel 2k+1).
+__global__ void __launch_bounds__(256) k_mp_adjoint_colour(LevelGeom g, const float *__restrict__ v,
+                                                           const float *__restrict__ dT, float *__restrict__ out,
+                                                           int colour)
+{
+    const int cx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + (colour & 1);
+    const int cy = 2 * (blockIdx.y * blockDim.y + threadIdx.y) + ((colour >> 1) & 1);
+    const int cz = 2 * blockIdx.z + (colour >> 2);
+    if (cx >= g.n[0] - 1 || cy >= g.n[1] - 1 || cz >= g.n[2] - 1)
+        return;
+    float acc[8][3];
+#pragma unroll
+    for (int n = 0; n < 8; n++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            acc[n][c] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {   // the cell's voxels
+        const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+        float r[3];
+        mp_r(g, v, dT, 2 * cx + qx, 2 * cy + qy, 2 * cz + qz, r);
+        const float wx = qx ? 0.75f : 0.25f, wy = qy ? 0.75f : 0.25f, wz = qz ? 0.75f : 0.25f;
+#pragma unroll
+        for (int n = 0; n < 8; n++) {
+            const int a = n & 1, b = (n >> 1) & 1, e = n >> 2;
+            const float w = (a ? wx : 1.f - wx) * (b ? wy : 1.f - wy) * (e ? wz : 1.f - wz);
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                acc[n][c] = fmaf(w, r[c], acc[n][c]);
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < 8; n++) {
+        const size_t k = (cx + (n & 1)) + (size_t)g.n[0] * ((cy + ((n >> 1) & 1)) + (size_t)g.n[1] * (cz + (n >> 2)));
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            out[c * g.nn + k] += acc[n][c];
+    }
+}
+
 }  // namespace
 
 // Multi-pass D and grad D; D block partials go to partials[0 .. returned count).
@@ -134,9 +232,27 @@ cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const f
     dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
     k_mp_warp<<<gv, blk, 0, s>>>(g, L.T, ub, dir, t_dev, c->es.Tw, c->es.dT);
     k_mp_resid<<<gv, blk, 0, s>>>(g, c->es.Tw, L.R, (float)c->cfg.tau, (float)c->cfg.rho, c->es.v, partials);
-    k_mp_adjoint<<<gv, blk, 0, s>>>(g, c->es.v, c->es.dT, c->es.r);
-    k_mp_pt<<<gn, blk, 0, s>>>(g, c->es.r, grad);
     *n_partials = (int)(gv.x * gv.y * gv.z);
-    c->launches += 4;
+    const int pt = mp_pt_variant(c, level);
+    if (pt == 0) {   // node-centric gather (Eq. 3)
+        k_mp_adjoint<<<gv, blk, 0, s>>>(g, c->es.v, c->es.dT, c->es.r);
+        k_mp_pt<<<gn, blk, 0, s>>>(g, c->es.r, grad);
+        c->launches += 4;
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * 3 * L.nn, s);
+    if (e != cudaSuccess)
+        return e;
+    if (pt == 1) {   // atomic scatter
+        k_mp_adjoint_atomic<<<gv, blk, 0, s>>>(g, c->es.v, c->es.dT, grad);
+        c->launches += 3;
+        return cudaGetLastError();
+    }
+    // 8-colour scatter over the node cells
+    const int cells[3] = {L.n[0] - 1, L.n[1] - 1, L.n[2] - 1};
+    dim3 gc(((cells[0] + 1) / 2 + 31) / 32, ((cells[1] + 1) / 2 + 7) / 8, (cells[2] + 1) / 2);
+    for (int colour = 0; colour < 8; colour++)
+        k_mp_adjoint_colour<<<gc, blk, 0, s>>>(g, c->es.v, c->es.dT, grad, colour);
+    c->launches += 10;
     return cudaGetLastError();
 }

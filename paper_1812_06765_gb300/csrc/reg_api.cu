@@ -82,7 +82,7 @@ int validate_config(const reg_config *cfg, std::string &msg)
         msg = buf;
     } else if (cfg->max_backtracks < 1) msg = "max_backtracks must be >= 1";
     else if (cfg->start_level >= cfg->levels) msg = "start_level must be < levels";
-    else if (cfg->eval_impl != 0 && cfg->eval_impl != 1) msg = "eval_impl must be 0 or 1";
+    else if (cfg->eval_impl < 0 || cfg->eval_impl > 3) msg = "eval_impl must be 0, 1, 2 or 3";
     else if (cfg->image_dtype != 0 && cfg->image_dtype != 1) msg = "image_dtype must be 0 (FP32) or 1 (BF16)";
     else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
     else if (cfg->autotune != 0 && cfg->autotune != 1) msg = "autotune must be 0 or 1";

@@ -22,7 +22,9 @@ def reg_mod():
     return reg
 
 
-EVAL_IMPLS = [0, 1]   # 0: fused pass (ratio-2 grids), 1: multi-pass
+# 0: fused pass (ratio-2 grids); 1: multi-pass with the gather P^T of Eq. 3;
+# A/B baselines of P^T: 2 atomic scatter, 3 8-colour scatter (ratio-2 levels)
+EVAL_IMPLS = [0, 1, 2, 3]
 
 # (dims, spacing, nodes or None, tau, rho, alpha, amplitude of u in mm)
 CASES = [
