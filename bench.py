@@ -193,8 +193,10 @@ def committed_traffic(kernel, digest):
 
 
 def workload(config_id, rank):
-    from synth import CONFIGS, make_pair, batch_sizes
+    from synth import CONFIGS, make_pair, make_pair_parallel, batch_sizes
     c = CONFIGS[config_id]
+    if c.get("slab_noise"):   # full-resolution volume: planes generated by a process pool
+        return c, make_pair_parallel(config_id, pair=rank)
     dims = batch_sizes(rank + 1)[rank] if c["dims"] is None else None
     p = make_pair(config_id, pair=rank, dims=dims)
     return c, p

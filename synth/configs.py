@@ -36,6 +36,11 @@ CONFIGS = {
             spacing=(0.97, 0.97, 2.5), levels=4, eta=0.1, alpha=50.0, mem=5,
             max_iter=100, c1=1e-4, kind="lung", max_cc_mm=20.0,
             max_lat_mm=5.0, landmarks=300),
+    # full-resolution CT (the size the paper's GPU could not hold): 512^3 at 0.75 mm,
+    # 5 levels, nodes 257^3; the noise is drawn per slab so slabs can be made apart
+    5: dict(name="c5_ct512_fullres_5level", dims=(512, 512, 512), spacing=(0.75, 0.75, 0.75),
+            levels=5, eta=0.1, alpha=50.0, mem=5, max_iter=100, c1=1e-4,
+            kind="ct", max_disp_mm=15.0, organs=30, slab_noise=32),
     # batch of 64 uneven pairs at 1.5 mm, 3 levels, 60 iterations per level
     4: dict(name="c4_batch64_uneven", dims=None, spacing=(1.5, 1.5, 1.5),
             levels=3, eta=0.1, alpha=50.0, mem=5, max_iter=60, c1=1e-4,

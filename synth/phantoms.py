@@ -286,10 +286,11 @@ def make_pair(config_id, pair=0, dims=None):
         R = _sample(ph, dims, spacing)
         T = _sample(ph, dims, spacing, field, margin) + rng.normal(0.0, 0.01, size=(dims[2], dims[1], dims[0]))
         R, T = np.clip(R, 0, 1), np.clip(T, 0, 1)
+    elif kind == "ct" and cfg.get("slab_noise"):
+        ph, field = _ct_model(rng, dims, spacing, cfg)
+        R, T = _ct_slab_pair(ph, field, dims, spacing, cfg, seed_for(config_id, pair), 0, dims[2])
     elif kind == "ct":
-        ph = _ct_phantom(rng, dims, spacing, cfg["organs"])
-        field = ModeField(rng, L, 4, 2, breathing=Breathing(L, decay_apex=False), mode_share=0.2)
-        field.normalise(dims, spacing, cfg["max_disp_mm"])
+        ph, field = _ct_model(rng, dims, spacing, cfg)
         margin = cfg["max_disp_mm"]
         noise = lambda: rng.normal(0.0, 20.0, size=(dims[2], dims[1], dims[0]))  # noqa: E731
         R = _hu_to_unit(_sample(ph, dims, spacing) + noise())
@@ -314,6 +315,65 @@ def make_pair(config_id, pair=0, dims=None):
     out["T"] = np.ascontiguousarray(T, dtype=np.float32)
     out["field"] = field
     return out
+
+
+def _ct_model(rng, dims, spacing, cfg):
+    """CT phantom and its breathing-like field (the draws every CT workload makes first)."""
+    L = np.asarray(dims, float) * np.asarray(spacing, float)
+    ph = _ct_phantom(rng, dims, spacing, cfg["organs"])
+    field = ModeField(rng, L, 4, 2, breathing=Breathing(L, decay_apex=False), mode_share=0.2)
+    field.normalise(dims, spacing, cfg["max_disp_mm"])
+    return ph, field
+
+
+def _ct_slab_pair(ph, field, dims, spacing, cfg, seed, z0, z1):
+    """Planes z0 .. z1-1 of R and T of a slab-noise CT workload: noise of slab
+    s = z // slab from its own PCG64 stream (seed * 4096 + s), so any split of
+    the planes gives the same volume."""
+    slab = int(cfg["slab_noise"])
+    mx, my, _ = dims
+    R = np.empty((z1 - z0, my, mx), dtype=np.float32)
+    T = np.empty((z1 - z0, my, mx), dtype=np.float32)
+    for s0 in range((z0 // slab) * slab, z1, slab):
+        a, b = max(s0, z0), min(s0 + slab, z1)
+        nrng = _rng(int(seed) * 4096 + s0 // slab)
+        nR = nrng.normal(0.0, 20.0, size=(slab, my, mx))[a - s0:b - s0]
+        nT = nrng.normal(0.0, 20.0, size=(slab, my, mx))[a - s0:b - s0]
+        X, Y, Z = voxel_centres(dims, spacing, a, b)
+        R[a - z0:b - z0] = _hu_to_unit(ph(X, Y, Z) + nR)
+        d = field(X, Y, Z)
+        T[a - z0:b - z0] = _hu_to_unit(ph(X + d[0], Y + d[1], Z + d[2], margin=cfg["max_disp_mm"]) + nT)
+    return R, T
+
+
+def _slab_job(job):
+    config_id, pair, dims, z0, z1 = job
+    cfg = CONFIGS[config_id]
+    rng = _rng(seed_for(config_id, pair))
+    spacing = tuple(cfg["spacing"])
+    ph, field = _ct_model(rng, dims, spacing, cfg)
+    return z0, _ct_slab_pair(ph, field, dims, spacing, cfg, seed_for(config_id, pair), z0, z1)
+
+
+def make_pair_parallel(config_id, pair=0, dims=None, procs=None):
+    """make_pair of a slab-noise workload, its planes generated by a spawn pool
+    (the same arrays and field as make_pair)."""
+    import multiprocessing as mp
+    import os
+    cfg = CONFIGS[config_id]
+    dims = tuple(dims if dims is not None else cfg["dims"])
+    slab = int(cfg["slab_noise"])
+    jobs = [(config_id, pair, dims, z0, min(dims[2], z0 + slab)) for z0 in range(0, dims[2], slab)]
+    procs = procs or min(len(jobs), os.cpu_count() or 1, 16)
+    R = np.empty((dims[2], dims[1], dims[0]), dtype=np.float32)
+    T = np.empty_like(R)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for z0, (r, t) in pool.imap_unordered(_slab_job, jobs):
+            R[z0:z0 + r.shape[0]] = r
+            T[z0:z0 + t.shape[0]] = t
+    rng = _rng(seed_for(config_id, pair))
+    ph, field = _ct_model(rng, dims, tuple(cfg["spacing"]), cfg)
+    return dict(dims=dims, spacing=tuple(cfg["spacing"]), config=config_id, pair=pair, R=R, T=T, field=field)
 
 
 def _landmarks(rng, lungs, field, extent, n):
