@@ -179,8 +179,9 @@ def source_digest(files):
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel, digest):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+def committed_traffic(kernel, digest, workload_name, tz):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    this source, this workload and this tiling (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -188,6 +189,8 @@ def committed_traffic(kernel, digest):
         d = json.load(f)
     e = d.get(kernel)
     if not e or e.get("source_digest") != digest:
+        return None
+    if e.get("workload") != workload_name or e.get("fused_tz") != tz:
         return None
     return e.get("dram_bytes_per_launch_full_size")
 
@@ -359,7 +362,7 @@ def run_ours(args):
     part_bytes = 4 * tiles * (tz // 2 + 1) * 315 if impl == 0 else 12 * nn
     kernel_bytes = 8 * nv + 12 * nn + part_bytes
     achieved = kernel_bytes / (ngf_ms * 1e-3) / 1e9
-    traffic = committed_traffic(kernel, source_digest(FUSED_KERNEL_SOURCES))
+    traffic = committed_traffic(kernel, source_digest(FUSED_KERNEL_SOURCES), c["name"], tz)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
