@@ -462,6 +462,8 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
     levels = c["levels"]
     kw = dict(levels=levels, tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"], c1=c["c1"])
+    if args.fused_tz is not None:
+        kw["fused_tz"] = args.fused_tz
     regs = [reg_pkg.Registration(reg_pkg.make_config(**kw), stream=stream) for _ in range(n)]
     Rd = [torch.from_numpy(p[0]).to(dev) for p in pairs]
     Td = [torch.from_numpy(p[1]).to(dev) for p in pairs]
@@ -527,15 +529,17 @@ def run_batch(args):
     pairs_s_batch = pairs_all / (tb / 1000.0)
     pairs_s_loop = pairs_all / (tl / 1000.0)
 
-    # equal accuracy: the batch gives each pair the result of its own registration
+    # accuracy of both forms: the batch tiles the fused pass for throughput and the
+    # loop for one pair at a time, so the two runs round differently; compare the
+    # reached NGF distance and the displacements
     max_diff = max(float((ub - ul).abs().max()) for (ub, _), (ul, _) in zip(res_b, res_l))
-    same_counts = all(sb["iters"] == sl["iters"] and sb["evals"] == sl["evals"]
-                      for (_, sb), (_, sl) in zip(res_b, res_l))
-    d_ratio = []
+    mean_diff = statistics.mean(float((ub - ul).abs().mean()) for (ub, _), (ul, _) in zip(res_b, res_l))
+    d_ratio, d_ratio_l = [], []
     for i in range(n):
         z = torch.zeros(regs[i].node_shape(0), dtype=torch.float32, device=dev)
         J0, D0, _, _ = regs[i].eval(z, 0)
         d_ratio.append(res_b[i][1]["D_final"] / D0)
+        d_ratio_l.append(res_l[i][1]["D_final"] / D0)
 
     # algorithmic evaluation bytes (images, u and grad J at every evaluation) over the batch's step time
     eval_bytes = 0
@@ -585,9 +589,13 @@ def run_batch(args):
                               "own_time_p99_ms": percentile_ms(own_loop, 99),
                               "gpu_launches_per_step": launches_loop // max(1, args.steps)},
             "batched_over_loop": pairs_s_batch / pairs_s_loop,
-            "equal_accuracy": {"max_abs_u_diff_mm": max_diff, "same_iterations_and_evaluations": same_counts,
-                               "D_final_over_D0_median": float(np.median(d_ratio)),
-                               "D_final_over_D0_max": float(np.max(d_ratio))},
+            "equal_accuracy": {"D_final_over_D0_median_batched": float(np.median(d_ratio)),
+                               "D_final_over_D0_median_loop": float(np.median(d_ratio_l)),
+                               "D_final_over_D0_max_batched": float(np.max(d_ratio)),
+                               "D_final_over_D0_max_loop": float(np.max(d_ratio_l)),
+                               "mean_abs_u_diff_mm": mean_diff, "max_abs_u_diff_mm": max_diff,
+                               "tiling": "batched: throughput rule per level; loop: autotuned per pair "
+                                         "(tests/test_gpu_batch.py: with the same tiling the two are bit-identical)"},
             "effective_eval_gbs": eff_gbs,
             "roofline": None,
             "e2e": {"value": world * n / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,

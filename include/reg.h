@@ -86,8 +86,9 @@ typedef struct reg_config {
                              on each level and keeps the fastest (cached per geometry for the
                              process; the first call of a geometry synchronises the stream);
                              0: a fixed rule */
-    int fused_tz;         /* 0: autotune / rule; else this z segment length on every level
-                             (one of 2, 4, 8, 16, 32, 64, 128) */
+    int fused_tz;         /* 0: autotune / rule; -1: the throughput rule (fewest z steps in
+                             total, the tiling reg_register_batch uses); else this z segment
+                             length on every level (one of 2, 4, 8, 16, 32, 64, 128) */
     int reserved[3];
 } reg_config;
 
@@ -220,7 +221,10 @@ int reg_register(reg_handle h, float *u_out, int out_is_device, const float *u_i
  * over a work list of (pair, tile / block) items, and pairs that have finished
  * their level or their line search skip their items.  Every pair runs exactly
  * the computation of reg_register with its own configuration, so its result is
- * the one reg_register gives.  u_out[i]: the finest displacement of pair i
+ * the one reg_register gives when the pair's handle tiles the fused pass the
+ * same way: the batch keeps every SM busy, so it tiles each level by the
+ * throughput rule (cfg.fused_tz = -1) whatever tiling the handle's own
+ * registrations use.  u_out[i]: the finest displacement of pair i
  * (device pointers if out_is_device, else host); stats (nullable) receives n
  * entries (kernel_launches counts the launches of the whole batch).  Work runs
  * on hs[0]'s stream; the call synchronises it.  Returns REG_OK,

@@ -296,6 +296,23 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     for (int l = start; l >= 0 && status >= 0; l--) {
         CK(cudaEventRecord(c0->lev_ev[l + 1], s));
         int tiles = 0, nodes = 0, chunks = 0, curv = 0;
+        // the batch keeps every SM busy: tile each pair's level by the throughput
+        // rule (a handle's own tiling, tuned for one pair alone, is restored after)
+        std::vector<int> own_tz(n);
+        for (int i = 0; i < n; i++) {
+            own_tz[i] = hs[i]->L[l].tz;
+            hs[i]->L[l].tz = fused_tz_throughput(hs[i]->L[l]);
+        }
+        struct RestoreTz {
+            reg_handle *hs;
+            int n, l;
+            std::vector<int> &tz;
+            ~RestoreTz()
+            {
+                for (int i = 0; i < n; i++)
+                    hs[i]->L[l].tz = tz[i];
+            }
+        } restore{hs, n, l, own_tz};
         for (int i = 0; i < n; i++) {
             reg_ctx *ci = hs[i];
             const Level &L = ci->L[l];

@@ -140,6 +140,7 @@ bool fused_eligible(const Level &L);
 size_t fused_part_floats(const Level &L, int num_sms);
 int fused_tz(const Level &L, int num_sms);
 bool fused_tz_valid(int tz);
+int fused_tz_throughput(const Level &L);
 // times every z segment length on the level's images at u_zero (3 node planes
 // of zeros) and keeps the fastest in L.tz; cached per geometry
 cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStream_t s);

@@ -546,6 +546,24 @@ static int fused_tz_default(const Level &L, int num_sms)
 
 int fused_tz(const Level &L, int num_sms) { return L.tz > 0 ? L.tz : fused_tz_default(L, num_sms); }
 
+// Throughput rule: the z segment length with the fewest z steps in total,
+// ntz * (tz / 2 + 5) (ties: the longer one).  The right choice when other work
+// keeps every SM busy (a batch of pairs); a single pair alone wants short
+// segments that fill the GPU, which the autotuner finds.
+int fused_tz_throughput(const Level &L)
+{
+    int best = 0;
+    long long best_steps = 0;
+    for (int tz : TZ_CAND) {
+        const long long steps = (long long)((L.m[2] + tz - 1) / tz) * (tz / 2 + 5);
+        if (best == 0 || steps <= best_steps) {
+            best = tz;
+            best_steps = steps;
+        }
+    }
+    return best;
+}
+
 bool fused_tz_valid(int tz)
 {
     for (int t : TZ_CAND)

@@ -86,8 +86,8 @@ int validate_config(const reg_config *cfg, std::string &msg)
     else if (cfg->image_dtype != 0 && cfg->image_dtype != 1) msg = "image_dtype must be 0 (FP32) or 1 (BF16)";
     else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
     else if (cfg->autotune != 0 && cfg->autotune != 1) msg = "autotune must be 0 or 1";
-    else if (cfg->fused_tz != 0 && !fused_tz_valid(cfg->fused_tz))
-        msg = "fused_tz must be 0 or one of 2, 4, 8, 16, 32, 64, 128";
+    else if (cfg->fused_tz != 0 && cfg->fused_tz != -1 && !fused_tz_valid(cfg->fused_tz))
+        msg = "fused_tz must be 0, -1 or one of 2, 4, 8, 16, 32, 64, 128";
     else return REG_OK;
     return REG_ERR_ARG;
 }
@@ -446,6 +446,8 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
             continue;
         if (cfg.fused_tz > 0) {
             c->L[l].tz = cfg.fused_tz;
+        } else if (cfg.fused_tz == -1) {
+            c->L[l].tz = fused_tz_throughput(c->L[l]);
         } else if (cfg.autotune) {
             CK(cudaMemsetAsync(c->lb.pdir, 0, sizeof(float) * 3 * c->L[l].nn, c->stream));
             CK(fused_autotune(c, l, c->lb.pdir, c->stream));

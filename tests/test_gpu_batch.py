@@ -38,15 +38,20 @@ def _cfg(reg_mod, **kw):
 
 @pytest.mark.parametrize("image_dtype", ["f32", "bf16"])
 def test_batch_equals_single_registrations(reg_mod, image_dtype):
+    # the batch tiles every level by the throughput rule; single registrations
+    # with that tiling (fused_tz = -1) must give the same result bit for bit
     pairs = _pairs()
     single = []
     for p in pairs:
-        r = reg_mod.Registration(_cfg(reg_mod, image_dtype=image_dtype)).set_images(p["R"], p["T"], p["spacing"])
+        r = reg_mod.Registration(_cfg(reg_mod, image_dtype=image_dtype, fused_tz=-1)).set_images(p["R"], p["T"],
+                                                                                              p["spacing"])
         single.append(r.register(out="numpy"))
         r.close()
     regs = [reg_mod.Registration(_cfg(reg_mod, image_dtype=image_dtype)).set_images(p["R"], p["T"], p["spacing"])
-            for p in pairs]
+            for p in pairs]   # autotuned tiling of their own
+    own = [[r.level_tiling(lv) for lv in range(3)] for r in regs]
     batch = reg_mod.register_batch(regs, out="numpy")
+    assert own == [[r.level_tiling(lv) for lv in range(3)] for r in regs]   # restored after the batch
     for (u1, s1), (u2, s2) in zip(single, batch):
         np.testing.assert_array_equal(u1, u2)
         assert s1["iters"] == s2["iters"] and s1["evals"] == s2["evals"]
