@@ -464,6 +464,8 @@ def run_batch(args):
     kw = dict(levels=levels, tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"], c1=c["c1"])
     if args.fused_tz is not None:
         kw["fused_tz"] = args.fused_tz
+    if args.host_loop:
+        kw["use_graph"] = False
     regs = [reg_pkg.Registration(reg_pkg.make_config(**kw), stream=stream) for _ in range(n)]
     Rd = [torch.from_numpy(p[0]).to(dev) for p in pairs]
     Td = [torch.from_numpy(p[1]).to(dev) for p in pairs]

@@ -227,7 +227,8 @@ int reg_register(reg_handle h, float *u_out, int out_is_device, const float *u_i
  * registrations use.  u_out[i]: the finest displacement of pair i
  * (device pointers if out_is_device, else host); stats (nullable) receives n
  * entries (kernel_launches counts the launches of the whole batch).  Work runs
- * on hs[0]'s stream; the call synchronises it.  Returns REG_OK,
+ * on hs[0]'s stream, as one CUDA graph per level, or queued from the host when
+ * hs[0]'s cfg.use_graph is 0; the call synchronises the stream.  Returns REG_OK,
  * REG_WARN_LINESEARCH (some pair), or an error (argument errors are described
  * by reg_last_error(NULL), CUDA errors by reg_last_error(hs[0])). */
 int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_is_device, reg_stats *stats);

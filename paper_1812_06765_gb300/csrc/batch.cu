@@ -82,7 +82,7 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
 struct BatchDev {
     PairLevel *pl = nullptr;
     int *off = nullptr;      // [4][npairs + 1]: tiles, gather blocks, vector blocks, curvature blocks
-    int *counters = nullptr; // [2]: runs of the iteration and search conditions
+    int *counters = nullptr; // [4]: runs of the iteration and search conditions, then their last values
 };
 
 struct CaptureGuard {
@@ -240,6 +240,51 @@ cudaError_t build_batch_graph(const BatchLaunch &B, cudaStream_t cs, cudaGraphEx
 
 int cap(long long v, long long hi) { return (int)(v < 1 ? 1 : (v > hi ? hi : v)); }
 
+// The same level, queued from the host (use_graph = 0): the kernels of the graph
+// in the same order, the loop conditions read back after each condition kernel.
+// For profilers that cannot see the kernels inside conditional graph nodes.
+cudaError_t run_batch_level_host(const BatchLaunch &B, int *counters, cudaStream_t s, int max_rounds)
+{
+    int h[4];
+    auto cond = [&](int which, bool &out) -> cudaError_t {
+        cudaError_t e = B.cond(which, 0, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h, counters, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        out = h[2 + which] != 0;
+        return e;
+    };
+#define HK(call)                             \
+    do {                                     \
+        cudaError_t _e = (call);             \
+        if (_e != cudaSuccess) return _e;    \
+    } while (0)
+    bool it = false, ls = false;
+    HK(B.eval(0, s));
+    HK(B.vec(0, s));
+    HK(B.ctl(LB_INIT, s));
+    HK(cond(0, it));
+    int rounds = 0;   // bounded like the graph: every pair stops after its own bounded loops
+    while (it && rounds++ < max_rounds) {
+        HK(B.vec(1, s));
+        HK(B.ctl(LB_DIR, s));
+        HK(B.vec(2, s));
+        HK(B.ctl(LB_DIR_REDO, s));
+        HK(cond(1, ls));
+        while (ls && rounds++ < max_rounds) {
+            HK(B.eval(1, s));
+            HK(B.ctl(LB_ARMIJO, s));
+            HK(cond(1, ls));
+        }
+        HK(B.vec(3, s));
+        HK(B.ctl(LB_ACCEPTED, s));
+        HK(cond(0, it));
+    }
+#undef HK
+    return rounds > max_rounds ? cudaErrorTimeout : cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_is_device, reg_stats *stats)
@@ -280,7 +325,7 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     BatchDev d;
     CK(cudaMallocAsync((void **)&d.pl, sizeof(PairLevel) * n, s));
     CK(cudaMallocAsync((void **)&d.off, sizeof(int) * 4 * (n + 1), s));
-    CK(cudaMallocAsync((void **)&d.counters, sizeof(int) * 2, s));
+    CK(cudaMallocAsync((void **)&d.counters, sizeof(int) * 4, s));
     // every pair's own stream work (prolongations, state uploads) is ordered on c0's stream
     for (int i = 0; i < n; i++) {
         CK(cudaMemsetAsync(hs[i]->lb.u, 0, sizeof(float) * 3 * hs[i]->L[start].nn, s));
@@ -340,25 +385,37 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
         hoff[3 * (n + 1) + n] = curv;
         CK(cudaMemcpyAsync(d.pl, hpl.data(), sizeof(PairLevel) * n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d.off, hoff.data(), sizeof(int) * hoff.size(), cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(d.counters, 0, sizeof(int) * 2, s));
+        CK(cudaMemsetAsync(d.counters, 0, sizeof(int) * 4, s));
         BatchLaunch B{&d, n, tiles, nodes, chunks, curv, cap(tiles, c0->num_sms), cap(nodes, 8LL * c0->num_sms),
                       cap(chunks, 4LL * c0->num_sms), cap(curv, 8LL * c0->num_sms), bf16, c0->device,
                       c0->side, c0->ev_fork, c0->ev_join};
-        cudaGraphExec_t exec = nullptr;
-        cudaError_t e = build_batch_graph(B, c0->cap_stream, &exec);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(d.pl, s);
-            cudaFreeAsync(d.off, s);
-            cudaFreeAsync(d.counters, s);
-            return cuda_err(c0, e, "reg_register_batch: building the level graph");
+        cudaError_t e = cudaSuccess;
+        if (c0->cfg.use_graph) {
+            cudaGraphExec_t exec = nullptr;
+            e = build_batch_graph(B, c0->cap_stream, &exec);
+            if (e != cudaSuccess) {
+                cudaFreeAsync(d.pl, s);
+                cudaFreeAsync(d.off, s);
+                cudaFreeAsync(d.counters, s);
+                return cuda_err(c0, e, "reg_register_batch: building the level graph");
+            }
+            e = cudaGraphLaunch(exec, s);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(exec);
+        } else {
+            int max_it = 0, max_bt = 0;
+            for (int i = 0; i < n; i++) {
+                max_it = max_it > hs[i]->cfg.max_iter[l] ? max_it : hs[i]->cfg.max_iter[l];
+                max_bt = max_bt > hs[i]->cfg.max_backtracks ? max_bt : hs[i]->cfg.max_backtracks;
+            }
+            e = run_batch_level_host(B, d.counters, s, 4 * (max_it + 1) * (max_bt + 1) + 16);
         }
-        e = cudaGraphLaunch(exec, s);
         int cnt[2] = {0, 0};
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(cnt, d.counters, sizeof cnt, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(s);
-        cudaGraphExecDestroy(exec);
         CK(e);
         // launches: init 7; per iteration body 8; per search round 6
         const long long bodies = cnt[0] - 1, rounds = cnt[1] - bodies;

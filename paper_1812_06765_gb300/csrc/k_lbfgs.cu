@@ -141,6 +141,8 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
         }
     }
     __syncthreads();
+    if (!s_run && tail.phase < 0)   // nothing to compute and no control phase to reach: done
+        return;
     float v[2] = {0.f, 0.f};
     if (s_run) {   // otherwise only the arrival below (partials unused)
         const int dc = s_dc;
@@ -227,6 +229,8 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
             s_slot[j] = st->lslot[j];
     }
     __syncthreads();
+    if (!s_ok && tail.phase < 0)   // nothing to compute and no control phase to reach: done
+        return;
     float v[ND_ACC];
 #pragma unroll
     for (int d = 0; d < ND_ACC; d++)
@@ -375,13 +379,15 @@ __global__ void k_batch_condition(const PairLevel *__restrict__ pl, int npairs, 
                                   int *__restrict__ counters)
 {
     if (threadIdx.x == 0 && counters)
-        counters[which]++;
+        counters[which]++;   // counters[2 + which]: the last value (read by a host-driven loop)
     int any = 0;
     for (int p = threadIdx.x; p < npairs; p += 32) {
         const LbfgsState *st = pl[p].st;
         any |= which == 0 ? st->iter_continue : (st->active && st->ls_continue);
     }
     any = __any_sync(0xffffffffu, any);
+    if (threadIdx.x == 0 && counters)
+        counters[2 + which] = any;
 #if CUDART_VERSION >= 12040
     if (threadIdx.x == 0 && h)
         cudaGraphSetConditional((cudaGraphConditionalHandle)h, any ? 1u : 0u);

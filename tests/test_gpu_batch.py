@@ -79,3 +79,21 @@ def test_batch_rejects_mixed_or_repeated_inputs(reg_mod):
         reg_mod.register_batch([regs[0], r_lv])
     for r in regs + [r_odd, r_lv]:
         r.close()
+
+
+def test_batch_host_driven_equals_graph(reg_mod):
+    """use_graph = 0 queues the batched level's kernels from the host in the
+    graph's order (for profilers): the same result bit for bit."""
+    pairs = _pairs()[:3]
+    out = []
+    for graph in (1, 0):
+        regs = [reg_mod.Registration(_cfg(reg_mod, use_graph=graph)).set_images(p["R"], p["T"], p["spacing"])
+                for p in pairs]
+        out.append(reg_mod.register_batch(regs, out="numpy"))
+        for r in regs:
+            r.close()
+    for (u1, s1), (u2, s2) in zip(*out):
+        np.testing.assert_array_equal(u1, u2)
+        assert s1["iters"] == s2["iters"] and s1["evals"] == s2["evals"]
+        assert s1["kernel_launches"] == s2["kernel_launches"]
+
