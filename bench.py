@@ -584,6 +584,7 @@ def run_batch(args):
             "batched": {"pairs_s": pairs_s_batch, "p50_ms": percentile_ms(done_batch, 50),
                         "p99_ms": percentile_ms(done_batch, 99), "step_ms": statistics.mean(t_batch),
                         "level_device_s": res_b[0][1]["level_seconds"],
+                        "tiling_rule_per_level": res_b[0][1]["tiling"],
                         "gpu_launches_per_step": launches_batch // max(1, args.steps)},
             "per_pair_loop": {"pairs_s": pairs_s_loop, "p50_ms": percentile_ms(done_loop, 50),
                               "p99_ms": percentile_ms(done_loop, 99), "step_ms": statistics.mean(t_loop),
@@ -596,8 +597,9 @@ def run_batch(args):
                                "D_final_over_D0_max_batched": float(np.max(d_ratio)),
                                "D_final_over_D0_max_loop": float(np.max(d_ratio_l)),
                                "mean_abs_u_diff_mm": mean_diff, "max_abs_u_diff_mm": max_diff,
-                               "tiling": "batched: throughput rule per level; loop: autotuned per pair "
-                                         "(tests/test_gpu_batch.py: with the same tiling the two are bit-identical)"},
+                               "tiling": "batched: the batch autotuner's rule per level (batched.tiling_rule_per_level); "
+                                         "loop: each pair's single-pair autotuned tiling (tests/test_gpu_batch.py: "
+                                         "with the same tiling the two forms are bit-identical)"},
             "effective_eval_gbs": eff_gbs,
             "roofline": None,
             "e2e": {"value": world * n / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,

@@ -105,6 +105,10 @@ typedef struct reg_stats {
     int status;
     double level_seconds[REG_MAX_LEVELS]; /* device time of each level, its prolongation included
                                              (CUDA events on the handle's stream) */
+    int tiling[REG_MAX_LEVELS];       /* fused-pass tiling per level: reg_register, the z segment
+                                         length (0: multi-pass level); reg_register_batch, the
+                                         rule the batch used (0 each pair's own tiling, -1 the
+                                         throughput rule, T > 0 one segment length T) */
 } reg_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */

@@ -172,7 +172,8 @@ class Registration:
         stats = dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L],
                      level_status=list(st.level_status)[:L], J=list(st.J)[:L], J_final=st.J_final,
                      D_final=st.D_final, S_final=st.S_final, seconds=st.seconds,
-                     kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L])
+                     kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L],
+                     tiling=list(st.tiling)[:L])
         return u, stats
 
     def _node_tensor(self, u, level):
@@ -216,7 +217,8 @@ def _stats_dict(rc, st):
     L = st.levels
     return dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L], level_status=list(st.level_status)[:L],
                 J=list(st.J)[:L], J_final=st.J_final, D_final=st.D_final, S_final=st.S_final,
-                kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L])
+                kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L],
+                tiling=list(st.tiling)[:L])
 
 
 def register_batch(regs, out="torch"):

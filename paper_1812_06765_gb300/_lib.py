@@ -43,7 +43,7 @@ class RegStats(ctypes.Structure):
         ("level_status", ctypes.c_int * MAX_LEVELS), ("J", ctypes.c_double * MAX_LEVELS),
         ("J_final", ctypes.c_double), ("D_final", ctypes.c_double), ("S_final", ctypes.c_double),
         ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong), ("status", ctypes.c_int),
-        ("level_seconds", ctypes.c_double * MAX_LEVELS),
+        ("level_seconds", ctypes.c_double * MAX_LEVELS), ("tiling", ctypes.c_int * MAX_LEVELS),
     ]
 
 

@@ -11,6 +11,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "batch.h"
@@ -240,6 +242,97 @@ cudaError_t build_batch_graph(const BatchLaunch &B, cudaStream_t cs, cudaGraphEx
 
 int cap(long long v, long long hi) { return (int)(v < 1 ? 1 : (v > hi ? hi : v)); }
 
+// Tiling rules of a batched level: 0 each pair's own tiling (its single-pair
+// autotuning), -1 the throughput rule (fewest z steps in total), T > 0 one z
+// segment length T for every pair (capped at the first candidate that spans
+// the pair's depth).
+int rule_tz(int rule, const Level &L, int own)
+{
+    if (rule == 0)
+        return own > 0 ? own : fused_tz_throughput(L);
+    if (rule < 0)
+        return fused_tz_throughput(L);
+    int tz = rule;
+    while (tz > 2 && tz / 2 >= L.m[2])
+        tz /= 2;
+    return tz;
+}
+
+std::mutex g_btune_mu;
+std::map<std::vector<int>, int> g_btune;   // (level, SMs, image type, pair dims...) -> rule
+
+// Batch autotuner: times the batched fused pass (at the pairs' current u) under
+// each candidate rule - one warm launch, then the better of two event timings -
+// and returns the fastest rule.  Cached per batch geometry for the process.
+int batch_tiling_rule(reg_handle *hs, int n, int l, const std::vector<int> &own_tz, BatchDev &d,
+                      std::vector<PairLevel> &hpl, std::vector<int> &hoff, bool bf16, cudaStream_t s,
+                      cudaError_t *err)
+{
+    reg_ctx *c0 = hs[0];
+    std::vector<int> key{l, c0->num_sms, bf16 ? 1 : 0};
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++)
+            key.push_back(hs[i]->L[l].m[k]);
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        auto it = g_btune.find(key);
+        if (it != g_btune.end())
+            return it->second;
+    }
+    static const int rules[] = {0, -1, 16, 32, 64, 128};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    int best = -1;
+    float best_ms = 0.f;
+    for (int rule : rules) {
+        if (e != cudaSuccess)
+            break;
+        int tiles = 0;
+        for (int i = 0; i < n; i++) {
+            hs[i]->L[l].tz = rule_tz(rule, hs[i]->L[l], own_tz[i]);
+            fill_pair_level(hs[i], l, hpl[i]);
+            hoff[i] = tiles;
+            tiles += hpl[i].nD;
+        }
+        hoff[n] = tiles;
+        e = cudaMemcpyAsync(d.pl, hpl.data(), sizeof(PairLevel) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d.off, hoff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
+        float t = 0.f;
+        for (int r = -1; r < 2 && e == cudaSuccess; r++) {
+            if (r >= 0)
+                e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess)
+                e = launch_fused_batch(d.pl, d.off, n, tiles, 0, bf16, cap(tiles, c0->num_sms), c0->device, s);
+            if (e == cudaSuccess && r >= 0)
+                e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess && r >= 0)
+                e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess && r >= 0)
+                e = cudaEventElapsedTime(&ms, e0, e1);
+            if (r >= 0)
+                t = (r == 0 || ms < t) ? ms : t;
+        }
+        if (e == cudaSuccess && (best == -1 || t < best_ms)) {
+            best = rule;
+            best_ms = t;
+        }
+    }
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    *err = e;
+    if (e != cudaSuccess)
+        return -1;
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    g_btune[key] = best;
+    return best;
+}
+
 // The same level, queued from the host (use_graph = 0): the kernels of the graph
 // in the same order, the loop conditions read back after each condition kernel.
 // For profilers that cannot see the kernels inside conditional graph nodes.
@@ -341,13 +434,13 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     for (int l = start; l >= 0 && status >= 0; l--) {
         CK(cudaEventRecord(c0->lev_ev[l + 1], s));
         int tiles = 0, nodes = 0, chunks = 0, curv = 0;
-        // the batch keeps every SM busy: tile each pair's level by the throughput
-        // rule (a handle's own tiling, tuned for one pair alone, is restored after)
+        // Tiling of the batched level: the batch keeps every SM busy, so the
+        // single-pair tiling of each handle is not necessarily the right one.
+        // hs[0]'s cfg.fused_tz forces a rule; otherwise the batch autotuner picks
+        // one (each handle's own tiling is restored after the level).
         std::vector<int> own_tz(n);
-        for (int i = 0; i < n; i++) {
+        for (int i = 0; i < n; i++)
             own_tz[i] = hs[i]->L[l].tz;
-            hs[i]->L[l].tz = fused_tz_throughput(hs[i]->L[l]);
-        }
         struct RestoreTz {
             reg_handle *hs;
             int n, l;
@@ -358,14 +451,29 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
                     hs[i]->L[l].tz = tz[i];
             }
         } restore{hs, n, l, own_tz};
+        if (l < start)   // u at the level start: prolonged from the coarser level
+            for (int i = 0; i < n; i++) {
+                reg_ctx *ci = hs[i];
+                CK(launch_prolong(ci->L[l + 1], ci->L[l], ci->lb.u, ci->lb.g, s));
+                CK(cudaMemcpyAsync(ci->lb.u, ci->lb.g, sizeof(float) * 3 * ci->L[l].nn, cudaMemcpyDeviceToDevice,
+                                   s));
+                launches++;
+            }
+        int rule = c0->cfg.fused_tz;
+        if (rule == 0 && !c0->cfg.autotune)
+            rule = -1;
+        if (rule == 0) {   // timed at the pairs' u of the level start
+            cudaError_t te = cudaSuccess;
+            rule = batch_tiling_rule(hs, n, l, own_tz, d, hpl, hoff, bf16, s, &te);
+            CK(te);
+        }
+        for (int i = 0; i < n; i++)
+            hs[i]->L[l].tz = rule_tz(rule, hs[i]->L[l], own_tz[i]);
+        for (int i = 0; i < n; i++)
+            st[i].tiling[l] = rule;
         for (int i = 0; i < n; i++) {
             reg_ctx *ci = hs[i];
             const Level &L = ci->L[l];
-            if (l < start) {
-                CK(launch_prolong(ci->L[l + 1], L, ci->lb.u, ci->lb.g, s));
-                CK(cudaMemcpyAsync(ci->lb.u, ci->lb.g, sizeof(float) * 3 * L.nn, cudaMemcpyDeviceToDevice, s));
-                launches++;
-            }
             double Hmin = fmin(L.H[0], fmin(L.H[1], L.H[2]));
             lbfgs_state_reset_host(ci->lb.st_host, ci->cfg, ci->cfg.max_iter[l], Hmin);
             CK(cudaMemcpyAsync(ci->lb.st, ci->lb.st_host, sizeof(LbfgsState), cudaMemcpyHostToDevice, s));

@@ -667,6 +667,7 @@ int reg_register(reg_handle c, float *u_out, int out_is_device, const float *u_i
         local.iters[l] = sh->k;
         local.evals[l] = sh->evals;
         local.J[l] = sh->J;
+        local.tiling[l] = use_fused(c, l) ? fused_tz(c->L[l], c->num_sms) : 0;
         if (sh->status == -5) return set_err(c, REG_ERR_NUMERIC, "reg_register: non-finite J or gradient at level %d", l);
         if (sh->status == -6)
             return set_err(c, REG_ERR_TIMEOUT, "reg_register: level %d exceeded its loop bound", l);

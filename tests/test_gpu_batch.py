@@ -47,11 +47,10 @@ def test_batch_equals_single_registrations(reg_mod, image_dtype):
                                                                                               p["spacing"])
         single.append(r.register(out="numpy"))
         r.close()
-    regs = [reg_mod.Registration(_cfg(reg_mod, image_dtype=image_dtype)).set_images(p["R"], p["T"], p["spacing"])
-            for p in pairs]   # autotuned tiling of their own
-    own = [[r.level_tiling(lv) for lv in range(3)] for r in regs]
+    regs = [reg_mod.Registration(_cfg(reg_mod, image_dtype=image_dtype, fused_tz=-1)).set_images(
+        p["R"], p["T"], p["spacing"]) for p in pairs]
     batch = reg_mod.register_batch(regs, out="numpy")
-    assert own == [[r.level_tiling(lv) for lv in range(3)] for r in regs]   # restored after the batch
+    assert all(s["tiling"] == [-1, -1, -1] for _, s in batch)
     for (u1, s1), (u2, s2) in zip(single, batch):
         np.testing.assert_array_equal(u1, u2)
         assert s1["iters"] == s2["iters"] and s1["evals"] == s2["evals"]
@@ -96,4 +95,22 @@ def test_batch_host_driven_equals_graph(reg_mod):
         np.testing.assert_array_equal(u1, u2)
         assert s1["iters"] == s2["iters"] and s1["evals"] == s2["evals"]
         assert s1["kernel_launches"] == s2["kernel_launches"]
+
+
+def test_batch_autotuned_tiling(reg_mod):
+    """Without a forced rule the batch autotuner picks the tiling of each level
+    (cached per batch geometry); the handles keep their own tiling."""
+    pairs = _pairs()[:4]
+    regs = [reg_mod.Registration(_cfg(reg_mod)).set_images(p["R"], p["T"], p["spacing"]) for p in pairs]
+    own = [[r.level_tiling(lv) for lv in range(3)] for r in regs]
+    first = reg_mod.register_batch(regs, out="numpy")
+    assert own == [[r.level_tiling(lv) for lv in range(3)] for r in regs]
+    rules = first[0][1]["tiling"]
+    assert all(rule in (0, -1, 16, 32, 64, 128) for rule in rules)
+    again = reg_mod.register_batch(regs, out="numpy")
+    for (u1, s1), (u2, s2) in zip(first, again):
+        assert s1["tiling"] == s2["tiling"] == rules
+        np.testing.assert_array_equal(u1, u2)
+    for r in regs:
+        r.close()
 
