@@ -179,20 +179,31 @@ def source_digest(files):
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel, digest, workload_name, tz):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    this source, this workload and this tiling (else None)."""
+def committed_profile(kernel, digest, workload_name, tz):
+    """The committed ncu figures of a kernel launch (DRAM bytes, warp instructions),
+    if they were taken on this source, this workload and this tiling (else {})."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
-        return None
+        return {}
     with open(path) as f:
         d = json.load(f)
     e = d.get(kernel)
     if not e or e.get("source_digest") != digest:
-        return None
+        return {}
     if e.get("workload") != workload_name or e.get("fused_tz") != tz:
-        return None
-    return e.get("dram_bytes_per_launch_full_size")
+        return {}
+    return e
+
+
+def issue_peak_warp_inst_per_s():
+    """GB300 instruction issue ceiling: 152 SMs x 4 schedulers x 1 warp
+    instruction per cycle at the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return 152 * 4 * mhz * 1e6
 
 
 def workload(config_id, rank):
@@ -362,7 +373,17 @@ def run_ours(args):
     part_bytes = 4 * tiles * (tz // 2 + 1) * 315 if impl == 0 else 12 * nn
     kernel_bytes = 8 * nv + 12 * nn + part_bytes
     achieved = kernel_bytes / (ngf_ms * 1e-3) / 1e9
-    traffic = committed_traffic(kernel, source_digest(FUSED_KERNEL_SOURCES), c["name"], tz)
+    prof = committed_profile(kernel, source_digest(FUSED_KERNEL_SOURCES), c["name"], tz)
+    traffic = prof.get("dram_bytes_per_launch_full_size")
+    issue = None
+    if prof.get("warp_instructions_per_launch"):
+        rate = prof["warp_instructions_per_launch"] / (ngf_ms * 1e-3)
+        peak_issue = issue_peak_warp_inst_per_s()
+        issue = {"bound": "issue", "kernel": "k_ngf_fused", "achieved": rate, "peak": peak_issue,
+                 "unit": "warp instructions/s", "frac": rate / peak_issue,
+                 "warp_instructions_per_launch": prof["warp_instructions_per_launch"],
+                 "what": "the kernel's binding limit: ncu instruction count per launch over the live event time, "
+                         "against 152 SMs x 4 schedulers x 1 instruction/cycle at the maximum SM clock"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -397,6 +418,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_ngf_fused" if impl == 0 else kernel,
                          "algorithmic_bytes": kernel_bytes, "launch_ms": ngf_ms, "peak_kind": peak_kind,
                          "note": "issue-bound, not HBM-bound: see the evaluation line and the ncu summary"},
+            "issue_roofline": issue,
             "eval_roofline": {"bound": "hbm", "achieved": eval_achieved, "peak": peak, "unit": "GB/s",
                               "frac": eval_achieved / peak, "algorithmic_bytes": eval_bytes, "eval_ms": eval_ms,
                               "what": "whole objective+gradient evaluation (fused pass, curvature, gather, "

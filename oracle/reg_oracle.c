@@ -172,13 +172,12 @@ void orc_PT(const int m[3], const double h[3], const int mn[3], const double *r,
  * (R5).  The gradient is that of the interpolant inside the cell
  * c = floor(p/h - 1/2).
  * ------------------------------------------------------------------------- */
-static void interp_point(const int m[3], const double h[3], const double *T, const double p[3],
-                         double *val, double grad[3])
+static void interp_voxel_units(const int m[3], const double h[3], const double *T, const double t[3],
+                               double *val, double grad[3])
 {
-    double t[3], f[3];
+    double f[3];
     long c[3];
     for (int d = 0; d < 3; d++) {
-        t[d] = p[d] / h[d] - 0.5;
         c[d] = (long)floor(t[d]);
         f[d] = t[d] - (double)c[d];
     }
@@ -205,6 +204,16 @@ static void interp_point(const int m[3], const double h[3], const double *T, con
     grad[0] = g0;
     grad[1] = g1;
     grad[2] = g2;
+}
+
+/* T and its gradient at a physical point p (mm): t = p / h - 1/2 in voxel units. */
+static void interp_point(const int m[3], const double h[3], const double *T, const double p[3],
+                         double *val, double grad[3])
+{
+    double t[3];
+    for (int d = 0; d < 3; d++)
+        t[d] = p[d] / h[d] - 0.5;
+    interp_voxel_units(m, h, T, t, val, grad);
 }
 
 void orc_interp(const int m[3], const double h[3], const double *T, size_t n, const double *p,
@@ -366,18 +375,25 @@ void orc_objective(const int m[3], const double h[3], const double *R, const dou
     /* (1) grid conversion, per component */
     for (int c = 0; c < 3; c++)
         orc_P(m, h, mn, u + c * nn, yhat + c * nv);
-    /* deformed points p_i = x_i + yhat_i (P reproduces the node positions xi) */
+    /* (2) deformed template at p_i = x_i + yhat_i (P reproduces the node
+     * positions xi) and its interpolant gradient.  With x_i = (i + 1/2) h (R1)
+     * the voxel coordinate p_i / h - 1/2 is exactly i + yhat_i / h; it is formed
+     * that way, so that a sample on a cell face (yhat a whole number of voxels)
+     * lands on the integer and takes the cell to its right (R5), instead of
+     * rounding below it through the product (i + 1/2) h. */
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < m[2]; z++)
         for (int y = 0; y < m[1]; y++)
             for (int x = 0; x < m[0]; x++) {
                 size_t i = IDX3(x, y, z, m[0], m[1]);
-                yhat[i] += (x + 0.5) * h[0];
-                yhat[nv + i] += (y + 0.5) * h[1];
-                yhat[2 * nv + i] += (z + 0.5) * h[2];
+                double t[3] = {x + yhat[i] / h[0], y + yhat[nv + i] / h[1], z + yhat[2 * nv + i] / h[2]};
+                double gr[3];
+                interp_voxel_units(m, h, T, t, &Tw[i], gr);
+                dT[i] = gr[0];
+                dT[nv + i] = gr[1];
+                dT[2 * nv + i] = gr[2];
             }
-    /* (2) deformed template and its interpolant gradient, NGF, chain rule */
-    orc_interp(m, h, T, nv, yhat, Tw, dT);
+    /* NGF, chain rule */
     double Dv = orc_ngf(m, h, Tw, R, tau, rho, v);
     orc_ngf_adjoint(m, h, v, g);
     double *r = yhat; /* reuse: r_c = g * dT_c */

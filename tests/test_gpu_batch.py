@@ -114,3 +114,17 @@ def test_batch_autotuned_tiling(reg_mod):
     for r in regs:
         r.close()
 
+
+
+def test_batch_reports_numeric_error(reg_mod):
+    from paper_1812_06765_gb300 import _lib
+    pairs = _pairs()[:2]
+    bad = dict(pairs[1])
+    bad["T"] = bad["T"].copy()
+    bad["T"][5, 6, 7] = np.nan
+    regs = [reg_mod.Registration(_cfg(reg_mod)).set_images(p["R"], p["T"], p["spacing"]) for p in (pairs[0], bad)]
+    with pytest.raises(_lib.RegError) as ei:
+        reg_mod.register_batch(regs, out="numpy")
+    assert ei.value.code == _lib.REG_ERR_NUMERIC
+    for r in regs:
+        r.close()

@@ -137,3 +137,49 @@ def test_graph_registration_matches_oracle(reg_mod, orc):
     mean_vox = float(np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0)).mean()) / min(p["spacing"])
     assert mean_vox <= 0.1, (mean_vox, st, sto)
     r.close()
+
+
+def test_register_mixed_levels_and_start_level(reg_mod, orc):
+    """Odd dimensions on the coarser levels (60 x 44 x 38 -> 30 x 22 x 19 -> 15 x 11 x 10):
+    the fused pass serves the finest level, the multi-pass kernels the others;
+    a fixed number of steps per level follows the oracle's trajectory, also
+    when the pyramid starts below its coarsest level."""
+    dims, h = (60, 44, 38), (1.2, 1.0, 1.5)
+    R = random_image(dims, 21)
+    T = np.roll(random_image(dims, 21), shift=(1, -1, 2), axis=(0, 1, 2))
+    for start in (-1, 1):
+        kw = dict(levels=3, tau=0.05, alpha=5.0, mem=4, max_iter=[6, 6, 6], fixed_iters=True, start_level=start)
+        r = reg_mod.Registration(reg_mod.make_config(**kw)).set_images(R, T, h)
+        assert r.level_tiling(0)[0] > 0 and r.level_tiling(1) == (0, 0) and r.level_tiling(2) == (0, 0)
+        u, st = r.register(out="numpy")
+        uo, sto = orc.register(dims, h, R, T, orc.make_config(**kw))
+        first = 2 if start < 0 else start
+        assert st["iters"][:first + 1] == sto["iters"][:first + 1] == [6] * (first + 1)
+        du = np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0))
+        assert du.mean() / min(h) <= 0.02, (start, du.mean(), st, sto)
+        for lv in range(first + 1):
+            # same evaluation count: the same line-search path, J to 1e-4; an Armijo test
+            # that FP32 and FP64 decide differently branches the path, J then to 1e-2
+            tol = 1e-4 if st["evals"][lv] == sto["evals"][lv] else 1e-2
+            assert abs(st["J"][lv] - sto["J"][lv]) <= tol * abs(sto["J"][lv]), (start, lv, st, sto)
+        r.close()
+
+
+def test_register_reports_numeric_error(reg_mod):
+    """A NaN in the images ends the registration with REG_ERR_NUMERIC (from the
+    device-side control, through the level graph), not with a fault."""
+    from paper_1812_06765_gb300 import _lib
+    dims = (32, 32, 24)
+    R = random_image(dims, 31)
+    T = random_image(dims, 32)
+    T[10, 12, 14] = np.nan
+    r = reg_mod.Registration(reg_mod.make_config(levels=2, tau=0.05, alpha=1.0, max_iter=5)).set_images(
+        R, T, (1.0, 1.0, 1.0))
+    with pytest.raises(reg_mod.RegError) as ei:
+        r.register(out="numpy")
+    assert ei.value.code == _lib.REG_ERR_NUMERIC
+    # the handle stays usable
+    r.set_images(R, random_image(dims, 32), (1.0, 1.0, 1.0))
+    u, st = r.register(out="numpy")
+    assert st["status"] == 0 and np.isfinite(u).all()
+    r.close()

@@ -395,3 +395,33 @@ def test_lbfgs_converges_to_quadratic_minimiser(orc):
         ref = u0[c].ravel() - Ap @ (A @ u0[c].ravel())
         np.testing.assert_allclose(u[c].ravel(), ref, rtol=0, atol=1e-6)
     assert st["status"] == 0
+
+
+def test_objective_on_cell_faces_takes_the_right_cell(orc):
+    """At u = 0 every sample sits on a voxel centre, i.e. on a cell face of the
+    interpolant; R5 takes the cell to its right there, so grad T is the forward
+    difference (T_{i+1} - T_i) / h with T = 0 past the last voxel.  The objective's
+    gradient must equal P^T (g grad T) assembled from that definition, also for
+    spacings that are not dyadic fractions: with h = 2.4 mm, forming the
+    coordinate through the physical position, (i + 1/2) h / h - 1/2, rounds below
+    the integer for i = 15 and 28."""
+    dims, h = (32, 9, 8), (2.4, 2.0, 3.0)
+    nodes = orc.default_nodes(dims)
+    rng = np.random.default_rng(7)
+    R = rng.random((dims[2], dims[1], dims[0]))
+    T = rng.random((dims[2], dims[1], dims[0]))
+    tau = rho = 0.05
+    u = np.zeros((3, nodes[2], nodes[1], nodes[0]))
+    J, D, S, grad = orc.objective(dims, h, R, T, nodes, u, tau, rho, 1.0)
+    D_ref, v = orc.ngf(dims, h, T, R, tau, rho)        # the deformed template is T itself
+    g = orc.ngf_adjoint(dims, h, v)
+    dT = []
+    for ax, hd in zip((2, 1, 0), h):                     # axes of x, y, z in (z, y, x) arrays
+        nxt = np.roll(T, -1, axis=ax)
+        idx = [slice(None)] * 3
+        idx[ax] = -1
+        nxt[tuple(idx)] = 0.0                            # zero extension
+        dT.append((nxt - T) / hd)
+    ref = np.stack([orc.PT(dims, h, nodes, g * dT[c]) for c in range(3)])
+    assert D == pytest.approx(D_ref, rel=1e-14) and S == 0.0
+    np.testing.assert_allclose(grad, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
