@@ -183,9 +183,26 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
         return e;
     double hy = L.H[0] * L.H[1] * L.H[2];
     int nS = (int)(gw.x * gw.y * gw.z);
-    if (fused)   // grad = (tile partials of P^T r) + alpha hbar_y L^T w; then J, D, S (+ control)
+    // grad = (tile partials of P^T r) + alpha hbar_y L^T w; then J, D, S (+ control).  On
+    // small grids the gather's completing block does the final reduction (one launch
+    // fewer); on large ones (>= 4096 blocks, whose arrivals on one counter would
+    // serialise) the reduction is a kernel of its own.
+    const long long gather_blocks = (long long)gn.x * gn.y * gn.z;
+    if (fused && gather_blocks < 4096)
         return launch_gather_fin(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, nD, pS, nS, scal_out,
                                  ctl_phase, s);
+    if (fused) {
+        cudaError_t ge = launch_gather_grad(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, s);
+        if (ge != cudaSuccess)
+            return ge;
+        double hbar = L.h[0] * L.h[1] * L.h[2];
+        c->launches += 1;
+        if (ctl_phase >= 0)
+            return launch_finalize_ctl(c, c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out,
+                                       ctl_phase, s);
+        k_finalize<<<1, 512, 0, s>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out);
+        return cudaGetLastError();
+    }
     // multi-pass: grad += alpha hbar_y L^T w, then the final reduction
     k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);
     double hbar = L.h[0] * L.h[1] * L.h[2];
