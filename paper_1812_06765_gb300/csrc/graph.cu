@@ -10,10 +10,11 @@
 //
 // Each control phase runs in FP64 in the last block of the kernel before it
 // (the block that completes that kernel's cross-block reduction), so a level
-// runs without a host round trip and without separate control launches.  Termination does not depend on the
-// host: every search ends after max_backtracks trials and the control kernel
-// ends the level after max_iter accepted steps, a failed search, a non-finite
-// value, or (a bound that should never bind) 2 max_iter + 8 loop bodies.
+// runs without a host round trip and without separate control launches.
+// Termination does not depend on the host: every search ends after
+// max_backtracks trials, and the control phases end the level after max_iter
+// accepted steps, a failed search, a non-finite value, or (a bound that should
+// never bind) 2 max_iter + 8 loop bodies.
 #include <vector>
 
 #include "internal.h"

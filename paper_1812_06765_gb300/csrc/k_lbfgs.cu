@@ -6,7 +6,8 @@
 // recursion in exact arithmetic but needs only two passes over the history:
 // one multi-dot pass (fused with the accept step) and one combination pass.
 // All scalar decisions (coefficients, curvature test, Armijo test, stopping)
-// are taken by a one-block control kernel in FP64 on the device, so the host
+// are taken in FP64 on the device (lbfgs_control.cuh) by the block that
+// completes the cross-block reduction of the kernel before them, so the host
 // never has to read a scalar to continue, and an iteration can be replayed as
 // one CUDA graph.
 //
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(VT) k_lb_vector_batch(const PairLevel *__restr
     }
 }
 
-// one block per pair; phase as in k_lb_control, scalars of the objective at u
+// one block per pair: control phase `phase` of each pair, on its group sums; scalars of the objective at u
 // (INIT) or at the trial point (ARMIJO)
 __global__ void __launch_bounds__(CT) k_lb_control_batch(const PairLevel *__restrict__ pl, int phase)
 {

@@ -1,6 +1,7 @@
-// Device-resident L-BFGS state (FP64 scalars).  One instance per handle; the
-// control kernel is its only writer on the device, the host writes it only
-// before a level starts.
+// Device-resident L-BFGS state (FP64 scalars).  One instance per handle; on
+// the device only the control phases write it (run by one block: the one that
+// completes a kernel's cross-block reduction, or a control kernel of the
+// batched form); the host writes it only before a level starts.
 #pragma once
 
 #define LB_MAXM 8
