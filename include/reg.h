@@ -82,13 +82,13 @@ typedef struct reg_config {
     int use_graph;        /* 1: each pyramid level runs as one CUDA graph launch */
     int image_dtype;      /* 0: FP32 images; 1: the fused pass reads BF16 copies of R and T
                              (arithmetic stays FP32; levels without the fused pass use FP32) */
-    int autotune;         /* 1: reg_set_images times every z segment length of the fused pass
-                             on each level and keeps the fastest (cached per geometry for the
-                             process; the first call of a geometry synchronises the stream);
-                             0: a fixed rule */
-    int fused_tz;         /* 0: autotune / rule; -1: the throughput rule (fewest z steps in
-                             total, the tiling reg_register_batch uses); else this z segment
-                             length on every level (one of 2, 4, 8, 16, 32, 64, 128) */
+    int autotune;         /* 1: reg_set_images times the z segment lengths of the fused pass
+                             that a wave model ranks best on each level and keeps the fastest
+                             (cached per geometry for the process; the first call of a
+                             geometry synchronises the stream); 0: the model's choice */
+    int fused_tz;         /* 0: autotune / model; -1: the throughput rule (fewest z steps in
+                             total over 2, 4, 8, .. 128, the tiling reg_register_batch uses);
+                             else this z segment length on every level (even, 2 .. 512) */
     int reserved[3];
 } reg_config;
 
@@ -175,6 +175,8 @@ int reg_last_ngf_ms(reg_handle h, double *ms);
  * device).  The paper has no counterpart: it is an interface of this library.
  *   R, T: device images, dims[3] = (m_x, m_y, m_z), each even and >= 4 (the
  *     deformation grid is m_d / 2 + 1 nodes per dimension), spacing_mm[3] > 0;
+ *     R must be 8-byte aligned (it is read two voxels at a time; any cudaMalloc
+ *     pointer is), else REG_ERR_ARG;
  *   u, grad: device, 3 planes of the node count (grad is overwritten);
  *   tau, rho > 0, alpha >= 0: the parameters of Eq. 1-2;
  *   jds: device, 3 doubles receiving J, D and S;

@@ -141,8 +141,11 @@ size_t fused_part_floats(const Level &L, int num_sms);
 int fused_tz(const Level &L, int num_sms);
 bool fused_tz_valid(int tz);
 int fused_tz_throughput(const Level &L);
-// times every z segment length on the level's images at u_zero (3 node planes
-// of zeros) and keeps the fastest in L.tz; cached per geometry
+// z segment length and tile grid the fused pass uses on the level
+void fused_tiling(const Level &L, int num_sms, int *tz, int *ntx, int *nty, int *ntz);
+// times the z segment lengths the wave model ranks best on the level's images
+// at u_zero (3 node planes of zeros) and keeps the fastest in L.tz; cached per
+// geometry
 cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStream_t s);
 cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
                              float *grad, double *partials, int *n_partials, cudaStream_t s);

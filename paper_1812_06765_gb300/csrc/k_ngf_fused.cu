@@ -7,32 +7,38 @@
 // node-parallel kernel adds up the (at most 8) tile partials of each node and
 // the curvature gradient.  Nothing per voxel goes to HBM.
 //
-// Tiling.  A CTA of 32 x 16 threads owns the voxel columns of a 28 x 12 output
-// tile plus a 2-voxel halo (the stencil chain T~ -> a -> v -> g reaches two
-// voxels), and marches along z through a segment of TZ output planes.  With
-// ratio 2 the P weights are 1/4 and 3/4 and a node gathers voxels 2k-2 .. 2k+1
-// with weights 1/4, 3/4, 3/4, 1/4 per dimension, so an output tile of
-// 28 x 12 x TZ voxels feeds 15 x 7 x (TZ/2 + 1) nodes; neighbouring tiles share
-// one node plane per dimension and the gather kernel sums them.
+// Tiling.  A CTA of 16 x 32 threads owns a 32 x 32 block of voxel columns:
+// thread (tx, ty) holds the two adjacent columns 2 tx and 2 tx + 1 of row ty.
+// The inner 28 x 28 columns are the output tile; the 2-voxel halo is what the
+// stencil chain T~ -> a -> v -> g reaches.  The CTA marches along z through a
+// segment of TZ output planes.  With ratio 2 the P weights are 1/4 and 3/4;
+// tiles start at even x, so the two columns of a thread always lie in the
+// same node interval (x weights 1/4 and 3/4 of the same nodes), and the node
+// loads, P's integer cell and the x reduction of P^T are shared by the pair.
+// A node gathers voxels 2k-2 .. 2k+1 with weights 1/4, 3/4, 3/4, 1/4 per
+// dimension, so an output tile of 28 x 28 x TZ voxels feeds 15 x 15 x
+// (TZ/2 + 1) nodes; neighbouring tiles share one node plane per dimension and
+// the gather kernel sums them.
 //
-// Pipeline.  Step s (zA = z0 - 2 + 2 s, even) handles two planes, exactly one
-// node interval, between two barriers:
-//   A-finish zA, zA+1   : interpolate T on both planes from the corners loaded
-//                         last step
-//   A-issue  zA+2, zA+3 : P on the next node interval, the coordinates of both
-//                         planes, loads of their 2 x 8 corners and of R into
-//                         registers (used one step later); cp.async of the
-//                         node-plane tile two intervals ahead
-//   B  zA-3, zA-2       : v from T~ and R planes zA-4 .. zA-1
-//   C  zA-6, zA-5       : r from v planes zA-7 .. zA-4; x reduction by warp shuffles
-//   D  zA-8, zA-7       : y reduction of last step's rows, accumulation of one
-//                         node interval along z
+// Pipeline.  Step s works on plane zA = z0 - 2 + s and the lagging planes
+//   A-finish zA    : interpolate T at both columns from the corners loaded
+//                    last step
+//   A-issue  zA+1  : at the first plane of a node interval, P on the interval
+//                    (both planes) and the cp.async of the node-plane tile two
+//                    intervals ahead; the coordinates of plane zA+1 and the
+//                    loads of its 2 x 8 corners and of R into registers, first
+//                    used one step later
+//   B  zA-2        : v from T~ and R planes zA-3 .. zA-1
+//   C  zA-4        : r from v planes zA-5 .. zA-3; x reduction to node columns
+//   D  zA-5        : y reduction of last step's rows, accumulation along z
 // Every phase reads only what earlier steps wrote, so one barrier per step
-// suffices; the global loads of two planes overlap a whole step of compute, and
-// the two planes of each phase are independent work the compiler interleaves.
+// suffices, and the global loads of a plane overlap a whole step of compute.
+#include <algorithm>
 #include <array>
 #include <map>
 #include <mutex>
+#include <type_traits>
+#include <vector>
 
 #include "batch.h"
 #include "internal.h"
@@ -41,24 +47,29 @@
 
 namespace {
 
-constexpr int BX = 32, BY = 16;                   // threads (voxel columns incl. halo)
-constexpr int OX = 28, OY = 12;                   // output voxels per tile
-constexpr int NX = OX / 2 + 1, NY = OY / 2 + 1;   // 15 x 7 node columns per tile
-constexpr int NE = 3 * NX * NY;                   // partial entries per node plane (315)
-constexpr int PLANE = BX * BY;                    // floats of one shared plane
-constexpr int TNX = BX / 2 + 1, TNY = BY / 2 + 1; // node tile of the columns: 17 x 9
+constexpr int BX = 16, BY = 32;                   // threads; each holds two voxel columns
+constexpr int NT = BX * BY;                       // 512 threads
+constexpr int CW = 2 * BX;                        // voxel columns per tile row, halo included
+constexpr int OX = 28, OY = 28;                   // output voxels per tile
+constexpr int NX = OX / 2 + 1, NY = OY / 2 + 1;   // 15 x 15 node columns per tile
+constexpr int NE = 3 * NX * NY;                   // partial entries per node plane (675)
+constexpr int PLANE = CW * BY;                    // floats of one shared plane
+constexpr int TNX = BX + 1, TNY = BY / 2 + 1;     // node tile of the columns: 17 x 17
 constexpr int TNP = 3 * TNY * TNX;                // floats of one node plane tile per array
+constexpr int NCOPY = (2 * TNP + NT - 1) / NT;    // node-tile entries copied per thread
 
-// shared layout (floats); the plane rings hold 8 planes (slot z & 7)
-constexpr int OFF_T = 0;                          // T~ ring [8][PLANE]
-constexpr int OFF_R = OFF_T + 8 * PLANE;          // R ring [8][PLANE]
-constexpr int OFF_V = OFF_R + 8 * PLANE;          // v ring [8][3][PLANE]
-constexpr int OFF_G = OFF_V + 24 * PLANE;         // grad T ring [8][3][PLANE]
-constexpr int RED_PLANE = BY * NX * 3;            // x-reduced rows of one plane
-constexpr int OFF_RED = OFF_G + 24 * PLANE;       // x-reduced rows [2 steps][2 planes][BY][NX][3]
-constexpr int OFF_N = OFF_RED + 4 * RED_PLANE;    // node planes [4][2][TNP] (u, dir)
+// shared layout (floats); the ring slot of plane z is z & 3 (z & 7 for grad T)
+constexpr int OFF_T = 0;                          // T~ ring [4][PLANE]
+constexpr int OFF_R = OFF_T + 4 * PLANE;          // R ring [4][PLANE]
+constexpr int OFF_V = OFF_R + 4 * PLANE;          // v ring [4][3][PLANE]
+constexpr int OFF_G = OFF_V + 12 * PLANE;         // grad T ring [8][3][PLANE]
+constexpr int RED_PLANE = BY * NX * 3;            // x-reduced rows of one plane [BY][NX][3]
+constexpr int OFF_RED = OFF_G + 24 * PLANE;       // x-reduced rows [2 steps][RED_PLANE]
+constexpr int OFF_N = OFF_RED + 2 * RED_PLANE;    // node planes [4][2][TNP] (u, dir)
 constexpr int SMEM_FLOATS = OFF_N + 4 * 2 * TNP;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
+static_assert(SMEM_BYTES <= 227 * 1024, "fused pass exceeds the shared memory of one CTA");
+static_assert((OFF_R | OFF_V | OFF_G | OFF_RED | OFF_N | PLANE) % 2 == 0, "float2 rows need even offsets");
 
 
 __device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc, bool valid)
@@ -71,53 +82,58 @@ __device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc, bo
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+__device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void sts2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+
 // One thread's share of the cooperative copy of a node plane (u and, with a
-// direction, dir) of the CTA's 17 x 9 node tile: entries tid and tid + PLANE.
-// The in-plane offsets do not change along z, so they are computed once.
+// direction, dir) of the CTA's 17 x 17 node tile: entries tid + q NT.  The
+// in-plane offsets do not change along z, so they are computed once.
 struct NodeCopy {
-    const float *src[2];   // node (kx, ky, plane 0) of the entry's component and array
-    int dst[2];            // offset inside a ring slot
-    bool in[2];            // node column inside the grid
+    int src[NCOPY];   // offset of the entry's node in plane 0 of u or dir; -1: outside the grid
+    int dst[NCOPY];   // entry in a ring slot (>= TNP: the dir tile); -1: no entry
 };
 
 template <bool HAS_DIR>
-__device__ __forceinline__ NodeCopy node_copy_setup(const FusedArgs &a, int kx0, int ky0, int tid)
+__device__ __forceinline__ NodeCopy node_copy_setup(const LevelGeom &g, int kx0, int ky0, int tid)
 {
-    const LevelGeom &g = a.g;
     const int nn = (int)g.nn, total = (HAS_DIR ? 2 : 1) * TNP;
     NodeCopy nc;
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-        const int e = tid + q * PLANE;
-        const int arr = e / TNP, r = e - arr * TNP;
+    for (int q = 0; q < NCOPY; q++) {
+        const int e = tid + q * NT;
+        const int r = e >= TNP ? e - TNP : e;
         const int c = r / (TNY * TNX), r2 = r - c * (TNY * TNX);
         const int ly = r2 / TNX, lx = r2 - ly * TNX;
         const int kx = kx0 + lx, ky = ky0 + ly;
-        nc.in[q] = e < total && kx >= 0 && kx < g.n[0] && ky >= 0 && ky < g.n[1];
+        const bool in = e < total && kx >= 0 && kx < g.n[0] && ky >= 0 && ky < g.n[1];
         nc.dst[q] = e < total ? e : -1;
-        nc.src[q] = nc.in[q] ? (arr ? a.dir : a.ub) + c * nn + (kx + g.n[0] * ky) : a.ub;
+        nc.src[q] = in ? c * nn + kx + g.n[0] * ky : -1;
     }
     return nc;
 }
 
-// copy node plane K into ring slot K % 4; nodes outside the grid read as zero
-__device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, float *sm, int K, int nz, int plane_stride)
+// copy node plane K into ring slot K & 3; nodes outside the grid read as zero
+__device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float *ub, const float *dir, float *sm,
+                                                 int K, int nz, size_t plane_stride)
 {
     float *dst = sm + OFF_N + (K & 3) * 2 * TNP;
     const bool kin = K >= 0 && K < nz;
+    const size_t kofs = kin ? plane_stride * (size_t)K : 0;
 #pragma unroll
-    for (int q = 0; q < 2; q++)
+    for (int q = 0; q < NCOPY; q++)
         if (nc.dst[q] >= 0) {
-            const bool in = kin && nc.in[q];
-            cp_async4(dst + nc.dst[q], in ? nc.src[q] + (size_t)plane_stride * K : nc.src[q], in);
+            const bool in = kin && nc.src[q] >= 0;
+            const float *base = nc.dst[q] >= TNP ? dir : ub;
+            cp_async4(dst + nc.dst[q], in ? base + kofs + nc.src[q] : ub, in);
         }
 }
 
-// displacement plane K of a column from the shared node tile: the value at the
-// first node (U) and the bilinear interpolation of the in-plane differences (Bd)
+// displacement plane K of the thread's two columns from the shared node tile:
+// the value at the interval's first node (U, shared) and the bilinear
+// interpolation of the in-plane differences (Bd, x weight 1/4 and 3/4)
 template <bool HAS_DIR>
-__device__ __forceinline__ void column_plane(const float *sm, int K, int lkx, int lky, float wx, float wy, float t,
-                                             float U[3], float Bd[3])
+__device__ __forceinline__ void column_pair_plane(const float *sm, int K, int lkx, int lky, float wy, float t,
+                                                  float U[3], float Bd[2][3])
 {
     const float *nu = sm + OFF_N + (K & 3) * 2 * TNP;
     const float *np = nu + TNP;
@@ -131,14 +147,22 @@ __device__ __forceinline__ void column_plane(const float *sm, int K, int lkx, in
             u01 = fmaf(t, np[o + TNX], u01);
             u11 = fmaf(t, np[o + TNX + 1], u11);
         }
+        const float dx = u10 - u00, dy = u01 - u00, dxy = u11 - u00;
         U[c] = u00;
-        Bd[c] = lerpf(wx * (u10 - u00), lerpf(u01 - u00, u11 - u00, wx), wy);
+        Bd[0][c] = lerpf(0.25f * dx, lerpf(dy, dxy, 0.25f), wy);
+        Bd[1][c] = lerpf(0.75f * dx, lerpf(dy, dxy, 0.75f), wy);
     }
 }
 
 // image element loads: FP32, or BF16 widened to FP32 (all arithmetic is FP32)
 __device__ __forceinline__ float ldimg(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ldimg(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+// two adjacent elements starting at an even index (8- or 4-byte aligned)
+__device__ __forceinline__ float2 ldimg2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ float2 ldimg2(const __nv_bfloat16 *p)
+{
+    return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+}
 
 template <typename IMG>
 __device__ __forceinline__ float ldimg_zero_ext(const IMG *T, int mx, int my, int mz, int x, int y, int z)
@@ -154,238 +178,290 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int t
 {
     const LevelGeom &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int sp = 2 * tx + CW * ty;                  // shared-plane index of the thread's first column
     const int x0 = tile_x * OX, y0 = tile_y * OY, z0 = tile_z * a.tz;
-    const int x = x0 - 2 + tx, y = y0 - 2 + ty;
+    const int xa = x0 - 2 + 2 * tx, y = y0 - 2 + ty;  // the thread's columns: xa (even) and xa + 1
     const int mx = g.m[0], my = g.m[1], mz = g.m[2];
     const int sxy = mx * my;
-    const bool col_in = x >= 0 && x < mx && y >= 0 && y < my;
+    // mx is even, so both columns lie inside the image or neither does
+    const bool col_in = xa >= 0 && xa < mx && y >= 0 && y < my;
     const float t = HAS_DIR ? (float)__ldg(a.t_dev) : 0.f;
-    // ratio 2: voxel i lies between nodes i/2 and i/2 + 1, weight of the second 1/4 or 3/4
-    const int lkx = tx >> 1, lky = ty >> 1;           // node of the column inside the tile
+    // ratio 2: voxel i lies between nodes i/2 and i/2 + 1, weight of the second
+    // 1/4 (i even) or 3/4 (i odd); both columns lie in node interval kx0 + tx
+    const int lky = ty >> 1;
     const int kx0 = (x0 >> 1) - 1, ky0 = (y0 >> 1) - 1;
-    const float wx = (x & 1) ? 0.75f : 0.25f, wy = (y & 1) ? 0.75f : 0.25f;
+    const float wy = (y & 1) ? 0.75f : 0.25f;
     const float hx = 0.5f * g.ih[0], hy = 0.5f * g.ih[1], hz = 0.5f * g.ih[2];
     const float half_hbar = 0.5f * g.hbar;
     const int zend = z0 + a.tz;                       // first plane after the segment's output planes
     const size_t tile_lin = (size_t)tile_x + (size_t)a.ntx * (tile_y + (size_t)a.nty * tile_z);
     float *part_tile = a.part + tile_lin * (size_t)(a.tz / 2 + 1) * NE;
-    const NodeCopy nc = node_copy_setup<HAS_DIR>(a, kx0, ky0, tid);
-    const int node_plane = g.n[0] * g.n[1];
+    const NodeCopy nc = node_copy_setup<HAS_DIR>(g, kx0, ky0, tid);
+    const size_t node_plane = (size_t)g.n[0] * g.n[1];
     const IMG *Tim = static_cast<const IMG *>(a.T);
-    const IMG *Rcol = static_cast<const IMG *>(a.R) + (col_in ? x + mx * y : 0);
-    // output columns and the rows phases B and C run on
+    const IMG *Rcol = static_cast<const IMG *>(a.R) + (col_in ? xa + mx * y : 0);
+    // rows phases B and C run on; output columns (both of the thread's columns)
     const bool rowB = ty >= 1 && ty < BY - 1, rowC = ty >= 2 && ty < BY - 2;
-    const bool colB = tx >= 1 && tx < BX - 1, colC = tx >= 2 && tx < BX - 2;
-    const bool intxy = col_in && x >= 1 && x <= mx - 2 && y >= 1 && y <= my - 2;
-    // phase D: partial entry tid = (component, node row jy, node column jx)
-    const bool dD = tid < NE;
-    const int dc = tid / (NX * NY), drem = tid - dc * (NX * NY), djy = drem / NX, djx = drem - djy * NX;
-    const int dofs = ((2 * djy) * NX + djx) * 3 + dc;
+    const bool outxy = rowC && tx >= 1 && tx < BX - 1;
+    const bool iny = y >= 1 && y <= my - 2;
+    const bool intA = col_in && iny && xa >= 1, intB = col_in && iny && xa + 1 <= mx - 2;
+    // phase D: partial entries tid and tid + NT = (component, node row jy, node column jx)
+    bool dD[2];
+    int dofs[2];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int e = tid + q * NT;
+        dD[q] = e < NE;
+        const int dc = e / (NX * NY), drem = e - dc * (NX * NY), djy = drem / NX, djx = drem - djy * NX;
+        dofs[q] = ((2 * djy) * NX + djx) * 3 + dc;
+    }
 
-    float Uhi[3], Bhi[3];                             // node plane of the interval's upper end, this column
-    float pc[2][8];                                   // corners of the next two planes, loaded a step ahead
-    float fr[2][3];                                   // their fractions
-    float rnext[2];                                   // R of the next two planes
-    float acc_lo = 0.f;                               // node plane of the interval's lower end (entry tid)
+    float Uhi[3], Bhi[2][3];   // node plane at the top of the current interval, both columns
+    float fo[2][3];            // fractions of the interval's odd plane
+    int qb[3];                 // integer part of y-hat / h on the interval
+    bool iv_ok[2];             // displacement of the interval representable
+    float pc[2][8], fr[2][3];  // corners and fractions of the next plane, loaded a step ahead
+    float2 rnext;              // R of the next plane
+    float acc_lo[2] = {0.f, 0.f}, hold[2] = {0.f, 0.f};
     KahanF psi_sum;
 
     // rows of the x-reduction buffers that no output row writes stay zero
-    for (int e = tid; e < 4 * RED_PLANE; e += PLANE)
+    for (int e = tid; e < 2 * RED_PLANE; e += NT)
         sm[OFF_RED + e] = 0.f;
 
-    // ---- A-issue: P on the node interval of planes z1 (even) and z1 + 1, their
-    // coordinates and the loads of their corners and of R, into registers that
-    // are first used one step later
-    auto a_issue = [&](int z1, bool first) {
-        const int K1 = z1 >> 1;
-        int qb[3] = {0, 0, 0};
-        float fe[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};
-        bool iv_ok = false;
-        if (col_in) {
-            float Ulo[3], Blo[3];
+    // ---- A-issue of plane z1: at an even plane (the start of node interval
+    // z1 / 2), P on the interval; then the coordinates of plane z1 and the
+    // loads of its corners and of R, into registers first used one step later
+    auto a_issue = [&](int z1, auto odd_t, bool first) {
+        constexpr bool ODD = decltype(odd_t)::value;
+        float f[2][3];
+        if (!ODD) {
+            const int K1 = z1 >> 1;
+            float Ulo[3], Blo[2][3];
             if (first) {
-                column_plane<HAS_DIR>(sm, K1, lkx, lky, wx, wy, t, Ulo, Blo);
+                column_pair_plane<HAS_DIR>(sm, K1, tx, lky, wy, t, Ulo, Blo);
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     Ulo[c] = Uhi[c];
-                    Blo[c] = Bhi[c];
+                    Blo[0][c] = Bhi[0][c];
+                    Blo[1][c] = Bhi[1][c];
                 }
             }
-            column_plane<HAS_DIR>(sm, K1 + 1, lkx, lky, wx, wy, t, Uhi, Bhi);
+            column_pair_plane<HAS_DIR>(sm, K1 + 1, tx, lky, wy, t, Uhi, Bhi);
             // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz) with wz = 1/4 (even z) or
             // 3/4 (odd z).  The sampling coordinate i + y-hat / h is kept as an integer
-            // part plus a small fraction (see sample_coord); both depend only on the
-            // interval and the parity of z, so they are formed here once.
-            iv_ok = true;
+            // part plus a small fraction; both depend only on the interval and the
+            // parity of z, so they are formed once per interval.
+            iv_ok[0] = iv_ok[1] = true;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const float ih = g.ih[c];
                 const float q0 = Ulo[c] * ih;
-                const float d1 = (Uhi[c] - Ulo[c]) + Bhi[c];
-                iv_ok = iv_ok && fabsf(q0) < 1.0e6f && fabsf(Blo[c] * ih) < 1.0e6f && fabsf(d1 * ih) < 1.0e6f;
                 const float qi = floorf(q0);
                 const float rem = fmaf(-qi, g.h[c], Ulo[c]);   // |rem| <~ h
-                fe[c] = (rem + lerpf(Blo[c], d1, 0.25f)) * ih;
-                fo[c] = (rem + lerpf(Blo[c], d1, 0.75f)) * ih;
                 qb[c] = (int)qi;
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    const float d1 = (Uhi[c] - Ulo[c]) + Bhi[k][c];
+                    iv_ok[k] = iv_ok[k] && fabsf(q0) < 1.0e6f && fabsf(Blo[k][c] * ih) < 1.0e6f &&
+                               fabsf(d1 * ih) < 1.0e6f;
+                    f[k][c] = (rem + lerpf(Blo[k][c], d1, 0.25f)) * ih;
+                    fo[k][c] = (rem + lerpf(Blo[k][c], d1, 0.75f)) * ih;
+                }
             }
+            issue_node_plane(nc, a.ub, a.dir, sm, K1 + 2, g.n[2], node_plane);
+            cp_async_commit();
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    f[k][c] = fo[k][c];
         }
-        issue_node_plane(nc, sm, K1 + 2, g.n[2], node_plane);
-        cp_async_commit();
+        const bool zin = col_in && z1 >= 0 && z1 < mz;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int zz = z1 + h;
-            const bool zin = col_in && zz >= 0 && zz < mz;
+        for (int k = 0; k < 2; k++) {
 #pragma unroll
-            for (int k = 0; k < 8; k++)
-                pc[h][k] = 0.f;
+            for (int j = 0; j < 8; j++)
+                pc[k][j] = 0.f;
             int cc[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const float f = h ? fo[c] : fe[c];
-                const float fl = floorf(f);
-                fr[h][c] = f - fl;
+                const float fl = floorf(f[k][c]);
+                fr[k][c] = f[k][c] - fl;
                 cc[c] = qb[c] + (int)fl;
             }
-            const int cx = cc[0] + x, cy = cc[1] + y, cz = cc[2] + zz;
-            if (zin && iv_ok) {
+            const int cx = cc[0] + xa + k, cy = cc[1] + y, cz = cc[2] + z1;
+            if (zin && iv_ok[k]) {
                 if ((unsigned)cx < (unsigned)(mx - 1) && (unsigned)cy < (unsigned)(my - 1) &&
                     (unsigned)cz < (unsigned)(mz - 1)) {   // all 8 corners inside
                     const IMG *p = Tim + (cx + mx * (cy + my * cz));
-                    pc[h][0] = ldimg(p);
-                    pc[h][1] = ldimg(p + 1);
-                    pc[h][2] = ldimg(p + mx);
-                    pc[h][3] = ldimg(p + mx + 1);
-                    pc[h][4] = ldimg(p + sxy);
-                    pc[h][5] = ldimg(p + sxy + 1);
-                    pc[h][6] = ldimg(p + sxy + mx);
-                    pc[h][7] = ldimg(p + sxy + mx + 1);
+                    pc[k][0] = ldimg(p);
+                    pc[k][1] = ldimg(p + 1);
+                    pc[k][2] = ldimg(p + mx);
+                    pc[k][3] = ldimg(p + mx + 1);
+                    pc[k][4] = ldimg(p + sxy);
+                    pc[k][5] = ldimg(p + sxy + 1);
+                    pc[k][6] = ldimg(p + sxy + mx);
+                    pc[k][7] = ldimg(p + sxy + mx + 1);
                 } else {   // zero extension corner by corner
 #pragma unroll
-                    for (int k = 0; k < 8; k++)
-                        pc[h][k] = ldimg_zero_ext(Tim, mx, my, mz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
+                    for (int j = 0; j < 8; j++)
+                        pc[k][j] = ldimg_zero_ext(Tim, mx, my, mz, cx + (j & 1), cy + ((j >> 1) & 1), cz + (j >> 2));
                 }
             }
-            rnext[h] = zin ? ldimg(Rcol + sxy * zz) : 0.f;
         }
+        rnext = zin ? ldimg2(Rcol + (size_t)sxy * z1) : make_float2(0.f, 0.f);
     };
 
-    // prologue: node planes of the first interval, then the loads of planes z0 - 2, z0 - 1
+    // ---- one step of the pipeline; ODD: planes zA + 1 and zA - 5 are odd
+    auto step = [&](int s, auto odd_t) {
+        constexpr bool ODD = decltype(odd_t)::value;
+        const int zA = z0 - 2 + s;
+        // ---- A-finish: T~ and grad T on plane zA
+        if (zA <= zend + 1) {
+            float val[2], gx[2], gy[2], gz[2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const float t000 = pc[k][0], t100 = pc[k][1], t010 = pc[k][2], t110 = pc[k][3];
+                const float t001 = pc[k][4], t101 = pc[k][5], t011 = pc[k][6], t111 = pc[k][7];
+                const float f0 = fr[k][0], f1 = fr[k][1], f2 = fr[k][2];
+                const float a00 = lerpf(t000, t100, f0), a10 = lerpf(t010, t110, f0);
+                const float a01 = lerpf(t001, t101, f0), a11 = lerpf(t011, t111, f0);
+                const float b0 = lerpf(a00, a10, f1), b1 = lerpf(a01, a11, f1);
+                val[k] = lerpf(b0, b1, f2);
+                const float dx0 = lerpf(t100 - t000, t110 - t010, f1), dx1 = lerpf(t101 - t001, t111 - t011, f1);
+                gx[k] = lerpf(dx0, dx1, f2) * g.ih[0];
+                gy[k] = lerpf(a10 - a00, a11 - a01, f2) * g.ih[1];
+                gz[k] = (b1 - b0) * g.ih[2];
+            }
+            const int slot = zA & 3;
+            sts2(sm + OFF_T + slot * PLANE + sp, val[0], val[1]);
+            sts2(sm + OFF_R + slot * PLANE + sp, rnext.x, rnext.y);
+            float *gq = sm + OFF_G + (zA & 7) * 3 * PLANE + sp;
+            sts2(gq, gx[0], gx[1]);
+            sts2(gq + PLANE, gy[0], gy[1]);
+            sts2(gq + 2 * PLANE, gz[0], gz[1]);
+        }
+        // ---- A-issue for plane zA + 1
+        if (zA <= zend)
+            a_issue(zA + 1, std::integral_constant<bool, ODD>{}, false);
+        // ---- B: v on plane zA - 2 (rows 1 .. 30)
+        const int zB = zA - 2;
+        if (rowB && zB >= z0 - 1 && zB <= zend) {
+            float va[3] = {0.f, 0.f, 0.f}, vb[3] = {0.f, 0.f, 0.f};
+            if ((intA || intB) && zB >= 1 && zB <= mz - 2) {
+                const int o0 = (zB & 3) * PLANE + sp;
+                const int op = ((zB + 1) & 3) * PLANE + sp, om = ((zB - 1) & 3) * PLANE + sp;
+                const float *T0 = sm + OFF_T + o0, *R0 = sm + OFF_R + o0;
+                const float2 t0 = lds2(T0), typ = lds2(T0 + CW), tym = lds2(T0 - CW);
+                const float2 tzp = lds2(sm + OFF_T + op), tzm = lds2(sm + OFF_T + om);
+                const float tl = T0[-1], tr = T0[2];
+                const float2 r0 = lds2(R0), ryp = lds2(R0 + CW), rym = lds2(R0 - CW);
+                const float2 rzp = lds2(sm + OFF_R + op), rzm = lds2(sm + OFF_R + om);
+                const float rl = R0[-1], rr = R0[2];
+                const bool out = outxy && zB >= z0 && zB < zend;
+                if (intA) {
+                    const float av[3] = {(t0.y - tl) * hx, (typ.x - tym.x) * hy, (tzp.x - tzm.x) * hz};
+                    const float bv[3] = {(r0.y - rl) * hx, (ryp.x - rym.x) * hy, (rzp.x - rzm.x) * hz};
+                    const float psi = ngf_residual(av, bv, a.tau, a.rho, va);
+                    if (out)
+                        psi_sum.add(psi);
+                }
+                if (intB) {
+                    const float av[3] = {(tr - t0.x) * hx, (typ.y - tym.y) * hy, (tzp.y - tzm.y) * hz};
+                    const float bv[3] = {(rr - r0.x) * hx, (ryp.y - rym.y) * hy, (rzp.y - rzm.y) * hz};
+                    const float psi = ngf_residual(av, bv, a.tau, a.rho, vb);
+                    if (out)
+                        psi_sum.add(psi);
+                }
+            }
+            float *vq = sm + OFF_V + (zB & 3) * 3 * PLANE + sp;
+            sts2(vq, va[0], vb[0]);
+            sts2(vq + PLANE, va[1], vb[1]);
+            sts2(vq + 2 * PLANE, va[2], vb[2]);
+        }
+        // ---- C: r on plane zA - 4 (rows 2 .. 29), x reduction into node columns
+        const int zC = zA - 4;
+        if (rowC && zC >= z0 && zC < zend) {   // uniform per warp (a warp holds rows 2w, 2w + 1)
+            float ra[3] = {0.f, 0.f, 0.f}, rb[3] = {0.f, 0.f, 0.f};
+            if (outxy && col_in && zC < mz) {
+                const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + sp;
+                const float *Vzm = sm + OFF_V + ((zC - 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
+                const float *Vzp = sm + OFF_V + ((zC + 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
+                const float2 vx = lds2(V0);
+                const float vl = V0[-1], vr = V0[2];
+                const float2 vyp = lds2(V0 + PLANE + CW), vym = lds2(V0 + PLANE - CW);
+                const float2 vzm = lds2(Vzm), vzp = lds2(Vzp);
+                const float gja = half_hbar * ((vl - vx.y) * hx + (vym.x - vyp.x) * hy + (vzm.x - vzp.x) * hz);
+                const float gjb = half_hbar * ((vx.x - vr) * hx + (vym.y - vyp.y) * hy + (vzm.y - vzp.y) * hz);
+                const float *gq = sm + OFF_G + (zC & 7) * 3 * PLANE + sp;
+                const float2 g0 = lds2(gq), g1 = lds2(gq + PLANE), g2 = lds2(gq + 2 * PLANE);
+                ra[0] = gja * g0.x;
+                ra[1] = gja * g1.x;
+                ra[2] = gja * g2.x;
+                rb[0] = gjb * g0.y;
+                rb[1] = gjb * g1.y;
+                rb[2] = gjb * g2.y;
+            }
+            // node column j (0..14) gathers columns 2j .. 2j+3 with weights 1/4, 3/4,
+            // 3/4, 1/4: the first two are thread j's pair, the last two thread j+1's
+            float *red = sm + OFF_RED + (ODD ? 0 : 1) * RED_PLANE + ty * NX * 3;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float lo = 0.25f * ra[c] + 0.75f * rb[c], hi = 0.75f * ra[c] + 0.25f * rb[c];
+                const float nv = lo + __shfl_down_sync(0xffffffffu, hi, 1, BX);
+                if (tx < NX)
+                    red[tx * 3 + c] = nv;
+            }
+        }
+        // ---- D: y reduction of plane zA - 5 (written last step) and accumulation
+        // along z: an even plane gives 3/4 to the lower node plane of its interval
+        // and 1/4 to the upper, an odd plane the reverse
+        const int zD = zA - 5;
+        if (zD >= z0 && zD < zend) {
+            const float *red = sm + OFF_RED + (ODD ? 1 : 0) * RED_PLANE;
+            const int lz = zD - z0;
+#pragma unroll
+            for (int q = 0; q < 2; q++)
+                if (dD[q]) {
+                    const float *rp = red + dofs[q];
+                    const float v = 0.25f * (rp[0] + rp[3 * NX * 3]) + 0.75f * (rp[NX * 3] + rp[2 * NX * 3]);
+                    if (!ODD) {
+                        hold[q] = v;
+                    } else {
+                        const int e = tid + q * NT;
+                        part_tile[(size_t)(lz >> 1) * NE + e] = acc_lo[q] + (0.75f * hold[q] + 0.25f * v);
+                        acc_lo[q] = 0.25f * hold[q] + 0.75f * v;
+                        if (lz == a.tz - 1)
+                            part_tile[(size_t)(a.tz >> 1) * NE + e] = acc_lo[q];
+                    }
+                }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    };
+
+    // prologue: node planes of the first interval, then the loads of plane z0 - 2
     {
         const int K0 = (z0 - 2) >> 1;
-        issue_node_plane(nc, sm, K0, g.n[2], node_plane);
-        issue_node_plane(nc, sm, K0 + 1, g.n[2], node_plane);
+        issue_node_plane(nc, a.ub, a.dir, sm, K0, g.n[2], node_plane);
+        issue_node_plane(nc, a.ub, a.dir, sm, K0 + 1, g.n[2], node_plane);
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        a_issue(z0 - 2, true);
+        a_issue(z0 - 2, std::false_type{}, true);
         cp_async_wait_all();
         __syncthreads();
     }
 
-    const int nsteps = a.tz / 2 + 5;
-    for (int s = 0; s < nsteps; s++) {
-        const int zA = z0 - 2 + 2 * s;
-        // ---- A-finish: T~ and grad T on planes zA, zA + 1
-        if (zA <= zend) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const float t000 = pc[h][0], t100 = pc[h][1], t010 = pc[h][2], t110 = pc[h][3];
-                const float t001 = pc[h][4], t101 = pc[h][5], t011 = pc[h][6], t111 = pc[h][7];
-                const float f0 = fr[h][0], f1 = fr[h][1], f2 = fr[h][2];
-                const float a00 = lerpf(t000, t100, f0), a10 = lerpf(t010, t110, f0);
-                const float a01 = lerpf(t001, t101, f0), a11 = lerpf(t011, t111, f0);
-                const float b0 = lerpf(a00, a10, f1), b1 = lerpf(a01, a11, f1);
-                const float val = lerpf(b0, b1, f2);
-                const float dx0 = lerpf(t100 - t000, t110 - t010, f1), dx1 = lerpf(t101 - t001, t111 - t011, f1);
-                const int slot = (zA + h) & 7;
-                sm[OFF_T + slot * PLANE + tid] = val;
-                sm[OFF_R + slot * PLANE + tid] = rnext[h];
-                float *gq = sm + OFF_G + slot * 3 * PLANE + tid;
-                gq[0] = lerpf(dx0, dx1, f2) * g.ih[0];
-                gq[PLANE] = lerpf(a10 - a00, a11 - a01, f2) * g.ih[1];
-                gq[2 * PLANE] = (b1 - b0) * g.ih[2];
-            }
-        }
-        // ---- A-issue for planes zA + 2, zA + 3
-        if (zA + 2 <= zend)
-            a_issue(zA + 2, false);
-        // ---- B: v on planes zA - 3, zA - 2 (rows 1 .. 14, lanes 1 .. 30)
-        if (rowB && zA - 3 >= z0 - 1 && zA - 3 <= zend) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int zB = zA - 3 + h;
-                float v[3] = {0.f, 0.f, 0.f};
-                if (colB) {
-                    if (intxy && zB >= 1 && zB <= mz - 2) {
-                        const float *T0 = sm + OFF_T + (zB & 7) * PLANE + tid;
-                        const float *R0 = sm + OFF_R + (zB & 7) * PLANE + tid;
-                        float av[3], bv[3];
-                        av[0] = (T0[1] - T0[-1]) * hx;
-                        av[1] = (T0[BX] - T0[-BX]) * hy;
-                        av[2] = (sm[OFF_T + ((zB + 1) & 7) * PLANE + tid] - sm[OFF_T + ((zB - 1) & 7) * PLANE + tid]) * hz;
-                        bv[0] = (R0[1] - R0[-1]) * hx;
-                        bv[1] = (R0[BX] - R0[-BX]) * hy;
-                        bv[2] = (sm[OFF_R + ((zB + 1) & 7) * PLANE + tid] - sm[OFF_R + ((zB - 1) & 7) * PLANE + tid]) * hz;
-                        const float psi = ngf_residual(av, bv, a.tau, a.rho, v);
-                        if (colC && rowC && zB >= z0 && zB < zend)
-                            psi_sum.add(psi);
-                    }
-                    float *vq = sm + OFF_V + (zB & 7) * 3 * PLANE + tid;
-                    vq[0] = v[0];
-                    vq[PLANE] = v[1];
-                    vq[2 * PLANE] = v[2];
-                }
-            }
-        }
-        // ---- C: r on planes zA - 6, zA - 5 (rows 2 .. 13), x reduction into node columns
-        if (rowC && zA - 6 >= z0 && zA - 5 < zend) {
-            float *redb = sm + OFF_RED + (s & 1) * 2 * RED_PLANE + ty * NX * 3;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int zC = zA - 6 + h;
-                float r[3] = {0.f, 0.f, 0.f};
-                if (colC && col_in && zC < mz) {
-                    const float *V0 = sm + OFF_V + (zC & 7) * 3 * PLANE + tid;
-                    const float gs = (V0[-1] - V0[1]) * hx + (V0[PLANE - BX] - V0[PLANE + BX]) * hy +
-                                     (sm[OFF_V + ((zC - 1) & 7) * 3 * PLANE + 2 * PLANE + tid] -
-                                      sm[OFF_V + ((zC + 1) & 7) * 3 * PLANE + 2 * PLANE + tid]) * hz;
-                    const float gj = half_hbar * gs;
-                    const float *gq = sm + OFF_G + (zC & 7) * 3 * PLANE + tid;
-                    r[0] = gj * gq[0];
-                    r[1] = gj * gq[PLANE];
-                    r[2] = gj * gq[2 * PLANE];
-                }
-                // node column j (0..14) gathers lanes 2j .. 2j+3 with weights 1/4, 3/4, 3/4, 1/4
-                float *red = redb + h * RED_PLANE;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const float r1 = __shfl_down_sync(0xffffffffu, r[c], 1);
-                    const float r2 = __shfl_down_sync(0xffffffffu, r[c], 2);
-                    const float r3 = __shfl_down_sync(0xffffffffu, r[c], 3);
-                    // written nodes have tx = 2j <= 28, so lanes tx + 1 .. tx + 3 exist
-                    if (!(tx & 1) && (tx >> 1) < NX)
-                        red[(tx >> 1) * 3 + c] = 0.25f * (r[c] + r3) + 0.75f * (r1 + r2);
-                }
-            }
-        }
-        // ---- D: y reduction of planes zA - 8, zA - 7 (one node interval) and
-        // accumulation of its two node planes along z
-        if (dD && zA - 8 >= z0 && zA - 7 < zend) {
-            const int lz = zA - 8 - z0;                   // even
-            const float *red = sm + OFF_RED + ((s - 1) & 1) * 2 * RED_PLANE + dofs;
-            const float v0 = 0.25f * red[0] + 0.75f * red[NX * 3] + 0.75f * red[2 * NX * 3] + 0.25f * red[3 * NX * 3];
-            red += RED_PLANE;
-            const float v1 = 0.25f * red[0] + 0.75f * red[NX * 3] + 0.75f * red[2 * NX * 3] + 0.25f * red[3 * NX * 3];
-            // even plane: 3/4 to the lower node plane, 1/4 to the upper; odd plane: the reverse
-            part_tile[(size_t)(lz >> 1) * NE + tid] = acc_lo + (0.75f * v0 + 0.25f * v1);
-            acc_lo = 0.25f * v0 + 0.75f * v1;
-            if (lz == a.tz - 2)
-                part_tile[(size_t)(a.tz >> 1) * NE + tid] = acc_lo;
-        }
-        cp_async_wait_all();
-        __syncthreads();
+    // z0 is even: zA + 1 is odd on even steps
+    const int nsteps = a.tz + 7;
+    for (int s = 0; s < nsteps; s += 2) {
+        step(s, std::true_type{});
+        if (s + 1 < nsteps)
+            step(s + 1, std::false_type{});
     }
     double ssum = block_sum_to_f64(psi_sum.s, reinterpret_cast<double *>(sm + OFF_RED));
     if (tid == 0)
@@ -530,32 +606,67 @@ bool fused_eligible(const Level &L)
     return true;
 }
 
-// z segment lengths the autotuner tries (even: a segment covers whole node intervals)
+// z segment lengths the throughput rule picks from (even: a segment covers
+// whole node intervals)
 constexpr int TZ_CAND[] = {2, 4, 8, 16, 32, 64, 128};
 
-// Default z segment length when the level was not tuned: the longest of 8 ..
-// 128 that still gives >= 2 CTAs per SM (each segment pays 7 pipeline-fill steps).
-static int fused_tz_default(const Level &L, int num_sms)
+// Pipeline steps a segment pays beyond its tz planes (fill and drain)
+constexpr int FUSED_FILL = 7;
+// longest z segment (the tile partial buffers are sized for every even length up to it)
+constexpr int TZ_MAX = 512;
+
+// Even z segment lengths that cut a depth of mz planes into ntz = 1, 2, ...
+// nearly equal segments, tz = 2 ceil(mz / (2 ntz)), longest first, each once.
+static std::vector<int> tz_splits(int mz)
 {
-    long long cols = (long long)((L.m[0] + OX - 1) / OX) * ((L.m[1] + OY - 1) / OY);
-    int tz = 128;
-    while (tz > 8 && cols * ((L.m[2] + tz - 1) / tz) < 2LL * num_sms)
-        tz /= 2;
-    return tz;
+    std::vector<int> v;
+    for (int ntz = 1;; ntz++) {
+        const int tz = 2 * ((mz + 2 * ntz - 1) / (2 * ntz));
+        if (tz <= TZ_MAX && (v.empty() || tz < v.back()))
+            v.push_back(tz);
+        if (tz <= 2)
+            break;
+    }
+    return v;
 }
+
+// Modelled duration of the pass in CTA steps: one CTA is resident per SM, so
+// the CTAs run in waves of num_sms, each as long as one segment (tz + 7 steps).
+static long long fused_cost(int cols, int mz, int tz, int num_sms)
+{
+    const long long ctas = (long long)cols * ((mz + tz - 1) / tz);
+    return (ctas + num_sms - 1) / num_sms * (tz + FUSED_FILL);
+}
+
+static int fused_cols(const int m[3]) { return ((m[0] + OX - 1) / OX) * ((m[1] + OY - 1) / OY); }
+
+// z segment lengths of the splits, cheapest first under the wave model (ties: the longer)
+static std::vector<int> tz_ranked(const int m[3], int num_sms)
+{
+    std::vector<int> v = tz_splits(m[2]);
+    const int cols = fused_cols(m);
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+        return fused_cost(cols, m[2], a, num_sms) < fused_cost(cols, m[2], b, num_sms);
+    });
+    return v;
+}
+
+// Default z segment length when the level was not tuned: the cheapest split
+// under the wave model
+static int fused_tz_default(const Level &L, int num_sms) { return tz_ranked(L.m, num_sms > 0 ? num_sms : 1)[0]; }
 
 int fused_tz(const Level &L, int num_sms) { return L.tz > 0 ? L.tz : fused_tz_default(L, num_sms); }
 
-// Throughput rule: the z segment length with the fewest z steps in total,
-// ntz * (tz / 2 + 5) (ties: the longer one).  The right choice when other work
-// keeps every SM busy (a batch of pairs); a single pair alone wants short
-// segments that fill the GPU, which the autotuner finds.
+// Throughput rule: the z segment length of TZ_CAND with the fewest pipeline
+// steps in total, ntz * (tz + 7) (ties: the longer one).  The right choice
+// when other work keeps every SM busy (a batch of pairs); a single pair alone
+// wants segments that fill the GPU in whole waves, which the autotuner finds.
 int fused_tz_throughput(const Level &L)
 {
     int best = 0;
     long long best_steps = 0;
     for (int tz : TZ_CAND) {
-        const long long steps = (long long)((L.m[2] + tz - 1) / tz) * (tz / 2 + 5);
+        const long long steps = (long long)((L.m[2] + tz - 1) / tz) * (tz + FUSED_FILL);
         if (best == 0 || steps <= best_steps) {
             best = tz;
             best_steps = steps;
@@ -564,13 +675,7 @@ int fused_tz_throughput(const Level &L)
     return best;
 }
 
-bool fused_tz_valid(int tz)
-{
-    for (int t : TZ_CAND)
-        if (t == tz)
-            return true;
-    return false;
-}
+bool fused_tz_valid(int tz) { return tz >= 2 && tz <= TZ_MAX && tz % 2 == 0; }
 
 void fused_grid(const Level &L, int tz, int &ntx, int &nty, int &ntz)
 {
@@ -580,12 +685,12 @@ void fused_grid(const Level &L, int tz, int &ntx, int &nty, int &ntz)
 }
 
 // tile-partial floats of the level: the largest over every z segment length
-// the autotuner may pick
+// that may be used (any even length cfg.fused_tz may force covers the rules)
 size_t fused_part_floats(const Level &L, int num_sms)
 {
     (void)num_sms;
     size_t best = 0;
-    for (int tz : TZ_CAND) {
+    for (int tz = 2; tz <= TZ_MAX; tz += 2) {
         int ntx, nty, ntz;
         fused_grid(L, tz, ntx, nty, ntz);
         size_t p = (size_t)ntx * nty * ntz * (tz / 2 + 1) * NE;
@@ -686,16 +791,19 @@ cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alph
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the z segment length (the tile depth of the fused pass).  For
-// every candidate the pass runs on the level's own images at u = u_zero (one
-// warm launch, then the median of three CUDA-event timings); the fastest wins.
-// Short segments start more CTAs (small levels fill the GPU) but pay the 7
-// pipeline-fill steps and the shared node planes more often, so the best
-// depth depends on the level and the GPU.  Choices are cached per (image
-// dims, SM count, image type, device) for the life of the process: handles of
-// the same geometry tune once and pick the same tiling.
+// Autotuner of the z segment length (the tile depth of the fused pass).  The
+// candidates are the TUNE_CAND splits of the depth into equal even segments
+// that the wave model ranks cheapest; for each the pass runs on the level's
+// own images at u = u_zero (one warm launch, then the median of three
+// CUDA-event timings) and the fastest wins.  Short segments start more CTAs
+// (small levels fill the GPU) but pay the 7 pipeline-fill steps and the
+// shared node planes more often, and the last wave of CTAs may leave SMs
+// idle, so the best depth depends on the level and the GPU.  Choices are
+// cached per (image dims, SM count, image type, device) for the life of the
+// process: handles of the same geometry tune once and pick the same tiling.
 // ---------------------------------------------------------------------------
 namespace {
+constexpr int TUNE_CAND = 6;
 std::mutex g_tune_mu;
 std::map<std::array<int, 6>, int> g_tune;
 }
@@ -719,10 +827,11 @@ cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStrea
         e = cudaEventCreate(&e1);
     int best = 0;
     float best_ms = 0.f;
-    for (int tz : TZ_CAND) {
+    std::vector<int> cand = tz_ranked(L.m, c->num_sms > 0 ? c->num_sms : 1);
+    if (cand.size() > (size_t)TUNE_CAND)
+        cand.resize(TUNE_CAND);
+    for (int tz : cand) {
         if (e != cudaSuccess)
-            break;
-        if (tz > 2 && tz / 2 >= L.m[2])   // the previous candidate already spans the whole depth
             break;
         L.tz = tz;
         int nD = 0;
@@ -766,14 +875,7 @@ cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStrea
 // own every buffer themselves (the allocation-free entry point).  Geometry
 // comes in as a LevelGeom of a ratio-2 grid; no per-dimension tables are used.
 // ---------------------------------------------------------------------------
-static int fused_tz_dims(const int m[3], int num_sms)
-{
-    long long cols = (long long)((m[0] + OX - 1) / OX) * ((m[1] + OY - 1) / OY);
-    int tz = 64;
-    while (tz > 8 && cols * ((m[2] + tz - 1) / tz) < 2LL * num_sms)
-        tz /= 2;
-    return tz;
-}
+static int fused_tz_dims(const int m[3], int num_sms) { return tz_ranked(m, num_sms > 0 ? num_sms : 1)[0]; }
 
 void fused_layout_dims(const int m[3], int num_sms, int *tz, int *tiles, size_t *part_floats)
 {

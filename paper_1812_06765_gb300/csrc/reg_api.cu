@@ -87,7 +87,7 @@ int validate_config(const reg_config *cfg, std::string &msg)
     else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
     else if (cfg->autotune != 0 && cfg->autotune != 1) msg = "autotune must be 0 or 1";
     else if (cfg->fused_tz != 0 && cfg->fused_tz != -1 && !fused_tz_valid(cfg->fused_tz))
-        msg = "fused_tz must be 0, -1 or one of 2, 4, 8, 16, 32, 64, 128";
+        msg = "fused_tz must be 0, -1 or an even length in 2 .. 512";
     else return REG_OK;
     return REG_ERR_ARG;
 }
@@ -451,6 +451,8 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
         } else if (cfg.autotune) {
             CK(cudaMemsetAsync(c->lb.pdir, 0, sizeof(float) * 3 * c->L[l].nn, c->stream));
             CK(fused_autotune(c, l, c->lb.pdir, c->stream));
+        } else {
+            c->L[l].tz = fused_tz(c->L[l], c->num_sms);
         }
     }
     if (!ptr_is_device) CK(cudaStreamSynchronize(c->stream));  // host arrays may be released on return
@@ -466,9 +468,9 @@ int reg_level_tiling(reg_handle c, int level, int *tz, int *tiles)
         return set_err(c, REG_ERR_ARG, "reg_level_tiling: level %d out of range", level);
     int z = 0, n = 0;
     if (use_fused(c, level)) {
-        const Level &L = c->L[level];
-        z = fused_tz(L, c->num_sms);
-        n = ((L.m[0] + 27) / 28) * ((L.m[1] + 11) / 12) * ((L.m[2] + z - 1) / z);
+        int ntx, nty, ntz;
+        fused_tiling(c->L[level], c->num_sms, &z, &ntx, &nty, &ntz);
+        n = ntx * nty * ntz;
     }
     if (tz) *tz = z;
     if (tiles) *tiles = n;

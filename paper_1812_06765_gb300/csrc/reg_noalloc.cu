@@ -16,6 +16,7 @@
 // the first call on each device looks the address up with
 // cudaGetSymbolAddress while that device is current, and caches it.
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <mutex>
@@ -41,8 +42,8 @@ namespace {
 //   tile partial sums of P^T r : 2^21 floats      (8 MiB)
 //   curvature Laplacian w      : 2^20 floats      (4 MiB)
 //   block partial sums         : 2^16 doubles     (512 KiB)
-// 256^3 images do not fit (their tile partials need about 9.2 M floats); a
-// 128^3 pair needs 1.25 M + 0.82 M floats and 2.2 K doubles.
+// 256^3 images do not fit; a 128^3 pair needs about 1.2 M + 0.82 M floats
+// and 2.2 K doubles, and the Laplacian w limits the size to about 136^3.
 constexpr size_t CAP_PART = size_t(1) << 21;
 constexpr size_t CAP_W = size_t(1) << 20;
 constexpr size_t CAP_PARTIALS = size_t(1) << 16;
@@ -105,6 +106,8 @@ extern "C" int reg_eval_objective_grad_noalloc(const float *R, const float *T, c
         return set_err(nullptr, REG_ERR_ARG, "%s: NULL argument", fn);
     if (!(tau > 0) || !(rho > 0) || !(alpha >= 0))
         return set_err(nullptr, REG_ERR_ARG, "%s: need tau > 0, rho > 0, alpha >= 0", fn);
+    if (reinterpret_cast<uintptr_t>(R) % 8 != 0)   // R is read two voxels at a time
+        return set_err(nullptr, REG_ERR_ARG, "%s: R must be 8-byte aligned", fn);
     LevelGeom g;
     memset(&g, 0, sizeof g);
     double H[3];

@@ -43,8 +43,8 @@ def test_config_default_and_version(libreg):
 
 def test_create_rejects_bad_config_before_touching_the_gpu(libreg):
     for field, value in (("levels", 0), ("levels", 9), ("lbfgs_mem", 0), ("tau", 0.0), ("c1", 1.5),
-                         ("max_backtracks", 0), ("eval_impl", 7), ("autotune", 2), ("fused_tz", 6),
-                         ("fused_tz", 256), ("fused_tz", -2), ("eval_impl", -1)):
+                         ("max_backtracks", 0), ("eval_impl", 7), ("autotune", 2), ("fused_tz", 7),
+                         ("fused_tz", 514), ("fused_tz", -2), ("eval_impl", -1)):
         cfg = libreg.reg_config_default()
         setattr(cfg, field, value)
         with pytest.raises(libreg.RegError) as ei:

@@ -28,9 +28,11 @@ EVAL_IMPLS = [0, 1, 2, 3]
 
 # (dims, spacing, nodes or None, tau, rho, alpha, amplitude of u in mm)
 CASES = [
-    ((30, 26, 22), (1.0, 1.0, 1.0), None, 0.05, 0.05, 1.0, 1.5),          # ragged tiles (28 x 12 x 8)
+    ((30, 26, 22), (1.0, 1.0, 1.0), None, 0.05, 0.05, 1.0, 1.5),          # ragged tiles (28 x 28 output)
     ((58, 38, 70), (1.2, 0.8, 1.0), None, 0.05, 0.03, 2.0, 2.5),          # several tiles and z segments
-    ((28, 12, 8), (1.0, 1.0, 1.0), None, 0.1, 0.1, 1.0, 0.8),             # exactly one tile
+    ((28, 12, 8), (1.0, 1.0, 1.0), None, 0.1, 0.1, 1.0, 0.8),             # one tile, ragged in y
+    ((28, 28, 8), (1.0, 1.0, 1.0), None, 0.1, 0.1, 1.0, 0.8),             # exactly one tile
+    ((86, 58, 12), (1.0, 1.0, 1.0), None, 0.05, 0.05, 1.0, 1.5),          # 4 x 3 tiles, one thin column
     ((4, 6, 4), (1.0, 1.0, 1.0), None, 0.1, 0.1, 1.0, 0.3),               # smallest even grid
     ((16, 16, 16), (1.0, 1.0, 1.0), None, 0.05, 0.05, 1.0, 1.0),          # one tile
     ((37, 29, 23), (1.0, 1.1, 0.9), None, 0.05, 0.02, 3.0, 1.5),          # ragged, non-integer ratio
@@ -263,20 +265,22 @@ def test_bf16_image_storage(reg_mod, orc, config_id):
     r.close()
 
 
-TZ_CANDIDATES = [2, 4, 8, 16, 32, 64, 128]
+# z segment lengths: the throughput rule's powers of two, splits of the depth
+# 70 into equal even segments (what the model and the autotuner pick from),
+# ragged last segments, segments as long as or longer than the image
+TZ_LENGTHS = [2, 4, 6, 10, 16, 24, 36, 70, 72, 128]
 
 
-@pytest.mark.parametrize("tz", TZ_CANDIDATES)
+@pytest.mark.parametrize("tz", TZ_LENGTHS)
 def test_every_fused_tile_depth_matches_oracle(reg_mod, orc, tz):
-    # every z segment length the autotuner may pick: ragged segments, segments
-    # longer than the image, tiles sharing node planes in z
+    # tiles sharing node planes in z, a forced segment length on every level
     dims, h, tau, rho, alpha = (58, 38, 70), (1.2, 0.8, 1.0), 0.05, 0.03, 2.0
     R = random_image(dims, 71)
     T = random_image(dims, 72)
     cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=tz)
     r = reg_mod.Registration(cfg).set_images(R, T, h)
     z, tiles = r.level_tiling(0)
-    assert z == tz and tiles == 3 * 4 * -(-dims[2] // tz)
+    assert z == tz and tiles == 3 * 2 * -(-dims[2] // tz)
     u = random_field(r.level_info(0)["nodes"], 73, 2.5)
     e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
     assert e["eJ"] <= J_RTOL and e["eg"] <= GRAD_RTOL, e
@@ -289,12 +293,14 @@ def test_autotuned_tiling_is_cached_per_geometry(reg_mod):
     cfg = reg_mod.make_config(levels=3, tau=0.05, alpha=1.0)
     r1 = reg_mod.Registration(cfg).set_images(R, R, h)
     r2 = reg_mod.Registration(cfg).set_images(R, R, h)
+    def even_splits(depth):   # 2 ceil(depth / 2k): depth cut into k nearly equal even segments
+        return {2 * -(-depth // (2 * k)) for k in range(1, depth + 1)}
     for lv in range(3):
         t1, t2 = r1.level_tiling(lv), r2.level_tiling(lv)
-        assert t1 == t2 and t1[0] in TZ_CANDIDATES and t1[1] > 0
+        assert t1 == t2 and t1[0] in even_splits(r1.level_info(lv)["dims"][2]) and t1[1] > 0
     off = reg_mod.Registration(reg_mod.make_config(levels=3, tau=0.05, alpha=1.0, autotune=False))
     off.set_images(R, R, h)
-    assert all(off.level_tiling(lv)[0] in (8, 16, 32, 64, 128) for lv in range(3))
+    assert all(off.level_tiling(lv)[0] in even_splits(off.level_info(lv)["dims"][2]) for lv in range(3))
     for r in (r1, r2, off):
         r.close()
 

@@ -67,4 +67,9 @@ def test_noalloc_refuses_sizes_beyond_its_capacity(reg_mod):
                                                  u.data_ptr(), 0.1, 0.1, 1.0, jds.data_ptr())
         assert ei.value.code == _lib.REG_ERR_ARG
         assert _lib.reg_last_error(None)
+    # R is read two voxels at a time: a pointer 4 bytes off an 8-byte boundary is refused before any launch
+    with pytest.raises(_lib.RegError) as ei:
+        _lib.reg_eval_objective_grad_noalloc(img.data_ptr() + 4, img.data_ptr(), (32, 32, 32), (1.0, 1.0, 1.0),
+                                             u.data_ptr(), u.data_ptr(), 0.1, 0.1, 1.0, jds.data_ptr())
+    assert ei.value.code == _lib.REG_ERR_ARG and "aligned" in _lib.reg_last_error(None)
     assert float(jds.abs().sum()) == 0.0           # nothing was written
