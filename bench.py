@@ -179,6 +179,11 @@ def source_digest(files):
     return h.hexdigest()[:16]
 
 
+# partial sums one fused-pass tile writes per node plane: 3 components x 15 x 15
+# node columns (a 28 x 28 output tile reaches 28 / 2 + 1 nodes per dimension)
+FUSED_TILE_NODE_ENTRIES = 3 * 15 * 15
+
+
 def committed_profile(kernel, digest, workload_name, tz):
     """The committed ncu figures of a kernel launch (DRAM bytes, warp instructions),
     if they were taken on this source, this workload and this tiling (else {})."""
@@ -370,7 +375,7 @@ def run_ours(args):
     kernel = "objective_pass_fused" if impl == 0 else "objective_pass_multipass"
     tz, tiles = reg.level_tiling(0)
     # the dominant kernel: read R, T and u once, write its tile partials of P^T r
-    part_bytes = 4 * tiles * (tz // 2 + 1) * 315 if impl == 0 else 12 * nn
+    part_bytes = 4 * tiles * (tz // 2 + 1) * FUSED_TILE_NODE_ENTRIES if impl == 0 else 12 * nn
     kernel_bytes = 8 * nv + 12 * nn + part_bytes
     achieved = kernel_bytes / (ngf_ms * 1e-3) / 1e9
     prof = committed_profile(kernel, source_digest(FUSED_KERNEL_SOURCES), c["name"], tz)
