@@ -99,6 +99,26 @@ struct KahanF {
     }
 };
 
+// Ordered FP64 sum (is_max: max) of count values x[i0], x[i0 + step], ...,
+// starting from s.  The loads go out 8 at a time so that their L2 round trips
+// overlap; the additions keep the index order, so the result is the plain
+// sequential one.
+__device__ __forceinline__ double ordered_reduce(const double *__restrict__ x, long long i0, int count,
+                                                 long long step, bool is_max, double s)
+{
+    for (int k0 = 0; k0 < count; k0 += 8) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            v[k] = k0 + k < count ? __ldcg(x + i0 + (long long)(k0 + k) * step) : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (k0 + k < count)
+                s = is_max ? fmax(s, v[k]) : s + v[k];
+    }
+    return s;
+}
+
 // Deterministic FP64 sum of block partials: scal = [J, D, S].  The summation
 // order is a fixed 512-wide layout (strided sums, then a halving tree), the
 // same for any block size, so every kernel that ends an evaluation with it
@@ -110,13 +130,8 @@ __device__ __forceinline__ void finalize_body(const double *__restrict__ pD, int
     __shared__ double sd[512], ss[512];
     const int t = linear_tid(), nt = nthreads();
     for (int v = t; v < 512; v += nt) {
-        double a = 0.0, b = 0.0;
-        for (int i = v; i < nD; i += 512)
-            a += pD[i];
-        for (int i = v; i < nS; i += 512)
-            b += pS[i];
-        sd[v] = a;
-        ss[v] = b;
+        sd[v] = ordered_reduce(pD, v, v < nD ? (nD - v + 511) / 512 : 0, 512, false, 0.0);
+        ss[v] = ordered_reduce(pS, v, v < nS ? (nS - v + 511) / 512 : 0, 512, false, 0.0);
     }
     __syncthreads();
     for (int o = 256; o > 0; o >>= 1) {

@@ -15,6 +15,9 @@
 // pdir (current direction), P and Y rings of m + 1 slots each (s_j = t_j P_j).
 #include <math.h>
 
+#include <algorithm>
+#include <atomic>
+
 #include "batch.h"
 #include "internal.h"
 #include "lbfgs_control.cuh"
@@ -53,6 +56,23 @@ __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restr
                                          int bx, int nblocks)
 {
     __shared__ int s_last;
+    if (nblocks <= LB_DIRECT) {
+        if (t.phase < 0)
+            return;   // the control kernel that follows reduces the block partials
+        __threadfence();   // this block's partials, before its arrival is counted
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_last = atomicAdd(&t.cnt[0], 1u) == (unsigned)(nblocks - 1);
+            if (s_last)
+                t.cnt[0] = 0;
+        }
+        __syncthreads();
+        if (!s_last)
+            return;
+        __threadfence();
+        lb_control_body(t.phase, t.st, partials, nblocks, t.scal, t.h_ls, t.h_iter, t.h_redo);
+        return;
+    }
     __threadfence();   // this block's partials, before its arrival is counted
     __syncthreads();
     const int g = bx / LB_RG, g0 = g * LB_RG, gs = min(LB_RG, nblocks - g0);
@@ -63,14 +83,8 @@ __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restr
     if (!s_last)
         return;
     __threadfence();
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
-        double s = 0.0;   // the max entry is a max of absolute values: 0 is its identity
-        for (int k = 0; k < gs; k++) {
-            const double x = __ldcg(partials + (size_t)(g0 + k) * nd + d);
-            s = (d == imax) ? fmax(s, x) : s + x;
-        }
-        t.gpart[(size_t)g * nd + d] = s;
-    }
+    for (int d = threadIdx.x; d < nd; d += blockDim.x)   // the max entry: a max of absolute values, 0 its identity
+        t.gpart[(size_t)g * nd + d] = ordered_reduce(partials, (long long)g0 * nd + d, gs, nd, d == imax, 0.0);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -122,6 +136,64 @@ __global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *_
     lb_init_dots_body(n, g, partials, tail, blockIdx.x, gridDim.x);
 }
 
+// Element loop of the direction pass for DC stored pairs: straight-line code,
+// so every load of an element (g and the 2 DC history vectors) is issued
+// before the first one is used.  (With the pair count a run-time bound, the
+// loads of pair j sat behind a branch and waited for pair j - 1's FMAs: up to
+// 2 m + 1 dependent memory round trips per element.)
+template <int DC>
+__device__ __forceinline__ float4 direction_elem(const float4 &gv, const float4 (&a)[DC > 0 ? DC : 1],
+                                                 const float4 (&b)[DC > 0 ? DC : 1], float cg,
+                                                 const float (&cp)[LB_MAXM], const float (&cy)[LB_MAXM])
+{
+    float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+        p.x = fmaf(cp[j], a[j].x, fmaf(cy[j], b[j].x, p.x));
+        p.y = fmaf(cp[j], a[j].y, fmaf(cy[j], b[j].y, p.y));
+        p.z = fmaf(cp[j], a[j].z, fmaf(cy[j], b[j].z, p.z));
+        p.w = fmaf(cp[j], a[j].w, fmaf(cy[j], b[j].w, p.w));
+    }
+    return p;
+}
+
+// Element loop of the direction pass for DC stored pairs: straight-line code
+// over two elements at a time, so every load of both (g and the 2 DC history
+// vectors each) is in flight before the first store.  (With the pair count a
+// run-time bound, the loads of pair j sat behind a branch and waited for pair
+// j - 1's FMAs: up to 2 m + 1 dependent memory round trips per element.)
+template <int DC>
+__device__ __forceinline__ void direction_span(long long e0, long long n4, long long step, float cg,
+                                               const float4 *__restrict__ g4, const float4 *__restrict__ P4,
+                                               const float4 *__restrict__ Y4, const int (&off)[LB_MAXM],
+                                               const float (&cp)[LB_MAXM], const float (&cy)[LB_MAXM],
+                                               float4 *__restrict__ p4, float (&v)[2])
+{
+    constexpr int K = DC > 0 ? DC : 1;
+    for (long long e = e0; e < n4; e += 2 * step) {
+        const long long e1 = e + step < n4 ? e + step : e;   // the second element, or the first again
+        const float4 g0 = g4[e], g1 = g4[e1];
+        float4 a0[K], b0[K], a1[K], b1[K];
+#pragma unroll
+        for (int j = 0; j < DC; j++) {
+            a0[j] = P4[off[j] + e];
+            b0[j] = Y4[off[j] + e];
+            a1[j] = P4[off[j] + e1];
+            b1[j] = Y4[off[j] + e1];
+        }
+        const float4 p0 = direction_elem<DC>(g0, a0, b0, cg, cp, cy);
+        const float4 p1 = direction_elem<DC>(g1, a1, b1, cg, cp, cy);
+        p4[e] = p0;
+        v[0] += dot4(g0, p0);
+        v[1] += dot4(p0, p0);
+        if (e1 != e) {
+            p4[e1] = p1;
+            v[0] += dot4(g1, p1);
+            v[1] += dot4(p1, p1);
+        }
+    }
+}
+
 // p = cg g + sum_j cp_j P_j + cy_j Y_j, written to pdir; partial sums of g'p and p'p.
 __device__ __forceinline__ void lb_direction_body(long long n, long long stride, const LbfgsState *st,
                                                      const float *__restrict__ g, const float *__restrict__ P,
@@ -148,34 +220,29 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
     if (s_run) {   // otherwise only the arrival below (partials unused)
         const int dc = s_dc;
         const float cg = s_cg;
-        const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
+        // slot j of both rings starts off[j] float4s in (the slot stride is a multiple of 4 floats)
+        const float4 *P4 = reinterpret_cast<const float4 *>(P), *Y4 = reinterpret_cast<const float4 *>(Y);
+        int off[LB_MAXM];
         float cp[LB_MAXM], cy[LB_MAXM];
 #pragma unroll
         for (int j = 0; j < LB_MAXM; j++) {
-            const int sl = j < dc ? s_slot[j] : 0;
-            Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
-            Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
+            off[j] = j < dc ? (int)(s_slot[j] * (stride >> 2)) : 0;
             cp[j] = s_cp[j];
             cy[j] = s_cy[j];
         }
-        const long long n4 = n >> 2;
+        const long long n4 = n >> 2, e0 = bx * (long long)VT + threadIdx.x, step = (long long)gdx * VT;
         const float4 *g4 = reinterpret_cast<const float4 *>(g);
         float4 *p4 = reinterpret_cast<float4 *>(pdir);
-        for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
-            float4 gv = g4[e];
-            float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
-#pragma unroll
-            for (int j = 0; j < LB_MAXM; j++)
-                if (j < dc) {
-                    float4 a = Pj[j][e], b = Yj[j][e];
-                    p.x = fmaf(cp[j], a.x, fmaf(cy[j], b.x, p.x));
-                    p.y = fmaf(cp[j], a.y, fmaf(cy[j], b.y, p.y));
-                    p.z = fmaf(cp[j], a.z, fmaf(cy[j], b.z, p.z));
-                    p.w = fmaf(cp[j], a.w, fmaf(cy[j], b.w, p.w));
-                }
-            p4[e] = p;
-            v[0] += dot4(gv, p);
-            v[1] += dot4(p, p);
+        switch (dc) {
+        case 0: direction_span<0>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 1: direction_span<1>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 2: direction_span<2>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 3: direction_span<3>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 4: direction_span<4>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 5: direction_span<5>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 6: direction_span<6>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 7: direction_span<7>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        default: direction_span<8>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
         }
         if (bx == 0 && threadIdx.x < (n & 3)) {
             const long long e = 4 * n4 + threadIdx.x;
@@ -212,6 +279,51 @@ __device__ __forceinline__ void accept_elem(float gn, float go, float pf, float 
     u = fmaf(t, pf, u);
 }
 
+// Element loop of the accept pass for NP stored pairs before the free slot:
+// all loads of an element (g_new, g, p, u and the 2 NP history vectors) come
+// before its stores, in straight-line code, so they are in flight together.
+// The stored slots are never the free slot this pass writes.
+template <int NP>
+__device__ __forceinline__ void accept_span(long long e0, long long n4, long long step, float t,
+                                            const float4 *__restrict__ gt4, float4 *__restrict__ g4,
+                                            const float4 *__restrict__ pd4, float4 *__restrict__ u4,
+                                            const float4 *P4, const float4 *Y4, const int (&off)[LB_MAXM],
+                                            float4 *Pf4, float4 *Yf4, float (&v)[ND_ACC], float (&fr)[4])
+{
+    for (long long e = e0; e < n4; e += step) {
+        const float4 gn = gt4[e], go = g4[e], pf = pd4[e];
+        float4 uu = u4[e];
+        float4 pj[NP > 0 ? NP : 1], yj[NP > 0 ? NP : 1];
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+            pj[j] = P4[off[j] + e];
+            yj[j] = Y4[off[j] + e];
+        }
+        float4 yn;
+        accept_elem(gn.x, go.x, pf.x, uu.x, t, yn.x);
+        accept_elem(gn.y, go.y, pf.y, uu.y, t, yn.y);
+        accept_elem(gn.z, go.z, pf.z, uu.z, t, yn.z);
+        accept_elem(gn.w, go.w, pf.w, uu.w, t, yn.w);
+        v[0] += dot4(gn, gn);
+        v[1] = fmaxf(v[1], max4(gn));
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+            v[2 + 4 * j] += dot4(pj[j], gn);
+            v[3 + 4 * j] += dot4(yj[j], gn);
+            v[4 + 4 * j] += dot4(pj[j], yn);
+            v[5 + 4 * j] += dot4(yj[j], yn);
+        }
+        fr[0] += dot4(pf, gn);
+        fr[1] += dot4(yn, gn);
+        fr[2] += dot4(pf, yn);
+        fr[3] += dot4(yn, yn);
+        u4[e] = uu;
+        g4[e] = gn;
+        Pf4[e] = pf;
+        Yf4[e] = yn;
+    }
+}
+
 __device__ __forceinline__ void lb_accept_body(long long n, long long stride, const LbfgsState *st,
                                                   float *__restrict__ u, float *__restrict__ g,
                                                   const float *__restrict__ gt, const float *__restrict__ pdir,
@@ -239,46 +351,28 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
     if (s_ok) {   // otherwise only the arrival below (partials unused)
         const int np = s_lc - 1;    // stored pairs before the free slot
         const float t = s_t;
-        const float4 *Pj[LB_MAXM], *Yj[LB_MAXM];
+        const float4 *P4 = reinterpret_cast<const float4 *>(P), *Y4 = reinterpret_cast<const float4 *>(Y);
+        int off[LB_MAXM];   // slot j of both rings starts off[j] float4s in
 #pragma unroll
-        for (int j = 0; j < LB_MAXM; j++) {
-            const int sl = j < np ? s_slot[j] : 0;
-            Pj[j] = reinterpret_cast<const float4 *>(P + (size_t)sl * stride);
-            Yj[j] = reinterpret_cast<const float4 *>(Y + (size_t)sl * stride);
-        }
+        for (int j = 0; j < LB_MAXM; j++)
+            off[j] = j < np ? (int)(s_slot[j] * (stride >> 2)) : 0;
         float *Pf = P + (size_t)s_free * stride;
         float *Yf = Y + (size_t)s_free * stride;
         float fr[4] = {0.f, 0.f, 0.f, 0.f};   // dots of the free slot (p, y_new) with g_new, y_new
-        const long long n4 = n >> 2;
-        for (long long e = bx * (long long)VT + threadIdx.x; e < n4; e += (long long)gdx * VT) {
-            float4 gn = reinterpret_cast<const float4 *>(gt)[e];
-            float4 go = reinterpret_cast<float4 *>(g)[e];
-            float4 pf = reinterpret_cast<const float4 *>(pdir)[e];
-            float4 uu = reinterpret_cast<float4 *>(u)[e];
-            float4 yn;
-            accept_elem(gn.x, go.x, pf.x, uu.x, t, yn.x);
-            accept_elem(gn.y, go.y, pf.y, uu.y, t, yn.y);
-            accept_elem(gn.z, go.z, pf.z, uu.z, t, yn.z);
-            accept_elem(gn.w, go.w, pf.w, uu.w, t, yn.w);
-            reinterpret_cast<float4 *>(u)[e] = uu;
-            reinterpret_cast<float4 *>(g)[e] = gn;
-            reinterpret_cast<float4 *>(Pf)[e] = pf;
-            reinterpret_cast<float4 *>(Yf)[e] = yn;
-            v[0] += dot4(gn, gn);
-            v[1] = fmaxf(v[1], max4(gn));
-#pragma unroll
-            for (int j = 0; j < LB_MAXM; j++)
-                if (j < np) {
-                    float4 pj = Pj[j][e], yj = Yj[j][e];
-                    v[2 + 4 * j] += dot4(pj, gn);
-                    v[3 + 4 * j] += dot4(yj, gn);
-                    v[4 + 4 * j] += dot4(pj, yn);
-                    v[5 + 4 * j] += dot4(yj, yn);
-                }
-            fr[0] += dot4(pf, gn);
-            fr[1] += dot4(yn, gn);
-            fr[2] += dot4(pf, yn);
-            fr[3] += dot4(yn, yn);
+        const long long n4 = n >> 2, e0 = bx * (long long)VT + threadIdx.x, step = (long long)gdx * VT;
+        const float4 *gt4 = reinterpret_cast<const float4 *>(gt), *pd4 = reinterpret_cast<const float4 *>(pdir);
+        float4 *g4 = reinterpret_cast<float4 *>(g), *u4 = reinterpret_cast<float4 *>(u);
+        float4 *Pf4 = reinterpret_cast<float4 *>(Pf), *Yf4 = reinterpret_cast<float4 *>(Yf);
+        switch (np) {
+        case 0: accept_span<0>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 1: accept_span<1>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 2: accept_span<2>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 3: accept_span<3>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 4: accept_span<4>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 5: accept_span<5>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 6: accept_span<6>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 7: accept_span<7>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        default: accept_span<8>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
         }
         if (bx == 0 && threadIdx.x < (n & 3)) {
             const long long e = 4 * n4 + threadIdx.x;
@@ -370,8 +464,9 @@ __global__ void __launch_bounds__(VT) k_lb_vector_batch(const PairLevel *__restr
 __global__ void __launch_bounds__(CT) k_lb_control_batch(const PairLevel *__restrict__ pl, int phase)
 {
     const PairLevel &P = pl[blockIdx.x];
-    lb_control_body(phase, P.st, P.lgpart, (P.nchunks + LB_RG - 1) / LB_RG, phase == LB_INIT ? P.scal : P.scal_t,
-                    0ULL, 0ULL, 0ULL);
+    const bool direct = P.nchunks <= LB_DIRECT;   // block partials, else group sums (vec_tail)
+    lb_control_body(phase, P.st, direct ? P.lpart : P.lgpart, direct ? P.nchunks : (P.nchunks + LB_RG - 1) / LB_RG,
+                    phase == LB_INIT ? P.scal : P.scal_t, 0ULL, 0ULL, 0ULL);
 }
 
 // condition of a batched loop: 1 while any pair still iterates (which = 0) or
@@ -499,10 +594,31 @@ __global__ void k_lb_pair_setup(LbfgsState *__restrict__ st, int count, const do
 
 }  // namespace
 
+// Blocks of the vector passes that fit on one SM at once (the fewer of the
+// accept and direction kernels, whose register counts set it; at most 4, the
+// group buffers' bound).  With every block resident the grid-stride loops run
+// in one wave instead of a full wave and a partial one.
+static int vec_blocks_per_sm()
+{
+    static std::atomic<int> cached{0};
+    int v = cached.load();
+    if (v > 0)
+        return v;
+    int a = 0, d = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_lb_accept, VT, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_lb_direction, VT, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 2;
+    }
+    v = std::max(1, std::min(4, std::min(a, d)));
+    cached.store(v);
+    return v;
+}
+
 int num_blocks_for(reg_ctx *c, long long n, int threads)
 {
     long long b = (n + threads - 1) / threads;
-    long long cap = 4LL * (c->num_sms > 0 ? c->num_sms : 148);
+    long long cap = (long long)vec_blocks_per_sm() * (c->num_sms > 0 ? c->num_sms : 148);
     if (b > cap)
         b = cap;
     if (b < 1)

@@ -92,12 +92,9 @@ __device__ __forceinline__ void control_reduce(const double *__restrict__ partia
         J = CT / nd;
     if (t < nd * J) {
         const int d = t % nd, j = t / nd;
-        double s = 0.0;   // the max entry is a max of absolute values: 0 is its identity
-        for (int b = j; b < nblocks; b += J) {
-            const double x = __ldcg(partials + (size_t)b * nd + d);
-            s = (d == imax) ? fmax(s, x) : s + x;
-        }
-        scratch[t] = s;
+        // blocks j, j + J, ...; the max entry is a max of absolute values: 0 is its identity
+        const int count = j < nblocks ? (nblocks - j + J - 1) / J : 0;
+        scratch[t] = ordered_reduce(partials, (long long)j * nd + d, count, (long long)J * nd, d == imax, 0.0);
     }
     __syncthreads();
     if (t < nd) {
