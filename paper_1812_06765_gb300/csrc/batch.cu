@@ -539,7 +539,7 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
             st[i].evals[l] = sh->evals;
             st[i].J[l] = sh->J;
             st[i].level_status[l] = sh->status == 1 ? REG_WARN_LINESEARCH : REG_OK;
-            if (sh->status == -5 || sh->status == -6)
+            if (sh->status == -5 || sh->status == -6 || sh->status == -7)
                 status = sh->status == -5 ? REG_ERR_NUMERIC : REG_ERR_TIMEOUT;
             else if (sh->status == 1 && status == REG_OK)
                 status = REG_WARN_LINESEARCH;

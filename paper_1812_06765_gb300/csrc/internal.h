@@ -134,6 +134,8 @@ cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const
                                        const float *g, float *p, double Hmin, cudaStream_t s);
 int eval_partials_needed(const Level &L);
 int num_blocks_for(reg_ctx *c, long long n, int threads);
+// raises the shared-memory limit of the streamed L-BFGS vector passes on a device (once)
+cudaError_t lbfgs_kernels_setup(int device);
 
 // objective pass variants (k_ngf_fused.cu, k_ngf_multipass.cu)
 bool fused_eligible(const Level &L);

@@ -136,62 +136,179 @@ __global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *_
     lb_init_dots_body(n, g, partials, tail, blockIdx.x, gridDim.x);
 }
 
-// Element loop of the direction pass for DC stored pairs: straight-line code,
-// so every load of an element (g and the 2 DC history vectors) is issued
-// before the first one is used.  (With the pair count a run-time bound, the
-// loads of pair j sat behind a branch and waited for pair j - 1's FMAs: up to
-// 2 m + 1 dependent memory round trips per element.)
-template <int DC>
-__device__ __forceinline__ float4 direction_elem(const float4 &gv, const float4 (&a)[DC > 0 ? DC : 1],
-                                                 const float4 (&b)[DC > 0 ? DC : 1], float cg,
-                                                 const float (&cp)[LB_MAXM], const float (&cy)[LB_MAXM])
+// ---------------------------------------------------------------------------
+// Bulk streaming of the direction and accept passes.  Each reads 1 + 2 m or
+// 4 + 2 m vectors of n floats and is bound by HBM.  Loads issued by threads
+// kept about half the HBM bandwidth busy at 16 warps per SM, whether the
+// bytes in flight came from more warps or from more loads per thread, so the
+// passes stream their inputs instead with bulk asynchronous copies
+// (cp.async.bulk, the TMA engine) into a ring of shared-memory stages.  Each
+// stage completes on its own mbarrier, and the threads compute from shared
+// memory.  A block owns the chunks bx, bx + gdx, ... of CHUNK4 float4 per
+// vector (thread t takes float4 t of each); thread 0 keeps every stage in
+// flight.
+// ---------------------------------------------------------------------------
+constexpr int CHUNK4 = VT;                       // float4 per vector and chunk: one per thread
+constexpr int CHUNK_BYTES = CHUNK4 * 16;         // 4 KB
+constexpr int VEC_SMEM = 200 * 1024;             // dynamic shared memory of a vector-pass block
+constexpr int MAX_STAGES = 4;
+constexpr unsigned WAIT_POLLS = 1u << 22;        // polls of a stage barrier before the pass gives up
+
+// stages that fit for NS vectors per chunk
+constexpr int stages_for(int ns)
 {
-    float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
-#pragma unroll
-    for (int j = 0; j < DC; j++) {
-        p.x = fmaf(cp[j], a[j].x, fmaf(cy[j], b[j].x, p.x));
-        p.y = fmaf(cp[j], a[j].y, fmaf(cy[j], b[j].y, p.y));
-        p.z = fmaf(cp[j], a[j].z, fmaf(cy[j], b[j].z, p.z));
-        p.w = fmaf(cp[j], a[j].w, fmaf(cy[j], b[j].w, p.w));
-    }
-    return p;
+    return VEC_SMEM / (ns * CHUNK_BYTES) < MAX_STAGES ? VEC_SMEM / (ns * CHUNK_BYTES) : MAX_STAGES;
 }
 
-// Element loop of the direction pass for DC stored pairs: straight-line code
-// over two elements at a time, so every load of both (g and the 2 DC history
-// vectors each) is in flight before the first store.  (With the pair count a
-// run-time bound, the loads of pair j sat behind a branch and waited for pair
-// j - 1's FMAs: up to 2 m + 1 dependent memory round trips per element.)
-template <int DC>
-__device__ __forceinline__ void direction_span(long long e0, long long n4, long long step, float cg,
-                                               const float4 *__restrict__ g4, const float4 *__restrict__ P4,
-                                               const float4 *__restrict__ Y4, const int (&off)[LB_MAXM],
-                                               const float (&cp)[LB_MAXM], const float (&cy)[LB_MAXM],
-                                               float4 *__restrict__ p4, float (&v)[2])
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
 {
-    constexpr int K = DC > 0 ? DC : 1;
-    for (long long e = e0; e < n4; e += 2 * step) {
-        const long long e1 = e + step < n4 ? e + step : e;   // the second element, or the first again
-        const float4 g0 = g4[e], g1 = g4[e1];
-        float4 a0[K], b0[K], a1[K], b1[K];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long *b)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared, completing on b
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(b))
+                 : "memory");
+}
+// true once the barrier's phase of this parity has completed; false after WAIT_POLLS polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
+{
+    for (unsigned i = 0; i < WAIT_POLLS; i++) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(smem_addr(b)), "r"(parity)
+                     : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// The stage ring of one vector pass: STAGES stages of NS vectors x CHUNK4 float4.
+template <int NS>
+struct ChunkRing {
+    static constexpr int STAGES = stages_for(NS);
+    static_assert(STAGES >= 2, "a chunk of every vector must fit twice");
+    float4 *buf;                      // dynamic shared memory, VEC_SMEM bytes
+    unsigned long long *full;         // [MAX_STAGES] barriers, static shared memory
+    long long n4, first;              // float4 per vector; this block's first chunk
+    int gdx, chunks;                  // chunk stride; chunks of this block
+
+    __device__ ChunkRing(float4 *b, unsigned long long *f, long long n4_, int bx, int gdx_)
+        : buf(b), full(f), n4(n4_), first(bx), gdx(gdx_)
+    {
+        const long long nch = (n4 + CHUNK4 - 1) / CHUNK4;
+        chunks = nch > bx ? (int)((nch - 1 - bx) / gdx + 1) : 0;
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < STAGES; i++)
+                mbar_init(&full[i], 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
+    __device__ long long elem0(int k) const { return (first + (long long)k * gdx) * CHUNK4; }
+    __device__ float4 *stage(int k) const { return buf + (size_t)(k % STAGES) * NS * CHUNK4; }
+    // thread 0: copy chunk k of the NS source vectors src(i) into its stage
+    template <typename Src>
+    __device__ void issue(int k, Src src) const
+    {
+        const long long e0 = elem0(k);
+        const long long left = n4 - e0;
+        const unsigned bytes = (unsigned)((left < CHUNK4 ? left : CHUNK4) * 16);
+        unsigned long long *b = &full[k % STAGES];
+        float4 *dst = stage(k);
+        mbar_expect_tx(b, bytes * NS);
+#pragma unroll
+        for (int i = 0; i < NS; i++)
+            bulk_g2s(dst + i * CHUNK4, src(i) + e0, bytes, b);
+    }
+    __device__ bool wait(int k) const { return mbar_wait(&full[k % STAGES], (unsigned)((k / STAGES) & 1)); }
+    // after a failed wait at chunk k: wait (bounded) for the copies still in flight, chunks k .. k + STAGES - 1
+    __device__ void drain(int k) const
+    {
+        for (int j = k; j < chunks && j < k + STAGES; j++)
+            (void)wait(j);
+    }
+    __device__ void release() const
+    {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = 0; i < STAGES; i++)
+                mbar_inval(&full[i]);
+        __syncthreads();
+    }
+};
+
+// Streams the chunks of a block through the ring: compute(k, stage) per chunk.
+// Returns false if a stage never completed (the block's sums are then
+// incomplete and the caller flags the pass).
+template <int NS, typename Src, typename Compute>
+__device__ __forceinline__ bool stream_chunks(ChunkRing<NS> &ring, Src src, Compute compute)
+{
+    constexpr int S = ChunkRing<NS>::STAGES;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < S && k < ring.chunks; k++)
+            ring.issue(k, src);
+    for (int k = 0; k < ring.chunks; k++) {
+        const bool ok = ring.wait(k);
+        if (ok)
+            compute(k, ring.stage(k));
+        // every thread is done with the stage (or one timed out: all leave together)
+        if (!__syncthreads_and(ok)) {
+            ring.drain(k);
+            ring.release();
+            return false;
+        }
+        if (threadIdx.x == 0 && k + S < ring.chunks)
+            ring.issue(k + S, src);
+    }
+    ring.release();
+    return true;
+}
+
+// direction for DC stored pairs from one stage: vectors g, P_0..P_{DC-1}, Y_0..Y_{DC-1}
+template <int DC>
+__device__ __forceinline__ bool direction_stream(long long n4, int bx, int gdx, float cg, const float4 *g4,
+                                                 const float4 *P4, const float4 *Y4, const int (&off)[LB_MAXM],
+                                                 const float (&cp)[LB_MAXM], const float (&cy)[LB_MAXM],
+                                                 float4 *__restrict__ p4, float (&v)[2], float4 *buf,
+                                                 unsigned long long *full)
+{
+    constexpr int NS = 1 + 2 * DC;
+    ChunkRing<NS> ring(buf, full, n4, bx, gdx);
+    auto src = [&](int i) -> const float4 * { return i == 0 ? g4 : (i <= DC ? P4 + off[i - 1] : Y4 + off[i - 1 - DC]); };
+    return stream_chunks<NS>(ring, src, [&](int k, const float4 *sb) {
+        const long long e = ring.elem0(k) + threadIdx.x;
+        if (e >= n4)
+            return;
+        const float4 gv = sb[threadIdx.x];
+        float4 p = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
 #pragma unroll
         for (int j = 0; j < DC; j++) {
-            a0[j] = P4[off[j] + e];
-            b0[j] = Y4[off[j] + e];
-            a1[j] = P4[off[j] + e1];
-            b1[j] = Y4[off[j] + e1];
+            const float4 a = sb[(1 + j) * CHUNK4 + threadIdx.x], b = sb[(1 + DC + j) * CHUNK4 + threadIdx.x];
+            p.x = fmaf(cp[j], a.x, fmaf(cy[j], b.x, p.x));
+            p.y = fmaf(cp[j], a.y, fmaf(cy[j], b.y, p.y));
+            p.z = fmaf(cp[j], a.z, fmaf(cy[j], b.z, p.z));
+            p.w = fmaf(cp[j], a.w, fmaf(cy[j], b.w, p.w));
         }
-        const float4 p0 = direction_elem<DC>(g0, a0, b0, cg, cp, cy);
-        const float4 p1 = direction_elem<DC>(g1, a1, b1, cg, cp, cy);
-        p4[e] = p0;
-        v[0] += dot4(g0, p0);
-        v[1] += dot4(p0, p0);
-        if (e1 != e) {
-            p4[e1] = p1;
-            v[0] += dot4(g1, p1);
-            v[1] += dot4(p1, p1);
-        }
-    }
+        p4[e] = p;
+        v[0] += dot4(gv, p);
+        v[1] += dot4(p, p);
+    });
 }
 
 // p = cg g + sum_j cp_j P_j + cy_j Y_j, written to pdir; partial sums of g'p and p'p.
@@ -230,20 +347,25 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
             cp[j] = s_cp[j];
             cy[j] = s_cy[j];
         }
-        const long long n4 = n >> 2, e0 = bx * (long long)VT + threadIdx.x, step = (long long)gdx * VT;
+        const long long n4 = n >> 2;
         const float4 *g4 = reinterpret_cast<const float4 *>(g);
         float4 *p4 = reinterpret_cast<float4 *>(pdir);
+        extern __shared__ float4 vec_buf[];
+        __shared__ unsigned long long s_full[MAX_STAGES];
+        bool ok;
         switch (dc) {
-        case 0: direction_span<0>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        case 1: direction_span<1>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        case 2: direction_span<2>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        case 3: direction_span<3>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        case 4: direction_span<4>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        case 5: direction_span<5>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        case 6: direction_span<6>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        case 7: direction_span<7>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
-        default: direction_span<8>(e0, n4, step, cg, g4, P4, Y4, off, cp, cy, p4, v); break;
+        case 0: ok = direction_stream<0>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 1: ok = direction_stream<1>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 2: ok = direction_stream<2>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 3: ok = direction_stream<3>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 4: ok = direction_stream<4>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 5: ok = direction_stream<5>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 6: ok = direction_stream<6>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 7: ok = direction_stream<7>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        default: ok = direction_stream<8>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
         }
+        if (!ok && threadIdx.x == 0)
+            atomicOr(const_cast<int *>(&st->wait_err), 1);
         if (bx == 0 && threadIdx.x < (n & 3)) {
             const long long e = 4 * n4 + threadIdx.x;
             float gv = g[e], p = cg * gv;
@@ -279,26 +401,28 @@ __device__ __forceinline__ void accept_elem(float gn, float go, float pf, float 
     u = fmaf(t, pf, u);
 }
 
-// Element loop of the accept pass for NP stored pairs before the free slot:
-// all loads of an element (g_new, g, p, u and the 2 NP history vectors) come
-// before its stores, in straight-line code, so they are in flight together.
-// The stored slots are never the free slot this pass writes.
+// accept for NP stored pairs before the free slot from one stage: vectors
+// g_new, g, p, u, P_0..P_{NP-1}, Y_0..Y_{NP-1}; the stored slots are never the
+// free slot this pass writes
 template <int NP>
-__device__ __forceinline__ void accept_span(long long e0, long long n4, long long step, float t,
-                                            const float4 *__restrict__ gt4, float4 *__restrict__ g4,
-                                            const float4 *__restrict__ pd4, float4 *__restrict__ u4,
-                                            const float4 *P4, const float4 *Y4, const int (&off)[LB_MAXM],
-                                            float4 *Pf4, float4 *Yf4, float (&v)[ND_ACC], float (&fr)[4])
+__device__ __forceinline__ bool accept_stream(long long n4, int bx, int gdx, float t, const float4 *gt4, float4 *g4,
+                                              const float4 *pd4, float4 *u4, const float4 *P4, const float4 *Y4,
+                                              const int (&off)[LB_MAXM], float4 *Pf4, float4 *Yf4,
+                                              float (&v)[ND_ACC], float (&fr)[4], float4 *buf,
+                                              unsigned long long *full)
 {
-    for (long long e = e0; e < n4; e += step) {
-        const float4 gn = gt4[e], go = g4[e], pf = pd4[e];
-        float4 uu = u4[e];
-        float4 pj[NP > 0 ? NP : 1], yj[NP > 0 ? NP : 1];
-#pragma unroll
-        for (int j = 0; j < NP; j++) {
-            pj[j] = P4[off[j] + e];
-            yj[j] = Y4[off[j] + e];
-        }
+    constexpr int NS = 4 + 2 * NP;
+    ChunkRing<NS> ring(buf, full, n4, bx, gdx);
+    auto src = [&](int i) -> const float4 * {
+        return i == 0 ? gt4 : i == 1 ? g4 : i == 2 ? pd4 : i == 3 ? u4 : (i < 4 + NP ? P4 + off[i - 4] : Y4 + off[i - 4 - NP]);
+    };
+    return stream_chunks<NS>(ring, src, [&](int k, const float4 *sb) {
+        const long long e = ring.elem0(k) + threadIdx.x;
+        if (e >= n4)
+            return;
+        const int q = threadIdx.x;
+        const float4 gn = sb[q], go = sb[CHUNK4 + q], pf = sb[2 * CHUNK4 + q];
+        float4 uu = sb[3 * CHUNK4 + q];
         float4 yn;
         accept_elem(gn.x, go.x, pf.x, uu.x, t, yn.x);
         accept_elem(gn.y, go.y, pf.y, uu.y, t, yn.y);
@@ -308,10 +432,11 @@ __device__ __forceinline__ void accept_span(long long e0, long long n4, long lon
         v[1] = fmaxf(v[1], max4(gn));
 #pragma unroll
         for (int j = 0; j < NP; j++) {
-            v[2 + 4 * j] += dot4(pj[j], gn);
-            v[3 + 4 * j] += dot4(yj[j], gn);
-            v[4 + 4 * j] += dot4(pj[j], yn);
-            v[5 + 4 * j] += dot4(yj[j], yn);
+            const float4 pj = sb[(4 + j) * CHUNK4 + q], yj = sb[(4 + NP + j) * CHUNK4 + q];
+            v[2 + 4 * j] += dot4(pj, gn);
+            v[3 + 4 * j] += dot4(yj, gn);
+            v[4 + 4 * j] += dot4(pj, yn);
+            v[5 + 4 * j] += dot4(yj, yn);
         }
         fr[0] += dot4(pf, gn);
         fr[1] += dot4(yn, gn);
@@ -321,7 +446,7 @@ __device__ __forceinline__ void accept_span(long long e0, long long n4, long lon
         g4[e] = gn;
         Pf4[e] = pf;
         Yf4[e] = yn;
-    }
+    });
 }
 
 __device__ __forceinline__ void lb_accept_body(long long n, long long stride, const LbfgsState *st,
@@ -359,21 +484,28 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
         float *Pf = P + (size_t)s_free * stride;
         float *Yf = Y + (size_t)s_free * stride;
         float fr[4] = {0.f, 0.f, 0.f, 0.f};   // dots of the free slot (p, y_new) with g_new, y_new
-        const long long n4 = n >> 2, e0 = bx * (long long)VT + threadIdx.x, step = (long long)gdx * VT;
+        const long long n4 = n >> 2;
         const float4 *gt4 = reinterpret_cast<const float4 *>(gt), *pd4 = reinterpret_cast<const float4 *>(pdir);
         float4 *g4 = reinterpret_cast<float4 *>(g), *u4 = reinterpret_cast<float4 *>(u);
         float4 *Pf4 = reinterpret_cast<float4 *>(Pf), *Yf4 = reinterpret_cast<float4 *>(Yf);
+        extern __shared__ float4 vec_buf[];
+        __shared__ unsigned long long s_full[MAX_STAGES];
+        bool ok;
+#define ACCEPT_CASE(K) ok = accept_stream<K>(n4, bx, gdx, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr, vec_buf, s_full)
         switch (np) {
-        case 0: accept_span<0>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        case 1: accept_span<1>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        case 2: accept_span<2>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        case 3: accept_span<3>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        case 4: accept_span<4>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        case 5: accept_span<5>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        case 6: accept_span<6>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        case 7: accept_span<7>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
-        default: accept_span<8>(e0, n4, step, t, gt4, g4, pd4, u4, P4, Y4, off, Pf4, Yf4, v, fr); break;
+        case 0: ACCEPT_CASE(0); break;
+        case 1: ACCEPT_CASE(1); break;
+        case 2: ACCEPT_CASE(2); break;
+        case 3: ACCEPT_CASE(3); break;
+        case 4: ACCEPT_CASE(4); break;
+        case 5: ACCEPT_CASE(5); break;
+        case 6: ACCEPT_CASE(6); break;
+        case 7: ACCEPT_CASE(7); break;
+        default: ACCEPT_CASE(8); break;
         }
+#undef ACCEPT_CASE
+        if (!ok && threadIdx.x == 0)
+            atomicOr(const_cast<int *>(&st->wait_err), 1);
         if (bx == 0 && threadIdx.x < (n & 3)) {
             const long long e = 4 * n4 + threadIdx.x;
             float gn = gt[e], go = g[e], pf = pdir[e], uu = u[e], yn;
@@ -598,6 +730,26 @@ __global__ void k_lb_pair_setup(LbfgsState *__restrict__ st, int count, const do
 // accept and direction kernels, whose register counts set it; at most 4, the
 // group buffers' bound).  With every block resident the grid-stride loops run
 // in one wave instead of a full wave and a partial one.
+// The streamed vector passes take VEC_SMEM bytes of dynamic shared memory,
+// above the 48 KB default: the limit is raised once per device (before the
+// first launch, which may be inside a stream capture).
+cudaError_t lbfgs_kernels_setup(int device)
+{
+    static std::atomic<bool> done[64];
+    const int dev = device >= 0 && device < 64 ? device : 0;
+    if (done[dev].load())
+        return cudaSuccess;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_lb_direction, at, VEC_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lb_accept, at, VEC_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lb_vector_batch, at, VEC_SMEM);
+    if (e == cudaSuccess)
+        done[dev].store(true);
+    return e;
+}
+
 static int vec_blocks_per_sm()
 {
     static std::atomic<int> cached{0};
@@ -605,8 +757,8 @@ static int vec_blocks_per_sm()
     if (v > 0)
         return v;
     int a = 0, d = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_lb_accept, VT, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_lb_direction, VT, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_lb_accept, VT, VEC_SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_lb_direction, VT, VEC_SMEM) != cudaSuccess) {
         (void)cudaGetLastError();
         return 2;
     }
@@ -685,7 +837,7 @@ cudaError_t lbfgs_launch_direction(reg_ctx *c, int level, cudaStream_t s)
 {
     long long n = 3 * c->L[level].nn, sd = ring_stride(n);
     int nb = num_blocks_for(c, (n + 3) / 4, VT);
-    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0,
+    k_lb_direction<<<nb, VT, VEC_SMEM, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 0,
                                      tail_of(c, LB_DIR, nullptr, true, false, true));
     c->launches += 1;
     return cudaGetLastError();
@@ -698,7 +850,7 @@ cudaError_t lbfgs_launch_redo(reg_ctx *c, int level, cudaStream_t s)
 {
     long long n = 3 * c->L[level].nn, sd = ring_stride(n);
     int nb = num_blocks_for(c, (n + 3) / 4, VT);
-    k_lb_direction<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1,
+    k_lb_direction<<<nb, VT, VEC_SMEM, s>>>(n, sd, c->lb.st, c->lb.g, c->lb.P, c->lb.Y, c->lb.pdir, c->lb.partials, 1,
                                      tail_of(c, LB_DIR_REDO, nullptr, true, false));
     c->launches += 1;
     return cudaGetLastError();
@@ -721,7 +873,7 @@ cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s)
 {
     long long n = 3 * c->L[level].nn, sd = ring_stride(n);
     int nb = num_blocks_for(c, (n + 3) / 4, VT);
-    k_lb_accept<<<nb, VT, 0, s>>>(n, sd, c->lb.st, c->lb.u, c->lb.g, c->lb.gt, c->lb.pdir, c->lb.P, c->lb.Y,
+    k_lb_accept<<<nb, VT, VEC_SMEM, s>>>(n, sd, c->lb.st, c->lb.u, c->lb.g, c->lb.gt, c->lb.pdir, c->lb.P, c->lb.Y,
                                   c->lb.partials, tail_of(c, LB_ACCEPTED, nullptr, false, true));
     c->launches += 1;
     return cudaGetLastError();
@@ -755,7 +907,7 @@ cudaError_t lbfgs_direction_standalone(reg_ctx *c, long long n, int count, const
 cudaError_t launch_lb_vector_batch(const PairLevel *pl, const int *chunk_off, int npairs, int total, int step,
                                    int grid, cudaStream_t s)
 {
-    k_lb_vector_batch<<<grid, VT, 0, s>>>(pl, chunk_off, npairs, total, step);
+    k_lb_vector_batch<<<grid, VT, VEC_SMEM, s>>>(pl, chunk_off, npairs, total, step);
     return cudaGetLastError();
 }
 

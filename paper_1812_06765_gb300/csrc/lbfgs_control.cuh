@@ -318,6 +318,16 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
     default:
         break;
     }
+    if (st->wait_err) {   // a vector pass lost chunks: its sums are incomplete, stop the level
+        st->wait_err = 0;
+        st->status = -7;
+        st->done = 1;
+        st->iter_continue = 0;
+        st->ls_continue = 0;
+        st->redo_dir = 0;
+        s_store = 0;
+        s_compact = 0;
+    }
     }   // thread 0
     __syncthreads();
     if (linear_tid() < 32 && (s_store || s_compact)) {

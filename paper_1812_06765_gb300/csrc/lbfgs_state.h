@@ -36,7 +36,8 @@ struct LbfgsState {
     int active;        // this pair runs the current iteration body (set by the direction
                        // control; in a batch, finished pairs skip every later phase)
     int done;
-    int status;        // 0, 1 (line search warning) or -5 (numeric)
+    int status;        // 0, 1 (line search warning), -5 (numeric), -6 (loop bound), -7 (copy wait expired)
+    int wait_err;      // set by a vector pass whose bulk-copy wait expired; the next control phase stops the level
     // pair memory: order[0..count-1] are slots oldest..newest, free_slot holds p
     int count, free_slot;
     int order[LB_MAXM];
@@ -66,7 +67,7 @@ struct LbfgsState {
 // reduces the block partials themselves.  The sums do not depend on the
 // completion order.
 #define LB_RG 16
-#define LB_DIRECT 128
+#define LB_DIRECT 256
 struct VecTail {
     double *gpart;                   // [groups][nd] group sums
     unsigned *cnt;                   // [groups + 1] arrival counters, zero between launches

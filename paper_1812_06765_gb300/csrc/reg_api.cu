@@ -328,6 +328,7 @@ int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream)
     c->cfg = *cfg;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = lbfgs_kernels_setup(c->device);
     if (e == cudaSuccess) {
         // NULL is the legacy default stream (ordered with every blocking stream)
         c->stream = (cudaStream_t)cuda_stream;
@@ -673,6 +674,8 @@ int reg_register(reg_handle c, float *u_out, int out_is_device, const float *u_i
         if (sh->status == -5) return set_err(c, REG_ERR_NUMERIC, "reg_register: non-finite J or gradient at level %d", l);
         if (sh->status == -6)
             return set_err(c, REG_ERR_TIMEOUT, "reg_register: level %d exceeded its loop bound", l);
+        if (sh->status == -7)
+            return set_err(c, REG_ERR_TIMEOUT, "reg_register: a bulk-copy wait of an L-BFGS pass expired at level %d", l);
         local.level_status[l] = sh->status == 1 ? REG_WARN_LINESEARCH : REG_OK;
         if (sh->status == 1) status = REG_WARN_LINESEARCH;
         if (l == 0) {
