@@ -42,7 +42,6 @@ struct EvalScratch {
     double *partials = nullptr;   // block partial sums
     int max_partials = 0;
     double *scal = nullptr;       // [J, D, S] on the device
-    unsigned *fin_cnt = nullptr;  // arrival counter of the gather that ends a fused evaluation
     size_t part_floats = 0;
 };
 
@@ -153,7 +152,10 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
                              float *grad, double *partials, int *n_partials, cudaStream_t s);
 cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
                                  float *grad, double *partials, int *n_partials, cudaStream_t s);
+
 cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alpha_hy, float *grad, cudaStream_t s);
+// gather grids from this many blocks up run the final reduction beside the gather (side stream)
+constexpr long long GATHER_SPLIT_BLOCKS = 4096;
 
 cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out);
 int eval_kernel_count(const reg_ctx *c, int level);

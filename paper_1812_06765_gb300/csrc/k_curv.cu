@@ -183,25 +183,38 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
         return e;
     double hy = L.H[0] * L.H[1] * L.H[2];
     int nS = (int)(gw.x * gw.y * gw.z);
-    // grad = (tile partials of P^T r) + alpha hbar_y L^T w; then J, D, S (+ control).  On
-    // small grids the gather's completing block does the final reduction (one launch
-    // fewer); on large ones (>= 4096 blocks, whose arrivals on one counter would
-    // serialise) the reduction is a kernel of its own.
+    // grad = (tile partials of P^T r) + alpha hbar_y L^T w, and J, D, S (+ control).  The
+    // final reduction reads only the block partials of the kernels before, not the
+    // gradient.  On small grids block 0 of the gather runs it first (one launch); on
+    // large ones it is a one-block kernel on the side stream beside the gather, since
+    // the control code in the gather would cost the large grid occupancy.
     const long long gather_blocks = (long long)gn.x * gn.y * gn.z;
-    if (fused && gather_blocks < 4096)
+    if (fused && gather_blocks < GATHER_SPLIT_BLOCKS)
         return launch_gather_fin(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, nD, pS, nS, scal_out,
                                  ctl_phase, s);
     if (fused) {
-        cudaError_t ge = launch_gather_grad(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, s);
-        if (ge != cudaSuccess)
-            return ge;
-        double hbar = L.h[0] * L.h[1] * L.h[2];
-        c->launches += 1;
-        if (ctl_phase >= 0)
-            return launch_finalize_ctl(c, c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out,
-                                       ctl_phase, s);
-        k_finalize<<<1, 512, 0, s>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out);
-        return cudaGetLastError();
+        const double hbar = L.h[0] * L.h[1] * L.h[2];
+        e = cudaEventRecord(c->ev_fork, s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        if (e == cudaSuccess) {
+            if (ctl_phase >= 0) {
+                e = launch_finalize_ctl(c, c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy, scal_out,
+                                        ctl_phase, c->side);
+            } else {
+                k_finalize<<<1, 512, 0, c->side>>>(c->es.partials, nD, pS, nS, 0.5 * hbar, c->cfg.alpha, 0.5 * hy,
+                                                    scal_out);
+                e = cudaGetLastError();
+            }
+            c->launches += 1;
+        }
+        if (e == cudaSuccess)
+            e = launch_gather_grad(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(c->ev_join, c->side);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, c->ev_join, 0);
+        return e;
     }
     // multi-pass: grad += alpha hbar_y L^T w, then the final reduction
     k_curv_grad<<<gn, blk, 0, s>>>(g, c->es.w, (float)(c->cfg.alpha * hy), grad);

@@ -823,8 +823,6 @@ cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s)
     // arrival counters start the level at zero (every launch leaves them so)
     cudaError_t e = cudaMemsetAsync(c->lb.cnt, 0, sizeof(unsigned) * c->lb.cnt_len, s);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(c->es.fin_cnt, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess)
         e = launch_eval(c, level, c->lb.u, nullptr, nullptr, c->lb.g, c->es.scal, -1, s);
     if (e != cudaSuccess)
         return e;

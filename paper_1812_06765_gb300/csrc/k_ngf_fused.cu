@@ -559,16 +559,16 @@ __global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *_
     gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// The end of an evaluation after the gather: the block that completes the
-// launch reduces the D and S block partials into scal = [J, D, S] (the fixed
-// order of finalize_body) and, for phase >= 0, takes that L-BFGS control phase
-// (the Armijo decision of a trial point) in the same block.
+// The end of an evaluation in the gather launch.  The final reduction reads
+// only the D and S block partials of the kernels before, not the gradient, so
+// block 0 reduces them into scal = [J, D, S] (the fixed order of
+// finalize_body) and, for phase >= 0, takes that L-BFGS control phase (the
+// Armijo decision of a trial point) first, while the other blocks gather.
 struct FinArgs {
     const double *pD, *pS;  // block partials of D (fused tiles) and S (curvature blocks)
     int nD, nS;
     double hbar_half, alpha, hy_half;
     double *scal;
-    unsigned *cnt;          // arrival counter, zero between launches
     int phase;              // -1: no control phase
     LbfgsState *st;
     unsigned long long h_ls;
@@ -578,22 +578,14 @@ __global__ void __launch_bounds__(256) k_gather_fin(LevelGeom g, const float *__
                                                     int nty, int ntz, const float *__restrict__ w, float alpha_hy,
                                                     float *__restrict__ grad, FinArgs f)
 {
-    gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
-    __shared__ int s_last;
-    __syncthreads();
-    if (linear_tid() == 0)
-        s_last = atomicAdd(f.cnt, 1u) == gridDim.x * gridDim.y * gridDim.z - 1u;
-    __syncthreads();
-    if (!s_last)
-        return;
-    __threadfence();
-    finalize_body(f.pD, f.nD, f.pS, f.nS, f.hbar_half, f.alpha, f.hy_half, f.scal);
-    if (linear_tid() == 0)
-        *f.cnt = 0;
-    if (f.phase >= 0) {
-        __syncthreads();
-        lb_control_body(f.phase, f.st, nullptr, 0, f.scal, f.h_ls, 0ULL, 0ULL);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+        finalize_body(f.pD, f.nD, f.pS, f.nS, f.hbar_half, f.alpha, f.hy_half, f.scal);
+        if (f.phase >= 0) {
+            __syncthreads();
+            lb_control_body(f.phase, f.st, nullptr, 0, f.scal, f.h_ls, 0ULL, 0ULL);
+        }
     }
+    gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace
@@ -769,7 +761,6 @@ cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha
     f.alpha = c->cfg.alpha;
     f.hy_half = 0.5 * L.H[0] * L.H[1] * L.H[2];
     f.scal = scal;
-    f.cnt = c->es.fin_cnt;
     f.phase = phase;
     f.st = c->lb.st;
     f.h_ls = phase >= 0 ? lbfgs_graph_handle_ls() : 0ULL;

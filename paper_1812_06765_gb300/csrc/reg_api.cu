@@ -49,7 +49,6 @@ void free_buffers(reg_ctx *c)
     cudaFree(e.part);
     cudaFree(e.partials);
     cudaFree(e.scal);
-    cudaFree(e.fin_cnt);
     c->es = EvalScratch();
     LbfgsBuffers &b = c->lb;
     cudaFree(b.u);
@@ -262,8 +261,6 @@ int allocate_buffers(reg_ctx *c)
     CK(cudaMalloc(&es.w, sizeof(float) * nmax));
     CK(cudaMalloc(&es.partials, sizeof(double) * maxpart));
     CK(cudaMalloc(&es.scal, sizeof(double) * 4));
-    CK(cudaMalloc(&es.fin_cnt, sizeof(unsigned)));
-    CK(cudaMemset(es.fin_cnt, 0, sizeof(unsigned)));
     es.max_partials = maxpart;
     LbfgsBuffers &b = c->lb;
     b.n = nmax;
