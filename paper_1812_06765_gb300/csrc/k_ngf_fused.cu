@@ -498,54 +498,53 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused_batch(const PairLevel 
 
 // grad J at node k = sum of the tile partials that contain k (P^T r) plus
 // alpha hbar_y L^T w (curvature), one thread per node, 3 components.
+// Along each dimension the node's owner tile is t = min(k / step, nt - 1) at
+// local index j = k - step t; when j = 0 and t > 0 the lower tile also holds
+// it, at j = step.  The up to 8 partials are added owner first, lower x before
+// lower y before lower z, each one reached from the owner's by fixed offsets.
 __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float *__restrict__ part, int tz, int ntx,
                                                  int nty, int ntz, const float *__restrict__ w, float alpha_hy,
                                                  float *__restrict__ grad, int bx, int by, int bz)
 {
-    int kx = bx * blockDim.x + threadIdx.x;
-    int ky = by * blockDim.y + threadIdx.y;
-    int kz = bz;
+    const int kx = bx * blockDim.x + threadIdx.x;
+    const int ky = by * blockDim.y + threadIdx.y;
+    const int kz = bz;
     if (kx >= g.n[0] || ky >= g.n[1])
         return;   // (only this function: a caller's barrier after it is still reached)
     const int hz = tz / 2;
-    const size_t plane_stride = (size_t)(hz + 1) * NE;
+    const long long plane_stride = (long long)(hz + 1) * NE;
+    const int tx = min(kx / (NX - 1), ntx - 1), ty = min(ky / (NY - 1), nty - 1), tzi = min(kz / hz, ntz - 1);
+    const int jx = kx - (NX - 1) * tx, jy = ky - (NY - 1) * ty, jz = kz - hz * tzi;
+    const bool lx = jx == 0 && tx > 0, ly = jy == 0 && ty > 0, lz = jz == 0 && tzi > 0;
+    const float *p0 = part + (long long)(tx + ntx * (ty + nty * tzi)) * plane_stride + (jz * NE + jy * NX + jx);
+    // offsets to the lower tile's copy of the node: one tile back, local index step instead of 0
+    const long long dX = -plane_stride + (NX - 1);
+    const long long dY = -plane_stride * ntx + (NY - 1) * NX;
+    const long long dZ = -plane_stride * ((long long)ntx * nty) + (long long)hz * NE;
     float s[3] = {0.f, 0.f, 0.f};
-    // candidate tiles per dimension: t = k / step and t - 1, local index k - step * t in [0, step]
-    for (int dz = 0; dz < 2; dz++) {
-        int tzi = kz / hz - dz;
-        int jz = kz - hz * tzi;
-        if (tzi < 0 || tzi >= ntz || jz > hz)
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const bool ux = q & 1, uy = (q >> 1) & 1, uz = q >> 2;
+        if ((ux && !lx) || (uy && !ly) || (uz && !lz))
             continue;
-        for (int dy = 0; dy < 2; dy++) {
-            int tyi = ky / (NY - 1) - dy;
-            int jy = ky - (NY - 1) * tyi;
-            if (tyi < 0 || tyi >= nty || jy > NY - 1)
-                continue;
-            for (int dx = 0; dx < 2; dx++) {
-                int txi = kx / (NX - 1) - dx;
-                int jx = kx - (NX - 1) * txi;
-                if (txi < 0 || txi >= ntx || jx > NX - 1)
-                    continue;
-                size_t tile = (size_t)txi + (size_t)ntx * (tyi + (size_t)nty * tzi);
-                const float *p = part + tile * plane_stride + (size_t)jz * NE + jy * NX + jx;
-                s[0] += __ldg(p);
-                s[1] += __ldg(p + NX * NY);
-                s[2] += __ldg(p + 2 * NX * NY);
-            }
-        }
+        const float *p = p0 + (ux ? dX : 0) + (uy ? dY : 0) + (uz ? dZ : 0);
+        s[0] += __ldg(p);
+        s[1] += __ldg(p + NX * NY);
+        s[2] += __ldg(p + 2 * NX * NY);
     }
-    size_t k = kx + (size_t)g.n[0] * (ky + (size_t)g.n[1] * kz);
-    size_t st[3] = {1, (size_t)g.n[0], (size_t)g.n[0] * g.n[1]};
-    int j[3] = {kx, ky, kz};
+    const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
+    const int k = kx + n0 * ky + n01 * kz;
+    const int st[3] = {1, n0, n01};
+    const int j[3] = {kx, ky, kz};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const float *wc = w + c * g.nn;
-        float w0 = __ldg(wc + k);
+        const float w0 = __ldg(wc + k);
         float l = 0.f;
 #pragma unroll
         for (int e = 0; e < 3; e++) {
-            float lo = j[e] > 0 ? __ldg(wc + k - st[e]) : 0.f;
-            float hi = j[e] < g.n[e] - 1 ? __ldg(wc + k + st[e]) : 0.f;
+            const float lo = j[e] > 0 ? __ldg(wc + k - st[e]) : 0.f;
+            const float hi = j[e] < g.n[e] - 1 ? __ldg(wc + k + st[e]) : 0.f;
             l = fmaf(lo + hi - 2.f * w0, g.iH2[e], l);
         }
         grad[c * g.nn + k] = fmaf(alpha_hy, l, s[c]);
