@@ -52,52 +52,59 @@ __device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, dou
 }
 
 // Called by every block of a vector pass after block_reduce_write (see VecTail).
+// The arrivals follow the pattern of a grid barrier: block barrier, one
+// thread's fence, atomic; the last block's thread fences again before the
+// block reads the others' partials.  preloaded: ctl_state() holds the state.
 __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restrict__ partials, int nd, int imax,
-                                         int bx, int nblocks)
+                                         int bx, int nblocks, bool preloaded = false)
 {
     __shared__ int s_last;
     if (nblocks <= LB_DIRECT) {
         if (t.phase < 0)
             return;   // the control kernel that follows reduces the block partials
-        __threadfence();   // this block's partials, before its arrival is counted
         __syncthreads();
         if (threadIdx.x == 0) {
+            fence_acq_rel_gpu();   // this block's partials, before its arrival is counted
             s_last = atomicAdd(&t.cnt[0], 1u) == (unsigned)(nblocks - 1);
-            if (s_last)
+            if (s_last) {
+                fence_acq_rel_gpu();   // every block's partials, before they are read
                 t.cnt[0] = 0;
+            }
         }
         __syncthreads();
         if (!s_last)
             return;
-        __threadfence();
-        lb_control_body(t.phase, t.st, partials, nblocks, t.scal, t.h_ls, t.h_iter, t.h_redo);
+        lb_control_body(t.phase, t.st, partials, nblocks, t.scal, t.h_ls, t.h_iter, t.h_redo, preloaded);
         return;
     }
-    __threadfence();   // this block's partials, before its arrival is counted
     __syncthreads();
     const int g = bx / LB_RG, g0 = g * LB_RG, gs = min(LB_RG, nblocks - g0);
     const int ng = (nblocks + LB_RG - 1) / LB_RG;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        fence_acq_rel_gpu();
         s_last = atomicAdd(&t.cnt[g], 1u) == (unsigned)(gs - 1);
+        if (s_last)
+            fence_acq_rel_gpu();
+    }
     __syncthreads();
     if (!s_last)
         return;
-    __threadfence();
     for (int d = threadIdx.x; d < nd; d += blockDim.x)   // the max entry: a max of absolute values, 0 its identity
         t.gpart[(size_t)g * nd + d] = ordered_reduce(partials, (long long)g0 * nd + d, gs, nd, d == imax, 0.0);
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         t.cnt[g] = 0;
+        fence_acq_rel_gpu();
         s_last = atomicAdd(&t.cnt[ng], 1u) == (unsigned)(ng - 1);
-        if (s_last)
+        if (s_last) {
+            fence_acq_rel_gpu();
             t.cnt[ng] = 0;
+        }
     }
     __syncthreads();
     if (!s_last || t.phase < 0)
         return;
-    __threadfence();
-    lb_control_body(t.phase, t.st, t.gpart, ng, t.scal, t.h_ls, t.h_iter, t.h_redo);
+    lb_control_body(t.phase, t.st, t.gpart, ng, t.scal, t.h_ls, t.h_iter, t.h_redo, preloaded);
 }
 
 // All vector passes read and write 16-byte vectors: u, g, gt and pdir are
@@ -320,14 +327,17 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
 {
     __shared__ int s_run, s_dc, s_slot[LB_MAXM];
     __shared__ float s_cg, s_cp[LB_MAXM], s_cy[LB_MAXM];
+    ctl_state_load(st);   // also the copy the control phase works on
+    __syncthreads();
     if (threadIdx.x == 0) {
-        s_run = redo ? st->redo_dir : (st->iter_continue && !st->done);
-        s_dc = st->dcount;
-        s_cg = (float)st->cg;
+        const LbfgsState &S = ctl_state();
+        s_run = redo ? S.redo_dir : (S.iter_continue && !S.done);
+        s_dc = S.dcount;
+        s_cg = (float)S.cg;
         for (int j = 0; j < LB_MAXM; j++) {
-            s_slot[j] = st->dslot[j];
-            s_cp[j] = (float)st->cp[j];
-            s_cy[j] = (float)st->cy[j];
+            s_slot[j] = S.dslot[j];
+            s_cp[j] = (float)S.cp[j];
+            s_cy[j] = (float)S.cy[j];
         }
     }
     __syncthreads();
@@ -379,7 +389,7 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
         }
     }
     block_reduce_write<2>(v, -1, partials + 2 * bx);
-    vec_tail(tail, partials, 2, -1, bx, gdx);
+    vec_tail(tail, partials, 2, -1, bx, gdx, true);
 }
 
 __global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stride, const LbfgsState *st,
@@ -458,13 +468,16 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
 {
     __shared__ int s_ok, s_lc, s_free, s_slot[LB_MAXS];
     __shared__ float s_t;
+    ctl_state_load(st);   // also the copy the control phase works on
+    __syncthreads();
     if (threadIdx.x == 0) {
-        s_ok = st->active && st->ls == LS_ACCEPTED;
-        s_lc = st->lcount;
-        s_free = st->free_slot;
-        s_t = (float)st->t;
+        const LbfgsState &S = ctl_state();
+        s_ok = S.active && S.ls == LS_ACCEPTED;
+        s_lc = S.lcount;
+        s_free = S.free_slot;
+        s_t = (float)S.t;
         for (int j = 0; j < LB_MAXS; j++)
-            s_slot[j] = st->lslot[j];
+            s_slot[j] = S.lslot[j];
     }
     __syncthreads();
     if (!s_ok && tail.phase < 0)   // nothing to compute and no control phase to reach: done
@@ -541,7 +554,7 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
             }
     }
     block_reduce_write<ND_ACC>(v, 1, partials + (size_t)ND_ACC * bx);
-    vec_tail(tail, partials, ND_ACC, 1, bx, gdx);
+    vec_tail(tail, partials, ND_ACC, 1, bx, gdx, true);
 }
 
 __global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride, const LbfgsState *st,

@@ -108,21 +108,48 @@ __device__ __forceinline__ void control_reduce(const double *__restrict__ partia
     __syncthreads();
 }
 
+// The control state in shared memory, one copy per block: the single decision
+// thread works on it there (one coalesced copy in and out instead of hundreds
+// of dependent global accesses).  A vector pass loads it when it starts, so the
+// block that ends up running the control does not wait for it.
+constexpr int STATE_WORDS = (int)(sizeof(LbfgsState) / sizeof(int));
+
+__device__ __forceinline__ LbfgsState &ctl_state()
+{
+    __shared__ LbfgsState S;
+    return S;
+}
+
+// every thread of the block; the caller synchronises before reading
+__device__ __forceinline__ void ctl_state_load(const LbfgsState *gst)
+{
+    int *dst = reinterpret_cast<int *>(&ctl_state());
+    const int *src = reinterpret_cast<const int *>(gst);
+    for (int i = linear_tid(); i < STATE_WORDS; i += nthreads())
+        dst[i] = src[i];
+}
+
+// Fence of one thread after a block barrier: with the barrier it orders the
+// block's earlier writes before the arrival that follows (release), or the
+// other blocks' writes before the block's reads (acquire).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// preloaded: ctl_state() already holds gst (ctl_state_load at the kernel's start)
 __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
                                                     const double *__restrict__ partials, int nblocks,
                                                     const double *__restrict__ scal, unsigned long long h_ls,
-                                                    unsigned long long h_iter, unsigned long long h_redo)
+                                                    unsigned long long h_iter, unsigned long long h_redo,
+                                                    bool preloaded = false)
 {
-    // the state lives in shared memory while the single decision thread works
-    // on it: one coalesced copy in and out instead of hundreds of dependent
-    // global accesses
-    __shared__ LbfgsState S;
     __shared__ double red[ND_ACC];
     __shared__ double scratch[CT];
     __shared__ int s_store, s_compact;
-    constexpr int NW = (int)(sizeof(LbfgsState) / sizeof(int));
-    for (int i = linear_tid(); i < NW; i += nthreads())
-        reinterpret_cast<int *>(&S)[i] = reinterpret_cast<const int *>(gst)[i];
+    constexpr int NW = STATE_WORDS;
+    LbfgsState &S = ctl_state();
+    if (!preloaded)
+        ctl_state_load(gst);
+    else if (linear_tid() == 0)   // set by another block of this pass after the preload
+        S.wait_err = *reinterpret_cast<volatile const int *>(&gst->wait_err);
     __syncthreads();
     LbfgsState *st = &S;
     const int nd = phase == LB_ACCEPTED ? ND_ACC : 2;
