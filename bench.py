@@ -69,6 +69,8 @@ def parse_args(argv=None):
                          "gather (Eq. 3), multi-pass atomic scatter, multi-pass 8-colour scatter")
     ap.add_argument("--pairs", type=int, default=None, help="pairs of the uneven batch (workload 4; default 64)")
     ap.add_argument("--gen-procs", type=int, default=None, help="processes that generate the batch's pairs")
+    ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
+                    help="image size of the full-resolution workload (5) instead of its 512^3")
     return ap.parse_args(argv)
 
 
@@ -211,11 +213,11 @@ def issue_peak_warp_inst_per_s():
     return 152 * 4 * mhz * 1e6
 
 
-def workload(config_id, rank):
+def workload(config_id, rank, dims=None):
     from synth import CONFIGS, make_pair, make_pair_parallel, batch_sizes
     c = CONFIGS[config_id]
     if c.get("slab_noise"):   # full-resolution volume: planes generated by a process pool
-        return c, make_pair_parallel(config_id, pair=rank)
+        return c, make_pair_parallel(config_id, pair=rank, dims=dims)
     dims = batch_sizes(rank + 1)[rank] if c["dims"] is None else None
     p = make_pair(config_id, pair=rank, dims=dims)
     return c, p
@@ -258,7 +260,7 @@ def run_ours(args):
     _, _, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    c, p = workload(args.config, rank)
+    c, p = workload(args.config, rank, args.dims)
     kw = dict(levels=c["levels"], tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"], c1=c["c1"])
     if args.eval_impl is not None:
         kw["eval_impl"] = args.eval_impl
