@@ -89,7 +89,12 @@ typedef struct reg_config {
     int fused_tz;         /* 0: autotune / model; -1: the throughput rule (fewest z steps in
                              total over 2, 4, 8, .. 128, the tiling reg_register_batch uses);
                              else this z segment length on every level (even, 2 .. 512) */
-    int reserved[3];
+    int test_expire_wait; /* test hook, 0 in normal use: 1 makes block 0 of the first L-BFGS
+                             direction pass of reg_register arm one bulk-copy stage without
+                             issuing its copies, so that its bounded wait expires (after about
+                             1 s); the level then stops and reg_register returns
+                             REG_ERR_TIMEOUT.  Nothing faults: no copy is left in flight. */
+    int reserved[2];
 } reg_config;
 
 /* Per-registration statistics (filled by reg_register). */

@@ -159,7 +159,7 @@ constexpr int CHUNK4 = VT;                       // float4 per vector and chunk:
 constexpr int CHUNK_BYTES = CHUNK4 * 16;         // 4 KB
 constexpr int VEC_SMEM = 200 * 1024;             // dynamic shared memory of a vector-pass block
 constexpr int MAX_STAGES = 4;
-constexpr unsigned WAIT_POLLS = 1u << 22;        // polls of a stage barrier before the pass gives up
+constexpr unsigned long long WAIT_NS = 1000000000ULL;   // a stage barrier not complete after 1 s: the pass gives up
 
 // stages that fit for NS vectors per chunk
 constexpr int stages_for(int ns)
@@ -189,20 +189,34 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  "l"(src), "r"(bytes), "r"(smem_addr(b))
                  : "memory");
 }
-// true once the barrier's phase of this parity has completed; false after WAIT_POLLS polls
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(smem_addr(b)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// true once the barrier's phase of this parity has completed; false once WAIT_NS have passed
 __device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
 {
-    for (unsigned i = 0; i < WAIT_POLLS; i++) {
-        unsigned done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done)
-                     : "r"(smem_addr(b)), "r"(parity)
-                     : "memory");
-        if (done)
+    if (mbar_try_wait(b, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(b, parity))
             return true;
+        if (global_ns() - t0 > WAIT_NS)
+            return false;
     }
-    return false;
 }
 
 // The stage ring of one vector pass: STAGES stages of NS vectors x CHUNK4 float4.
@@ -229,9 +243,10 @@ struct ChunkRing {
     }
     __device__ long long elem0(int k) const { return (first + (long long)k * gdx) * CHUNK4; }
     __device__ float4 *stage(int k) const { return buf + (size_t)(k % STAGES) * NS * CHUNK4; }
-    // thread 0: copy chunk k of the NS source vectors src(i) into its stage
+    // thread 0: copy chunk k of the NS source vectors src(i) into its stage;
+    // drop (test hook): arm the stage's barrier but issue no copy
     template <typename Src>
-    __device__ void issue(int k, Src src) const
+    __device__ void issue(int k, Src src, bool drop = false) const
     {
         const long long e0 = elem0(k);
         const long long left = n4 - e0;
@@ -239,6 +254,8 @@ struct ChunkRing {
         unsigned long long *b = &full[k % STAGES];
         float4 *dst = stage(k);
         mbar_expect_tx(b, bytes * NS);
+        if (drop)
+            return;
 #pragma unroll
         for (int i = 0; i < NS; i++)
             bulk_g2s(dst + i * CHUNK4, src(i) + e0, bytes, b);
@@ -262,14 +279,15 @@ struct ChunkRing {
 
 // Streams the chunks of a block through the ring: compute(k, stage) per chunk.
 // Returns false if a stage never completed (the block's sums are then
-// incomplete and the caller flags the pass).
+// incomplete and the caller flags the pass).  drop_first: test hook, the
+// first chunk's copies are not issued.
 template <int NS, typename Src, typename Compute>
-__device__ __forceinline__ bool stream_chunks(ChunkRing<NS> &ring, Src src, Compute compute)
+__device__ __forceinline__ bool stream_chunks(ChunkRing<NS> &ring, Src src, Compute compute, bool drop_first = false)
 {
     constexpr int S = ChunkRing<NS>::STAGES;
     if (threadIdx.x == 0)
         for (int k = 0; k < S && k < ring.chunks; k++)
-            ring.issue(k, src);
+            ring.issue(k, src, drop_first && k == 0);
     for (int k = 0; k < ring.chunks; k++) {
         const bool ok = ring.wait(k);
         if (ok)
@@ -293,7 +311,7 @@ __device__ __forceinline__ bool direction_stream(long long n4, int bx, int gdx, 
                                                  const float4 *P4, const float4 *Y4, const int (&off)[LB_MAXM],
                                                  const float (&cp)[LB_MAXM], const float (&cy)[LB_MAXM],
                                                  float4 *__restrict__ p4, float (&v)[2], float4 *buf,
-                                                 unsigned long long *full)
+                                                 unsigned long long *full, bool drop_first)
 {
     constexpr int NS = 1 + 2 * DC;
     ChunkRing<NS> ring(buf, full, n4, bx, gdx);
@@ -315,7 +333,7 @@ __device__ __forceinline__ bool direction_stream(long long n4, int bx, int gdx, 
         p4[e] = p;
         v[0] += dot4(gv, p);
         v[1] += dot4(p, p);
-    });
+    }, drop_first);
 }
 
 // p = cg g + sum_j cp_j P_j + cy_j Y_j, written to pdir; partial sums of g'p and p'p.
@@ -362,17 +380,18 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
         float4 *p4 = reinterpret_cast<float4 *>(pdir);
         extern __shared__ float4 vec_buf[];
         __shared__ unsigned long long s_full[MAX_STAGES];
+        const bool drop = bx == 0 && ctl_state().test_drop;   // test hook: one chunk goes missing
         bool ok;
         switch (dc) {
-        case 0: ok = direction_stream<0>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        case 1: ok = direction_stream<1>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        case 2: ok = direction_stream<2>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        case 3: ok = direction_stream<3>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        case 4: ok = direction_stream<4>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        case 5: ok = direction_stream<5>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        case 6: ok = direction_stream<6>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        case 7: ok = direction_stream<7>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
-        default: ok = direction_stream<8>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full); break;
+        case 0: ok = direction_stream<0>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        case 1: ok = direction_stream<1>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        case 2: ok = direction_stream<2>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        case 3: ok = direction_stream<3>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        case 4: ok = direction_stream<4>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        case 5: ok = direction_stream<5>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        case 6: ok = direction_stream<6>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        case 7: ok = direction_stream<7>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
+        default: ok = direction_stream<8>(n4, bx, gdx, cg, g4, P4, Y4, off, cp, cy, p4, v, vec_buf, s_full, drop); break;
         }
         if (!ok && threadIdx.x == 0)
             atomicOr(const_cast<int *>(&st->wait_err), 1);
@@ -804,6 +823,7 @@ void lbfgs_state_reset_host(LbfgsState *st, const reg_config &cfg, int max_iter,
     st->tol_j_rel = cfg.tol_j_rel;
     st->Hmin = Hmin;
     st->t = 1.0;
+    st->test_drop = cfg.test_expire_wait;
 }
 
 static unsigned long long g_h_ls = 0, g_h_iter = 0, g_h_redo = 0;  // conditional handles while capturing

@@ -347,6 +347,7 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
     }
     if (st->wait_err) {   // a vector pass lost chunks: its sums are incomplete, stop the level
         st->wait_err = 0;
+        st->test_drop = 0;
         st->status = -7;
         st->done = 1;
         st->iter_continue = 0;

@@ -38,6 +38,7 @@ struct LbfgsState {
     int done;
     int status;        // 0, 1 (line search warning), -5 (numeric), -6 (loop bound), -7 (copy wait expired)
     int wait_err;      // set by a vector pass whose bulk-copy wait expired; the next control phase stops the level
+    int test_drop;     // test hook (reg_config.test_expire_wait): the next direction pass loses one chunk
     // pair memory: order[0..count-1] are slots oldest..newest, free_slot holds p
     int count, free_slot;
     int order[LB_MAXM];

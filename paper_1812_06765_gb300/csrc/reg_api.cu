@@ -85,6 +85,7 @@ int validate_config(const reg_config *cfg, std::string &msg)
     else if (cfg->image_dtype != 0 && cfg->image_dtype != 1) msg = "image_dtype must be 0 (FP32) or 1 (BF16)";
     else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
     else if (cfg->autotune != 0 && cfg->autotune != 1) msg = "autotune must be 0 or 1";
+    else if (cfg->test_expire_wait != 0 && cfg->test_expire_wait != 1) msg = "test_expire_wait must be 0 or 1";
     else if (cfg->fused_tz != 0 && cfg->fused_tz != -1 && !fused_tz_valid(cfg->fused_tz))
         msg = "fused_tz must be 0, -1 or an even length in 2 .. 512";
     else return REG_OK;

@@ -37,6 +37,7 @@ def test_config_default_and_version(libreg):
     assert cfg.lbfgs_mem == 5 and cfg.max_backtracks == 20 and cfg.levels == 1
     assert list(cfg.max_iter) == [50] * 8 and cfg.start_level == -1
     assert cfg.autotune == 1 and cfg.fused_tz == 0 and cfg.use_graph == 1 and cfg.image_dtype == 0
+    assert cfg.test_expire_wait == 0
     assert libreg.reg_version() >= 10000
     assert ctypes.sizeof(libreg.RegConfig) == 8 * 6 + 4 * 6 + 4 * 8 + 4 * 24 + 4 * 8
 
@@ -44,7 +45,7 @@ def test_config_default_and_version(libreg):
 def test_create_rejects_bad_config_before_touching_the_gpu(libreg):
     for field, value in (("levels", 0), ("levels", 9), ("lbfgs_mem", 0), ("tau", 0.0), ("c1", 1.5),
                          ("max_backtracks", 0), ("eval_impl", 7), ("autotune", 2), ("fused_tz", 7),
-                         ("fused_tz", 514), ("fused_tz", -2), ("eval_impl", -1)):
+                         ("fused_tz", 514), ("fused_tz", -2), ("eval_impl", -1), ("test_expire_wait", 2)):
         cfg = libreg.reg_config_default()
         setattr(cfg, field, value)
         with pytest.raises(libreg.RegError) as ei:

@@ -1,4 +1,6 @@
 """End-to-end registration parity: the device L-BFGS against the oracle's."""
+import time
+
 import numpy as np
 import pytest
 
@@ -56,6 +58,28 @@ def test_register_fixed_iterations_trajectory(reg_mod, orc):
     assert du.mean() / min(h) <= 0.02, (du.mean(), st, sto)
     for lv in range(3):
         assert abs(st["J"][lv] - sto["J"][lv]) <= 1e-4 * abs(sto["J"][lv]), (lv, st["J"], sto["J"])
+    r.close()
+
+
+@pytest.mark.parametrize("mem", [1, 8])
+def test_register_lbfgs_memory_extremes_follow_oracle(reg_mod, orc, mem):
+    """The L-BFGS direction and accept passes at the smallest and the largest
+    memory (1 + 2m and 4 + 2m vectors per chunk; at m = 8 two ring stages):
+    96^3 images, 49^3 nodes, so blocks stream more chunks than their ring holds.
+    A fixed number of accepted steps follows the oracle's trajectory."""
+    dims, h = (96, 96, 96), (1.0, 1.0, 1.0)
+    p = make_pair(0, dims=dims)
+    kw = dict(levels=1, tau=0.05, alpha=10.0, mem=mem, max_iter=12, fixed_iters=True)
+    r = reg_mod.Registration(reg_mod.make_config(**kw)).set_images(p["R"], p["T"], h)
+    u, st = r.register(out="numpy")
+    uo, sto = orc.register(dims, h, p["R"], p["T"], orc.make_config(**kw))
+    assert st["iters"] == sto["iters"] == [12]
+    du = np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0))
+    assert du.mean() / min(h) <= 0.02, (mem, du.mean(), st, sto)
+    # same evaluation count: the same line-search path, J to 1e-4; otherwise an
+    # Armijo test that FP32 and FP64 decide differently branched it, J to 1e-2
+    tol = 1e-4 if st["evals"] == sto["evals"] else 1e-2
+    assert abs(st["J"][0] - sto["J"][0]) <= tol * abs(sto["J"][0]), (mem, st, sto)
     r.close()
 
 
@@ -180,6 +204,30 @@ def test_register_reports_numeric_error(reg_mod):
     assert ei.value.code == _lib.REG_ERR_NUMERIC
     # the handle stays usable
     r.set_images(R, random_image(dims, 32), (1.0, 1.0, 1.0))
+    u, st = r.register(out="numpy")
+    assert st["status"] == 0 and np.isfinite(u).all()
+    r.close()
+
+
+def test_register_expired_copy_wait_reports_timeout(reg_mod):
+    """A bulk-copy wait that runs out stops the level with REG_ERR_TIMEOUT, and
+    the context stays usable.  The test hook arms one stage of the first
+    direction pass without issuing its copies: nothing is in flight and nothing
+    faults; the wait gives up after its 1 s limit."""
+    from paper_1812_06765_gb300 import _lib
+    dims, h = (32, 32, 24), (1.0, 1.0, 1.0)
+    R, T = random_image(dims, 41), random_image(dims, 42)
+    cfg = reg_mod.make_config(levels=1, tau=0.05, alpha=1.0, max_iter=5)
+    cfg.test_expire_wait = 1
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    t0 = time.perf_counter()
+    with pytest.raises(reg_mod.RegError) as ei:
+        r.register(out="numpy")
+    assert ei.value.code == _lib.REG_ERR_TIMEOUT and "bulk-copy" in str(ei.value)
+    assert time.perf_counter() - t0 < 60
+    r.close()
+    cfg.test_expire_wait = 0
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
     u, st = r.register(out="numpy")
     assert st["status"] == 0 and np.isfinite(u).all()
     r.close()
