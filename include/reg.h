@@ -82,10 +82,10 @@ typedef struct reg_config {
     int use_graph;        /* 1: each pyramid level runs as one CUDA graph launch */
     int image_dtype;      /* 0: FP32 images; 1: the fused pass reads BF16 copies of R and T
                              (arithmetic stays FP32; levels without the fused pass use FP32) */
-    int autotune;         /* 1: reg_set_images times the z segment lengths of the fused pass
-                             that a wave model ranks best on each level and keeps the fastest
-                             (cached per geometry for the process; the first call of a
-                             geometry synchronises the stream); 0: the model's choice */
+    int autotune;         /* 1: reg_set_images times the z splits of the fused pass that a
+                             load model ranks best on each level and keeps the fastest (cached
+                             per geometry for the process; the first call of a geometry
+                             synchronises the stream); 0: the model's choice */
     int fused_tz;         /* 0: autotune / model; -1: the throughput rule (fewest z steps in
                              total over 2, 4, 8, .. 128, the tiling reg_register_batch uses);
                              else this z segment length on every level (even, 2 .. 512) */
@@ -94,7 +94,10 @@ typedef struct reg_config {
                              issuing its copies, so that its bounded wait expires (after about
                              1 s); the level then stops and reg_register returns
                              REG_ERR_TIMEOUT.  Nothing faults: no copy is left in flight. */
-    int reserved[2];
+    int fused_split[5];   /* all 0: not forced.  Else (l1, n1, l2, n2, lr): on every fused
+                             level whose depth is n1 l1 + n2 l2 + lr, z segments of n1 x l1,
+                             then n2 x l2, then lr planes (lengths even; before fused_tz) */
+    int reserved[1];
 } reg_config;
 
 /* Per-registration statistics (filled by reg_register). */

@@ -22,10 +22,12 @@ __all__ = ["make_config", "Registration", "RegObjective", "register", "register_
 
 def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1=1e-4, max_backtracks=20,
                 tol_grad_rel=1e-5, tol_j_rel=1e-7, tol_j_count=3, fixed_iters=False, start_level=-1,
-                node_dims=None, eval_impl=None, use_graph=None, image_dtype=None, autotune=None, fused_tz=None):
+                node_dims=None, eval_impl=None, use_graph=None, image_dtype=None, autotune=None, fused_tz=None,
+                fused_split=None):
     """A reg_config; max_iter is one value for every level or a per-level list (index 0 = finest).
     image_dtype: "f32" (default) or "bf16" (the fused pass reads BF16 copies of the images).
-    autotune: time the fused pass's z segment lengths per level (default on); fused_tz: force one."""
+    autotune: time the fused pass's z splits per level (default on); fused_tz: force equal segments
+    of that length; fused_split: force (l1, n1, l2, n2, lr) on levels of that depth."""
     cfg = _lib.reg_config_default()
     cfg.tau = float(tau)
     cfg.rho = float(tau if rho is None else rho)
@@ -56,6 +58,9 @@ def make_config(levels=1, tau=0.01, rho=None, alpha=10.0, mem=5, max_iter=50, c1
         cfg.autotune = int(bool(autotune))
     if fused_tz is not None:
         cfg.fused_tz = int(fused_tz)
+    if fused_split is not None:
+        for i, v in enumerate(fused_split):
+            cfg.fused_split[i] = int(v)
     return cfg
 
 

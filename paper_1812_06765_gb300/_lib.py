@@ -34,7 +34,7 @@ class RegConfig(ctypes.Structure):
         ("max_iter", ctypes.c_int * MAX_LEVELS), ("node_dims", (ctypes.c_int * 3) * MAX_LEVELS),
         ("eval_impl", ctypes.c_int), ("use_graph", ctypes.c_int), ("image_dtype", ctypes.c_int),
         ("autotune", ctypes.c_int), ("fused_tz", ctypes.c_int), ("test_expire_wait", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("fused_split", ctypes.c_int * 5), ("reserved", ctypes.c_int * 1),
     ]
 
 

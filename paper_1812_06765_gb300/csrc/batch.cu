@@ -26,8 +26,9 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     const Level &L = c->L[level];
     memset(&P, 0, sizeof P);
     P.geom = L.geom();
-    int tz, ntx, nty, ntz;
-    fused_tiling(L, c->num_sms, &tz, &ntx, &nty, &ntz);
+    FusedSplit split;
+    int ntx, nty;
+    fused_tiling(L, c->num_sms, &split, &ntx, &nty);
     const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
     FusedArgs a;
     memset(&a, 0, sizeof a);
@@ -39,22 +40,20 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     a.t_dev = nullptr;
     a.tau = (float)c->cfg.tau;
     a.rho = (float)c->cfg.rho;
-    a.tz = tz;
+    a.split = split;
     a.ntx = ntx;
     a.nty = nty;
-    a.ntz = ntz;
     a.part = c->es.part;
     a.partials = c->es.partials;
     P.fa_init = a;
     a.dir = c->lb.pdir;
     a.t_dev = &c->lb.st->t;
     P.fa_trial = a;
-    P.tz = tz;
     P.ntx = ntx;
     P.nty = nty;
     P.ncx = (L.n[0] + 31) / 32;
     P.ncy = (L.n[1] + 7) / 8;
-    P.nD = ntx * nty * ntz;
+    P.nD = ntx * nty * split.count();
     P.nS = P.ncx * P.ncy * curv_zchunks(L.n[2]);
     P.ngather = P.ncx * P.ncy * L.n[2];
     P.w = c->es.w;
@@ -242,20 +241,20 @@ cudaError_t build_batch_graph(const BatchLaunch &B, cudaStream_t cs, cudaGraphEx
 
 int cap(long long v, long long hi) { return (int)(v < 1 ? 1 : (v > hi ? hi : v)); }
 
-// Tiling rules of a batched level: 0 each pair's own tiling (its single-pair
-// autotuning), -1 the throughput rule (fewest z steps in total), T > 0 one z
-// segment length T for every pair (capped at the first candidate that spans
-// the pair's depth).
-int rule_tz(int rule, const Level &L, int own)
+// Tiling rules of a batched level: 0 each pair's own split (its single-pair
+// autotuning), -1 the throughput rule (fewest z steps in total), T > 0 equal
+// segments of T planes for every pair (halved while a segment would span the
+// pair's depth twice).
+FusedSplit rule_split(int rule, const Level &L, const FusedSplit &own)
 {
-    if (rule == 0)
-        return own > 0 ? own : fused_tz_throughput(L);
-    if (rule < 0)
-        return fused_tz_throughput(L);
+    if (rule == 0 && own.valid())
+        return own;
+    if (rule <= 0)
+        return fused_split_uniform(fused_tz_throughput(L), L.m[2]);
     int tz = rule;
     while (tz > 2 && tz / 2 >= L.m[2])
         tz /= 2;
-    return tz;
+    return fused_split_uniform(tz, L.m[2]);
 }
 
 std::mutex g_btune_mu;
@@ -264,7 +263,7 @@ std::map<std::vector<int>, int> g_btune;   // (level, SMs, image type, pair dims
 // Batch autotuner: times the batched fused pass (at the pairs' current u) under
 // each candidate rule - one warm launch, then the better of two event timings -
 // and returns the fastest rule.  Cached per batch geometry for the process.
-int batch_tiling_rule(reg_handle *hs, int n, int l, const std::vector<int> &own_tz, BatchDev &d,
+int batch_tiling_rule(reg_handle *hs, int n, int l, const std::vector<FusedSplit> &own, BatchDev &d,
                       std::vector<PairLevel> &hpl, std::vector<int> &hoff, bool bf16, cudaStream_t s,
                       cudaError_t *err)
 {
@@ -291,7 +290,7 @@ int batch_tiling_rule(reg_handle *hs, int n, int l, const std::vector<int> &own_
             break;
         int tiles = 0;
         for (int i = 0; i < n; i++) {
-            hs[i]->L[l].tz = rule_tz(rule, hs[i]->L[l], own_tz[i]);
+            hs[i]->L[l].split = rule_split(rule, hs[i]->L[l], own[i]);
             fill_pair_level(hs[i], l, hpl[i]);
             hoff[i] = tiles;
             tiles += hpl[i].nD;
@@ -438,19 +437,19 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
         // single-pair tiling of each handle is not necessarily the right one.
         // hs[0]'s cfg.fused_tz forces a rule; otherwise the batch autotuner picks
         // one (each handle's own tiling is restored after the level).
-        std::vector<int> own_tz(n);
+        std::vector<FusedSplit> own(n);
         for (int i = 0; i < n; i++)
-            own_tz[i] = hs[i]->L[l].tz;
-        struct RestoreTz {
+            own[i] = hs[i]->L[l].split;
+        struct RestoreSplit {
             reg_handle *hs;
             int n, l;
-            std::vector<int> &tz;
-            ~RestoreTz()
+            std::vector<FusedSplit> &split;
+            ~RestoreSplit()
             {
                 for (int i = 0; i < n; i++)
-                    hs[i]->L[l].tz = tz[i];
+                    hs[i]->L[l].split = split[i];
             }
-        } restore{hs, n, l, own_tz};
+        } restore{hs, n, l, own};
         if (l < start)   // u at the level start: prolonged from the coarser level
             for (int i = 0; i < n; i++) {
                 reg_ctx *ci = hs[i];
@@ -464,11 +463,11 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
             rule = -1;
         if (rule == 0) {   // timed at the pairs' u of the level start
             cudaError_t te = cudaSuccess;
-            rule = batch_tiling_rule(hs, n, l, own_tz, d, hpl, hoff, bf16, s, &te);
+            rule = batch_tiling_rule(hs, n, l, own, d, hpl, hoff, bf16, s, &te);
             CK(te);
         }
         for (int i = 0; i < n; i++)
-            hs[i]->L[l].tz = rule_tz(rule, hs[i]->L[l], own_tz[i]);
+            hs[i]->L[l].split = rule_split(rule, hs[i]->L[l], own[i]);
         for (int i = 0; i < n; i++)
             st[i].tiling[l] = rule;
         for (int i = 0; i < n; i++) {

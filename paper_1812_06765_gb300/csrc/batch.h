@@ -11,9 +11,9 @@ struct FusedArgs {
     const float *ub, *dir;
     const double *t_dev;
     float tau, rho;
-    int tz;                 // output planes per z segment (even)
-    int ntx, nty, ntz;      // tiles
-    float *part;            // [tile][TZ/2 + 1][NE]
+    FusedSplit split;       // z segments (the same for every tile column)
+    int ntx, nty;           // tile columns
+    float *part;            // per segment (z order): [tile column][len/2 + 1][NE]
     double *partials;       // D block partials
 };
 
@@ -37,7 +37,7 @@ struct PairLevel {
     double *lgpart;         // their group sums
     unsigned *lcnt;         // arrival counters of the groups
     int nchunks;            // blocks of the vector passes
-    int tz, ntx, nty;       // fused tiling (also inside fa_*)
+    int ntx, nty;           // fused tile columns (also inside fa_*)
     int ncx, ncy;           // curvature / gather blocks along x and y (32 x 8 nodes each)
 };
 
@@ -80,4 +80,4 @@ cudaError_t launch_lb_control_batch(const PairLevel *pl, int npairs, int phase, 
 // counts its runs in counters[which]
 cudaError_t launch_batch_condition(const PairLevel *pl, int npairs, int which, unsigned long long h, int *counters,
                                    cudaStream_t s);
-void fused_tiling(const Level &L, int num_sms, int *tz, int *ntx, int *nty, int *ntz);
+void fused_tiling(const Level &L, int num_sms, FusedSplit *split, int *ntx, int *nty);

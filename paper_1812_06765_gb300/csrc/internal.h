@@ -9,6 +9,52 @@
 #include "common.cuh"
 #include "lbfgs_state.h"
 
+// z segmentation of the fused pass, the same for every tile column: from
+// plane 0, n1 segments of l1 planes, then n2 of l2, then one of lr (lr = 0:
+// none).  Lengths are even and add up to the level's depth, so segments of
+// different lengths can balance the SMs' load where equal ones leave a
+// partial last wave.
+struct FusedSplit {
+    int l1 = 0, n1 = 0, l2 = 0, n2 = 0, lr = 0;
+    __host__ __device__ int count() const { return n1 + n2 + (lr > 0 ? 1 : 0); }
+    __host__ __device__ bool valid() const { return count() > 0; }
+    // segment s in z order: first plane and length
+    __host__ __device__ void seg(int s, int &z0, int &len) const
+    {
+        if (s < n1) {
+            z0 = s * l1;
+            len = l1;
+        } else if (s < n1 + n2) {
+            z0 = n1 * l1 + (s - n1) * l2;
+            len = l2;
+        } else {
+            z0 = n1 * l1 + n2 * l2;
+            len = lr;
+        }
+    }
+    // node planes of one tile (length / 2 + 1) summed over the segments before s
+    __host__ __device__ long long planes_before(int s) const
+    {
+        long long p = (long long)(s < n1 ? s : n1) * (l1 / 2 + 1);
+        if (s > n1)
+            p += (long long)(s - n1 < n2 ? s - n1 : n2) * (l2 / 2 + 1);
+        if (s > n1 + n2 && lr > 0)
+            p += lr / 2 + 1;
+        return p;
+    }
+    __host__ __device__ int longest() const
+    {
+        int m = n1 > 0 ? l1 : 0;
+        if (n2 > 0 && l2 > m)
+            m = l2;
+        return lr > m ? lr : m;
+    }
+    bool operator==(const FusedSplit &o) const
+    {
+        return l1 == o.l1 && n1 == o.n1 && l2 == o.l2 && n2 == o.n2 && lr == o.lr;
+    }
+};
+
 // Image, table and geometry buffers of one pyramid level.
 struct Level {
     int m[3];
@@ -27,7 +73,7 @@ struct Level {
     // prolongation from level + 1 onto this level's nodes
     int *qk0[3] = {nullptr, nullptr, nullptr};
     float *qw1[3] = {nullptr, nullptr, nullptr};
-    int tz = 0;   // z segment length of the fused pass (0: the default rule)
+    FusedSplit split;   // z segments of the fused pass (not valid: not chosen yet)
     LevelGeom geom() const;
 };
 
@@ -139,13 +185,16 @@ cudaError_t lbfgs_kernels_setup(int device);
 // objective pass variants (k_ngf_fused.cu, k_ngf_multipass.cu)
 bool fused_eligible(const Level &L);
 size_t fused_part_floats(const Level &L, int num_sms);
-int fused_tz(const Level &L, int num_sms);
 bool fused_tz_valid(int tz);
 int fused_tz_throughput(const Level &L);
+// tz-plane segments and the remainder
+FusedSplit fused_split_uniform(int tz, int mz);
+// L.split, or the load model's choice if none has been set
+FusedSplit fused_split(const Level &L, int num_sms);
 // z segment length and tile grid the fused pass uses on the level
-void fused_tiling(const Level &L, int num_sms, int *tz, int *ntx, int *nty, int *ntz);
-// times the z segment lengths the wave model ranks best on the level's images
-// at u_zero (3 node planes of zeros) and keeps the fastest in L.tz; cached per
+void fused_tiling(const Level &L, int num_sms, FusedSplit *split, int *ntx, int *nty);
+// times the z splits the load model ranks best on the level's images at
+// u_zero (3 node planes of zeros) and keeps the fastest in L.split; cached per
 // geometry
 cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStream_t s);
 cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,

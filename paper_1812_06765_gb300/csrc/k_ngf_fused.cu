@@ -37,6 +37,7 @@
 #include <array>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <type_traits>
 #include <vector>
 
@@ -171,15 +172,52 @@ __device__ __forceinline__ float ldimg_zero_ext(const IMG *T, int mx, int my, in
     return in ? ldimg(T + (x + mx * (y + my * z))) : 0.f;
 }
 
-// One output tile (tile_x, tile_y, tile_z) of the fused pass; sm is the CTA's
-// dynamic shared memory (SMEM_BYTES).
+// Launch order of the tiles: the segment groups of the split by length,
+// longest first (so that the short tiles fill the SMs the long ones leave
+// free), then segment, then tile column.  Tile id -> (segment s in z order,
+// column).
+__device__ __forceinline__ void tile_seg_col(const FusedSplit &sp, int ncols, int id, int &s, int &col)
+{
+    int len[3] = {sp.l1, sp.l2, sp.lr}, start[3] = {0, sp.n1, sp.n1 + sp.n2};
+    int cnt[3] = {sp.n1, sp.n2, sp.lr > 0 ? 1 : 0};
+    int ord[3] = {0, 1, 2};
+#pragma unroll
+    for (int i = 0; i < 2; i++)   // sort the three groups by length, descending (stable)
+#pragma unroll
+        for (int j = 0; j < 2 - i; j++)
+            if (len[ord[j + 1]] > len[ord[j]]) {
+                const int t = ord[j];
+                ord[j] = ord[j + 1];
+                ord[j + 1] = t;
+            }
+    s = 0;
+    col = 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int gidx = ord[k], block = cnt[gidx] * ncols;
+        if (id < block) {
+            s = start[gidx] + id / ncols;
+            col = id - (id / ncols) * ncols;
+            return;
+        }
+        id -= block;
+    }
+}
+
+// One output tile (launch-order id, see tile_seg_col) of the fused pass; sm is
+// the CTA's dynamic shared memory (SMEM_BYTES).
 template <bool HAS_DIR, typename IMG>
-__device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int tile_y, int tile_z, float *sm)
+__device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, float *sm)
 {
     const LevelGeom &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int sp = 2 * tx + CW * ty;                  // shared-plane index of the thread's first column
-    const int x0 = tile_x * OX, y0 = tile_y * OY, z0 = tile_z * a.tz;
+    const int ncols = a.ntx * a.nty;
+    int seg, col, z0, tz;                             // segment (z order), tile column, its planes
+    tile_seg_col(a.split, ncols, tile_id, seg, col);
+    a.split.seg(seg, z0, tz);
+    const int tile_x = col % a.ntx, tile_y = col / a.ntx;
+    const int x0 = tile_x * OX, y0 = tile_y * OY;
     const int xa = x0 - 2 + 2 * tx, y = y0 - 2 + ty;  // the thread's columns: xa (even) and xa + 1
     const int mx = g.m[0], my = g.m[1], mz = g.m[2];
     const int sxy = mx * my;
@@ -193,9 +231,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int t
     const float wy = (y & 1) ? 0.75f : 0.25f;
     const float hx = 0.5f * g.ih[0], hy = 0.5f * g.ih[1], hz = 0.5f * g.ih[2];
     const float half_hbar = 0.5f * g.hbar;
-    const int zend = z0 + a.tz;                       // first plane after the segment's output planes
-    const size_t tile_lin = (size_t)tile_x + (size_t)a.ntx * (tile_y + (size_t)a.nty * tile_z);
-    float *part_tile = a.part + tile_lin * (size_t)(a.tz / 2 + 1) * NE;
+    const int zend = z0 + tz;                         // first plane after the segment's output planes
+    const size_t tile_lin = (size_t)tile_id;          // this tile's D partial
+    // the segment's block of partials: ncols tiles of tz / 2 + 1 node planes
+    float *part_tile = a.part + ((size_t)a.split.planes_before(seg) * ncols + (size_t)col * (tz / 2 + 1)) * NE;
     const NodeCopy nc = node_copy_setup<HAS_DIR>(g, kx0, ky0, tid);
     const size_t node_plane = (size_t)g.n[0] * g.n[1];
     const IMG *Tim = static_cast<const IMG *>(a.T);
@@ -434,8 +473,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int t
                         const int e = tid + q * NT;
                         part_tile[(size_t)(lz >> 1) * NE + e] = acc_lo[q] + (0.75f * hold[q] + 0.25f * v);
                         acc_lo[q] = 0.25f * hold[q] + 0.75f * v;
-                        if (lz == a.tz - 1)
-                            part_tile[(size_t)(a.tz >> 1) * NE + e] = acc_lo[q];
+                        if (lz == tz - 1)
+                            part_tile[(size_t)(tz >> 1) * NE + e] = acc_lo[q];
                     }
                 }
         }
@@ -457,7 +496,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_x, int t
     }
 
     // z0 is even: zA + 1 is odd on even steps
-    const int nsteps = a.tz + 7;
+    const int nsteps = tz + 7;
     for (int s = 0; s < nsteps; s += 2) {
         step(s, std::true_type{});
         if (s + 1 < nsteps)
@@ -472,7 +511,7 @@ template <bool HAS_DIR, typename IMG = float>
 __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
 {
     extern __shared__ float sm[];
-    fused_tile<HAS_DIR, IMG>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+    fused_tile<HAS_DIR, IMG>(a, blockIdx.x, sm);
 }
 
 // Batched fused pass: a persistent grid walks the tiles of all pairs.  Mode 0
@@ -489,21 +528,47 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused_batch(const PairLevel 
         if (HAS_DIR && !(P.st->active && P.st->ls_continue))
             continue;   // uniform over the CTA
         const FusedArgs &a = HAS_DIR ? P.fa_trial : P.fa_init;
-        const int local = item - __ldg(tile_off + p);
-        const int tx = local % a.ntx, rest = local / a.ntx;
-        fused_tile<HAS_DIR, IMG>(a, tx, rest % a.nty, rest / a.nty, sm);
+        fused_tile<HAS_DIR, IMG>(a, item - __ldg(tile_off + p), sm);
         __syncthreads();   // the next tile reuses the shared rings
+    }
+}
+
+// Segment (z order) and local node plane of node plane kz: the segment whose
+// planes z0 / 2 .. (z0 + len) / 2 - 1 contain it, or the last segment for the
+// last node plane.
+__device__ __forceinline__ void node_seg(const FusedSplit &sp, int kz, int &s, int &jz)
+{
+    const int h1 = sp.l1 / 2, h2 = sp.l2 / 2;
+    const int e1 = sp.n1 * h1, e2 = e1 + sp.n2 * h2;
+    if (kz < e1) {
+        s = kz / h1;
+        jz = kz - s * h1;
+    } else if (kz < e2) {
+        const int i = (kz - e1) / h2;
+        s = sp.n1 + i;
+        jz = kz - e1 - i * h2;
+    } else if (sp.lr > 0) {
+        s = sp.n1 + sp.n2;
+        jz = kz - e2;
+    } else {
+        s = sp.count() - 1;
+        int z0, len;
+        sp.seg(s, z0, len);
+        jz = kz - z0 / 2;
     }
 }
 
 // grad J at node k = sum of the tile partials that contain k (P^T r) plus
 // alpha hbar_y L^T w (curvature), one thread per node, 3 components.
-// Along each dimension the node's owner tile is t = min(k / step, nt - 1) at
-// local index j = k - step t; when j = 0 and t > 0 the lower tile also holds
-// it, at j = step.  The up to 8 partials are added owner first, lower x before
-// lower y before lower z, each one reached from the owner's by fixed offsets.
-__device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float *__restrict__ part, int tz, int ntx,
-                                                 int nty, int ntz, const float *__restrict__ w, float alpha_hy,
+// Along x and y the node's owner tile column is t = min(k / 14, nt - 1) at
+// local index j = k - 14 t; when j = 0 and t > 0 the lower column also holds
+// it, at j = 14.  Along z its owner is the segment holding its node plane
+// (node_seg); at the segment's first plane the previous segment also holds it,
+// at its last plane.  The up to 8 partials are added owner first, lower x
+// before lower y before lower z.
+__device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float *__restrict__ part,
+                                                 const FusedSplit &sp, int ntx, int nty,
+                                                 const float *__restrict__ w, float alpha_hy,
                                                  float *__restrict__ grad, int bx, int by, int bz)
 {
     const int kx = bx * blockDim.x + threadIdx.x;
@@ -511,23 +576,32 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
     const int kz = bz;
     if (kx >= g.n[0] || ky >= g.n[1])
         return;   // (only this function: a caller's barrier after it is still reached)
-    const int hz = tz / 2;
-    const long long plane_stride = (long long)(hz + 1) * NE;
-    const int tx = min(kx / (NX - 1), ntx - 1), ty = min(ky / (NY - 1), nty - 1), tzi = min(kz / hz, ntz - 1);
-    const int jx = kx - (NX - 1) * tx, jy = ky - (NY - 1) * ty, jz = kz - hz * tzi;
-    const bool lx = jx == 0 && tx > 0, ly = jy == 0 && ty > 0, lz = jz == 0 && tzi > 0;
-    const float *p0 = part + (long long)(tx + ntx * (ty + nty * tzi)) * plane_stride + (jz * NE + jy * NX + jx);
-    // offsets to the lower tile's copy of the node: one tile back, local index step instead of 0
-    const long long dX = -plane_stride + (NX - 1);
-    const long long dY = -plane_stride * ntx + (NY - 1) * NX;
-    const long long dZ = -plane_stride * ((long long)ntx * nty) + (long long)hz * NE;
+    const int tx = min(kx / (NX - 1), ntx - 1), ty = min(ky / (NY - 1), nty - 1);
+    const int jx = kx - (NX - 1) * tx, jy = ky - (NY - 1) * ty;
+    int so, jz;
+    node_seg(sp, kz, so, jz);
+    const bool lx = jx == 0 && tx > 0, ly = jy == 0 && ty > 0, lz = jz == 0 && so > 0;
+    const long long ncols = (long long)ntx * nty, col = tx + (long long)ntx * ty;
+    int z0, len;
+    sp.seg(so, z0, len);
+    const long long stride_o = (long long)(len / 2 + 1) * NE;   // one tile column of the owner segment
+    const float *po = part + sp.planes_before(so) * ncols * NE + col * stride_o + (jz * NE + jy * NX + jx);
+    long long stride_l = stride_o;
+    const float *pl = po;
+    if (lz) {   // the previous segment's last node plane
+        sp.seg(so - 1, z0, len);
+        stride_l = (long long)(len / 2 + 1) * NE;
+        pl = part + sp.planes_before(so - 1) * ncols * NE + col * stride_l + ((len / 2) * NE + jy * NX + jx);
+    }
     float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const bool ux = q & 1, uy = (q >> 1) & 1, uz = q >> 2;
         if ((ux && !lx) || (uy && !ly) || (uz && !lz))
             continue;
-        const float *p = p0 + (ux ? dX : 0) + (uy ? dY : 0) + (uz ? dZ : 0);
+        const long long stride = uz ? stride_l : stride_o;
+        // the lower column's copy: one column back, local index 14 instead of 0
+        const float *p = (uz ? pl : po) + (ux ? -stride + (NX - 1) : 0) + (uy ? -stride * ntx + (NY - 1) * NX : 0);
         s[0] += __ldg(p);
         s[1] += __ldg(p + NX * NY);
         s[2] += __ldg(p + 2 * NX * NY);
@@ -551,11 +625,11 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
     }
 }
 
-__global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *__restrict__ part, int tz, int ntx,
-                                                     int nty, int ntz, const float *__restrict__ w, float alpha_hy,
+__global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *__restrict__ part, FusedSplit sp,
+                                                     int ntx, int nty, const float *__restrict__ w, float alpha_hy,
                                                      float *__restrict__ grad)
 {
-    gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
+    gather_grad_body(g, part, sp, ntx, nty, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // The end of an evaluation in the gather launch.  The final reduction reads
@@ -573,8 +647,8 @@ struct FinArgs {
     unsigned long long h_ls;
 };
 
-__global__ void __launch_bounds__(256) k_gather_fin(LevelGeom g, const float *__restrict__ part, int tz, int ntx,
-                                                    int nty, int ntz, const float *__restrict__ w, float alpha_hy,
+__global__ void __launch_bounds__(256) k_gather_fin(LevelGeom g, const float *__restrict__ part, FusedSplit sp,
+                                                    int ntx, int nty, const float *__restrict__ w, float alpha_hy,
                                                     float *__restrict__ grad, FinArgs f)
 {
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
@@ -584,7 +658,7 @@ __global__ void __launch_bounds__(256) k_gather_fin(LevelGeom g, const float *__
             lb_control_body(f.phase, f.st, nullptr, 0, f.scal, f.h_ls, 0ULL, 0ULL);
         }
     }
-    gather_grad_body(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
+    gather_grad_body(g, part, sp, ntx, nty, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace
@@ -601,10 +675,21 @@ bool fused_eligible(const Level &L)
 // whole node intervals)
 constexpr int TZ_CAND[] = {2, 4, 8, 16, 32, 64, 128};
 
-// Pipeline steps a segment pays beyond its tz planes (fill and drain)
+// Pipeline steps a segment pays beyond its planes (fill and drain)
 constexpr int FUSED_FILL = 7;
-// longest z segment (the tile partial buffers are sized for every even length up to it)
+// longest z segment cfg.fused_tz may force
 constexpr int TZ_MAX = 512;
+
+static int fused_cols(const int m[3]) { return ((m[0] + OX - 1) / OX) * ((m[1] + OY - 1) / OY); }
+
+FusedSplit fused_split_uniform(int tz, int mz)
+{
+    FusedSplit sp;
+    sp.l1 = tz;
+    sp.n1 = mz / tz;
+    sp.lr = mz - sp.n1 * tz;   // even, as mz and tz are
+    return sp;
+}
 
 // Even z segment lengths that cut a depth of mz planes into ntz = 1, 2, ...
 // nearly equal segments, tz = 2 ceil(mz / (2 ntz)), longest first, each once.
@@ -621,37 +706,102 @@ static std::vector<int> tz_splits(int mz)
     return v;
 }
 
-// Modelled duration of the pass in CTA steps: one CTA is resident per SM, so
-// the CTAs run in waves of num_sms, each as long as one segment (tz + 7 steps).
-static long long fused_cost(int cols, int mz, int tz, int num_sms)
-{
-    const long long ctas = (long long)cols * ((mz + tz - 1) / tz);
-    return (ctas + num_sms - 1) / num_sms * (tz + FUSED_FILL);
-}
+// Load model of the pass.  A tile costs its planes + 7 steps, times a weight
+// for the share of its 32 x 32 columns inside the image (columns outside skip
+// the loads, the interpolation and the NGF work; about a third of a step's
+// work remains).  One CTA is resident per SM and the next free SM takes the
+// next tile in launch order (tile_seg_col), so the model replays that order
+// and returns the time the last SM finishes.
+struct SplitModel {
+    std::vector<double> colw;   // weight of each tile column, in column order
+    int mz, sms;
+    SplitModel(const int m[3], int num_sms) : mz(m[2]), sms(num_sms > 0 ? num_sms : 1)
+    {
+        const int ntx = (m[0] + OX - 1) / OX, nty = (m[1] + OY - 1) / OY;
+        auto frac = [](int t, int o, int width, int extent) {
+            int n = 0;
+            for (int i = t * o - 2; i < t * o - 2 + width; i++)
+                n += i >= 0 && i < extent;
+            return (double)n / width;
+        };
+        for (int ty = 0; ty < nty; ty++)
+            for (int tx = 0; tx < ntx; tx++)
+                colw.push_back(0.35 + 0.65 * frac(tx, OX, CW, m[0]) * frac(ty, OY, BY, m[1]));
+    }
+    double makespan(const FusedSplit &sp) const
+    {
+        // segment groups by length, longest first (stable), as tile_seg_col
+        int len[3] = {sp.l1, sp.l2, sp.lr}, cnt[3] = {sp.n1, sp.n2, sp.lr > 0 ? 1 : 0};
+        int ord[3] = {0, 1, 2};
+        std::stable_sort(ord, ord + 3, [&](int x, int y) { return len[x] > len[y]; });
+        std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+        for (int i = 0; i < sms; i++)
+            free_at.push(0.0);
+        double end = 0.0;
+        for (int k = 0; k < 3; k++)
+            for (int seg = 0; seg < cnt[ord[k]]; seg++)
+                for (double w : colw) {
+                    const double t = free_at.top() + w * (len[ord[k]] + FUSED_FILL);
+                    free_at.pop();
+                    free_at.push(t);
+                    end = std::max(end, t);
+                }
+        return end;
+    }
+};
 
-static int fused_cols(const int m[3]) { return ((m[0] + OX - 1) / OX) * ((m[1] + OY - 1) / OY); }
-
-// z segment lengths of the splits, cheapest first under the wave model (ties: the longer)
-static std::vector<int> tz_ranked(const int m[3], int num_sms)
+// Candidate splits of a depth: the equal splits, and for depths of 32 planes
+// and more one or two segments of l1 planes, one to three of l2 < l1 and the
+// remainder (lengths on a grid of mz / 32 planes).
+static std::vector<FusedSplit> split_candidates(int mz)
 {
-    std::vector<int> v = tz_splits(m[2]);
-    const int cols = fused_cols(m);
-    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
-        return fused_cost(cols, m[2], a, num_sms) < fused_cost(cols, m[2], b, num_sms);
-    });
+    std::vector<FusedSplit> v;
+    for (int tz : tz_splits(mz))
+        v.push_back(fused_split_uniform(tz, mz));
+    if (mz >= 32) {
+        const int step = std::max(2, (mz / 32) & ~1);
+        for (int l1 = step; l1 <= mz; l1 += step)
+            for (int n1 = 1; n1 <= 2 && n1 * l1 <= mz; n1++)
+                for (int l2 = step; l2 < l1; l2 += step)
+                    for (int n2 = 1; n2 <= 3 && n1 * l1 + n2 * l2 <= mz; n2++) {
+                        FusedSplit sp;
+                        sp.l1 = l1;
+                        sp.n1 = n1;
+                        sp.l2 = l2;
+                        sp.n2 = n2;
+                        sp.lr = mz - n1 * l1 - n2 * l2;
+                        v.push_back(sp);
+                    }
+    }
     return v;
 }
 
-// Default z segment length when the level was not tuned: the cheapest split
-// under the wave model
-static int fused_tz_default(const Level &L, int num_sms) { return tz_ranked(L.m, num_sms > 0 ? num_sms : 1)[0]; }
+// candidate splits, cheapest first under the load model (ties: fewer segments)
+static std::vector<FusedSplit> splits_ranked(const int m[3], int num_sms)
+{
+    const SplitModel model(m, num_sms);
+    std::vector<std::pair<double, FusedSplit>> r;
+    for (const FusedSplit &sp : split_candidates(m[2]))
+        r.push_back({model.makespan(sp), sp});
+    std::stable_sort(r.begin(), r.end(), [](const std::pair<double, FusedSplit> &x,
+                                            const std::pair<double, FusedSplit> &y) {
+        if (x.first != y.first)
+            return x.first < y.first;
+        return x.second.count() < y.second.count();
+    });
+    std::vector<FusedSplit> v;
+    for (auto &e : r)
+        v.push_back(e.second);
+    return v;
+}
 
-int fused_tz(const Level &L, int num_sms) { return L.tz > 0 ? L.tz : fused_tz_default(L, num_sms); }
+FusedSplit fused_split(const Level &L, int num_sms) { return L.split.valid() ? L.split : splits_ranked(L.m, num_sms)[0]; }
 
 // Throughput rule: the z segment length of TZ_CAND with the fewest pipeline
 // steps in total, ntz * (tz + 7) (ties: the longer one).  The right choice
 // when other work keeps every SM busy (a batch of pairs); a single pair alone
-// wants segments that fill the GPU in whole waves, which the autotuner finds.
+// wants segments that fill the GPU in whole waves, which the load model and
+// the autotuner find.
 int fused_tz_throughput(const Level &L)
 {
     int best = 0;
@@ -668,27 +818,13 @@ int fused_tz_throughput(const Level &L)
 
 bool fused_tz_valid(int tz) { return tz >= 2 && tz <= TZ_MAX && tz % 2 == 0; }
 
-void fused_grid(const Level &L, int tz, int &ntx, int &nty, int &ntz)
-{
-    ntx = (L.m[0] + OX - 1) / OX;
-    nty = (L.m[1] + OY - 1) / OY;
-    ntz = (L.m[2] + tz - 1) / tz;
-}
-
-// tile-partial floats of the level: the largest over every z segment length
-// that may be used (any even length cfg.fused_tz may force covers the rules)
+// tile-partial floats of the level, for any split: a tile of a segment of len
+// planes keeps len / 2 + 1 node planes, and the segments' lengths add up to
+// the depth, so a split keeps at most depth / 2 + count <= depth planes per column
 size_t fused_part_floats(const Level &L, int num_sms)
 {
     (void)num_sms;
-    size_t best = 0;
-    for (int tz = 2; tz <= TZ_MAX; tz += 2) {
-        int ntx, nty, ntz;
-        fused_grid(L, tz, ntx, nty, ntz);
-        size_t p = (size_t)ntx * nty * ntz * (tz / 2 + 1) * NE;
-        if (p > best)
-            best = p;
-    }
-    return best;
+    return (size_t)fused_cols(L.m) * (size_t)(L.m[2] + 2) * NE;
 }
 
 cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
@@ -706,11 +842,13 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     a.t_dev = t_dev;
     a.tau = (float)c->cfg.tau;
     a.rho = (float)c->cfg.rho;
-    a.tz = fused_tz(L, c->num_sms);
-    fused_grid(L, a.tz, a.ntx, a.nty, a.ntz);
+    a.split = fused_split(L, c->num_sms);
+    a.ntx = (L.m[0] + OX - 1) / OX;
+    a.nty = (L.m[1] + OY - 1) / OY;
     a.part = c->es.part;
     a.partials = partials;
-    dim3 blk(BX, BY, 1), grd(a.ntx, a.nty, a.ntz);
+    const int ntiles = a.ntx * a.nty * a.split.count();
+    dim3 blk(BX, BY, 1), grd(ntiles, 1, 1);
     // the shared rings exceed the 48 KB default; the limit is set once per device
     static bool attr_set[64] = {};
     const int dev = c->device >= 0 && c->device < 64 ? c->device : 0;
@@ -738,7 +876,7 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
         else
             k_ngf_fused<false, float><<<grd, blk, SMEM_BYTES, s>>>(a);
     }
-    *n_partials = a.ntx * a.nty * a.ntz;
+    *n_partials = ntiles;
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -747,8 +885,8 @@ cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha
                               const double *pS, int nS, double *scal, int phase, cudaStream_t s)
 {
     const Level &L = c->L[level];
-    int tz = fused_tz(L, c->num_sms), ntx, nty, ntz;
-    fused_grid(L, tz, ntx, nty, ntz);
+    const FusedSplit sp = fused_split(L, c->num_sms);
+    const int ntx = (L.m[0] + OX - 1) / OX, nty = (L.m[1] + OY - 1) / OY;
     dim3 blk(32, 8, 1);
     dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
     FinArgs f;
@@ -763,7 +901,7 @@ cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha
     f.phase = phase;
     f.st = c->lb.st;
     f.h_ls = phase >= 0 ? lbfgs_graph_handle_ls() : 0ULL;
-    k_gather_fin<<<gn, blk, 0, s>>>(L.geom(), c->es.part, tz, ntx, nty, ntz, w, alpha_hy, grad, f);
+    k_gather_fin<<<gn, blk, 0, s>>>(L.geom(), c->es.part, sp, ntx, nty, w, alpha_hy, grad, f);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -771,31 +909,31 @@ cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha
 cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alpha_hy, float *grad, cudaStream_t s)
 {
     const Level &L = c->L[level];
-    int tz = fused_tz(L, c->num_sms), ntx, nty, ntz;
-    fused_grid(L, tz, ntx, nty, ntz);
+    const FusedSplit sp = fused_split(L, c->num_sms);
+    const int ntx = (L.m[0] + OX - 1) / OX, nty = (L.m[1] + OY - 1) / OY;
     dim3 blk(32, 8, 1);
     dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
-    k_gather_grad<<<gn, blk, 0, s>>>(L.geom(), c->es.part, tz, ntx, nty, ntz, w, alpha_hy, grad);
+    k_gather_grad<<<gn, blk, 0, s>>>(L.geom(), c->es.part, sp, ntx, nty, w, alpha_hy, grad);
     c->launches += 1;
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the z segment length (the tile depth of the fused pass).  The
-// candidates are the TUNE_CAND splits of the depth into equal even segments
-// that the wave model ranks cheapest; for each the pass runs on the level's
-// own images at u = u_zero (one warm launch, then the median of three
-// CUDA-event timings) and the fastest wins.  Short segments start more CTAs
-// (small levels fill the GPU) but pay the 7 pipeline-fill steps and the
-// shared node planes more often, and the last wave of CTAs may leave SMs
-// idle, so the best depth depends on the level and the GPU.  Choices are
-// cached per (image dims, SM count, image type, device) for the life of the
-// process: handles of the same geometry tune once and pick the same tiling.
+// Autotuner of the z segmentation of the fused pass.  The candidates are the
+// TUNE_CAND splits the load model ranks cheapest plus its two best equal
+// splits (in case the model misjudges the weights); for each the pass runs on
+// the level's own images at u = u_zero (one warm launch, then the median of
+// three CUDA-event timings) and the fastest wins.  Short segments start more
+// CTAs (small levels fill the GPU) but pay the 7 pipeline-fill steps and the
+// shared node planes more often, and the last CTAs may leave SMs idle, so the
+// best split depends on the level and the GPU.  Choices are cached per (image
+// dims, SM count, image type, device) for the life of the process: handles of
+// the same geometry tune once and pick the same tiling.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int TUNE_CAND = 6;
 std::mutex g_tune_mu;
-std::map<std::array<int, 6>, int> g_tune;
+std::map<std::array<int, 6>, FusedSplit> g_tune;
 }
 
 cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStream_t s)
@@ -807,23 +945,35 @@ cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStrea
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            L.tz = it->second;
+            L.split = it->second;
             return cudaSuccess;
+        }
+    }
+    const std::vector<FusedSplit> ranked = splits_ranked(L.m, c->num_sms);
+    std::vector<FusedSplit> cand;
+    for (const FusedSplit &sp : ranked)
+        if ((int)cand.size() < TUNE_CAND)
+            cand.push_back(sp);
+    int uniform = 0;
+    for (const FusedSplit &sp : ranked) {
+        if (uniform == 2)
+            break;
+        if (sp.n2 == 0 && (sp.lr == 0 || sp.n1 == 0)) {   // equal segments (no remainder)
+            uniform++;
+            if (std::find(cand.begin(), cand.end(), sp) == cand.end())
+                cand.push_back(sp);
         }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess)
         e = cudaEventCreate(&e1);
-    int best = 0;
+    FusedSplit best;
     float best_ms = 0.f;
-    std::vector<int> cand = tz_ranked(L.m, c->num_sms > 0 ? c->num_sms : 1);
-    if (cand.size() > (size_t)TUNE_CAND)
-        cand.resize(TUNE_CAND);
-    for (int tz : cand) {
+    for (const FusedSplit &sp : cand) {
         if (e != cudaSuccess)
             break;
-        L.tz = tz;
+        L.split = sp;
         int nD = 0;
         float t[3];
         for (int r = -1; r < 3 && e == cudaSuccess; r++) {   // r = -1: warm launch
@@ -841,8 +991,8 @@ cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStrea
         if (e != cudaSuccess)
             break;
         const float med = fmaxf(fminf(t[0], t[1]), fminf(fmaxf(t[0], t[1]), t[2]));
-        if (best == 0 || med < best_ms) {
-            best = tz;
+        if (!best.valid() || med < best_ms) {
+            best = sp;
             best_ms = med;
         }
     }
@@ -851,10 +1001,10 @@ cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStrea
     if (e1)
         cudaEventDestroy(e1);
     if (e != cudaSuccess) {
-        L.tz = 0;
+        L.split = FusedSplit();
         return e;
     }
-    L.tz = best;
+    L.split = best;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = best;
     return cudaSuccess;
@@ -864,16 +1014,29 @@ cudaError_t fused_autotune(reg_ctx *c, int level, const float *u_zero, cudaStrea
 // Explicit-buffer launches of the fused pass and its gather, for callers that
 // own every buffer themselves (the allocation-free entry point).  Geometry
 // comes in as a LevelGeom of a ratio-2 grid; no per-dimension tables are used.
+// The split is the load model's first choice for the dims (cached per dims).
 // ---------------------------------------------------------------------------
-static int fused_tz_dims(const int m[3], int num_sms) { return tz_ranked(m, num_sms > 0 ? num_sms : 1)[0]; }
+static FusedSplit fused_split_dims(const int m[3], int num_sms)
+{
+    static std::mutex mu;
+    static std::map<std::array<int, 4>, FusedSplit> cache;
+    const std::array<int, 4> key{m[0], m[1], m[2], num_sms};
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end())
+        return it->second;
+    const FusedSplit sp = splits_ranked(m, num_sms)[0];
+    cache[key] = sp;
+    return sp;
+}
 
 void fused_layout_dims(const int m[3], int num_sms, int *tz, int *tiles, size_t *part_floats)
 {
-    const int z = fused_tz_dims(m, num_sms);
-    const int nt = ((m[0] + OX - 1) / OX) * ((m[1] + OY - 1) / OY) * ((m[2] + z - 1) / z);
-    *tz = z;
-    *tiles = nt;
-    *part_floats = (size_t)nt * (z / 2 + 1) * NE;
+    const FusedSplit sp = fused_split_dims(m, num_sms);
+    const int ncols = fused_cols(m);
+    *tz = sp.longest();
+    *tiles = ncols * sp.count();
+    *part_floats = (size_t)ncols * sp.planes_before(sp.count()) * NE;
 }
 
 cudaError_t fused_set_smem_limit()
@@ -897,13 +1060,12 @@ cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float
     a.t_dev = nullptr;
     a.tau = tau;
     a.rho = rho;
-    a.tz = fused_tz_dims(g.m, num_sms);
+    a.split = fused_split_dims(g.m, num_sms);
     a.ntx = (g.m[0] + OX - 1) / OX;
     a.nty = (g.m[1] + OY - 1) / OY;
-    a.ntz = (g.m[2] + a.tz - 1) / a.tz;
     a.part = part;
     a.partials = partials;
-    dim3 blk(BX, BY, 1), grd(a.ntx, a.nty, a.ntz);
+    dim3 blk(BX, BY, 1), grd(a.ntx * a.nty * a.split.count(), 1, 1);
     k_ngf_fused<false><<<grd, blk, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
@@ -911,11 +1073,11 @@ cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float
 cudaError_t launch_gather_grad_raw(const LevelGeom &g, const float *part, int num_sms, const float *w,
                                    float alpha_hy, float *grad, cudaStream_t s)
 {
-    const int tz = fused_tz_dims(g.m, num_sms);
-    const int ntx = (g.m[0] + OX - 1) / OX, nty = (g.m[1] + OY - 1) / OY, ntz = (g.m[2] + tz - 1) / tz;
+    const FusedSplit sp = fused_split_dims(g.m, num_sms);
+    const int ntx = (g.m[0] + OX - 1) / OX, nty = (g.m[1] + OY - 1) / OY;
     dim3 blk(32, 8, 1);
     dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]);
-    k_gather_grad<<<gn, blk, 0, s>>>(g, part, tz, ntx, nty, ntz, w, alpha_hy, grad);
+    k_gather_grad<<<gn, blk, 0, s>>>(g, part, sp, ntx, nty, w, alpha_hy, grad);
     return cudaGetLastError();
 }
 
@@ -969,7 +1131,7 @@ __global__ void __launch_bounds__(256) k_gather_batch(const PairLevel *__restric
         const int lin = item - __ldg(off + p);
         const int bx = lin % P.ncx, r = lin / P.ncx;
         const FusedArgs &a = P.fa_init;
-        gather_grad_body(P.geom, a.part, a.tz, a.ntx, a.nty, a.ntz, P.w, P.alpha_hy, mode ? P.gt : P.g, bx,
+        gather_grad_body(P.geom, a.part, a.split, a.ntx, a.nty, P.w, P.alpha_hy, mode ? P.gt : P.g, bx,
                          r % P.ncy, r / P.ncy);
     }
 }
@@ -984,8 +1146,9 @@ cudaError_t launch_gather_batch(const PairLevel *pl, const int *off, int npairs,
 }
 
 // tiling of a level of the fused pass, for the batch descriptors
-void fused_tiling(const Level &L, int num_sms, int *tz, int *ntx, int *nty, int *ntz)
+void fused_tiling(const Level &L, int num_sms, FusedSplit *split, int *ntx, int *nty)
 {
-    *tz = fused_tz(L, num_sms);
-    fused_grid(L, *tz, *ntx, *nty, *ntz);
+    *split = fused_split(L, num_sms);
+    *ntx = (L.m[0] + OX - 1) / OX;
+    *nty = (L.m[1] + OY - 1) / OY;
 }

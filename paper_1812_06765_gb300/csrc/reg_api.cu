@@ -67,6 +67,31 @@ void free_buffers(reg_ctx *c)
     c->have_images = false;
 }
 
+// cfg.fused_split: all zero, or counts >= 0 and even lengths in 2 .. 512 for
+// every group that is used, at least one segment
+static bool split_config_valid(const int v[5])
+{
+    if (!v[0] && !v[1] && !v[2] && !v[3] && !v[4])
+        return true;
+    if (v[1] < 0 || v[3] < 0 || v[0] < 0 || v[2] < 0 || v[4] < 0)
+        return false;
+    auto len_ok = [](int l) { return l >= 2 && l <= 512 && l % 2 == 0; };
+    if ((v[1] > 0 && !len_ok(v[0])) || (v[3] > 0 && !len_ok(v[2])) || (v[4] > 0 && !len_ok(v[4])))
+        return false;
+    return v[1] + v[3] + (v[4] > 0 ? 1 : 0) > 0;
+}
+
+static FusedSplit split_from_config(const int v[5])
+{
+    FusedSplit sp;
+    sp.l1 = v[0];
+    sp.n1 = v[1];
+    sp.l2 = v[2];
+    sp.n2 = v[3];
+    sp.lr = v[4];
+    return sp;
+}
+
 int validate_config(const reg_config *cfg, std::string &msg)
 {
     char buf[256];
@@ -86,6 +111,8 @@ int validate_config(const reg_config *cfg, std::string &msg)
     else if (!(cfg->tol_grad_rel >= 0) || !(cfg->tol_j_rel >= 0)) msg = "tolerances must be >= 0";
     else if (cfg->autotune != 0 && cfg->autotune != 1) msg = "autotune must be 0 or 1";
     else if (cfg->test_expire_wait != 0 && cfg->test_expire_wait != 1) msg = "test_expire_wait must be 0 or 1";
+    else if (!split_config_valid(cfg->fused_split))
+        msg = "fused_split must be all 0 or (l1, n1, l2, n2, lr): counts >= 0, lengths even, 2 .. 512 where used";
     else if (cfg->fused_tz != 0 && cfg->fused_tz != -1 && !fused_tz_valid(cfg->fused_tz))
         msg = "fused_tz must be 0, -1 or an even length in 2 .. 512";
     else return REG_OK;
@@ -441,17 +468,20 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
     // tiling of the fused pass per level: forced, autotuned (at u = 0, with the
     // direction buffer as the zero field) or the default rule
     for (int l = 0; l < c->levels; l++) {
-        if (!use_fused(c, l) || c->L[l].tz > 0)
+        if (!use_fused(c, l) || c->L[l].split.valid())
             continue;
-        if (cfg.fused_tz > 0) {
-            c->L[l].tz = cfg.fused_tz;
+        const FusedSplit forced = split_from_config(cfg.fused_split);
+        if (forced.valid() && forced.n1 * forced.l1 + forced.n2 * forced.l2 + forced.lr == c->L[l].m[2]) {
+            c->L[l].split = forced;
+        } else if (cfg.fused_tz > 0) {
+            c->L[l].split = fused_split_uniform(cfg.fused_tz, c->L[l].m[2]);
         } else if (cfg.fused_tz == -1) {
-            c->L[l].tz = fused_tz_throughput(c->L[l]);
+            c->L[l].split = fused_split_uniform(fused_tz_throughput(c->L[l]), c->L[l].m[2]);
         } else if (cfg.autotune) {
             CK(cudaMemsetAsync(c->lb.pdir, 0, sizeof(float) * 3 * c->L[l].nn, c->stream));
             CK(fused_autotune(c, l, c->lb.pdir, c->stream));
         } else {
-            c->L[l].tz = fused_tz(c->L[l], c->num_sms);
+            c->L[l].split = fused_split(c->L[l], c->num_sms);   // the load model's choice
         }
     }
     if (!ptr_is_device) CK(cudaStreamSynchronize(c->stream));  // host arrays may be released on return
@@ -467,9 +497,11 @@ int reg_level_tiling(reg_handle c, int level, int *tz, int *tiles)
         return set_err(c, REG_ERR_ARG, "reg_level_tiling: level %d out of range", level);
     int z = 0, n = 0;
     if (use_fused(c, level)) {
-        int ntx, nty, ntz;
-        fused_tiling(c->L[level], c->num_sms, &z, &ntx, &nty, &ntz);
-        n = ntx * nty * ntz;
+        FusedSplit sp;
+        int ntx, nty;
+        fused_tiling(c->L[level], c->num_sms, &sp, &ntx, &nty);
+        z = sp.longest();
+        n = ntx * nty * sp.count();
     }
     if (tz) *tz = z;
     if (tiles) *tiles = n;
@@ -668,7 +700,7 @@ int reg_register(reg_handle c, float *u_out, int out_is_device, const float *u_i
         local.iters[l] = sh->k;
         local.evals[l] = sh->evals;
         local.J[l] = sh->J;
-        local.tiling[l] = use_fused(c, l) ? fused_tz(c->L[l], c->num_sms) : 0;
+        local.tiling[l] = use_fused(c, l) ? fused_split(c->L[l], c->num_sms).longest() : 0;
         if (sh->status == -5) return set_err(c, REG_ERR_NUMERIC, "reg_register: non-finite J or gradient at level %d", l);
         if (sh->status == -6)
             return set_err(c, REG_ERR_TIMEOUT, "reg_register: level %d exceeded its loop bound", l);

@@ -39,7 +39,8 @@ def test_config_default_and_version(libreg):
     assert cfg.autotune == 1 and cfg.fused_tz == 0 and cfg.use_graph == 1 and cfg.image_dtype == 0
     assert cfg.test_expire_wait == 0
     assert libreg.reg_version() >= 10000
-    assert ctypes.sizeof(libreg.RegConfig) == 8 * 6 + 4 * 6 + 4 * 8 + 4 * 24 + 4 * 8
+    assert ctypes.sizeof(libreg.RegConfig) == 8 * 6 + 4 * 6 + 4 * 8 + 4 * 24 + 4 * 12
+    assert list(cfg.fused_split) == [0] * 5
 
 
 def test_create_rejects_bad_config_before_touching_the_gpu(libreg):
@@ -52,6 +53,12 @@ def test_create_rejects_bad_config_before_touching_the_gpu(libreg):
             libreg.reg_create(cfg)
         assert ei.value.code == libreg.REG_ERR_ARG
         assert libreg.reg_last_error(None)
+    for split in ((3, 1, 0, 0, 0), (4, -1, 0, 0, 0), (0, 0, 0, 0, 7), (4, 1, 514, 1, 0), (0, 1, 0, 0, 0)):
+        cfg = libreg.reg_config_default()
+        cfg.fused_split[:] = list(split)
+        with pytest.raises(libreg.RegError) as ei:
+            libreg.reg_create(cfg)
+        assert ei.value.code == libreg.REG_ERR_ARG
 
 
 def test_null_handle_calls_are_safe(libreg):

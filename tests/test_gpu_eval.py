@@ -280,7 +280,31 @@ def test_every_fused_tile_depth_matches_oracle(reg_mod, orc, tz):
     cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=tz)
     r = reg_mod.Registration(cfg).set_images(R, T, h)
     z, tiles = r.level_tiling(0)
-    assert z == tz and tiles == 3 * 2 * -(-dims[2] // tz)
+    assert z == min(tz, dims[2]) and tiles == 3 * 2 * -(-dims[2] // tz)
+    u = random_field(r.level_info(0)["nodes"], 73, 2.5)
+    e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
+    assert e["eJ"] <= J_RTOL and e["eg"] <= GRAD_RTOL, e
+    r.close()
+
+
+# z splits of the depth 70 into segments of different lengths (l1, n1, l2, n2, lr):
+# longest first in launch order, a short remainder, two groups without a
+# remainder, the remainder longest
+SPLITS = [(40, 1, 10, 2, 10), (30, 1, 20, 2, 0), (4, 2, 6, 3, 44), (16, 2, 2, 1, 36)]
+
+
+@pytest.mark.parametrize("split", SPLITS)
+def test_uneven_z_splits_match_oracle(reg_mod, orc, split):
+    # tiles of unequal segments share node planes in z; the gather finds each
+    # node plane's segment and the previous segment's last plane
+    dims, h, tau, rho, alpha = (58, 38, 70), (1.2, 0.8, 1.0), 0.05, 0.03, 2.0
+    R = random_image(dims, 71)
+    T = random_image(dims, 72)
+    cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_split=split)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    l1, n1, l2, n2, lr = split
+    z, tiles = r.level_tiling(0)
+    assert z == max(l1 if n1 else 0, l2 if n2 else 0, lr) and tiles == 3 * 2 * (n1 + n2 + (lr > 0))
     u = random_field(r.level_info(0)["nodes"], 73, 2.5)
     e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
     assert e["eJ"] <= J_RTOL and e["eg"] <= GRAD_RTOL, e
@@ -293,14 +317,15 @@ def test_autotuned_tiling_is_cached_per_geometry(reg_mod):
     cfg = reg_mod.make_config(levels=3, tau=0.05, alpha=1.0)
     r1 = reg_mod.Registration(cfg).set_images(R, R, h)
     r2 = reg_mod.Registration(cfg).set_images(R, R, h)
-    def even_splits(depth):   # 2 ceil(depth / 2k): depth cut into k nearly equal even segments
-        return {2 * -(-depth // (2 * k)) for k in range(1, depth + 1)}
-    for lv in range(3):
+    for lv in range(3):   # longest segment of the chosen split, and the tiles
         t1, t2 = r1.level_tiling(lv), r2.level_tiling(lv)
-        assert t1 == t2 and t1[0] in even_splits(r1.level_info(lv)["dims"][2]) and t1[1] > 0
+        depth = r1.level_info(lv)["dims"][2]
+        assert t1 == t2 and t1[0] % 2 == 0 and 2 <= t1[0] <= depth and t1[1] > 0
     off = reg_mod.Registration(reg_mod.make_config(levels=3, tau=0.05, alpha=1.0, autotune=False))
     off.set_images(R, R, h)
-    assert all(off.level_tiling(lv)[0] in even_splits(off.level_info(lv)["dims"][2]) for lv in range(3))
+    for lv in range(3):   # the load model's choice
+        tz, tiles = off.level_tiling(lv)
+        assert tz % 2 == 0 and 2 <= tz <= off.level_info(lv)["dims"][2] and tiles > 0
     for r in (r1, r2, off):
         r.close()
 
