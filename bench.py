@@ -61,6 +61,8 @@ def parse_args(argv=None):
                          "in the same order; ncu cannot list kernels inside graphs with conditional nodes)")
     ap.add_argument("--fused-tz", type=int, default=None,
                     help="force the fused pass's z segment length (no autotuning launches; for profiling)")
+    ap.add_argument("--fused-split", type=int, nargs=5, default=None, metavar=("L1", "N1", "L2", "N2", "LR"),
+                    help="force the fused pass's z split on levels of that depth (for profiling)")
     ap.add_argument("--report", action="store_true",
                     help="one JSON line per single-pair workload (64^3, 128^3, 256^3, 4D-CT shape): GPU registration "
                          "and evaluation times, accuracy, and the FP64 oracle on all host cores and on one core")
@@ -186,9 +188,9 @@ def source_digest(files):
 FUSED_TILE_NODE_ENTRIES = 3 * 15 * 15
 
 
-def committed_profile(kernel, digest, workload_name, tz):
+def committed_profile(kernel, digest, workload_name, split):
     """The committed ncu figures of a kernel launch (DRAM bytes, warp instructions),
-    if they were taken on this source, this workload and this tiling (else {})."""
+    if they were taken on this source, this workload and this z split (else {})."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return {}
@@ -197,9 +199,16 @@ def committed_profile(kernel, digest, workload_name, tz):
     e = d.get(kernel)
     if not e or e.get("source_digest") != digest:
         return {}
-    if e.get("workload") != workload_name or e.get("fused_tz") != tz:
+    if e.get("workload") != workload_name or e.get("fused_split") != list(split):
         return {}
     return e
+
+
+def split_partial_floats_per_column(split):
+    """Node planes x entries one tile column keeps over all z segments of a split."""
+    l1, n1, l2, n2, lr = split
+    planes = n1 * (l1 // 2 + 1) + n2 * (l2 // 2 + 1) + (lr // 2 + 1 if lr else 0)
+    return planes * FUSED_TILE_NODE_ENTRIES
 
 
 def issue_peak_warp_inst_per_s():
@@ -268,6 +277,8 @@ def run_ours(args):
         kw["use_graph"] = False
     if args.fused_tz is not None:
         kw["fused_tz"] = args.fused_tz
+    if args.fused_split is not None:
+        kw["fused_split"] = args.fused_split
     cfg = reg_pkg.make_config(**kw)
     stream = torch.cuda.current_stream(dev)
     reg = reg_pkg.Registration(cfg, stream=stream)
@@ -376,11 +387,14 @@ def run_ours(args):
     impl = reg.cfg.eval_impl
     kernel = "objective_pass_fused" if impl == 0 else "objective_pass_multipass"
     tz, tiles = reg.level_tiling(0)
+    split = reg.level_split(0)
+    nseg = split[1] + split[3] + (1 if split[4] else 0)
     # the dominant kernel: read R, T and u once, write its tile partials of P^T r
-    part_bytes = 4 * tiles * (tz // 2 + 1) * FUSED_TILE_NODE_ENTRIES if impl == 0 else 12 * nn
+    part_bytes = (4 * (tiles // nseg) * split_partial_floats_per_column(split) if impl == 0 and nseg
+                  else 12 * nn)
     kernel_bytes = 8 * nv + 12 * nn + part_bytes
     achieved = kernel_bytes / (ngf_ms * 1e-3) / 1e9
-    prof = committed_profile(kernel, source_digest(FUSED_KERNEL_SOURCES), c["name"], tz)
+    prof = committed_profile(kernel, source_digest(FUSED_KERNEL_SOURCES), c["name"], split)
     traffic = prof.get("dram_bytes_per_launch_full_size")
     issue = None
     if prof.get("warp_instructions_per_launch"):
@@ -413,7 +427,8 @@ def run_ours(args):
                        "level_device_s": level_s,
                        "eval_impl": "fused" if impl == 0 else "multi-pass",
                        "fused_tz_per_level": [reg.level_tiling(lv)[0] for lv in range(levels)],
-                       "tiling": "autotuned (z segment length timed per level)" if reg.cfg.autotune else "fixed rule",
+                       "fused_split_per_level": [list(reg.level_split(lv)) for lv in range(levels)],
+                       "tiling": "autotuned (z split timed per level)" if reg.cfg.autotune else "load model",
                        "lbfgs_loop": "one CUDA graph per level" if reg.cfg.use_graph else "host-driven",
                        "l2": "flushed between steps (2x L2 buffer written, untimed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
@@ -493,6 +508,8 @@ def run_batch(args):
     kw = dict(levels=levels, tau=c["eta"], alpha=c["alpha"], mem=c["mem"], max_iter=c["max_iter"], c1=c["c1"])
     if args.fused_tz is not None:
         kw["fused_tz"] = args.fused_tz
+    if args.fused_split is not None:
+        kw["fused_split"] = args.fused_split
     if args.host_loop:
         kw["use_graph"] = False
     regs = [reg_pkg.Registration(reg_pkg.make_config(**kw), stream=stream) for _ in range(n)]
@@ -742,6 +759,7 @@ def run_report(args):
                 "levels": c["levels"], "finest_nodes": list(info["nodes"]),
                 "iters_per_level": st["iters"], "evals_per_level": st["evals"],
                 "fused_tz_per_level": [reg.level_tiling(lv)[0] for lv in range(c["levels"])],
+                "fused_split_per_level": [list(reg.level_split(lv)) for lv in range(c["levels"])],
                 "gpu": {"registration_s_device_resident": statistics.median(dev_ms) / 1000.0,
                         "registration_s_from_host_arrays": statistics.median(host_s),
                         "level_device_s": st["level_seconds"],

@@ -147,11 +147,17 @@ int reg_level_info(reg_handle h, int level, int img_dims[3], int node_dims[3],
                    double spacing_mm[3], double node_spacing_mm[3]);
 
 /* Tiling of the fused objective pass on a level (no counterpart in the paper,
- * which uses separate kernels): *tz = the z segment length (output planes per
- * CTA, chosen by the autotuner, cfg.fused_tz or the fixed rule), *tiles = CTAs
- * per evaluation.  Both 0 on levels the multi-pass kernels serve.  Any output
- * pointer may be NULL. */
+ * which uses separate kernels): *tz = the longest z segment (output planes per
+ * CTA, chosen by the autotuner, cfg.fused_split, cfg.fused_tz or the load
+ * model), *tiles = CTAs per evaluation.  Both 0 on levels the multi-pass
+ * kernels serve.  Any output pointer may be NULL. */
 int reg_level_tiling(reg_handle h, int level, int *tz, int *tiles);
+
+/* The z split of the fused pass on a level, in the form of cfg.fused_split:
+ * split[5] = (l1, n1, l2, n2, lr), n1 segments of l1 planes, then n2 of l2,
+ * then lr planes (0: no remainder), every tile column alike.  All 0 on levels
+ * the multi-pass kernels serve.  REG_ERR_STATE before reg_set_images. */
+int reg_level_split(reg_handle h, int level, int split[5]);
 
 /* Copy pyramid image `which` (0 = R, 1 = T) of a level into out
  * (m_x m_y m_z floats; device pointer if out_is_device). */

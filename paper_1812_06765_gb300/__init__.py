@@ -107,8 +107,12 @@ class Registration:
         return dict(dims=m, nodes=n, spacing=h, node_spacing=H)
 
     def level_tiling(self, level=0):
-        """(z segment length, CTAs) of the fused pass on a level; (0, 0) for multi-pass levels."""
+        """(longest z segment, CTAs) of the fused pass on a level; (0, 0) for multi-pass levels."""
         return _lib.reg_level_tiling(self.h, level)
+
+    def level_split(self, level=0):
+        """(l1, n1, l2, n2, lr): the fused pass's z segments on a level; zeros for multi-pass levels."""
+        return _lib.reg_level_split(self.h, level)
 
     def node_shape(self, level=0):
         n = self.level_info(level)["nodes"]

@@ -73,6 +73,7 @@ def lib():
         L.reg_set_images.argtypes = [vp, fp, fp, ip, dp, ctypes.c_int]
         L.reg_level_info.argtypes = [vp, ctypes.c_int, ip, ip, dp, dp]
         L.reg_level_tiling.argtypes = [vp, ctypes.c_int, ip, ip]
+        L.reg_level_split.argtypes = [vp, ctypes.c_int, ip]
         L.reg_get_level_image.argtypes = [vp, ctypes.c_int, ctypes.c_int, fp, ctypes.c_int]
         L.reg_eval_objective_grad.argtypes = [vp, ctypes.c_int, fp, fp, dp, dp, dp]
         L.reg_prolong.argtypes = [vp, ctypes.c_int, fp, fp]
@@ -88,7 +89,8 @@ def lib():
         L.reg_register_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(fp), ctypes.c_int,
                                          ctypes.POINTER(RegStats)]
         L.reg_register_batch.restype = ctypes.c_int
-        for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_level_tiling", "reg_last_ngf_ms",
+        for name in ("reg_create", "reg_set_images", "reg_level_info", "reg_level_tiling", "reg_level_split",
+                     "reg_last_ngf_ms",
                      "reg_get_level_image",
                      "reg_eval_objective_grad", "reg_prolong", "reg_lbfgs_direction", "reg_register",
                      "reg_destroy"):
@@ -153,6 +155,12 @@ def reg_level_tiling(h, level):
     tz, tiles = ctypes.c_int(), ctypes.c_int()
     check(h, lib().reg_level_tiling(h, int(level), ctypes.byref(tz), ctypes.byref(tiles)))
     return tz.value, tiles.value
+
+
+def reg_level_split(h, level):
+    v = (ctypes.c_int * 5)()
+    check(h, lib().reg_level_split(h, int(level), v))
+    return tuple(v)
 
 
 def reg_get_level_image(h, level, which, out_ptr, out_is_device):

@@ -178,30 +178,36 @@ __device__ __forceinline__ float ldimg_zero_ext(const IMG *T, int mx, int my, in
 // column).
 __device__ __forceinline__ void tile_seg_col(const FusedSplit &sp, int ncols, int id, int &s, int &col)
 {
-    int len[3] = {sp.l1, sp.l2, sp.lr}, start[3] = {0, sp.n1, sp.n1 + sp.n2};
-    int cnt[3] = {sp.n1, sp.n2, sp.lr > 0 ? 1 : 0};
-    int ord[3] = {0, 1, 2};
-#pragma unroll
-    for (int i = 0; i < 2; i++)   // sort the three groups by length, descending (stable)
-#pragma unroll
-        for (int j = 0; j < 2 - i; j++)
-            if (len[ord[j + 1]] > len[ord[j]]) {
-                const int t = ord[j];
-                ord[j] = ord[j + 1];
-                ord[j + 1] = t;
-            }
-    s = 0;
-    col = 0;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const int gidx = ord[k], block = cnt[gidx] * ncols;
-        if (id < block) {
-            s = start[gidx] + id / ncols;
-            col = id - (id / ncols) * ncols;
-            return;
+    // groups (length, first segment, segments), sorted by length, descending and stable
+    int la = sp.l1, sa = 0, ca = sp.n1;
+    int lb = sp.l2, sb = sp.n1, cb = sp.n2;
+    int lc = sp.lr, sc = sp.n1 + sp.n2, cc = sp.lr > 0 ? 1 : 0;
+    auto swap3 = [](int &l0, int &s0, int &c0, int &l1, int &s1, int &c1) {
+        int t = l0; l0 = l1; l1 = t;
+        t = s0; s0 = s1; s1 = t;
+        t = c0; c0 = c1; c1 = t;
+    };
+    if (lb > la)
+        swap3(la, sa, ca, lb, sb, cb);
+    if (lc > lb)
+        swap3(lb, sb, cb, lc, sc, cc);
+    if (lb > la)
+        swap3(la, sa, ca, lb, sb, cb);
+    int first = sa;
+    if (id >= ca * ncols) {
+        id -= ca * ncols;
+        first = sb;
+        if (id >= cb * ncols) {
+            id -= cb * ncols;
+            first = sc;
         }
-        id -= block;
     }
+    (void)la;
+    (void)lc;
+    (void)cc;
+    const int k = id / ncols;
+    s = first + k;
+    col = id - k * ncols;
 }
 
 // One output tile (launch-order id, see tile_seg_col) of the fused pass; sm is

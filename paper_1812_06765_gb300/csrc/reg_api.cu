@@ -508,6 +508,23 @@ int reg_level_tiling(reg_handle c, int level, int *tz, int *tiles)
     return REG_OK;
 }
 
+int reg_level_split(reg_handle c, int level, int split[5])
+{
+    if (!c || !split) return set_err(c, REG_ERR_ARG, "reg_level_split: NULL argument");
+    if (!c->have_images) return set_err(c, REG_ERR_STATE, "reg_level_split: no images set");
+    if (level < 0 || level >= c->levels)
+        return set_err(c, REG_ERR_ARG, "reg_level_split: level %d out of range", level);
+    FusedSplit sp;
+    if (use_fused(c, level))
+        sp = fused_split(c->L[level], c->num_sms);
+    split[0] = sp.l1;
+    split[1] = sp.n1;
+    split[2] = sp.l2;
+    split[3] = sp.n2;
+    split[4] = sp.lr;
+    return REG_OK;
+}
+
 int reg_level_info(reg_handle c, int level, int img_dims[3], int node_dims[3], double spacing_mm[3],
                    double node_spacing_mm[3])
 {

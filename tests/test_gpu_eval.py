@@ -303,6 +303,7 @@ def test_uneven_z_splits_match_oracle(reg_mod, orc, split):
     cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_split=split)
     r = reg_mod.Registration(cfg).set_images(R, T, h)
     l1, n1, l2, n2, lr = split
+    assert r.level_split(0) == split
     z, tiles = r.level_tiling(0)
     assert z == max(l1 if n1 else 0, l2 if n2 else 0, lr) and tiles == 3 * 2 * (n1 + n2 + (lr > 0))
     u = random_field(r.level_info(0)["nodes"], 73, 2.5)
