@@ -153,6 +153,14 @@ int reg_level_info(reg_handle h, int level, int img_dims[3], int node_dims[3],
  * kernels serve.  Any output pointer may be NULL. */
 int reg_level_tiling(reg_handle h, int level, int *tz, int *tiles);
 
+/* The load model's z split of the fused pass for an image of dims[3] voxels
+ * (each even) on a GPU with num_sms SMs, without a GPU or a handle: the split
+ * a handle uses when cfg.autotune = 0 (the autotuner times it among others).
+ * split[5] as in cfg.fused_split; *model_steps (nullable) = the model's
+ * duration in pipeline steps of one CTA.  REG_ERR_ARG for odd or < 4 dims or
+ * num_sms < 1. */
+int reg_fused_split_plan(const int dims[3], int num_sms, int split[5], double *model_steps);
+
 /* The z split of the fused pass on a level, in the form of cfg.fused_split:
  * split[5] = (l1, n1, l2, n2, lr), n1 segments of l1 planes, then n2 of l2,
  * then lr planes (0: no remainder), every tile column alike.  All 0 on levels

@@ -74,6 +74,8 @@ def lib():
         L.reg_level_info.argtypes = [vp, ctypes.c_int, ip, ip, dp, dp]
         L.reg_level_tiling.argtypes = [vp, ctypes.c_int, ip, ip]
         L.reg_level_split.argtypes = [vp, ctypes.c_int, ip]
+        L.reg_fused_split_plan.argtypes = [ip, ctypes.c_int, ip, dp]
+        L.reg_fused_split_plan.restype = ctypes.c_int
         L.reg_get_level_image.argtypes = [vp, ctypes.c_int, ctypes.c_int, fp, ctypes.c_int]
         L.reg_eval_objective_grad.argtypes = [vp, ctypes.c_int, fp, fp, dp, dp, dp]
         L.reg_prolong.argtypes = [vp, ctypes.c_int, fp, fp]
@@ -155,6 +157,15 @@ def reg_level_tiling(h, level):
     tz, tiles = ctypes.c_int(), ctypes.c_int()
     check(h, lib().reg_level_tiling(h, int(level), ctypes.byref(tz), ctypes.byref(tiles)))
     return tz.value, tiles.value
+
+
+def reg_fused_split_plan(dims, num_sms):
+    """(split (l1, n1, l2, n2, lr), modelled steps) of the load model; host only."""
+    d = (ctypes.c_int * 3)(*[int(v) for v in dims])
+    v = (ctypes.c_int * 5)()
+    steps = ctypes.c_double()
+    check(None, lib().reg_fused_split_plan(d, int(num_sms), v, ctypes.byref(steps)))
+    return tuple(v), steps.value
 
 
 def reg_level_split(h, level):

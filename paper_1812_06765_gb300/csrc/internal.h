@@ -191,6 +191,8 @@ int fused_tz_throughput(const Level &L);
 FusedSplit fused_split_uniform(int tz, int mz);
 // L.split, or the load model's choice if none has been set
 FusedSplit fused_split(const Level &L, int num_sms);
+// the load model's choice for an image of m voxels (host only)
+FusedSplit fused_split_plan(const int m[3], int num_sms, double *model_steps);
 // z segment length and tile grid the fused pass uses on the level
 void fused_tiling(const Level &L, int num_sms, FusedSplit *split, int *ntx, int *nty);
 // times the z splits the load model ranks best on the level's images at

@@ -803,6 +803,14 @@ static std::vector<FusedSplit> splits_ranked(const int m[3], int num_sms)
 
 FusedSplit fused_split(const Level &L, int num_sms) { return L.split.valid() ? L.split : splits_ranked(L.m, num_sms)[0]; }
 
+FusedSplit fused_split_plan(const int m[3], int num_sms, double *model_steps)
+{
+    const FusedSplit sp = splits_ranked(m, num_sms)[0];
+    if (model_steps)
+        *model_steps = SplitModel(m, num_sms).makespan(sp);
+    return sp;
+}
+
 // Throughput rule: the z segment length of TZ_CAND with the fewest pipeline
 // steps in total, ntz * (tz + 7) (ties: the longer one).  The right choice
 // when other work keeps every SM busy (a batch of pairs); a single pair alone

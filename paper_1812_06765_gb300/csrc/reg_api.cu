@@ -508,6 +508,23 @@ int reg_level_tiling(reg_handle c, int level, int *tz, int *tiles)
     return REG_OK;
 }
 
+int reg_fused_split_plan(const int dims[3], int num_sms, int split[5], double *model_steps)
+{
+    if (!dims || !split) return set_err(nullptr, REG_ERR_ARG, "reg_fused_split_plan: NULL argument");
+    if (num_sms < 1) return set_err(nullptr, REG_ERR_ARG, "reg_fused_split_plan: num_sms must be >= 1");
+    for (int d = 0; d < 3; d++)
+        if (dims[d] < 4 || (dims[d] & 1))
+            return set_err(nullptr, REG_ERR_ARG, "reg_fused_split_plan: dims[%d] = %d must be even and >= 4", d,
+                           dims[d]);
+    const FusedSplit sp = fused_split_plan(dims, num_sms, model_steps);
+    split[0] = sp.l1;
+    split[1] = sp.n1;
+    split[2] = sp.l2;
+    split[3] = sp.n2;
+    split[4] = sp.lr;
+    return REG_OK;
+}
+
 int reg_level_split(reg_handle c, int level, int split[5])
 {
     if (!c || !split) return set_err(c, REG_ERR_ARG, "reg_level_split: NULL argument");
