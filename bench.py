@@ -199,9 +199,15 @@ def committed_profile(kernel, digest, workload_name, split):
     e = d.get(kernel)
     if not e or e.get("source_digest") != digest:
         return {}
-    if e.get("workload") != workload_name or e.get("fused_split") != list(split):
+    if e.get("workload") != workload_name or split_lengths(e.get("fused_split", [0] * 5)) != split_lengths(split):
         return {}
     return e
+
+
+def split_lengths(split):
+    """Segment lengths of a split, sorted: splits with the same lengths launch the same tiles."""
+    l1, n1, l2, n2, lr = split
+    return sorted([l1] * n1 + [l2] * n2 + ([lr] if lr else []), reverse=True)
 
 
 def split_partial_floats_per_column(split):
