@@ -394,18 +394,23 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             a_issue(zA + 1, std::integral_constant<bool, ODD>{}, false);
         // ---- B: v on plane zA - 2 (rows 1 .. 30)
         const int zB = zA - 2;
-        if (rowB && zB >= z0 - 1 && zB <= zend) {
+        if (zB >= z0 - 1 && zB <= zend) {
+            // the pair's own T~ and R (every row), and its x neighbours from the
+            // threads beside it: column 2tx - 1 is thread tx - 1's second column,
+            // 2tx + 2 thread tx + 1's first (lanes 0 and 31 get their own values;
+            // their v is never read)
+            const int o0 = (zB & 3) * PLANE + sp;
+            const float *T0 = sm + OFF_T + o0, *R0 = sm + OFF_R + o0;
+            const float2 t0 = lds2(T0), r0 = lds2(R0);
+            const float tl = __shfl_up_sync(0xffffffffu, t0.y, 1, BX), tr = __shfl_down_sync(0xffffffffu, t0.x, 1, BX);
+            const float rl = __shfl_up_sync(0xffffffffu, r0.y, 1, BX), rr = __shfl_down_sync(0xffffffffu, r0.x, 1, BX);
             float va[3] = {0.f, 0.f, 0.f}, vb[3] = {0.f, 0.f, 0.f};
-            if ((intA || intB) && zB >= 1 && zB <= mz - 2) {
-                const int o0 = (zB & 3) * PLANE + sp;
+            if (rowB && (intA || intB) && zB >= 1 && zB <= mz - 2) {
                 const int op = ((zB + 1) & 3) * PLANE + sp, om = ((zB - 1) & 3) * PLANE + sp;
-                const float *T0 = sm + OFF_T + o0, *R0 = sm + OFF_R + o0;
-                const float2 t0 = lds2(T0), typ = lds2(T0 + CW), tym = lds2(T0 - CW);
+                const float2 typ = lds2(T0 + CW), tym = lds2(T0 - CW);
                 const float2 tzp = lds2(sm + OFF_T + op), tzm = lds2(sm + OFF_T + om);
-                const float tl = T0[-1], tr = T0[2];
-                const float2 r0 = lds2(R0), ryp = lds2(R0 + CW), rym = lds2(R0 - CW);
+                const float2 ryp = lds2(R0 + CW), rym = lds2(R0 - CW);
                 const float2 rzp = lds2(sm + OFF_R + op), rzm = lds2(sm + OFF_R + om);
-                const float rl = R0[-1], rr = R0[2];
                 const bool out = outxy && zB >= z0 && zB < zend;
                 if (intA) {
                     const float av[3] = {(t0.y - tl) * hx, (typ.x - tym.x) * hy, (tzp.x - tzm.x) * hz};
@@ -422,21 +427,24 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                         psi_sum.add(psi);
                 }
             }
-            float *vq = sm + OFF_V + (zB & 3) * 3 * PLANE + sp;
-            sts2(vq, va[0], vb[0]);
-            sts2(vq + PLANE, va[1], vb[1]);
-            sts2(vq + 2 * PLANE, va[2], vb[2]);
+            if (rowB) {
+                float *vq = sm + OFF_V + (zB & 3) * 3 * PLANE + sp;
+                sts2(vq, va[0], vb[0]);
+                sts2(vq + PLANE, va[1], vb[1]);
+                sts2(vq + 2 * PLANE, va[2], vb[2]);
+            }
         }
         // ---- C: r on plane zA - 4 (rows 2 .. 29), x reduction into node columns
         const int zC = zA - 4;
         if (rowC && zC >= z0 && zC < zend) {   // uniform per warp (a warp holds rows 2w, 2w + 1)
             float ra[3] = {0.f, 0.f, 0.f}, rb[3] = {0.f, 0.f, 0.f};
+            // v_x of the pair and of its x neighbours (columns 2tx - 1, 2tx + 2) from the threads beside it
+            const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + sp;
+            const float2 vx = lds2(V0);
+            const float vl = __shfl_up_sync(0xffffffffu, vx.y, 1, BX), vr = __shfl_down_sync(0xffffffffu, vx.x, 1, BX);
             if (outxy && col_in && zC < mz) {
-                const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + sp;
                 const float *Vzm = sm + OFF_V + ((zC - 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
                 const float *Vzp = sm + OFF_V + ((zC + 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
-                const float2 vx = lds2(V0);
-                const float vl = V0[-1], vr = V0[2];
                 const float2 vyp = lds2(V0 + PLANE + CW), vym = lds2(V0 + PLANE - CW);
                 const float2 vzm = lds2(Vzm), vzp = lds2(Vzp);
                 const float gja = half_hbar * ((vl - vx.y) * hx + (vym.x - vyp.x) * hy + (vzm.x - vzp.x) * hz);
