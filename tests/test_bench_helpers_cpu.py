@@ -1,0 +1,43 @@
+"""Host helpers of bench.py (no GPU): split bookkeeping of the roofline line
+and the matching of committed ncu counters to a run."""
+import json
+import os
+
+import bench
+
+
+def test_split_lengths_ignore_the_z_order():
+    assert bench.split_lengths((160, 1, 80, 1, 16)) == bench.split_lengths((80, 1, 16, 1, 160)) == [160, 80, 16]
+    assert bench.split_lengths((86, 2, 0, 0, 84)) == [86, 86, 84]
+    assert bench.split_lengths((4, 16, 0, 0, 0)) == [4] * 16
+
+
+def test_partial_floats_per_column_count_node_planes():
+    # a segment of len planes keeps len / 2 + 1 node planes of 3 x 15 x 15 entries
+    entries = 3 * 15 * 15
+    assert bench.split_partial_floats_per_column((160, 1, 80, 1, 16)) == (81 + 41 + 9) * entries
+    assert bench.split_partial_floats_per_column((4, 16, 0, 0, 0)) == 16 * 3 * entries
+    assert bench.split_partial_floats_per_column((0, 0, 0, 0, 70)) == 36 * entries
+
+
+def test_committed_profile_needs_source_workload_and_split(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    entry = {"source_digest": "abc", "workload": "c2_ct256_4level", "fused_split": [160, 1, 80, 1, 16],
+             "dram_bytes_per_launch_full_size": 1, "warp_instructions_per_launch": 2}
+    with open(os.path.join(tmp_path, "profiles", "traffic.json"), "w") as f:
+        json.dump({"objective_pass_fused": entry}, f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    get = bench.committed_profile
+    assert get("objective_pass_fused", "abc", "c2_ct256_4level", (80, 1, 16, 1, 160))["warp_instructions_per_launch"] == 2
+    assert get("objective_pass_fused", "abd", "c2_ct256_4level", (160, 1, 80, 1, 16)) == {}   # source changed
+    assert get("objective_pass_fused", "abc", "c3_lung256x256x112_4level", (160, 1, 80, 1, 16)) == {}
+    assert get("objective_pass_fused", "abc", "c2_ct256_4level", (86, 2, 0, 0, 84)) == {}   # other tiling
+    assert get("objective_pass_multipass", "abc", "c2_ct256_4level", (160, 1, 80, 1, 16)) == {}
+
+
+def test_source_digest_follows_the_sources(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "a.cu").write_text("x")
+    d1 = bench.source_digest(["a.cu"])
+    (tmp_path / "a.cu").write_text("y")
+    assert bench.source_digest(["a.cu"]) != d1
