@@ -151,39 +151,27 @@ class Registration:
 
     # -- registration -------------------------------------------------------
     def register(self, u_init=None, out="torch"):
-        """Run the multilevel registration; returns (u on the finest nodes, stats dict)."""
-        shape = self.node_shape(0)
-        if out == "pinned":   # page-locked host tensor: the device-to-host copy runs at full speed
-            u = torch.empty(shape, dtype=torch.float32, pin_memory=True)
-            uptr, dev = u.data_ptr(), False
-            iptr = None
-            if u_init is not None:
-                u_init = u_init.to(torch.float32).contiguous().pin_memory()
-                iptr = u_init.data_ptr()
-        elif out == "numpy":
-            u = np.empty(shape, dtype=np.float32)
-            uptr, dev = u.ctypes.data, False
-            if u_init is not None:
+        """Run the multilevel registration; returns (u on the finest nodes, stats dict).
+        out: "torch" (CUDA tensor), "pinned" (page-locked host tensor) or "numpy"."""
+        if out not in _OUTS:
+            raise ValueError("out must be 'torch', 'pinned' or 'numpy'")
+        u = _output_array(self.node_shape(0), out)
+        iptr = None
+        if u_init is not None:   # the start level's field, in the memory kind of the output
+            if isinstance(u_init, torch.Tensor):
+                u_init = u_init.detach()
+            if out == "numpy":
+                if isinstance(u_init, torch.Tensor):
+                    u_init = u_init.cpu().numpy()
                 u_init = np.ascontiguousarray(u_init, dtype=np.float32)
                 iptr = u_init.ctypes.data
             else:
-                iptr = None
-        else:
-            u = torch.empty(shape, dtype=torch.float32, device="cuda")
-            uptr, dev = u.data_ptr(), True
-            if u_init is not None:
-                u_init = u_init.to(device="cuda", dtype=torch.float32).contiguous()
+                u_init = torch.as_tensor(u_init, dtype=torch.float32)
+                u_init = (u_init.to("cuda") if out == "torch" else u_init.cpu().pin_memory()).contiguous()
                 iptr = u_init.data_ptr()
-            else:
-                iptr = None
-        rc, st = _lib.reg_register(self.h, uptr, dev, iptr)
-        L = st.levels
-        stats = dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L],
-                     level_status=list(st.level_status)[:L], J=list(st.J)[:L], J_final=st.J_final,
-                     D_final=st.D_final, S_final=st.S_final, seconds=st.seconds,
-                     kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L],
-                     tiling=list(st.tiling)[:L])
-        return u, stats
+        uptr = u.ctypes.data if out == "numpy" else u.data_ptr()
+        rc, st = _lib.reg_register(self.h, uptr, out == "torch", iptr)
+        return u, _stats_dict(rc, st)
 
     def _node_tensor(self, u, level):
         shape = self.node_shape(level)
@@ -222,10 +210,23 @@ class RegObjective(torch.autograd.Function):
         return (gJ.to(grad.dtype) * grad).reshape(grad.shape), None, None
 
 
+_OUTS = ("torch", "pinned", "numpy")
+
+
+def _output_array(shape, out):
+    """Result array of a registration: a CUDA tensor, a page-locked host tensor
+    (the device-to-host copy runs at full speed) or a numpy array."""
+    if out == "torch":
+        return torch.empty(shape, dtype=torch.float32, device="cuda")
+    if out == "pinned":
+        return torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    return np.empty(shape, dtype=np.float32)
+
+
 def _stats_dict(rc, st):
     L = st.levels
     return dict(status=rc, iters=list(st.iters)[:L], evals=list(st.evals)[:L], level_status=list(st.level_status)[:L],
-                J=list(st.J)[:L], J_final=st.J_final, D_final=st.D_final, S_final=st.S_final,
+                J=list(st.J)[:L], J_final=st.J_final, D_final=st.D_final, S_final=st.S_final, seconds=st.seconds,
                 kernel_launches=st.kernel_launches, level_seconds=list(st.level_seconds)[:L],
                 tiling=list(st.tiling)[:L])
 
@@ -234,17 +235,9 @@ def register_batch(regs, out="torch"):
     """Register the pairs of several Registration handles together (one graph
     launch per pyramid level for all of them); returns a list of (u, stats).
     out: "torch" (CUDA tensors), "pinned" (page-locked host tensors) or "numpy"."""
-    if out not in ("torch", "pinned", "numpy"):
+    if out not in _OUTS:
         raise ValueError("out must be 'torch', 'pinned' or 'numpy'")
-    outs = []
-    for r in regs:
-        shape = r.node_shape(0)
-        if out == "torch":
-            outs.append(torch.empty(shape, dtype=torch.float32, device="cuda"))
-        elif out == "pinned":
-            outs.append(torch.empty(shape, dtype=torch.float32, pin_memory=True))
-        else:
-            outs.append(np.empty(shape, dtype=np.float32))
+    outs = [_output_array(r.node_shape(0), out) for r in regs]
     ptrs = [o.ctypes.data if out == "numpy" else o.data_ptr() for o in outs]
     rc, stats = _lib.reg_register_batch([r.h for r in regs], ptrs, out == "torch")
     return [(o, _stats_dict(rc, s)) for o, s in zip(outs, stats)]
