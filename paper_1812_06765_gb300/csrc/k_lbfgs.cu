@@ -802,7 +802,7 @@ static int vec_blocks_per_sm()
 int num_blocks_for(reg_ctx *c, long long n, int threads)
 {
     long long b = (n + threads - 1) / threads;
-    long long cap = (long long)vec_blocks_per_sm() * (c->num_sms > 0 ? c->num_sms : 148);
+    long long cap = (long long)vec_blocks_per_sm() * c->num_sms;
     if (b > cap)
         b = cap;
     if (b < 1)

@@ -246,7 +246,7 @@ int cuda_err(reg_ctx *c, cudaError_t e, const char *what)
 int allocate_buffers(reg_ctx *c)
 {
     const reg_config &cfg = c->cfg;
-    long long nv0 = c->L[0].nv, nmax = 0;
+    long long nmax = 0;
     int maxpart = 0;
     for (int l = 0; l < c->levels; l++) {
         Level &L = c->L[l];
@@ -269,7 +269,6 @@ int allocate_buffers(reg_ctx *c)
             mp_vox = c->L[l].nv;
         }
     }
-    (void)nv0;
     if (mp_vox > 0) {
         CK(cudaMalloc(&es.Tw, sizeof(float) * mp_vox));
         CK(cudaMalloc(&es.dT, sizeof(float) * 3 * mp_vox));
@@ -301,10 +300,10 @@ int allocate_buffers(reg_ctx *c)
     CK(cudaMalloc(&b.P, sizeof(float) * nring * b.slots));
     CK(cudaMalloc(&b.Y, sizeof(float) * nring * b.slots));
     // the largest per-block layout is that of reg_lbfgs_direction's pair dots
-    b.max_partials = 4 * (c->num_sms > 0 ? c->num_sms : 148) * (2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM) + 1024;
+    b.max_partials = 4 * c->num_sms * (2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM) + 1024;
     CK(cudaMalloc(&b.partials, sizeof(double) * b.max_partials));
     {   // group sums and arrival counters of the vector passes (<= 4 blocks per SM)
-        const int groups = (4 * (c->num_sms > 0 ? c->num_sms : 148) + LB_RG - 1) / LB_RG;
+        const int groups = (4 * c->num_sms + LB_RG - 1) / LB_RG;
         CK(cudaMalloc(&b.gpart, sizeof(double) * groups * (2 + 4 * LB_MAXS)));
         b.cnt_len = groups + 1;
         CK(cudaMalloc(&b.cnt, sizeof(unsigned) * b.cnt_len));
