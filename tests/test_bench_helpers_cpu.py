@@ -73,3 +73,11 @@ def test_reference_arm_runs_on_rank_0_only():
                      {"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_cpu_oracle_sample_runs_for_its_time_budget():
+    from synth import CONFIGS, make_pair
+    c = CONFIGS[0]
+    p = make_pair(0, dims=(16, 16, 16))
+    rate, n, el, cores = bench.cpu_oracle_rate(p, c, 0.5)
+    assert el >= 0.5 and n >= 1 and abs(rate - n / el) < 1e-9 * rate and cores >= 1
