@@ -31,9 +31,10 @@
  * on the stream given to reg_create plus one internal side stream (the template
  * pyramid, and the curvature pass that runs beside the NGF pass), forked from
  * and joined back to that stream with events.  Calls that return host values
- * synchronise that stream.  With use_graph = 1 the level graphs carry their own
- * kernel priorities, whatever the priority of that stream: the curvature pass
- * at the device's lowest stream priority, every other kernel at the highest.
+ * synchronise that stream.  The level graphs (use_graph = 1, and every
+ * reg_register_batch) carry their own kernel priorities, whatever the priority
+ * of that stream: the curvature pass at the device's lowest stream priority,
+ * every other kernel at the highest.
  */
 #ifndef REG_H
 #define REG_H

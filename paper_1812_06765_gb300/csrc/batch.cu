@@ -234,7 +234,9 @@ cudaError_t build_batch_graph(const BatchLaunch &B, cudaStream_t cs, cudaGraphEx
         guard.active = false;
         BK(cudaStreamEndCapture(cs, &g2));
     }
-    BK(cudaGraphInstantiate(out, G, 0));
+    for (cudaGraph_t g : {G, body, ls_body})   // the curvature pass fills the SMs the fused pass leaves idle
+        BK(set_graph_kernel_priorities(g, curv_w_batch_kernel()));
+    BK(cudaGraphInstantiate(out, G, cudaGraphInstantiateFlagUseNodePriority));
     cudaGraphDestroy(G);
     return cudaSuccess;
 }

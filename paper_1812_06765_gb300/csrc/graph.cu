@@ -66,15 +66,22 @@ cudaError_t add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, c
     return add_cond(g, deps, h, cudaGraphCondTypeWhile, node, body);
 }
 
+}  // namespace
+
 // Kernel node priorities of one graph (not its conditional bodies): the
-// curvature Laplacian, which runs beside the NGF pass, at the lowest priority
-// and every other kernel at the highest, so that the block scheduler hands out
-// the NGF pass's CTAs (one per SM) first and the curvature blocks take the SMs
-// that the NGF pass's last, shorter tiles leave idle.
-cudaError_t set_kernel_priorities(cudaGraph_t g, int lowest, int highest)
+// kernel low_func (the curvature Laplacian, which runs beside the NGF pass) at
+// the device's lowest stream priority and every other kernel at the highest,
+// so that the block scheduler hands out the NGF pass's CTAs (one per SM) first
+// and the curvature blocks take the SMs that the NGF pass's last, shorter tiles
+// leave idle.  The graph must be instantiated with
+// cudaGraphInstantiateFlagUseNodePriority for the priorities to apply.
+cudaError_t set_graph_kernel_priorities(cudaGraph_t g, const void *low_func)
 {
+    int lowest = 0, highest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lowest, &highest);
     size_t n = 0;
-    cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+    if (e == cudaSuccess)
+        e = cudaGraphGetNodes(g, nullptr, &n);
     if (e != cudaSuccess || n == 0)
         return e;
     std::vector<cudaGraphNode_t> nodes(n);
@@ -89,13 +96,11 @@ cudaError_t set_kernel_priorities(cudaGraph_t g, int lowest, int highest)
         if (e != cudaSuccess)
             break;
         cudaLaunchAttributeValue v = {};
-        v.priority = kp.func == curv_w_kernel() ? lowest : highest;
+        v.priority = kp.func == low_func ? lowest : highest;
         e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
     }
     return e;
 }
-
-}  // namespace
 
 #define GK(call)                                  \
     do {                                          \
@@ -186,10 +191,8 @@ cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out)
         GK(cudaStreamEndCapture(cs, &g2));
     }
     lbfgs_set_graph_handles(0, 0, 0);
-    int lowest = 0, highest = 0;
-    GK(cudaDeviceGetStreamPriorityRange(&lowest, &highest));
     for (cudaGraph_t g : {G, body, redo_body, ls_body})
-        GK(set_kernel_priorities(g, lowest, highest));
+        GK(set_graph_kernel_priorities(g, curv_w_kernel()));
     GK(cudaGraphInstantiate(out, G, cudaGraphInstantiateFlagUseNodePriority));
     cudaGraphDestroy(G);
     c->launches = launches0;

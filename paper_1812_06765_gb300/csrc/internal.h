@@ -209,8 +209,11 @@ cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alph
 constexpr long long GATHER_SPLIT_BLOCKS = 4096;
 
 cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out);
-// the curvature Laplacian kernel that runs beside the NGF pass (to tell its graph nodes apart)
+// the curvature Laplacian kernels that run beside the NGF pass (to tell their graph nodes apart)
 const void *curv_w_kernel();
+const void *curv_w_batch_kernel();
+// kernel nodes of g: low_func at the lowest priority, the others at the highest
+cudaError_t set_graph_kernel_priorities(cudaGraph_t g, const void *low_func);
 int eval_kernel_count(const reg_ctx *c, int level);
 
 // the fused pass serves levels whose grids have ratio exactly 2; others use the multi-pass kernels

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(512) k_finalize_batch(const PairLevel *__restr
 }  // namespace
 
 const void *curv_w_kernel() { return reinterpret_cast<const void *>(k_curv_w); }
+const void *curv_w_batch_kernel() { return reinterpret_cast<const void *>(k_curv_w_batch); }
 
 cudaError_t launch_curv_w_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
                                 cudaStream_t s)
