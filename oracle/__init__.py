@@ -88,6 +88,10 @@ def lib():
             L.orc_lbfgs_level.restype = ctypes.c_int
             L.orc_level_dims.argtypes = [ip, ctypes.POINTER(Config), ctypes.c_int, ip, ip]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_compensated_sums.argtypes = [ctypes.c_int]
+            L.orc_set_compensated_sums.restype = None
+            L.orc_sum.argtypes = [ctypes.c_size_t, dp]
+            L.orc_sum.restype = ctypes.c_double
     return _lib
 
 
@@ -109,6 +113,18 @@ def _f64(a):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_compensated_sums(on):
+    """Compensated (Neumaier) summation in every reduction of the oracle (default off:
+    the plain running sum; both add the terms in index order)."""
+    lib().orc_set_compensated_sums(int(bool(on)))
+
+
+def reduce_sum(a):
+    """The oracle's reduction of a 1-D array (plain or compensated, as set)."""
+    a = _f64(np.ravel(a))
+    return lib().orc_sum(a.size, _dp(a))
 
 
 def node_spacing(dims, spacing, nodes):

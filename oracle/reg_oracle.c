@@ -56,6 +56,45 @@ static double hat(double t)
 
 static size_t vol(const int m[3]) { return (size_t)m[0] * (size_t)m[1] * (size_t)m[2]; }
 
+/* Every reduction of the oracle (D, S, the L-BFGS dot products and norms) adds
+ * its terms one by one in index order.  With compensated sums switched on it
+ * carries the rounding error of each addition in a second word (Neumaier's
+ * variant of Kahan summation, 1974), so the result is the exact sum up to
+ * about one rounding; with them off (the default) it is the plain running
+ * sum. */
+static int g_compensated = 0;
+
+void orc_set_compensated_sums(int on) { g_compensated = on != 0; }
+
+typedef struct {
+    double s, c;
+} acc_t;
+
+static void acc_add(acc_t *a, double x)
+{
+    if (!g_compensated) {
+        a->s += x;
+        return;
+    }
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double acc_value(const acc_t *a) { return g_compensated ? a->s + a->c : a->s; }
+
+/* the reduction above applied to a[0 .. n-1] (exported to pin it) */
+double orc_sum(size_t n, const double *a)
+{
+    acc_t s = {0.0, 0.0};
+    for (size_t i = 0; i < n; i++)
+        acc_add(&s, a[i]);
+    return acc_value(&s);
+}
+
 void orc_node_spacing(const int m[3], const double h[3], const int mn[3], double H[3])
 {
     for (int d = 0; d < 3; d++)
@@ -268,11 +307,11 @@ double orc_ngf(const int m[3], const double h[3], const double *Tw, const double
                 for (int d = 0; d < 3; d++)
                     v[d * nv + i] = -2.0 * c * (b[d] / (na * nb) - c * a[d] / (na * na));
             }
-    double D = 0.0;
+    acc_t D = {0.0, 0.0};
     for (size_t i = 0; i < nv; i++)
-        D += psi[i];
+        acc_add(&D, psi[i]);
     free(psi);
-    return 0.5 * h[0] * h[1] * h[2] * D;
+    return 0.5 * h[0] * h[1] * h[2] * acc_value(&D);
 }
 
 /* g_j = d D / d Tw_j = hbar/2 sum_d (v_d[j - e_d] - v_d[j + e_d]) / (2 h_d),
@@ -315,7 +354,7 @@ double orc_curvature(const int mn[3], const double H[3], const double *u, double
     double hy = H[0] * H[1] * H[2];
     double iH2[3] = {1.0 / (H[0] * H[0]), 1.0 / (H[1] * H[1]), 1.0 / (H[2] * H[2])};
     double *w = (double *)malloc(sizeof(double) * nn);
-    double S = 0.0;
+    acc_t S = {0.0, 0.0};
     for (int c = 0; c < 3; c++) {
         const double *uc = u + c * nn;
 #pragma omp parallel for schedule(static)
@@ -331,7 +370,7 @@ double orc_curvature(const int mn[3], const double H[3], const double *u, double
                     w[k] = lap;
                 }
         for (size_t k = 0; k < nn; k++)
-            S += w[k] * w[k];
+            acc_add(&S, w[k] * w[k]);
         if (gradS) {
             double *gc = gradS + c * nn;
 #pragma omp parallel for schedule(static)
@@ -351,7 +390,7 @@ double orc_curvature(const int mn[3], const double H[3], const double *u, double
         }
     }
     free(w);
-    return 0.5 * hy * S;
+    return 0.5 * hy * acc_value(&S);
 }
 
 /* ---------------------------------------------------------------------------
@@ -489,10 +528,10 @@ void orc_prolong(const int mn_c[3], const double ext_c[3], const double *uc, con
  * ------------------------------------------------------------------------- */
 static double dot(size_t n, const double *a, const double *b)
 {
-    double s = 0.0;
+    acc_t s = {0.0, 0.0};
     for (size_t i = 0; i < n; i++)
-        s += a[i] * b[i];
-    return s;
+        acc_add(&s, a[i] * b[i]);
+    return acc_value(&s);
 }
 
 void orc_two_loop(size_t n, int count, const double *S, const double *Y, const double *g, double gamma,

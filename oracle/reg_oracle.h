@@ -121,6 +121,12 @@ int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const do
 
 int orc_num_threads(void);
 
+/* 1: every reduction (D, S, dot products, norms) uses compensated summation in
+ * index order; 0 (default): the plain running sum in index order. */
+void orc_set_compensated_sums(int on);
+/* that reduction of a[0 .. n-1] */
+double orc_sum(size_t n, const double *a);
+
 #ifdef __cplusplus
 }
 #endif

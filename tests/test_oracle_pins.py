@@ -425,3 +425,46 @@ def test_objective_on_cell_faces_takes_the_right_cell(orc):
     ref = np.stack([orc.PT(dims, h, nodes, g * dT[c]) for c in range(3)])
     assert D == pytest.approx(D_ref, rel=1e-14) and S == 0.0
     np.testing.assert_allclose(grad, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.fixture
+def compensated(orc):
+    orc.set_compensated_sums(True)
+    yield orc
+    orc.set_compensated_sums(False)
+
+
+def test_reduction_plain_and_compensated_definitions(orc, compensated):
+    """Compensated sums are exact where the running sum loses a term to rounding;
+    on many terms they match the correctly rounded sum (math.fsum, Shewchuk's
+    exact summation) to one rounding."""
+    import math
+    a = np.array([1e16, 1.0, -1e16])
+    assert compensated.reduce_sum(a) == 1.0
+    rng = np.random.Generator(np.random.PCG64(5))
+    x = rng.standard_normal(200_000) * 10.0 ** rng.integers(-8, 9, 200_000)
+    exact = math.fsum(x)
+    assert abs(compensated.reduce_sum(x) - exact) <= 2 * np.spacing(abs(exact))
+    orc.set_compensated_sums(False)
+    assert orc.reduce_sum(a) == 0.0                              # (1e16 + 1) rounds to 1e16
+    assert orc.reduce_sum(x) == float(np.cumsum(x)[-1])          # the running sum in index order
+
+
+def test_objective_reduction_order_is_far_below_the_tolerances(orc):
+    """The FP64 objective with compensated reductions agrees with the plain
+    index-order sums to 1e-12: the oracle's own rounding is negligible against
+    the 1e-5 (J) and 1e-4 (grad) parity tolerances."""
+    dims, h = (40, 36, 28), (1.0, 1.1, 0.9)
+    R = random_image(dims, 61).astype(np.float64)
+    T = random_image(dims, 62).astype(np.float64)
+    nodes = (21, 19, 15)
+    u = random_field(nodes, 63, 2.0).astype(np.float64)
+    plain = orc.objective(dims, h, R, T, nodes, u, 0.05, 0.05, 5.0)
+    orc.set_compensated_sums(True)
+    try:
+        comp = orc.objective(dims, h, R, T, nodes, u, 0.05, 0.05, 5.0)
+    finally:
+        orc.set_compensated_sums(False)
+    for a, b in zip(plain[:3], comp[:3]):
+        assert abs(a - b) <= 1e-12 * abs(b)
+    assert np.array_equal(plain[3], comp[3])   # the gradient holds no global reduction
