@@ -164,6 +164,22 @@ int reg_level_tiling(reg_handle h, int level, int *tz, int *tiles);
  * num_sms < 1. */
 int reg_fused_split_plan(const int dims[3], int num_sms, int split[5], double *model_steps);
 
+/* The per-dimension grid-conversion tables that reg_set_images uploads for one
+ * axis of m voxels of spacing h and n nodes (host only, no GPU; Sec. 2.2,
+ * Eq. 3: the index sets and weights of P and P^T are fixed beforehand and
+ * separately for each dimension).  With voxel centres at t_i = (i + 1/2) h / H
+ * in node units, H = m h / (n - 1), and the hat function phi(t) = max(0, 1 - |t|):
+ *   P:   k0[i] = floor(t_i) clamped to 0 .. n - 2 and w1[i] = t_i - k0[i]
+ *        (voxel i takes 1 - w1 of node k0 and w1 of node k0 + 1); m entries each;
+ *   P^T: node k gathers cnt[k] voxels from first[k] on, voxel first[k] + j with
+ *        weight w[k * max_w + j] = phi(t_{first[k] + j} - k) > 0 (zero-padded to
+ *        max_w); n entries in first and cnt, n * max_w in w.
+ * Caller-owned host arrays; any may be NULL to skip it.  *needed_w (nullable)
+ * receives the largest cnt.  REG_ERR_ARG for m < 4, n < 3, h not finite and
+ * > 0, or max_w below the largest cnt when w is given. */
+int reg_axis_tables(int m, double h, int n, int *k0, float *w1, int *first, int *cnt, float *w, int max_w,
+                    int *needed_w);
+
 /* The z split of the fused pass on a level, in the form of cfg.fused_split:
  * split[5] = (l1, n1, l2, n2, lr), n1 segments of l1 planes, then n2 of l2,
  * then lr planes (0: no remainder), every tile column alike.  All 0 on levels

@@ -76,6 +76,8 @@ def lib():
         L.reg_level_split.argtypes = [vp, ctypes.c_int, ip]
         L.reg_fused_split_plan.argtypes = [ip, ctypes.c_int, ip, dp]
         L.reg_fused_split_plan.restype = ctypes.c_int
+        L.reg_axis_tables.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ip, fp, ip, ip, fp, ctypes.c_int, ip]
+        L.reg_axis_tables.restype = ctypes.c_int
         L.reg_get_level_image.argtypes = [vp, ctypes.c_int, ctypes.c_int, fp, ctypes.c_int]
         L.reg_eval_objective_grad.argtypes = [vp, ctypes.c_int, fp, fp, dp, dp, dp]
         L.reg_prolong.argtypes = [vp, ctypes.c_int, fp, fp]
@@ -166,6 +168,20 @@ def reg_fused_split_plan(dims, num_sms):
     steps = ctypes.c_double()
     check(None, lib().reg_fused_split_plan(d, int(num_sms), v, ctypes.byref(steps)))
     return tuple(v), steps.value
+
+
+def reg_axis_tables(m, h, n):
+    """(k0, w1, first, cnt, w) of one axis as numpy arrays (w: n x max weights); host only."""
+    import numpy as np
+    need = ctypes.c_int()
+    check(None, lib().reg_axis_tables(int(m), float(h), int(n), None, None, None, None, None, 0, ctypes.byref(need)))
+    k0, first, cnt = (np.zeros(int(m), np.int32), np.zeros(int(n), np.int32), np.zeros(int(n), np.int32))
+    w1, w = np.zeros(int(m), np.float32), np.zeros((int(n), need.value), np.float32)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)   # noqa: E731
+    check(None, lib().reg_axis_tables(int(m), float(h), int(n), ctypes.cast(ptr(k0), ctypes.POINTER(ctypes.c_int)),
+                                      ptr(w1), ctypes.cast(ptr(first), ctypes.POINTER(ctypes.c_int)),
+                                      ctypes.cast(ptr(cnt), ctypes.POINTER(ctypes.c_int)), ptr(w), need.value, None))
+    return k0, w1, first, cnt, w
 
 
 def reg_level_split(h, level):

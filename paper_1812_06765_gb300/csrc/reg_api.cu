@@ -131,47 +131,58 @@ cudaError_t upload(T **dst, const std::vector<T> &src)
 // Per-dimension tables of P (voxel i -> node k0, weight of k0 + 1) and of P^T
 // (node k -> first voxel, count, weights), from the hat functions at voxel
 // centres t = (i + 1/2) h / H (Sec. 2.2, Eq. 3: weights and index sets are
-// determined beforehand, separately for each dimension).
+// determined beforehand, separately for each dimension).  Host only.
+struct AxisTables {
+    std::vector<int> k0, first, cnt;
+    std::vector<float> w1, tw;   // tw[k * maxw + j]: weight of voxel first[k] + j for node k
+    int maxw = 1;
+};
+
+AxisTables axis_tables(int m, double h, double H, int n)
+{
+    AxisTables a;
+    a.k0.resize(m);
+    a.w1.resize(m);
+    std::vector<double> t(m);
+    for (int i = 0; i < m; i++) {
+        t[i] = (i + 0.5) * h / H;
+        int k = (int)floor(t[i]);
+        if (k > n - 2) k = n - 2;
+        if (k < 0) k = 0;
+        a.k0[i] = k;
+        a.w1[i] = (float)(t[i] - k);
+    }
+    a.first.assign(n, 0);
+    a.cnt.assign(n, 0);
+    std::vector<std::vector<double>> ws(n);
+    for (int k = 0; k < n; k++) {
+        for (int i = 0; i < m; i++) {
+            double w = 1.0 - fabs(t[i] - k);
+            if (w > 0.0) {
+                if (ws[k].empty()) a.first[k] = i;
+                ws[k].push_back(w);
+            }
+        }
+        a.cnt[k] = (int)ws[k].size();
+        if (a.cnt[k] > a.maxw) a.maxw = a.cnt[k];
+    }
+    a.tw.assign((size_t)n * a.maxw, 0.f);
+    for (int k = 0; k < n; k++)
+        for (int j = 0; j < a.cnt[k]; j++) a.tw[(size_t)k * a.maxw + j] = (float)ws[k][j];
+    return a;
+}
+
 cudaError_t build_tables(Level &L)
 {
     for (int d = 0; d < 3; d++) {
-        const int m = L.m[d], n = L.n[d];
-        const double H = L.H[d], h = L.h[d];
-        std::vector<int> k0(m);
-        std::vector<float> w1(m);
-        std::vector<double> t(m);
-        for (int i = 0; i < m; i++) {
-            t[i] = (i + 0.5) * h / H;
-            int k = (int)floor(t[i]);
-            if (k > n - 2) k = n - 2;
-            if (k < 0) k = 0;
-            k0[i] = k;
-            w1[i] = (float)(t[i] - k);
-        }
-        std::vector<int> first(n, 0), cnt(n, 0);
-        std::vector<std::vector<double>> ws(n);
-        int maxw = 1;
-        for (int k = 0; k < n; k++) {
-            for (int i = 0; i < m; i++) {
-                double w = 1.0 - fabs(t[i] - k);
-                if (w > 0.0) {
-                    if (ws[k].empty()) first[k] = i;
-                    ws[k].push_back(w);
-                }
-            }
-            cnt[k] = (int)ws[k].size();
-            if (cnt[k] > maxw) maxw = cnt[k];
-        }
-        std::vector<float> tw((size_t)n * maxw, 0.f);
-        for (int k = 0; k < n; k++)
-            for (int j = 0; j < cnt[k]; j++) tw[(size_t)k * maxw + j] = (float)ws[k][j];
-        L.tmaxw[d] = maxw;
+        const AxisTables a = axis_tables(L.m[d], L.h[d], L.H[d], L.n[d]);
+        L.tmaxw[d] = a.maxw;
         cudaError_t e;
-        if ((e = upload(&L.pk0[d], k0)) != cudaSuccess) return e;
-        if ((e = upload(&L.pw1[d], w1)) != cudaSuccess) return e;
-        if ((e = upload(&L.tfirst[d], first)) != cudaSuccess) return e;
-        if ((e = upload(&L.tcnt[d], cnt)) != cudaSuccess) return e;
-        if ((e = upload(&L.tw[d], tw)) != cudaSuccess) return e;
+        if ((e = upload(&L.pk0[d], a.k0)) != cudaSuccess) return e;
+        if ((e = upload(&L.pw1[d], a.w1)) != cudaSuccess) return e;
+        if ((e = upload(&L.tfirst[d], a.first)) != cudaSuccess) return e;
+        if ((e = upload(&L.tcnt[d], a.cnt)) != cudaSuccess) return e;
+        if ((e = upload(&L.tw[d], a.tw)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -521,6 +532,28 @@ int reg_fused_split_plan(const int dims[3], int num_sms, int split[5], double *m
     split[2] = sp.l2;
     split[3] = sp.n2;
     split[4] = sp.lr;
+    return REG_OK;
+}
+
+int reg_axis_tables(int m, double h, int n, int *k0, float *w1, int *first, int *cnt, float *w, int max_w,
+                    int *needed_w)
+{
+    if (m < 4 || n < 3 || !(h > 0) || !isfinite(h))
+        return set_err(nullptr, REG_ERR_ARG, "reg_axis_tables: need m >= 4, n >= 3 and a finite h > 0");
+    const AxisTables a = axis_tables(m, h, m * h / (n - 1), n);
+    if (needed_w) *needed_w = a.maxw;
+    if (max_w < a.maxw && w)
+        return set_err(nullptr, REG_ERR_ARG, "reg_axis_tables: max_w = %d < %d weights per node", max_w, a.maxw);
+    for (int i = 0; i < m; i++) {
+        if (k0) k0[i] = a.k0[i];
+        if (w1) w1[i] = a.w1[i];
+    }
+    for (int k = 0; k < n; k++) {
+        if (first) first[k] = a.first[k];
+        if (cnt) cnt[k] = a.cnt[k];
+        if (w)
+            for (int j = 0; j < max_w; j++) w[(size_t)k * max_w + j] = j < a.maxw ? a.tw[(size_t)k * a.maxw + j] : 0.f;
+    }
     return REG_OK;
 }
 

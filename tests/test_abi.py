@@ -81,3 +81,58 @@ def test_product_path_has_no_cpu_fallback():
             "try:\n    _lib.lib()\nexcept RuntimeError as e:\n    print('raised', e)\n") % ROOT
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert "raised" in out.stdout, out.stdout + out.stderr
+
+
+def _golden_pt_rows():
+    with open(os.path.join(ROOT, "tests", "golden", "pt_tables.txt")) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def test_axis_tables_match_the_hand_derived_eq3_tables(libreg):
+    """The P^T index sets and weights the library uploads equal the hand-derived
+    Eq. 3 tables (unit spacing; FP32 weights)."""
+    from fractions import Fraction
+    rows = _golden_pt_rows()
+    assert rows
+    for r in rows:
+        m, n, k, first = int(r[0]), int(r[1]), int(r[2]), int(r[3])
+        w_ref = [float(Fraction(w)) for w in r[4:]]
+        _, _, f, cnt, w = libreg.reg_axis_tables(m, 1.0, n)
+        assert f[k] == first and cnt[k] == len(w_ref), r
+        assert abs(w[k, :cnt[k]] - w_ref).max() <= 1e-7, r
+        assert not w[k, cnt[k]:].any()
+
+
+@pytest.mark.parametrize("m,h,n", [(256, 1.0, 129), (112, 2.5, 57), (1577, 0.75, 789), (33, 1.5, 9),
+                                   (37, 1.1, 19), (8, 0.97, 3)])
+def test_axis_tables_agree_with_the_oracle_and_with_each_other(libreg, m, h, n):
+    """P^T tables against the FP64 oracle's; the P entries (k0, w1) are the
+    same weights seen from the voxel side: voxel i has 1 - w1 at node k0 and w1
+    at k0 + 1, and nothing elsewhere."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    k0, w1, first, cnt, w = libreg.reg_axis_tables(m, h, n)
+    dense = np.zeros((n, m))
+    for k in range(n):
+        f_o, w_o = oracle.PT_table(m, h, n, k)
+        assert first[k] == f_o and cnt[k] == len(w_o), k
+        assert np.abs(w[k, :cnt[k]] - w_o).max() <= 1e-6
+        dense[k, first[k]:first[k] + cnt[k]] = w[k, :cnt[k]]
+    from_p = np.zeros((n, m))
+    from_p[k0, np.arange(m)] += 1.0 - w1
+    from_p[k0 + 1, np.arange(m)] += w1
+    assert k0.min() >= 0 and k0.max() <= n - 2
+    assert np.abs(dense - from_p).max() <= 1e-6
+    np.testing.assert_allclose(dense.sum(axis=0), 1.0, atol=1e-6)   # partition of unity at every voxel
+
+
+def test_axis_tables_reject_bad_arguments(libreg):
+    L = libreg.lib()
+    for m, h, n in ((3, 1.0, 3), (16, 0.0, 9), (16, float("inf"), 9), (16, 1.0, 2)):
+        assert L.reg_axis_tables(m, h, n, None, None, None, None, None, 0, None) == libreg.REG_ERR_ARG
+    import ctypes
+    import numpy as np
+    w = np.zeros((9, 3), np.float32)
+    assert L.reg_axis_tables(16, 1.0, 9, None, None, None, None, ctypes.c_void_p(w.ctypes.data), 3,
+                             None) == libreg.REG_ERR_ARG   # 4 weights per node needed
