@@ -468,3 +468,26 @@ def test_objective_reduction_order_is_far_below_the_tolerances(orc):
     for a, b in zip(plain[:3], comp[:3]):
         assert abs(a - b) <= 1e-12 * abs(b)
     assert np.array_equal(plain[3], comp[3])   # the gradient holds no global reduction
+
+
+def test_failed_line_search_ends_the_level_with_the_warning(orc):
+    """R9 on the convex quadratic J = alpha S (R = T = 0): along any descent
+    direction J(u + t p) = J + t g'p + t^2 p'Ap / 2, so the Armijo test with c1
+    within 1e-9 of 1 fails for every trial t >= 1/4.  The first search (the p0
+    direction) uses its max_backtracks trials, the level ends with the warning
+    status, no step is accepted and u stays u0."""
+    dims, h, nodes = (10, 10, 10), (1.0, 1.0, 1.0), (6, 6, 6)
+    zero = np.zeros(dims[::-1])
+    u0 = random_field(nodes, 92, 1.0).astype(np.float64)
+    for trials in (1, 3):
+        cfg = orc.make_config(levels=1, tau=0.1, alpha=2.0, mem=5, max_iter=10, c1=1.0 - 1e-9,
+                              max_backtracks=trials)
+        u, st = orc.lbfgs_level(dims, h, zero, zero, nodes, cfg, 10, u0)
+        assert st["status"] == 1 and st["iters"] == 0
+        assert st["evals"] == 1 + trials        # the objective at u0, then one per trial
+        assert np.array_equal(u, u0)
+    # the same problem with the default c1 takes its steps
+    cfg = orc.make_config(levels=1, tau=0.1, alpha=2.0, mem=5, max_iter=10)
+    u, st = orc.lbfgs_level(dims, h, zero, zero, nodes, cfg, 10, u0)
+    assert st["status"] == 0 and st["iters"] >= 1 and st["J"] < orc.objective(dims, h, zero, zero, nodes, u0, 0.1,
+                                                                               0.1, 2.0)[0]
