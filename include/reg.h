@@ -45,6 +45,8 @@ extern "C" {
 
 #define REG_MAX_LEVELS 8
 #define REG_MAX_MEM 8
+#define REG_MAX_VOXELS 2147483647LL  /* voxels of an image, and 3 x nodes of a deformation grid */
+#define REG_MAX_PLANES 65535         /* m_z of an image, n_z of a deformation grid */
 
 #define REG_OK 0
 #define REG_WARN_LINESEARCH 1  /* a level ended on a failed Armijo search; u is its last accepted iterate */
@@ -140,7 +142,11 @@ int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream);
  * two streams (Sec. 2.2 "Generating the multi-level pyramid").  R and T are
  * device pointers if ptr_is_device, else host pointers; they are copied, the
  * caller keeps ownership.  Each level must keep >= 4 voxels and >= 3 nodes
- * per dimension (REG_ERR_ARG otherwise).  Replaces previous images. */
+ * per dimension, an image holds at most REG_MAX_VOXELS voxels and
+ * REG_MAX_PLANES planes, and a deformation grid at most REG_MAX_VOXELS / 3
+ * nodes and REG_MAX_PLANES node planes (the kernels index with 32-bit
+ * integers and launch one grid row per plane); REG_ERR_ARG otherwise, and the
+ * handle keeps its previous images.  Replaces previous images. */
 int reg_set_images(reg_handle h, const float *R, const float *T, const int dims[3],
                    const double spacing_mm[3], int ptr_is_device);
 

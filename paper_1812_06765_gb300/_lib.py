@@ -14,6 +14,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "reg.h")
 
 MAX_LEVELS = 8
 MAX_MEM = 8
+MAX_VOXELS = 2147483647   # voxels of an image, and 3 x nodes of a deformation grid
+MAX_PLANES = 65535        # m_z of an image, n_z of a deformation grid
 
 REG_OK = 0
 REG_WARN_LINESEARCH = 1

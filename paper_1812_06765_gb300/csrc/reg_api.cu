@@ -395,6 +395,10 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
         if (!(spacing_mm[d] > 0) || !isfinite(spacing_mm[d]))
             return set_err(c, REG_ERR_ARG, "reg_set_images: spacing[%d] must be finite and > 0", d);
     }
+    // the kernels index a volume with 32-bit integers and launch one grid row per plane
+    if ((long long)dims[0] * dims[1] * dims[2] > REG_MAX_VOXELS || dims[2] > REG_MAX_PLANES)
+        return set_err(c, REG_ERR_ARG, "reg_set_images: %d x %d x %d voxels (at most %lld voxels and %d planes)",
+                       dims[0], dims[1], dims[2], (long long)REG_MAX_VOXELS, REG_MAX_PLANES);
     CK(cudaStreamSynchronize(c->stream));
     const reg_config &cfg = c->cfg;
     // geometry of every level
@@ -413,6 +417,10 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
         }
         L.nv = (long long)L.m[0] * L.m[1] * L.m[2];
         L.nn = (long long)L.n[0] * L.n[1] * L.n[2];
+        if (3 * L.nn > REG_MAX_VOXELS || L.n[2] > REG_MAX_PLANES)
+            return set_err(c, REG_ERR_ARG,
+                           "reg_set_images: level %d has %d x %d x %d nodes (at most %lld unknowns and %d node planes)",
+                           l, L.n[0], L.n[1], L.n[2], (long long)REG_MAX_VOXELS, REG_MAX_PLANES);
     }
     // the same grid sizes again: keep every buffer and table (the tables depend
     // only on voxel and node counts), update the spacings

@@ -136,3 +136,12 @@ def test_axis_tables_reject_bad_arguments(libreg):
     w = np.zeros((9, 3), np.float32)
     assert L.reg_axis_tables(16, 1.0, 9, None, None, None, None, ctypes.c_void_p(w.ctypes.data), 3,
                              None) == libreg.REG_ERR_ARG   # 4 weights per node needed
+
+
+def test_header_limits_match_the_binding(libreg):
+    import re
+    text = open(libreg.HEADER).read()
+    limits = dict(re.findall(r"#define (REG_MAX_\w+) (\d+)", text))
+    assert int(limits["REG_MAX_VOXELS"]) == libreg.MAX_VOXELS == 2**31 - 1
+    assert int(limits["REG_MAX_PLANES"]) == libreg.MAX_PLANES == 65535
+    assert int(limits["REG_MAX_LEVELS"]) == libreg.MAX_LEVELS and int(limits["REG_MAX_MEM"]) == libreg.MAX_MEM
