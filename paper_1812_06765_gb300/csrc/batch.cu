@@ -24,14 +24,13 @@ long long ring_stride(long long n) { return (n + 3) & ~3LL; }
 void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
 {
     const Level &L = c->L[level];
-    memset(&P, 0, sizeof P);
+    P = PairLevel{};
     P.geom = L.geom();
     FusedSplit split;
     int ntx, nty;
     fused_tiling(L, c->num_sms, &split, &ntx, &nty);
     const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
-    FusedArgs a;
-    memset(&a, 0, sizeof a);
+    FusedArgs a{};
     a.g = P.geom;
     a.T = bf16 ? static_cast<const void *>(L.Tb) : static_cast<const void *>(L.T);
     a.R = bf16 ? static_cast<const void *>(L.Rb) : static_cast<const void *>(L.R);
