@@ -127,10 +127,12 @@ typedef struct reg_stats {
 /* Library version (major * 10000 + minor * 100 + patch). */
 int reg_version(void);
 
-/* Fill *cfg with the defaults listed above.  cfg must not be NULL. */
+/* Fill *cfg with the defaults listed above (the model parameters of Sec. 2.1,
+ * Eq. 1-2, and the solver's).  cfg must not be NULL. */
 void reg_config_default(reg_config *cfg);
 
-/* Create a handle.  cfg is copied (validated here: REG_ERR_ARG on bad values).
+/* Create a handle for one registration problem of Sec. 2.1 (Eq. 1) with the
+ * parameters of cfg.  cfg is copied (validated here: REG_ERR_ARG on bad values).
  * cuda_stream is a cudaStream_t of the current device, or NULL for the legacy
  * default stream (the stream PyTorch uses unless told otherwise); the caller
  * keeps ownership of a stream it passes.  On success *out owns the handle;
@@ -150,8 +152,10 @@ int reg_create(reg_handle *out, const reg_config *cfg, void *cuda_stream);
 int reg_set_images(reg_handle h, const float *R, const float *T, const int dims[3],
                    const double spacing_mm[3], int ptr_is_device);
 
-/* Geometry of one pyramid level: image dims, node dims, voxel spacing and
- * node spacing (mm).  Any output pointer may be NULL. */
+/* Geometry of one pyramid level (Sec. 2.2 "Generating the multi-level
+ * pyramid"; the deformation grid of Sec. 2.2 "Grid conversion"): image dims,
+ * node dims, voxel spacing and node spacing (mm).  Any output pointer may be
+ * NULL. */
 int reg_level_info(reg_handle h, int level, int img_dims[3], int node_dims[3],
                    double spacing_mm[3], double node_spacing_mm[3]);
 
@@ -162,9 +166,10 @@ int reg_level_info(reg_handle h, int level, int img_dims[3], int node_dims[3],
  * kernels serve.  Any output pointer may be NULL. */
 int reg_level_tiling(reg_handle h, int level, int *tz, int *tiles);
 
-/* The load model's z split of the fused pass for an image of dims[3] voxels
- * (each even) on a GPU with num_sms SMs, without a GPU or a handle: the split
- * a handle uses when cfg.autotune = 0 (the autotuner times it among others).
+/* (No counterpart in the paper.)  The load model's z split of the fused pass
+ * for an image of dims[3] voxels (each even) on a GPU with num_sms SMs,
+ * without a GPU or a handle: the split a handle uses when cfg.autotune = 0
+ * (the autotuner times it among others).
  * split[5] as in cfg.fused_split; *model_steps (nullable) = the model's
  * duration in pipeline steps of one CTA.  REG_ERR_ARG for odd or < 4 dims or
  * num_sms < 1. */
@@ -186,13 +191,15 @@ int reg_fused_split_plan(const int dims[3], int num_sms, int split[5], double *m
 int reg_axis_tables(int m, double h, int n, int *k0, float *w1, int *first, int *cnt, float *w, int max_w,
                     int *needed_w);
 
-/* The z split of the fused pass on a level, in the form of cfg.fused_split:
- * split[5] = (l1, n1, l2, n2, lr), n1 segments of l1 planes, then n2 of l2,
- * then lr planes (0: no remainder), every tile column alike.  All 0 on levels
- * the multi-pass kernels serve.  REG_ERR_STATE before reg_set_images. */
+/* (No counterpart in the paper.)  The z split of the fused pass on a level,
+ * in the form of cfg.fused_split: split[5] = (l1, n1, l2, n2, lr), n1
+ * segments of l1 planes, then n2 of l2, then lr planes (0: no remainder),
+ * every tile column alike.  All 0 on levels the multi-pass kernels serve.
+ * REG_ERR_STATE before reg_set_images. */
 int reg_level_split(reg_handle h, int level, int split[5]);
 
-/* Copy pyramid image `which` (0 = R, 1 = T) of a level into out
+/* Copy pyramid image `which` (0 = R, 1 = T) of a level (Sec. 2.2 "Generating
+ * the multi-level pyramid": 2 x 2 x 2 means) into out
  * (m_x m_y m_z floats; device pointer if out_is_device). */
 int reg_get_level_image(reg_handle h, int level, int which, float *out, int out_is_device);
 
@@ -211,7 +218,7 @@ int reg_eval_objective_grad(reg_handle h, int level, const float *u_dev, float *
  * CUDA events on the handle's stream around its launch; the curvature and
  * gradient-assembly kernels are not included.  Synchronises on that event.
  * REG_ERR_STATE before the first evaluation.  A profiling aid (the paper
- * reports whole-registration times only). */
+ * reports whole-registration times only, Sec. 3). */
 int reg_last_ngf_ms(reg_handle h, double *ms);
 
 /* Allocation-free evaluation: the same J, D_NGF, S and grad_u J as

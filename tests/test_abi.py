@@ -145,3 +145,20 @@ def test_header_limits_match_the_binding(libreg):
     assert int(limits["REG_MAX_VOXELS"]) == libreg.MAX_VOXELS == 2**31 - 1
     assert int(limits["REG_MAX_PLANES"]) == libreg.MAX_PLANES == 65535
     assert int(limits["REG_MAX_LEVELS"]) == libreg.MAX_LEVELS and int(limits["REG_MAX_MEM"]) == libreg.MAX_MEM
+
+
+def test_header_entries_cite_their_passage_or_say_they_have_none(libreg):
+    """Every compute or geometry entry point of the header cites the passage of
+    the paper that defines it (Sec. / Eq.), or states that it has no counterpart
+    there; the plain utilities (version, defaults, destroy, last error) are exempt."""
+    import re
+    text = open(libreg.HEADER).read()
+    found = {}
+    for m in re.finditer(r"/\*((?:(?!\*/).)*)\*/\s*\n((?:[^;/]|/(?!\*))*?\b(reg_\w+)\s*\([^;]*;)", text, re.S):
+        found[m.group(3)] = re.sub(r"\s*\n\s*\*?\s*", " ", m.group(1))
+    exempt = {"reg_version", "reg_destroy", "reg_last_error"}
+    assert set(found) >= set(libreg.header_functions())
+    for name, comment in found.items():
+        if name in exempt:
+            continue
+        assert re.search(r"Sec\. [0-9]|Eq\. [0-9]|counterpart in the paper|paper reports", comment), name
