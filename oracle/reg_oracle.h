@@ -27,7 +27,8 @@ extern "C" {
 #define ORC_MAX_LEVELS 8
 #define ORC_MAX_MEM 16
 
-/* node spacing H_d = m_d h_d / (mn_d - 1) */
+/* node spacing H_d = m_d h_d / (mn_d - 1) of the deformation grid (Sec. 2.1;
+ * reading R1) */
 void orc_node_spacing(const int m[3], const double h[3], const int mn[3], double H[3]);
 
 /* grid conversion P (Sec. 2.1, Eq. 1): yhat_i = sum_k prod_d phi(x_{i,d}/H_d - k_d) u_k,
@@ -43,8 +44,9 @@ void orc_PT(const int m[3], const double h[3], const int mn[3], const double *r,
  * returns the count */
 int orc_PT_table(int m, double h, int mn, int k, int *first, double *w, int max_w);
 
-/* trilinear interpolation of T at n physical points p (3 planes of n),
- * zero extension outside the image; value and interpolant gradient */
+/* trilinear interpolation of T at n physical points p (3 planes of n) as used
+ * for T(P y) in Eq. 1 (Sec. 2.1), zero extension outside the image (reading
+ * R5); value and interpolant gradient */
 void orc_interp(const int m[3], const double h[3], const double *T, size_t n,
                 const double *p, double *val, double *grad /* 3 planes of n */);
 
@@ -53,24 +55,27 @@ void orc_interp(const int m[3], const double h[3], const double *T, size_t n,
 double orc_ngf(const int m[3], const double h[3], const double *Tw, const double *R,
                double tau, double rho, double *v);
 
-/* adjoint of the central-difference gradient applied to v, times hbar/2 */
+/* adjoint of the central-difference gradient applied to v, times hbar/2: the
+ * chain-rule step of Sec. 2.2 "Distance measure and gradient computation" */
 void orc_ngf_adjoint(const int m[3], const double h[3], const double *v, double *g);
 
 /* curvature regulariser (Sec. 2.1; Fischer-Modersitzki): S and grad S for the
  * 3 components of u; returns S */
 double orc_curvature(const int mn[3], const double H[3], const double *u, double *gradS);
 
-/* full objective J = D + alpha S and its gradient w.r.t. u (3 planes) */
+/* full objective J = D + alpha S (Eq. 1) and its gradient w.r.t. u (3 planes),
+ * in the steps of Sec. 2.2 "Evaluating the objective function" */
 void orc_objective(const int m[3], const double h[3], const double *R, const double *T,
                    const int mn[3], const double *u, double tau, double rho, double alpha,
                    double *J, double *D, double *S, double *grad);
 
-/* pyramid: one 2x2x2 mean step; out dims ceil(m/2); an odd dimension
- * replicates its last slab */
+/* pyramid (Sec. 2.2 "Generating the multi-level pyramid"; reading R4): one
+ * 2x2x2 mean step; out dims ceil(m/2); an odd dimension replicates its last slab */
 void orc_restrict(const int m[3], const double *img, double *out);
 
 /* nodal trilinear prolongation of a displacement (3 planes) between two nodal
- * grids spanning the boxes ext_c and ext_f (mm) */
+ * grids spanning the boxes ext_c and ext_f (mm): the coarse-to-fine step of the
+ * multi-level scheme (Sec. 2.1) */
 void orc_prolong(const int mn_c[3], const double ext_c[3], const double *uc,
                  const int mn_f[3], const double ext_f[3], double *uf);
 
@@ -105,16 +110,17 @@ typedef struct {
     int m[ORC_MAX_LEVELS][3];
 } orc_stats;
 
-/* level-wise node dims and image dims of a pyramid */
+/* level-wise node dims and image dims of a pyramid (readings R1, R4) */
 void orc_level_dims(const int m[3], const orc_config *cfg, int level, int m_out[3], int mn_out[3]);
 
-/* multilevel L-BFGS registration; u_init on the start level's node grid
- * (NULL = zero); u_out on the finest node grid; returns 0 or 1 (a level ended
- * on a failed line search) */
+/* multilevel L-BFGS registration (Sec. 2.1; readings R9, R10); u_init on the
+ * start level's node grid (NULL = zero); u_out on the finest node grid;
+ * returns 0 or 1 (a level ended on a failed line search) */
 int orc_register(const int m[3], const double h[3], const double *R, const double *T,
                  const orc_config *cfg, const double *u_init, double *u_out, orc_stats *st);
 
-/* one L-BFGS level on fixed images (exposed for tests); u in/out */
+/* one L-BFGS level on fixed images (Sec. 2.1; readings R9, R10; exposed for
+ * tests); u in/out */
 int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const double *T,
                     const int mn[3], const orc_config *cfg, int max_iter, double *u,
                     int *iters, int *evals, double *J_out);
