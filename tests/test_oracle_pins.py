@@ -491,3 +491,36 @@ def test_failed_line_search_ends_the_level_with_the_warning(orc):
     u, st = orc.lbfgs_level(dims, h, zero, zero, nodes, cfg, 10, u0)
     assert st["status"] == 0 and st["iters"] >= 1 and st["J"] < orc.objective(dims, h, zero, zero, nodes, u0, 0.1,
                                                                                0.1, 2.0)[0]
+
+
+def test_multilevel_register_is_levels_joined_by_prolongation(orc):
+    """Sec. 2.1's coarse-to-fine scheme: an affine start field has S = 0 and, with
+    R = T = 0, a zero gradient, so no level iterates and the result is the same
+    affine field on the finest nodes (prolongation reproduces affine fields;
+    node spacings 4, 6, 8 mm and 2, 3, 4 mm keep every value exact).
+    With images, the multilevel driver equals its pieces run by hand: L-BFGS on
+    the 2x2x2-mean level, nodal prolongation onto the finer nodes of the same box,
+    L-BFGS on the finest level."""
+    dims, h = (20, 16, 12), (1.0, 1.5, 2.0)
+    cfg = orc.make_config(levels=2, tau=0.05, alpha=3.0, mem=4, max_iter=[5, 7])
+    (mc, nc), (_, nf) = orc.level_dims(dims, cfg, 1), orc.level_dims(dims, cfg, 0)
+    ext = tuple(dims[d] * h[d] for d in range(3))
+    Hc = tuple(ext[d] / (nc[d] - 1) for d in range(3))
+    Hf = tuple(ext[d] / (nf[d] - 1) for d in range(3))
+    # dyadic coefficients on integer node coordinates: every second difference is exactly 0
+    aff = lambda X, Y, Z: np.stack([0.125 * X - 0.0625 * Z + 0.25, 0.0625 * Y, -0.03125 * X + 0.125 * Z])  # noqa: E731
+    zero = np.zeros(dims[::-1])
+    u, st = orc.register(dims, h, zero, zero, cfg, u_init=aff(*node_coords(nc, Hc)))
+    assert st["status"] == 0 and st["iters"] == [0, 0]
+    np.testing.assert_allclose(u, aff(*node_coords(nf, Hf)), rtol=0, atol=1e-12)
+
+    R = random_image(dims, 101).astype(np.float64)
+    T = np.roll(R, shift=(1, -1, 1), axis=(0, 1, 2))
+    u0 = random_field(nc, 102, 0.5).astype(np.float64)
+    u, st = orc.register(dims, h, R, T, cfg, u_init=u0)
+    hc = tuple(2 * v for v in h)
+    u1, s1 = orc.lbfgs_level(mc, hc, orc.restrict(dims, R), orc.restrict(dims, T), nc, cfg, 7, u0)
+    uf, s0 = orc.lbfgs_level(dims, h, R, T, nf, cfg, 5, orc.prolong(nc, ext, u1, nf, ext))
+    assert st["iters"] == [s0["iters"], s1["iters"]] and st["evals"] == [s0["evals"], s1["evals"]]
+    assert s1["iters"] >= 1 and s0["iters"] >= 1
+    np.testing.assert_array_equal(u, uf)
