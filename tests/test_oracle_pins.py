@@ -524,3 +524,37 @@ def test_multilevel_register_is_levels_joined_by_prolongation(orc):
     assert st["iters"] == [s0["iters"], s1["iters"]] and st["evals"] == [s0["evals"], s1["evals"]]
     assert s1["iters"] >= 1 and s0["iters"] >= 1
     np.testing.assert_array_equal(u, uf)
+
+
+def test_oracle_result_does_not_depend_on_the_thread_count(orc):
+    """OpenMP only splits independent per-voxel and per-node maps and every sum
+    runs sequentially in index order, so one thread and all threads give the
+    same bits."""
+    import json
+    import subprocess
+    import sys
+    code = r"""
+import json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from synth import random_image, random_field
+dims, h = (24, 20, 18), (1.0, 1.2, 0.9)
+R, T = random_image(dims, 1).astype(np.float64), random_image(dims, 2).astype(np.float64)
+nodes = oracle.default_nodes(dims)
+J, D, S, g = oracle.objective(dims, h, R, T, nodes, random_field(nodes, 3, 0.8).astype(np.float64), 0.05, 0.05, 1.0)
+import hashlib
+print(json.dumps({"J": J.hex(), "D": D.hex(), "S": S.hex(), "g": hashlib.sha256(g.tobytes()).hexdigest(),
+                  "threads": oracle.num_threads()}))
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for threads in ("1", "4"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        r = subprocess.run([sys.executable, "-c", code, root], capture_output=True, text=True, env=env,
+                           timeout=300, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert outs[0]["threads"] == 1 and outs[1]["threads"] == 4
+    for key in ("J", "D", "S", "g"):
+        assert outs[0][key] == outs[1][key], key
