@@ -162,3 +162,42 @@ def test_header_entries_cite_their_passage_or_say_they_have_none(libreg):
         if name in exempt:
             continue
         assert re.search(r"Sec\. [0-9]|Eq\. [0-9]|counterpart in the paper|paper reports", comment), name
+
+
+def test_plain_c_client_compiles_links_and_runs(libreg, tmp_path):
+    """The header is plain C (C99, -pedantic): a C program includes it, links
+    libreg.so and calls the host-only entry points."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "client.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "reg.h"
+int main(void)
+{
+    reg_config cfg;
+    int dims[3] = {256, 256, 256}, split[5], first[9], cnt[9], need = 0;
+    double steps = 0.0;
+    float w[9 * 4];
+    reg_config_default(&cfg);
+    if (cfg.levels != 1 || cfg.lbfgs_mem != 5) return 1;
+    if (reg_fused_split_plan(dims, 152, split, &steps) != REG_OK) return 2;
+    if (reg_axis_tables(16, 1.0, 9, NULL, NULL, first, cnt, w, 4, &need) != REG_OK || need != 4) return 3;
+    if (reg_axis_tables(3, 1.0, 9, NULL, NULL, NULL, NULL, NULL, 0, NULL) != REG_ERR_ARG) return 4;
+    printf("%d %d %d %d %d %.1f %d %d %s\n", split[0], split[1], split[2], split[3], split[4], steps, first[1],
+           cnt[1], reg_last_error(NULL));
+    return 0;
+}
+""")
+    libdir = os.path.dirname(libreg.LIB_PATH)
+    exe = tmp_path / "client"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lreg", "-Wl,-rpath," + libdir,
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    fields = out.stdout.split()
+    assert tuple(int(v) for v in fields[:5]) == libreg.reg_fused_split_plan((256, 256, 256), 152)[0]
+    assert fields[6:8] == ["0", "4"] and "reg_axis_tables" in out.stdout
