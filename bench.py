@@ -38,10 +38,11 @@ if ROOT not in sys.path:
 METRIC = "NGF+curvature objective+gradient evals/s and % HBM roofline; s per 256³ registration"
 UNIT = "evals/s (full-resolution equivalent)"
 L2_BYTES = 129 * 1024 * 1024
-# the translation unit of the fused pass and the headers its device code uses:
-# the committed ncu traffic is valid only for this exact source
+# the translation unit of the fused pass and every header it includes: the
+# committed ncu traffic is valid only for this exact source
 FUSED_KERNEL_SOURCES = ["paper_1812_06765_gb300/csrc/" + f
-                        for f in ("k_ngf_fused.cu", "ngf_math.cuh", "common.cuh", "batch.h")]
+                        for f in ("k_ngf_fused.cu", "ngf_math.cuh", "common.cuh", "batch.h", "internal.h",
+                                  "lbfgs_control.cuh", "lbfgs_state.h")] + ["include/reg.h"]
 
 
 def parse_args(argv=None):
