@@ -58,6 +58,11 @@ class Stats(ctypes.Structure):
     ]
 
 
+# double fn(void *ctx, const double *u, double *g)
+EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double))
+
+
 def lib():
     global _lib
     with _lock:
@@ -86,6 +91,9 @@ def lib():
             L.orc_lbfgs_level.argtypes = [ip, dp, dp, dp, ip, ctypes.POINTER(Config), ctypes.c_int, dp,
                                           ip, ip, dp]
             L.orc_lbfgs_level.restype = ctypes.c_int
+            L.orc_lbfgs.argtypes = [ctypes.c_size_t, EVAL_FN, ctypes.c_void_p, ctypes.c_double,
+                                    ctypes.POINTER(Config), ctypes.c_int, dp, ip, ip, dp]
+            L.orc_lbfgs.restype = ctypes.c_int
             L.orc_level_dims.argtypes = [ip, ctypes.POINTER(Config), ctypes.c_int, ip, ip]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_set_compensated_sums.argtypes = [ctypes.c_int]
@@ -263,6 +271,34 @@ def lbfgs_level(dims, spacing, R, T, nodes, cfg, max_iter, u0):
     st = lib().orc_lbfgs_level(_i3(dims), _d3(spacing), _dp(R), _dp(T), _i3(nodes), ctypes.byref(cfg),
                                int(max_iter), _dp(u), ctypes.byref(it), ctypes.byref(ev), ctypes.byref(J))
     return u, dict(iters=it.value, evals=ev.value, J=J.value, status=st)
+
+
+def lbfgs(fun, x0, Hmin, cfg, max_iter):
+    """The oracle's L-BFGS driver on any objective: fun(x) -> (J, g) for a
+    float64 vector x.  Returns (x, dict(iters, evals, J, status)).  The level
+    driver runs the same code with the objective of Eq. 1."""
+    x = _f64(np.ravel(x0)).copy()
+    n = x.size
+    err = []
+
+    def cb(_ctx, up, gp):
+        try:
+            xv = np.ctypeslib.as_array(up, shape=(n,)).copy()
+            J, g = fun(xv)
+            np.ctypeslib.as_array(gp, shape=(n,))[:] = np.asarray(g, dtype=np.float64).ravel()
+            return float(J)
+        except Exception as e:  # noqa: BLE001 - reported after the C call returns
+            err.append(e)
+            np.ctypeslib.as_array(gp, shape=(n,))[:] = 0.0
+            return float("nan")
+
+    cfun = EVAL_FN(cb)
+    it, ev, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = lib().orc_lbfgs(n, cfun, None, float(Hmin), ctypes.byref(cfg), int(max_iter), _dp(x), ctypes.byref(it),
+                         ctypes.byref(ev), ctypes.byref(J))
+    if err:
+        raise err[0]
+    return x, dict(iters=it.value, evals=ev.value, J=J.value, status=st)
 
 
 def register(dims, spacing, R, T, cfg, u_init=None):

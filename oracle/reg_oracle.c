@@ -561,18 +561,30 @@ typedef struct {
     const int *m, *mn;
     const double *h, *R, *T;
     const orc_config *cfg;
-    int evals;
 } level_ctx;
 
-static double level_eval(level_ctx *L, const double *u, double *g, double *D, double *S)
+/* the objective of one pyramid level (Eq. 1) as an L-BFGS callback */
+static double level_eval(void *ctx, const double *u, double *g)
 {
-    double J;
-    orc_objective(L->m, L->h, L->R, L->T, L->mn, u, L->cfg->tau, L->cfg->rho, L->cfg->alpha, &J, D, S, g);
-    L->evals++;
+    const level_ctx *L = (const level_ctx *)ctx;
+    double J, D, S;
+    orc_objective(L->m, L->h, L->R, L->T, L->mn, u, L->cfg->tau, L->cfg->rho, L->cfg->alpha, &J, &D, &S, g);
     return J;
 }
 
-/* p0 = -g * min_d H_d / ||g||_inf: a first step of at most one node spacing */
+typedef struct {
+    orc_eval_fn fn;
+    void *ctx;
+    int evals;
+} counted_fn;
+
+static double eval_counted(counted_fn *f, const double *u, double *g)
+{
+    f->evals++;
+    return f->fn(f->ctx, u, g);
+}
+
+/* p0 = -g * Hmin / ||g||_inf: a first step of at most one node spacing (reading R9) */
 static double first_direction(size_t n, const double *g, double Hmin, double *p)
 {
     double gi = 0.0;
@@ -585,16 +597,16 @@ static double first_direction(size_t n, const double *g, double Hmin, double *p)
     return dot(n, g, p);
 }
 
-/* Armijo backtracking: t = 1, 1/2, ...; accept J(u + t p) <= J + c1 t g'p */
-static int line_search(level_ctx *L, size_t n, const double *u, const double *p, double J, double gtp,
-                       double *ut, double *gt, double *Jt, double *Dt, double *St, double *t_out)
+/* Armijo backtracking: t = 1, 1/2, ...; accept J(u + t p) <= J + c1 t g'p (reading R9) */
+static int line_search(counted_fn *f, const orc_config *cfg, size_t n, const double *u, const double *p,
+                       double J, double gtp, double *ut, double *gt, double *Jt, double *t_out)
 {
     double t = 1.0;
-    for (int trial = 0; trial < L->cfg->max_backtracks; trial++) {
+    for (int trial = 0; trial < cfg->max_backtracks; trial++) {
         for (size_t i = 0; i < n; i++)
             ut[i] = u[i] + t * p[i];
-        *Jt = level_eval(L, ut, gt, Dt, St);
-        if (*Jt <= J + L->cfg->c1 * t * gtp) {
+        *Jt = eval_counted(f, ut, gt);
+        if (*Jt <= J + cfg->c1 * t * gtp) {
             *t_out = t;
             return 1;
         }
@@ -603,15 +615,11 @@ static int line_search(level_ctx *L, size_t n, const double *u, const double *p,
     return 0;
 }
 
-int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const double *T, const int mn[3],
-                    const orc_config *cfg, int max_iter, double *u, int *iters, int *evals, double *J_out)
+int orc_lbfgs(size_t n, orc_eval_fn fn, void *ctx, double Hmin, const orc_config *cfg, int max_iter,
+              double *u, int *iters, int *evals, double *J_out)
 {
-    size_t nn = vol(mn), n = 3 * nn;
-    double H[3];
-    orc_node_spacing(m, h, mn, H);
-    double Hmin = fmin(H[0], fmin(H[1], H[2]));
     int mem = cfg->mem < 1 ? 1 : (cfg->mem > ORC_MAX_MEM ? ORC_MAX_MEM : cfg->mem);
-    level_ctx L = {m, mn, h, R, T, cfg, 0};
+    counted_fn F = {fn, ctx, 0};
 
     double *g = (double *)malloc(sizeof(double) * n);
     double *gt = (double *)malloc(sizeof(double) * n);
@@ -622,8 +630,8 @@ int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const do
     double *tmp = (double *)malloc(sizeof(double) * n);
     int count = 0, status = 0, k = 0, small = 0;
 
-    double D, S, Dt, St, Jt, t;
-    double J = level_eval(&L, u, g, &D, &S);
+    double Jt, t;
+    double J = eval_counted(&F, u, g);
     double J0 = J, g0n = sqrt(dot(n, g, g));
 
     while (k < max_iter && g0n > 0.0) {
@@ -644,11 +652,11 @@ int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const do
                 gtp = first_direction(n, g, Hmin, p);
             }
         }
-        int ok = line_search(&L, n, u, p, J, gtp, ut, gt, &Jt, &Dt, &St, &t);
+        int ok = line_search(&F, cfg, n, u, p, J, gtp, ut, gt, &Jt, &t);
         if (!ok && !use_p0) { /* one retry from a fresh memory */
             count = 0;
             gtp = first_direction(n, g, Hmin, p);
-            ok = line_search(&L, n, u, p, J, gtp, ut, gt, &Jt, &Dt, &St, &t);
+            ok = line_search(&F, cfg, n, u, p, J, gtp, ut, gt, &Jt, &t);
         }
         if (!ok) {
             status = 1;
@@ -676,10 +684,8 @@ int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const do
         double Jprev = J;
         memcpy(g, gt, sizeof(double) * n);
         J = Jt;
-        D = Dt;
-        S = St;
         k++;
-        if (!cfg->fixed_iters) {
+        if (!cfg->fixed_iters) { /* reading R10 */
             if (sqrt(dot(n, g, g)) <= cfg->tol_grad_rel * g0n)
                 break;
             if (fabs(Jprev - J) <= cfg->tol_j_rel * (1.0 + fabs(J0))) {
@@ -690,10 +696,8 @@ int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const do
             }
         }
     }
-    (void)D;
-    (void)S;
     *iters = k;
-    *evals = L.evals;
+    *evals = F.evals;
     *J_out = J;
     free(g);
     free(gt);
@@ -703,6 +707,16 @@ int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const do
     free(Ym);
     free(tmp);
     return status;
+}
+
+int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const double *T, const int mn[3],
+                    const orc_config *cfg, int max_iter, double *u, int *iters, int *evals, double *J_out)
+{
+    double H[3];
+    orc_node_spacing(m, h, mn, H);
+    level_ctx L = {m, mn, h, R, T, cfg};
+    return orc_lbfgs(3 * vol(mn), level_eval, &L, fmin(H[0], fmin(H[1], H[2])), cfg, max_iter, u, iters, evals,
+                     J_out);
 }
 
 void orc_level_dims(const int m[3], const orc_config *cfg, int level, int m_out[3], int mn_out[3])

@@ -119,6 +119,18 @@ void orc_level_dims(const int m[3], const orc_config *cfg, int level, int m_out[
 int orc_register(const int m[3], const double h[3], const double *R, const double *T,
                  const orc_config *cfg, const double *u_init, double *u_out, orc_stats *st);
 
+/* objective callback of the L-BFGS driver: returns J(u) and writes its
+ * gradient g (n values) */
+typedef double (*orc_eval_fn)(void *ctx, const double *u, double *g);
+
+/* L-BFGS with Armijo backtracking on any objective (Sec. 2.1 "L-BFGS", Nocedal
+ * 1980; readings R9, R10): memory cfg->mem, first step -g Hmin / ||g||_inf,
+ * curvature-pair test, reset and one p0 retry on a failed search, and the
+ * stopping tests of cfg; u in/out (n values); returns 0, or 1 when a line
+ * search failed twice.  evals counts calls of fn. */
+int orc_lbfgs(size_t n, orc_eval_fn fn, void *ctx, double Hmin, const orc_config *cfg, int max_iter,
+              double *u, int *iters, int *evals, double *J_out);
+
 /* one L-BFGS level on fixed images (Sec. 2.1; readings R9, R10; exposed for
  * tests); u in/out */
 int orc_lbfgs_level(const int m[3], const double h[3], const double *R, const double *T,
