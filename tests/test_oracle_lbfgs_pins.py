@@ -135,3 +135,41 @@ def test_failed_search_with_memory_retries_once_from_the_first_step_rule(orc):
     x, st = orc.lbfgs(fun, [0.0, 0.0], Hmin, cfg, 2)
     assert st["status"] == 1 and st["iters"] == 1 and st["evals"] == 2 + 2 * nb
     np.testing.assert_allclose(x, [-Hmin, 0.0], rtol=0, atol=1e-15)
+
+
+def dense_bfgs_inverse(pairs, gamma, n):
+    """H of the BFGS inverse update applied to H0 = gamma I, pairs oldest first."""
+    H = gamma * np.eye(n)
+    for s, y in pairs:
+        r = 1.0 / (s @ y)
+        V = np.eye(n) - r * np.outer(y, s)
+        H = V.T @ H @ V + r * np.outer(s, s)
+    return H
+
+
+def test_retry_after_a_failed_search_forgets_the_old_pairs(orc):
+    # As above in 2-D, one iteration further.  Evaluation 0: x0 = 0, g0 = (1, 0);
+    # evaluation 1: x1 = (-H, 0), g1 = (0.5, 0.5), pair 1 s1 = (-H, 0), y1 = (-0.5, 0.5)
+    # (s'y = H/2 > 0, stored).  The direction from pair 1 fails all 5 trials; the retry
+    # takes -H g1 / ||g1||_inf = (-H, -H) to x2 = (-2H, -H) with g2 = (0.2, 0.1), and
+    # stores pair 2 s2 = (-H, -H), y2 = (-0.3, -0.4).  The memory was reset before the
+    # retry, so the third direction uses pair 2 alone: x3 = x2 - H2 g2 with H2 the BFGS
+    # inverse of pair 2 on gamma = s2'y2 / y2'y2 (the dense formula).
+    Hm, nb = 0.25, 5
+    Js = [10.0, 9.0] + [100.0] * nb + [8.0, 7.0]
+    gs = [[1.0, 0.0], [0.5, 0.5]] + [[0.3, 0.0]] * nb + [[0.2, 0.1], [0.0, 0.0]]
+    fun, calls = scripted(Js, gs)
+    cfg = orc.make_config(mem=5, max_backtracks=nb, fixed_iters=True)
+    x, st = orc.lbfgs(fun, [0.0, 0.0], Hm, cfg, 3)
+    assert st["status"] == 0 and st["iters"] == 3 and st["evals"] == 2 + nb + 2
+    x2 = np.array([-2 * Hm, -Hm])
+    np.testing.assert_allclose(calls[-2], x2, rtol=0, atol=1e-15)
+    s1, y1 = np.array([-Hm, 0.0]), np.array([-0.5, 0.5])
+    s2, y2 = np.array([-Hm, -Hm]), np.array([-0.3, -0.4])
+    g2 = np.array([0.2, 0.1])
+    gamma = (s2 @ y2) / (y2 @ y2)
+    x3 = x2 - dense_bfgs_inverse([(s2, y2)], gamma, 2) @ g2
+    np.testing.assert_allclose(x, x3, rtol=0, atol=1e-13)
+    # keeping pair 1 would give a different third step
+    x3_kept = x2 - dense_bfgs_inverse([(s1, y1), (s2, y2)], gamma, 2) @ g2
+    assert np.max(np.abs(x3_kept - x3)) > 1e-3
