@@ -226,22 +226,25 @@ int reg_last_ngf_ms(reg_handle h, double *ms);
  * allocate device memory while they run - code hosted by a framework that owns
  * all device memory through its own pool and budget, or a latency-bound loop
  * that cannot go through cudaMalloc / cudaFree (which may synchronise the
- * device).  The paper has no counterpart: it is an interface of this library.
+ * device).  It has no counterpart in the paper: it is an interface of this library.
  *   R, T: device images, dims[3] = (m_x, m_y, m_z), each even and >= 4 (the
  *     deformation grid is m_d / 2 + 1 nodes per dimension), spacing_mm[3] > 0;
  *     R must be 8-byte aligned (it is read two voxels at a time; any cudaMalloc
  *     pointer is), else REG_ERR_ARG;
  *   u, grad: device, 3 planes of the node count (grad is overwritten);
- *   tau, rho > 0, alpha >= 0: the parameters of Eq. 1-2;
+ *   tau, rho > 0, alpha >= 0: the same parameters as reg_config's tau, rho and
+ *     alpha for reg_eval_objective_grad;
  *   jds: device, 3 doubles receiving J, D and S;
  *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
  * Every buffer is the caller's.  The working memory is one fixed 12.5 MiB array
  * in the library's device image, held by every GPU that loads the library until
  * the process exits; it fits images up to about 136^3 voxels (a 128^3 pair
  * needs 8.3 MiB), and larger sizes are rejected with REG_ERR_ARG before
- * anything is launched.  No call allocates memory.  The first call on each
- * device looks up the array's device address and sets a kernel attribute for
- * that device: make that first call before any stream capture.  All calls share
+ * anything is launched, as is any side above 4096 voxels.  No call allocates
+ * memory.  The first call on each device looks up the array's device address
+ * and sets a kernel attribute for that device (again on the first call after
+ * the device's context was reset, e.g. by cudaDeviceReset): make that first
+ * call before any stream capture.  All calls share
  * the array and every call overwrites what it reads, so calls that may overlap
  * on the GPU (different streams or threads) race and must be serialised by the
  * caller.  Returns REG_OK, REG_ERR_ARG or REG_ERR_CUDA; reg_last_error(NULL)

@@ -14,7 +14,10 @@
 // library holds it until the process exits.  Host code cannot use the name
 // g_noalloc_scratch as a device address (it names a host-side stand-in), so
 // the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current, and caches it.
+// cudaGetSymbolAddress while that device is current, and caches it with the
+// id of the device's context: after a device reset the context is new, and
+// the next call repeats the set-up.
+#include <cuda.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -53,6 +56,9 @@ constexpr size_t OFFB_PARTIALS = OFFB_W + CAP_W * sizeof(float);
 constexpr size_t SCRATCH_BYTES = OFFB_PARTIALS + CAP_PARTIALS * sizeof(double);
 
 constexpr int MAX_DEVICES = 64;
+// longest image side (voxels); with at least 4 voxels in the other two
+// dimensions the Laplacian's capacity allows up to about 77000
+constexpr int MAX_DIM = 4096;
 
 }  // namespace
 
@@ -63,18 +69,51 @@ namespace {
 struct DeviceSetup {
     void *scratch = nullptr;   // device address of g_noalloc_scratch on that device
     int num_sms = 0;
+    unsigned long long ctx_id = 0;   // context the address and the attribute belong to
 };
 
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[MAX_DEVICES];
 
-// Once per device, with that device current: the device address of the
-// scratch array, the SM count, and the fused kernel's shared-memory limit.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0: none current or the
+// driver lacks the query).  Driver entry points come through the runtime, so
+// the library needs no link against the driver library.
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Once per device and context, with that device current: the device address
+// of the scratch array, the SM count, and the fused kernel's shared-memory
+// limit.
 int device_setup(int dev, DeviceSetup *out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup &d = g_setup[dev];
-    if (!d.scratch) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!d.scratch || ctx == 0 || ctx != d.ctx_id) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess)
@@ -89,6 +128,7 @@ int device_setup(int dev, DeviceSetup *out)
                            cudaGetErrorString(e));
         d.num_sms = sms;
         d.scratch = ptr;
+        d.ctx_id = current_ctx_id();   // the look-up above made the context current if none was
     }
     *out = d;
     return REG_OK;
@@ -128,6 +168,16 @@ extern "C" int reg_eval_objective_grad_noalloc(const float *R, const float *T, c
     g.nv = (long long)g.m[0] * g.m[1] * g.m[2];
     g.nn = (long long)g.n[0] * g.n[1] * g.n[2];
 
+    // the cheap bound first: the node Laplacian w takes 3 floats per node, and
+    // each dimension is capped, so the split search below only sees sizes that
+    // fit (about 138 voxels per dimension for a cube)
+    const size_t w_floats = 3 * (size_t)g.nn;
+    if (w_floats > CAP_W || g.m[0] > MAX_DIM || g.m[1] > MAX_DIM || g.m[2] > MAX_DIM)
+        return set_err(nullptr, REG_ERR_ARG,
+                       "%s: %dx%dx%d needs %zu node floats (max %zu, at most %d voxels per dimension); use a "
+                       "handle (reg_create) for larger images",
+                       fn, g.m[0], g.m[1], g.m[2], w_floats, CAP_W, MAX_DIM);
+
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
@@ -143,7 +193,6 @@ extern "C" int reg_eval_objective_grad_noalloc(const float *R, const float *T, c
     int tz = 0, tiles = 0;
     size_t part_floats = 0;
     fused_layout_dims(g.m, ds.num_sms, &tz, &tiles, &part_floats);
-    const size_t w_floats = 3 * (size_t)g.nn;
     const int nS = curv_blocks(g);
     const size_t partials = (size_t)tiles + (size_t)nS;
     if (part_floats > CAP_PART || w_floats > CAP_W || partials > CAP_PARTIALS)

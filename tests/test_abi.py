@@ -61,6 +61,19 @@ def test_create_rejects_bad_config_before_touching_the_gpu(libreg):
         assert ei.value.code == libreg.REG_ERR_ARG
 
 
+def test_noalloc_refuses_oversized_dims_before_touching_the_gpu(libreg):
+    """The allocation-free entry point checks its fixed capacity (3 floats per node of
+    the Laplacian, at most 4096 voxels per side) before any CUDA call, so sizes
+    whose products overflow 32 bits are refused with REG_ERR_ARG; the pointers
+    are never dereferenced."""
+    fake = 256   # non-NULL, 8-byte aligned, never read
+    for dims in ((1 << 30, 4, 4), (4098, 4, 4), (4, 4, 4096 + 2), (1 << 20, 1 << 20, 1 << 20), (200, 200, 200)):
+        with pytest.raises(libreg.RegError) as ei:
+            libreg.reg_eval_objective_grad_noalloc(fake, fake, dims, (1.0, 1.0, 1.0), fake, fake, 0.1, 0.1, 1.0, fake)
+        assert ei.value.code == libreg.REG_ERR_ARG
+        assert "node floats" in libreg.reg_last_error(None)
+
+
 def test_null_handle_calls_are_safe(libreg):
     L = libreg.lib()
     assert L.reg_destroy(None) == 0

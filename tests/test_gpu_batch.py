@@ -128,3 +128,30 @@ def test_batch_reports_numeric_error(reg_mod):
     assert ei.value.code == _lib.REG_ERR_NUMERIC
     for r in regs:
         r.close()
+
+
+def test_batch_matches_oracle_per_pair(reg_mod, orc):
+    """Each pair of an uneven batch (one of the batch workload's sizes, 96^3, and three
+    smaller shapes) registered together through register_batch, against the FP64
+    oracle registering that pair alone: a fixed number of accepted steps on each of
+    3 levels, mean |u - u_oracle| <= 0.02 voxel, and J to 1e-4 on every level where
+    the two took the same number of evaluations (otherwise an Armijo test that FP32
+    and FP64 decided differently branched the search: J to 1e-2)."""
+    c = CONFIGS[4]
+    sizes = [(96, 96, 96), (64, 48, 40), (40, 56, 32), (32, 32, 48)]
+    pairs = [make_pair(4, pair=20 + i, dims=d) for i, d in enumerate(sizes)]
+    kw = dict(levels=c["levels"], tau=c["eta"], alpha=c["alpha"], mem=c["mem"], c1=c["c1"], max_iter=[6, 8, 8],
+              fixed_iters=True)
+    regs = [reg_mod.Registration(reg_mod.make_config(**kw)).set_images(p["R"], p["T"], p["spacing"]) for p in pairs]
+    batch = reg_mod.register_batch(regs, out="numpy")
+    for p, (u, st) in zip(pairs, batch):
+        uo, sto = orc.register(p["dims"], p["spacing"], p["R"], p["T"], orc.make_config(**kw))
+        assert st["status"] == 0 and sto["status"] == 0
+        assert st["iters"] == sto["iters"] == [6, 8, 8]
+        du = np.sqrt(((u.astype(np.float64) - uo) ** 2).sum(axis=0)).mean() / min(p["spacing"])
+        assert du <= 0.02, (p["dims"], du, st, sto)
+        for lv in range(c["levels"]):
+            tol = 1e-4 if st["evals"][lv] == sto["evals"][lv] else 1e-2
+            assert abs(st["J"][lv] - sto["J"][lv]) <= tol * abs(sto["J"][lv]), (p["dims"], lv, st, sto)
+    for r in regs:
+        r.close()
