@@ -32,7 +32,7 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
     FusedArgs a{};
     a.g = P.geom;
-    a.T = bf16 ? static_cast<const void *>(L.Tb) : static_cast<const void *>(L.T);
+    a.T = bf16 ? static_cast<const void *>(L.Tb) : static_cast<const void *>(L.Tp);   // zero-bordered copies
     a.R = bf16 ? static_cast<const void *>(L.Rb) : static_cast<const void *>(L.R);
     a.ub = c->lb.u;
     a.dir = nullptr;

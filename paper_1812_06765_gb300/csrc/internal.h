@@ -63,7 +63,10 @@ struct Level {
     double H[3];
     long long nv, nn;
     float *R = nullptr, *T = nullptr;        // device images
-    __nv_bfloat16 *Rb = nullptr, *Tb = nullptr;   // BF16 copies read by the fused pass (image_dtype 1)
+    // read by the fused pass: T with a 2-voxel zero border on every side (dims m + 4), FP32
+    // (image_dtype 0) or BF16 (Tb, image_dtype 1, beside the BF16 copy Rb of R)
+    float *Tp = nullptr;
+    __nv_bfloat16 *Rb = nullptr, *Tb = nullptr;
     int *pk0[3] = {nullptr, nullptr, nullptr};
     float *pw1[3] = {nullptr, nullptr, nullptr};
     int *tfirst[3] = {nullptr, nullptr, nullptr};
@@ -152,6 +155,10 @@ inline int curv_zchunks(int nz) { return (nz + CURV_ZB - 1) / CURV_ZB; }
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_restrict(const float *src, const int m[3], float *dst, cudaStream_t s);
 cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s);
+// the zero-bordered copy of a volume of dims m read by the fused pass (dims m + 4)
+long long padded_voxels(const int m[3]);
+cudaError_t launch_pad_template(const float *src, const int m[3], float *dst, cudaStream_t s);
+cudaError_t launch_pad_template(const float *src, const int m[3], __nv_bfloat16 *dst, cudaStream_t s);
 cudaError_t launch_prolong(const Level &coarse, const Level &fine, const float *uc, float *uf, cudaStream_t s);
 
 // objective + gradient at u_base + t_scale * dir (dir may be NULL: plain u_base);

@@ -20,14 +20,31 @@
 // (TZ/2 + 1) nodes; neighbouring tiles share one node plane per dimension and
 // the gather kernel sums them.
 //
+// Arithmetic.  The two columns of a thread run the same computation, so every
+// per-column quantity is a float2 pair (.x the first column, .y the second)
+// and the FP32 work is issued as packed two-lane instructions (fma/add/mul/sub
+// .f32x2): one issue slot serves both voxels.
+//
+// Template samples.  Handles keep a copy of T with a 2-voxel zero border on
+// every side (PAD): a sample cell is clamped into the border with one unsigned
+// min per axis, which reads the zero extension of R5 for any cell outside the
+// image, and the 8 corners load without tests.  Callers that pass their own
+// unpadded T (the allocation-free entry point) take bounds-tested loads.
+//
+// Scale factors.  The constant factors of r = (hbar / 2) g' (grad T') / h_c
+// are left to the gather: the pass accumulates g' (the unscaled adjoint
+// stencil of v) times the unscaled interpolant differences, and the gather
+// multiplies component c by hbar / (2 h_c).
+//
 // Pipeline.  Step s works on plane zA = z0 - 2 + s and the lagging planes
 //   A-finish zA    : interpolate T at both columns from the corners loaded
 //                    last step
 //   A-issue  zA+1  : at the first plane of a node interval, P on the interval
 //                    (both planes) and the cp.async of the node-plane tile two
-//                    intervals ahead; the coordinates of plane zA+1 and the
-//                    loads of its 2 x 8 corners and of R into registers, first
-//                    used one step later
+//                    intervals ahead; at its second plane, the trial node
+//                    values u + t dir of the plane that copy brought; the
+//                    coordinates of plane zA+1 and the loads of its 2 x 8
+//                    corners and of R into registers, first used one step later
 //   B  zA-2        : v from T~ and R planes zA-3 .. zA-1
 //   C  zA-4        : r from v planes zA-5 .. zA-3; x reduction to node columns
 //   D  zA-5        : y reduction of last step's rows, accumulation along z
@@ -58,20 +75,111 @@ constexpr int PLANE = CW * BY;                    // floats of one shared plane
 constexpr int TNX = BX + 1, TNY = BY / 2 + 1;     // node tile of the columns: 17 x 17
 constexpr int TNP = 3 * TNY * TNX;                // floats of one node plane tile per array
 constexpr int NCOPY = (2 * TNP + NT - 1) / NT;    // node-tile entries copied per thread
+constexpr int NCOMB = (TNP + NT - 1) / NT;        // trial node values formed per thread
 
-// shared layout (floats); the ring slot of plane z is z & 3 (z & 7 for grad T)
+// shared layout (floats).  The ring slot of plane z is z & 3 for T~, R and v;
+// grad T, written 4 steps before it is read, has a ring of 5 slots taken in
+// turn, one per step; node plane K sits in slot K mod 3.  The rings are kept
+// this small so that the CTA's shared memory leaves room for a larger L1,
+// which holds the template samples.
+constexpr int GSLOTS = 5;
+constexpr int NSLOTS = 3;
 constexpr int OFF_T = 0;                          // T~ ring [4][PLANE]
 constexpr int OFF_R = OFF_T + 4 * PLANE;          // R ring [4][PLANE]
 constexpr int OFF_V = OFF_R + 4 * PLANE;          // v ring [4][3][PLANE]
-constexpr int OFF_G = OFF_V + 12 * PLANE;         // grad T ring [8][3][PLANE]
+constexpr int OFF_G = OFF_V + 12 * PLANE;         // grad T ring [GSLOTS][3][PLANE]
 constexpr int RED_PLANE = BY * NX * 3;            // x-reduced rows of one plane [BY][NX][3]
-constexpr int OFF_RED = OFF_G + 24 * PLANE;       // x-reduced rows [2 steps][RED_PLANE]
-constexpr int OFF_N = OFF_RED + 2 * RED_PLANE;    // node planes [4][2][TNP] (u, dir)
-constexpr int SMEM_FLOATS = OFF_N + 4 * 2 * TNP;
+constexpr int OFF_RED = OFF_G + GSLOTS * 3 * PLANE;   // x-reduced rows [2 steps][RED_PLANE]
+constexpr int OFF_N = OFF_RED + 2 * RED_PLANE;    // node planes [NSLOTS][2][TNP] (u or u + t dir, dir)
+constexpr int SMEM_FLOATS = OFF_N + NSLOTS * 2 * TNP;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 static_assert(SMEM_BYTES <= 227 * 1024, "fused pass exceeds the shared memory of one CTA");
+__device__ __forceinline__ int node_slot(int K) { return (K + NSLOTS) % NSLOTS; }   // K >= -1
+
+// The fused kernels' dynamic shared memory, and a carveout preference of just
+// that much (with the 1 KB the system reserves per CTA) in percent of the
+// SM's 228 KB: the rest of the SM's 256 KB stays L1, where the template's
+// samples are cached.
+template <typename K>
+cudaError_t set_fused_smem(K kernel)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    const int pct = (int)((100 * (SMEM_BYTES + 1024) + 228 * 1024 - 1) / (228 * 1024));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    return e;
+}
 static_assert((OFF_R | OFF_V | OFF_G | OFF_RED | OFF_N | PLANE) % 2 == 0, "float2 rows need even offsets");
 
+// 1.5 * 2^23: adding it rounds a float to an integer (the rounding mode picks
+// which one); the low bits of the sum then hold that integer plus MAGI
+constexpr float MAGF = 12582912.0f;
+constexpr int MAGI = 0x4B400000;
+
+// ---- packed FP32 pairs
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    union {
+        float2 f;
+        unsigned long long u;
+    } x, y, d;
+    x.f = a;
+    y.f = b;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.u) : "l"(x.u), "l"(y.u));
+    return d.f;
+}
+// a + w (b - a), lane by lane: the pair form of lerpf
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 w) { return fma2(w, sub2(b, a), a); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// Kahan-compensated pair of running sums
+struct KahanF2 {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 x)
+    {
+        const float2 y = sub2(x, c);
+        const float2 t = add2(s, y);
+        c = sub2(sub2(t, s), y);
+        s = t;
+    }
+};
+
+// NGF residual of Eq. 2 for both columns (a = grad T~, b = grad R, 3 pairs
+// each): returns psi = 1 - c^2 per lane and writes v = d psi / d a.  psi is
+// evaluated through the exact identity
+//   (|a|^2 + tau^2)(|b|^2 + rho^2) - (a.b + tau rho)^2 = |a x b|^2 + |tau b - rho a|^2,
+// so no cancellation occurs where c is close to 1 (aligned or flat regions).
+__device__ __forceinline__ float2 ngf_residual2(const float2 a[3], const float2 b[3], float tau, float rho,
+                                                float2 v[3])
+{
+    const float2 TAU = bc2(tau), RHO = bc2(rho);
+    const float2 aa = fma2(a[2], a[2], fma2(a[1], a[1], mul2(a[0], a[0])));
+    const float2 bb = fma2(b[2], b[2], fma2(b[1], b[1], mul2(b[0], b[0])));
+    const float2 ab = fma2(a[2], b[2], fma2(a[1], b[1], mul2(a[0], b[0])));
+    const float2 na2 = add2(aa, bc2(tau * tau)), nb2 = add2(bb, bc2(rho * rho));
+    const float2 cx = sub2(mul2(a[1], b[2]), mul2(a[2], b[1]));
+    const float2 cy = sub2(mul2(a[2], b[0]), mul2(a[0], b[2]));
+    const float2 cz = sub2(mul2(a[0], b[1]), mul2(a[1], b[0]));
+    const float2 ex = sub2(mul2(TAU, b[0]), mul2(RHO, a[0]));
+    const float2 ey = sub2(mul2(TAU, b[1]), mul2(RHO, a[1]));
+    const float2 ez = sub2(mul2(TAU, b[2]), mul2(RHO, a[2]));
+    const float2 num = fma2(ez, ez, fma2(ey, ey, fma2(ex, ex, fma2(cz, cz, fma2(cy, cy, mul2(cx, cx))))));
+    const float2 den = mul2(na2, nb2);
+    const float2 rden = make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y));   // approximate: ~2 ulp
+    const float2 psi = mul2(num, rden);
+    const float2 rs = make_float2(rsqrtf(den.x), rsqrtf(den.y));   // 1 / (||a||_tau ||b||_rho)
+    const float2 c = mul2(add2(ab, bc2(tau * rho)), rs);
+    const float2 m2c = mul2(bc2(-2.f), c);
+    const float2 k1 = mul2(m2c, rs);                                // v = -2c (b / (na nb) - c a / na^2)
+    const float2 k2 = mul2(mul2(m2c, c), make_float2(-__fdividef(1.f, na2.x), -__fdividef(1.f, na2.y)));
+    v[0] = fma2(k1, b[0], mul2(k2, a[0]));
+    v[1] = fma2(k1, b[1], mul2(k2, a[1]));
+    v[2] = fma2(k1, b[2], mul2(k2, a[2]));
+    return psi;
+}
 
 __device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc, bool valid)
 {
@@ -84,7 +192,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-__device__ __forceinline__ void sts2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+__device__ __forceinline__ void sts2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 
 // One thread's share of the cooperative copy of a node plane (u and, with a
 // direction, dir) of the CTA's 17 x 17 node tile: entries tid + q NT.  The
@@ -113,11 +221,11 @@ __device__ __forceinline__ NodeCopy node_copy_setup(const LevelGeom &g, int kx0,
     return nc;
 }
 
-// copy node plane K into ring slot K & 3; nodes outside the grid read as zero
+// copy node plane K into its ring slot; nodes outside the grid read as zero
 __device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float *ub, const float *dir, float *sm,
                                                  int K, int nz, size_t plane_stride)
 {
-    float *dst = sm + OFF_N + (K & 3) * 2 * TNP;
+    float *dst = sm + OFF_N + node_slot(K) * 2 * TNP;
     const bool kin = K >= 0 && K < nz;
     const size_t kofs = kin ? plane_stride * (size_t)K : 0;
 #pragma unroll
@@ -129,29 +237,36 @@ __device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float
         }
 }
 
+// the trial point of node plane K (copied into its ring slot and visible to
+// every thread): u <- u + t dir in place, the same fmaf as the accepted update,
+// so the accepted iterate equals the evaluated one bit for bit
+__device__ __forceinline__ void trial_node_plane(float *sm, int K, float t, int tid)
+{
+    float *nu = sm + OFF_N + node_slot(K) * 2 * TNP;
+#pragma unroll
+    for (int q = 0; q < NCOMB; q++) {
+        const int e = tid + q * NT;
+        if (e < TNP)
+            nu[e] = fmaf(t, nu[e + TNP], nu[e]);
+    }
+}
+
 // displacement plane K of the thread's two columns from the shared node tile:
 // the value at the interval's first node (U, shared) and the bilinear
-// interpolation of the in-plane differences (Bd, x weight 1/4 and 3/4)
-template <bool HAS_DIR>
-__device__ __forceinline__ void column_pair_plane(const float *sm, int K, int lkx, int lky, float wy, float t,
-                                                  float U[3], float Bd[2][3])
+// interpolation of the in-plane differences (B, x weight 1/4 and 3/4 per lane)
+__device__ __forceinline__ void column_pair_plane(const float *sm, int K, int lkx, int lky, float2 WY, float U[3],
+                                                  float2 B[3])
 {
-    const float *nu = sm + OFF_N + (K & 3) * 2 * TNP;
-    const float *np = nu + TNP;
+    const float *nu = sm + OFF_N + node_slot(K) * 2 * TNP;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const int o = c * (TNY * TNX) + lky * TNX + lkx;
-        float u00 = nu[o], u10 = nu[o + 1], u01 = nu[o + TNX], u11 = nu[o + TNX + 1];
-        if (HAS_DIR) {   // trial point u + t dir, the same fmaf as the accepted update
-            u00 = fmaf(t, np[o], u00);
-            u10 = fmaf(t, np[o + 1], u10);
-            u01 = fmaf(t, np[o + TNX], u01);
-            u11 = fmaf(t, np[o + TNX + 1], u11);
-        }
-        const float dx = u10 - u00, dy = u01 - u00, dxy = u11 - u00;
+        const float u00 = nu[o], u10 = nu[o + 1], u01 = nu[o + TNX], u11 = nu[o + TNX + 1];
+        const float dx = u10 - u00, dy = u01 - u00, e = (u11 - u00) - dy;
         U[c] = u00;
-        Bd[0][c] = lerpf(0.25f * dx, lerpf(dy, dxy, 0.25f), wy);
-        Bd[1][c] = lerpf(0.75f * dx, lerpf(dy, dxy, 0.75f), wy);
+        const float2 X = make_float2(0.25f * dx, 0.75f * dx);
+        const float2 Y = make_float2(fmaf(0.25f, e, dy), fmaf(0.75f, e, dy));
+        B[c] = lerp2(X, Y, WY);
     }
 }
 
@@ -211,8 +326,9 @@ __device__ __forceinline__ void tile_seg_col(const FusedSplit &sp, int ncols, in
 }
 
 // One output tile (launch-order id, see tile_seg_col) of the fused pass; sm is
-// the CTA's dynamic shared memory (SMEM_BYTES).
-template <bool HAS_DIR, typename IMG>
+// the CTA's dynamic shared memory (SMEM_BYTES).  PAD: a.T is the zero-bordered
+// copy of T (dims m + 4, the image at offset 2 in every dimension).
+template <bool HAS_DIR, typename IMG, bool PAD>
 __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, float *sm)
 {
     const LevelGeom &g = a.g;
@@ -234,9 +350,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     // 1/4 (i even) or 3/4 (i odd); both columns lie in node interval kx0 + tx
     const int lky = ty >> 1;
     const int kx0 = (x0 >> 1) - 1, ky0 = (y0 >> 1) - 1;
-    const float wy = (y & 1) ? 0.75f : 0.25f;
-    const float hx = 0.5f * g.ih[0], hy = 0.5f * g.ih[1], hz = 0.5f * g.ih[2];
-    const float half_hbar = 0.5f * g.hbar;
+    const float2 WY = bc2((y & 1) ? 0.75f : 0.25f);
+    const float2 HX = bc2(0.5f * g.ih[0]), HY = bc2(0.5f * g.ih[1]), HZ = bc2(0.5f * g.ih[2]);
     const int zend = z0 + tz;                         // first plane after the segment's output planes
     const size_t tile_lin = (size_t)tile_id;          // this tile's D partial
     // the segment's block of partials: ncols tiles of tz / 2 + 1 node planes
@@ -245,11 +360,21 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     const size_t node_plane = (size_t)g.n[0] * g.n[1];
     const IMG *Tim = static_cast<const IMG *>(a.T);
     const IMG *Rcol = static_cast<const IMG *>(a.R) + (col_in ? xa + mx * y : 0);
+    // padded template: row pitch, plane pitch and the largest cell index (padded coordinates)
+    const int MXP = mx + 4;
+    const int MYP = my + 4;
+    const size_t SXYP = (size_t)MXP * MYP;
+    const unsigned CXM = (unsigned)mx + 2, CYM = (unsigned)my + 2, CZM = (unsigned)mz + 2;
+    constexpr int PADO = PAD ? 2 : 0;                 // image offset inside the template array
     // rows phases B and C run on; output columns (both of the thread's columns)
     const bool rowB = ty >= 1 && ty < BY - 1, rowC = ty >= 2 && ty < BY - 2;
     const bool outxy = rowC && tx >= 1 && tx < BX - 1;
     const bool iny = y >= 1 && y <= my - 2;
     const bool intA = col_in && iny && xa >= 1, intB = col_in && iny && xa + 1 <= mx - 2;
+    // lanes of the NGF residual that count: interior voxels (MI), and of those
+    // the output columns, whose psi is summed (MO)
+    const float2 MI = make_float2(intA ? 1.f : 0.f, intB ? 1.f : 0.f);
+    const float2 MO = make_float2(intA && outxy ? 1.f : 0.f, intB && outxy ? 1.f : 0.f);
     // phase D: partial entries tid and tid + NT = (component, node row jy, node column jx)
     bool dD[2];
     int dofs[2];
@@ -261,100 +386,141 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         dofs[q] = ((2 * djy) * NX + djx) * 3 + dc;
     }
 
-    float Uhi[3], Bhi[2][3];   // node plane at the top of the current interval, both columns
-    float fo[2][3];            // fractions of the interval's odd plane
-    int qb[3];                 // integer part of y-hat / h on the interval
-    bool iv_ok[2];             // displacement of the interval representable
-    float pc[2][8], fr[2][3];  // corners and fractions of the next plane, loaded a step ahead
+    float Uhi[3];              // node plane at the top of the current interval (first node)
+    float2 Bhi[3];             // its in-plane part, both columns
+    float2 fo[3];              // fractional sample coordinates of the interval's odd plane
+    int bx0, bx1, by, bz;      // integer bases of the sample cells (with MAGI taken off)
+    bool ok0 = true, ok1 = true;   // displacement of the interval representable, per column
+    float2 pc[8];              // corners of the next plane, both columns, loaded a step ahead
+    float2 fr[3];              // and their fractions
     float2 rnext;              // R of the next plane
     float acc_lo[2] = {0.f, 0.f}, hold[2] = {0.f, 0.f};
-    KahanF psi_sum;
+    KahanF2 psi_sum;
+    int gs = 0;                // grad T slot of this step's plane zA; zA - 4 is in slot gs + 1 (mod 5)
 
     // rows of the x-reduction buffers that no output row writes stay zero
     for (int e = tid; e < 2 * RED_PLANE; e += NT)
         sm[OFF_RED + e] = 0.f;
 
     // ---- A-issue of plane z1: at an even plane (the start of node interval
-    // z1 / 2), P on the interval; then the coordinates of plane z1 and the
-    // loads of its corners and of R, into registers first used one step later
+    // z1 / 2), P on the interval; at an odd plane, the trial values of the node
+    // plane copied at the interval start; then the coordinates of plane z1 and
+    // the loads of its corners and of R, into registers first used one step later
     auto a_issue = [&](int z1, auto odd_t, bool first) {
         constexpr bool ODD = decltype(odd_t)::value;
-        float f[2][3];
+        float2 f[3];
         if (!ODD) {
             const int K1 = z1 >> 1;
-            float Ulo[3], Blo[2][3];
+            float Ulo[3];
+            float2 Blo[3];
             if (first) {
-                column_pair_plane<HAS_DIR>(sm, K1, tx, lky, wy, t, Ulo, Blo);
+                column_pair_plane(sm, K1, tx, lky, WY, Ulo, Blo);
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     Ulo[c] = Uhi[c];
-                    Blo[0][c] = Bhi[0][c];
-                    Blo[1][c] = Bhi[1][c];
+                    Blo[c] = Bhi[c];
                 }
             }
-            column_pair_plane<HAS_DIR>(sm, K1 + 1, tx, lky, wy, t, Uhi, Bhi);
+            column_pair_plane(sm, K1 + 1, tx, lky, WY, Uhi, Bhi);
             // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz) with wz = 1/4 (even z) or
             // 3/4 (odd z).  The sampling coordinate i + y-hat / h is kept as an integer
             // part plus a small fraction; both depend only on the interval and the
             // parity of z, so they are formed once per interval.
-            iv_ok[0] = iv_ok[1] = true;
+            float q0max = 0.f;
+            float2 acc = make_float2(0.f, 0.f);
+            int qb[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const float ih = g.ih[c];
                 const float q0 = Ulo[c] * ih;
                 const float qi = floorf(q0);
                 const float rem = fmaf(-qi, g.h[c], Ulo[c]);   // |rem| <~ h
+                q0max = fmaxf(q0max, fabsf(q0));
                 qb[c] = (int)qi;
-#pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    const float d1 = (Uhi[c] - Ulo[c]) + Bhi[k][c];
-                    iv_ok[k] = iv_ok[k] && fabsf(q0) < 1.0e6f && fabsf(Blo[k][c] * ih) < 1.0e6f &&
-                               fabsf(d1 * ih) < 1.0e6f;
-                    f[k][c] = (rem + lerpf(Blo[k][c], d1, 0.25f)) * ih;
-                    fo[k][c] = (rem + lerpf(Blo[k][c], d1, 0.75f)) * ih;
-                }
+                const float du = Uhi[c] - Ulo[c];
+                const float2 d1 = make_float2(du + Bhi[c].x, du + Bhi[c].y);
+                f[c] = mul2(add2(bc2(rem), lerp2(Blo[c], d1, bc2(0.25f))), bc2(ih));
+                fo[c] = mul2(add2(bc2(rem), lerp2(Blo[c], d1, bc2(0.75f))), bc2(ih));
+                acc = fma2(f[c], f[c], fma2(fo[c], fo[c], acc));
             }
+            // every fraction below 1e6 voxels and finite (NaN fails the tests)
+            ok0 = q0max < 1.0e6f && acc.x < 1.0e12f;
+            ok1 = q0max < 1.0e6f && acc.y < 1.0e12f;
+            bx0 = qb[0] + xa + PADO - MAGI;
+            bx1 = bx0 + 1;
+            by = qb[1] + y + PADO - MAGI;
+            bz = qb[2] + z1 + PADO - MAGI;
             issue_node_plane(nc, a.ub, a.dir, sm, K1 + 2, g.n[2], node_plane);
             cp_async_commit();
         } else {
 #pragma unroll
-            for (int k = 0; k < 2; k++)
+            for (int c = 0; c < 3; c++)
+                f[c] = fo[c];
+            bz += 1;
+            if (HAS_DIR)   // copied at the interval start, visible since the last barrier
+                trial_node_plane(sm, (z1 >> 1) + 2, t, tid);
+        }
+        // integer cells and fractions of both columns: the sum with 1.5 2^23 rounded
+        // down holds floor(f) in its low bits
+        int ix[2][3];
 #pragma unroll
-                for (int c = 0; c < 3; c++)
-                    f[k][c] = fo[k][c];
+        for (int c = 0; c < 3; c++) {
+            const float2 fm = __fadd2_rd(f[c], bc2(MAGF));
+            fr[c] = sub2(f[c], sub2(fm, bc2(MAGF)));
+            ix[0][c] = __float_as_int(fm.x);
+            ix[1][c] = __float_as_int(fm.y);
         }
         const bool zin = col_in && z1 >= 0 && z1 < mz;
 #pragma unroll
         for (int k = 0; k < 2; k++) {
+            const bool okk = k ? ok1 : ok0;
+            const int cx = ix[k][0] + (k ? bx1 : bx0), cy = ix[k][1] + by, cz = ix[k][2] + bz;
+            float v[8];
+            if (PAD) {
+                // cells outside [-2, m] (padded [0, m + 2]) move to the far border, whose
+                // 8 corners are zeros; so do the columns whose displacement is unusable
+                const unsigned ux = okk ? min((unsigned)cx, CXM) : CXM;
+                const unsigned uy = min((unsigned)cy, CYM), uz = min((unsigned)cz, CZM);
+                const IMG *p = Tim + ((size_t)(uy + (unsigned)MYP * uz) * MXP + ux);
+                v[0] = ldimg(p);
+                v[1] = ldimg(p + 1);
+                v[2] = ldimg(p + MXP);
+                v[3] = ldimg(p + MXP + 1);
+                v[4] = ldimg(p + SXYP);
+                v[5] = ldimg(p + SXYP + 1);
+                v[6] = ldimg(p + SXYP + MXP);
+                v[7] = ldimg(p + SXYP + MXP + 1);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 8; j++)
-                pc[k][j] = 0.f;
-            int cc[3];
+                for (int j = 0; j < 8; j++)
+                    v[j] = 0.f;
+                if (zin && okk) {
+                    if ((unsigned)cx < (unsigned)(mx - 1) && (unsigned)cy < (unsigned)(my - 1) &&
+                        (unsigned)cz < (unsigned)(mz - 1)) {   // all 8 corners inside
+                        const IMG *p = Tim + (cx + mx * (cy + my * cz));
+                        v[0] = ldimg(p);
+                        v[1] = ldimg(p + 1);
+                        v[2] = ldimg(p + mx);
+                        v[3] = ldimg(p + mx + 1);
+                        v[4] = ldimg(p + sxy);
+                        v[5] = ldimg(p + sxy + 1);
+                        v[6] = ldimg(p + sxy + mx);
+                        v[7] = ldimg(p + sxy + mx + 1);
+                    } else {   // zero extension corner by corner
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float fl = floorf(f[k][c]);
-                fr[k][c] = f[k][c] - fl;
-                cc[c] = qb[c] + (int)fl;
-            }
-            const int cx = cc[0] + xa + k, cy = cc[1] + y, cz = cc[2] + z1;
-            if (zin && iv_ok[k]) {
-                if ((unsigned)cx < (unsigned)(mx - 1) && (unsigned)cy < (unsigned)(my - 1) &&
-                    (unsigned)cz < (unsigned)(mz - 1)) {   // all 8 corners inside
-                    const IMG *p = Tim + (cx + mx * (cy + my * cz));
-                    pc[k][0] = ldimg(p);
-                    pc[k][1] = ldimg(p + 1);
-                    pc[k][2] = ldimg(p + mx);
-                    pc[k][3] = ldimg(p + mx + 1);
-                    pc[k][4] = ldimg(p + sxy);
-                    pc[k][5] = ldimg(p + sxy + 1);
-                    pc[k][6] = ldimg(p + sxy + mx);
-                    pc[k][7] = ldimg(p + sxy + mx + 1);
-                } else {   // zero extension corner by corner
-#pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        pc[k][j] = ldimg_zero_ext(Tim, mx, my, mz, cx + (j & 1), cy + ((j >> 1) & 1), cz + (j >> 2));
+                        for (int j = 0; j < 8; j++)
+                            v[j] = ldimg_zero_ext(Tim, mx, my, mz, cx + (j & 1), cy + ((j >> 1) & 1),
+                                                  cz + (j >> 2));
+                    }
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (k)
+                    pc[j].y = v[j];
+                else
+                    pc[j].x = v[j];
             }
         }
         rnext = zin ? ldimg2(Rcol + (size_t)sxy * z1) : make_float2(0.f, 0.f);
@@ -364,30 +530,26 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     auto step = [&](int s, auto odd_t) {
         constexpr bool ODD = decltype(odd_t)::value;
         const int zA = z0 - 2 + s;
-        // ---- A-finish: T~ and grad T on plane zA
+        // ---- A-finish: T~ and the interpolant differences on plane zA
         if (zA <= zend + 1) {
-            float val[2], gx[2], gy[2], gz[2];
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const float t000 = pc[k][0], t100 = pc[k][1], t010 = pc[k][2], t110 = pc[k][3];
-                const float t001 = pc[k][4], t101 = pc[k][5], t011 = pc[k][6], t111 = pc[k][7];
-                const float f0 = fr[k][0], f1 = fr[k][1], f2 = fr[k][2];
-                const float a00 = lerpf(t000, t100, f0), a10 = lerpf(t010, t110, f0);
-                const float a01 = lerpf(t001, t101, f0), a11 = lerpf(t011, t111, f0);
-                const float b0 = lerpf(a00, a10, f1), b1 = lerpf(a01, a11, f1);
-                val[k] = lerpf(b0, b1, f2);
-                const float dx0 = lerpf(t100 - t000, t110 - t010, f1), dx1 = lerpf(t101 - t001, t111 - t011, f1);
-                gx[k] = lerpf(dx0, dx1, f2) * g.ih[0];
-                gy[k] = lerpf(a10 - a00, a11 - a01, f2) * g.ih[1];
-                gz[k] = (b1 - b0) * g.ih[2];
-            }
+            // corners: 0 = (0,0,0), 1 = (1,0,0), 2 = (0,1,0), 3 = (1,1,0), 4..7 the same at z + 1
+            const float2 d00 = sub2(pc[1], pc[0]), d10 = sub2(pc[3], pc[2]);
+            const float2 d01 = sub2(pc[5], pc[4]), d11 = sub2(pc[7], pc[6]);
+            const float2 a00 = fma2(fr[0], d00, pc[0]), a10 = fma2(fr[0], d10, pc[2]);
+            const float2 a01 = fma2(fr[0], d01, pc[4]), a11 = fma2(fr[0], d11, pc[6]);
+            const float2 e0 = sub2(a10, a00), e1 = sub2(a11, a01);
+            const float2 b0 = fma2(fr[1], e0, a00), b1 = fma2(fr[1], e1, a01);
+            const float2 gz = sub2(b1, b0);
+            const float2 val = fma2(fr[2], gz, b0);
+            const float2 gy = lerp2(e0, e1, fr[2]);
+            const float2 gx = lerp2(lerp2(d00, d10, fr[1]), lerp2(d01, d11, fr[1]), fr[2]);
             const int slot = zA & 3;
-            sts2(sm + OFF_T + slot * PLANE + sp, val[0], val[1]);
-            sts2(sm + OFF_R + slot * PLANE + sp, rnext.x, rnext.y);
-            float *gq = sm + OFF_G + (zA & 7) * 3 * PLANE + sp;
-            sts2(gq, gx[0], gx[1]);
-            sts2(gq + PLANE, gy[0], gy[1]);
-            sts2(gq + 2 * PLANE, gz[0], gz[1]);
+            sts2(sm + OFF_T + slot * PLANE + sp, val);
+            sts2(sm + OFF_R + slot * PLANE + sp, rnext);
+            float *gq = sm + OFF_G + gs * 3 * PLANE + sp;
+            sts2(gq, gx);
+            sts2(gq + PLANE, gy);
+            sts2(gq + 2 * PLANE, gz);
         }
         // ---- A-issue for plane zA + 1
         if (zA <= zend)
@@ -404,40 +566,35 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             const float2 t0 = lds2(T0), r0 = lds2(R0);
             const float tl = __shfl_up_sync(0xffffffffu, t0.y, 1, BX), tr = __shfl_down_sync(0xffffffffu, t0.x, 1, BX);
             const float rl = __shfl_up_sync(0xffffffffu, r0.y, 1, BX), rr = __shfl_down_sync(0xffffffffu, r0.x, 1, BX);
-            float va[3] = {0.f, 0.f, 0.f}, vb[3] = {0.f, 0.f, 0.f};
+            float2 v[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             if (rowB && (intA || intB) && zB >= 1 && zB <= mz - 2) {
                 const int op = ((zB + 1) & 3) * PLANE + sp, om = ((zB - 1) & 3) * PLANE + sp;
                 const float2 typ = lds2(T0 + CW), tym = lds2(T0 - CW);
                 const float2 tzp = lds2(sm + OFF_T + op), tzm = lds2(sm + OFF_T + om);
                 const float2 ryp = lds2(R0 + CW), rym = lds2(R0 - CW);
                 const float2 rzp = lds2(sm + OFF_R + op), rzm = lds2(sm + OFF_R + om);
-                const bool out = outxy && zB >= z0 && zB < zend;
-                if (intA) {
-                    const float av[3] = {(t0.y - tl) * hx, (typ.x - tym.x) * hy, (tzp.x - tzm.x) * hz};
-                    const float bv[3] = {(r0.y - rl) * hx, (ryp.x - rym.x) * hy, (rzp.x - rzm.x) * hz};
-                    const float psi = ngf_residual(av, bv, a.tau, a.rho, va);
-                    if (out)
-                        psi_sum.add(psi);
-                }
-                if (intB) {
-                    const float av[3] = {(tr - t0.x) * hx, (typ.y - tym.y) * hy, (tzp.y - tzm.y) * hz};
-                    const float bv[3] = {(rr - r0.x) * hx, (ryp.y - rym.y) * hy, (rzp.y - rzm.y) * hz};
-                    const float psi = ngf_residual(av, bv, a.tau, a.rho, vb);
-                    if (out)
-                        psi_sum.add(psi);
-                }
+                const float2 av[3] = {mul2(make_float2(t0.y - tl, tr - t0.x), HX), mul2(sub2(typ, tym), HY),
+                                      mul2(sub2(tzp, tzm), HZ)};
+                const float2 bv[3] = {mul2(make_float2(r0.y - rl, rr - r0.x), HX), mul2(sub2(ryp, rym), HY),
+                                      mul2(sub2(rzp, rzm), HZ)};
+                const float2 psi = ngf_residual2(av, bv, a.tau, a.rho, v);
+                v[0] = mul2(v[0], MI);
+                v[1] = mul2(v[1], MI);
+                v[2] = mul2(v[2], MI);
+                if (zB >= z0 && zB < zend)
+                    psi_sum.add(mul2(psi, MO));
             }
             if (rowB) {
                 float *vq = sm + OFF_V + (zB & 3) * 3 * PLANE + sp;
-                sts2(vq, va[0], vb[0]);
-                sts2(vq + PLANE, va[1], vb[1]);
-                sts2(vq + 2 * PLANE, va[2], vb[2]);
+                sts2(vq, v[0]);
+                sts2(vq + PLANE, v[1]);
+                sts2(vq + 2 * PLANE, v[2]);
             }
         }
         // ---- C: r on plane zA - 4 (rows 2 .. 29), x reduction into node columns
         const int zC = zA - 4;
         if (rowC && zC >= z0 && zC < zend) {   // uniform per warp (a warp holds rows 2w, 2w + 1)
-            float ra[3] = {0.f, 0.f, 0.f}, rb[3] = {0.f, 0.f, 0.f};
+            float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             // v_x of the pair and of its x neighbours (columns 2tx - 1, 2tx + 2) from the threads beside it
             const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + sp;
             const float2 vx = lds2(V0);
@@ -447,23 +604,20 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                 const float *Vzp = sm + OFF_V + ((zC + 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
                 const float2 vyp = lds2(V0 + PLANE + CW), vym = lds2(V0 + PLANE - CW);
                 const float2 vzm = lds2(Vzm), vzp = lds2(Vzp);
-                const float gja = half_hbar * ((vl - vx.y) * hx + (vym.x - vyp.x) * hy + (vzm.x - vzp.x) * hz);
-                const float gjb = half_hbar * ((vx.x - vr) * hx + (vym.y - vyp.y) * hy + (vzm.y - vzp.y) * hz);
-                const float *gq = sm + OFF_G + (zC & 7) * 3 * PLANE + sp;
-                const float2 g0 = lds2(gq), g1 = lds2(gq + PLANE), g2 = lds2(gq + 2 * PLANE);
-                ra[0] = gja * g0.x;
-                ra[1] = gja * g1.x;
-                ra[2] = gja * g2.x;
-                rb[0] = gjb * g0.y;
-                rb[1] = gjb * g1.y;
-                rb[2] = gjb * g2.y;
+                // adjoint of the central differences (without the factor hbar / 2)
+                const float2 gj = fma2(make_float2(vl - vx.y, vx.x - vr), HX,
+                                       fma2(sub2(vym, vyp), HY, mul2(sub2(vzm, vzp), HZ)));
+                const float *gq = sm + OFF_G + (gs == GSLOTS - 1 ? 0 : gs + 1) * 3 * PLANE + sp;
+                r[0] = mul2(gj, lds2(gq));
+                r[1] = mul2(gj, lds2(gq + PLANE));
+                r[2] = mul2(gj, lds2(gq + 2 * PLANE));
             }
             // node column j (0..14) gathers columns 2j .. 2j+3 with weights 1/4, 3/4,
             // 3/4, 1/4: the first two are thread j's pair, the last two thread j+1's
             float *red = sm + OFF_RED + (ODD ? 0 : 1) * RED_PLANE + ty * NX * 3;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const float lo = 0.25f * ra[c] + 0.75f * rb[c], hi = 0.75f * ra[c] + 0.25f * rb[c];
+                const float lo = fmaf(0.75f, r[c].y, 0.25f * r[c].x), hi = fmaf(0.25f, r[c].y, 0.75f * r[c].x);
                 const float nv = lo + __shfl_down_sync(0xffffffffu, hi, 1, BX);
                 if (tx < NX)
                     red[tx * 3 + c] = nv;
@@ -492,11 +646,13 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                     }
                 }
         }
+        gs = gs == GSLOTS - 1 ? 0 : gs + 1;
         cp_async_wait_all();
         __syncthreads();
     };
 
-    // prologue: node planes of the first interval, then the loads of plane z0 - 2
+    // prologue: node planes of the first interval (and their trial values), then
+    // the loads of plane z0 - 2
     {
         const int K0 = (z0 - 2) >> 1;
         issue_node_plane(nc, a.ub, a.dir, sm, K0, g.n[2], node_plane);
@@ -504,6 +660,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
+        if (HAS_DIR) {
+            trial_node_plane(sm, K0, t, tid);
+            trial_node_plane(sm, K0 + 1, t, tid);
+            __syncthreads();
+        }
         a_issue(z0 - 2, std::false_type{}, true);
         cp_async_wait_all();
         __syncthreads();
@@ -516,16 +677,17 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         if (s + 1 < nsteps)
             step(s + 1, std::false_type{});
     }
-    double ssum = block_sum_to_f64(psi_sum.s, reinterpret_cast<double *>(sm + OFF_RED));
+    const float2 ps = psi_sum.s;
+    double ssum = block_sum_to_f64(ps.x + ps.y, reinterpret_cast<double *>(sm + OFF_RED));
     if (tid == 0)
         a.partials[tile_lin] = ssum;
 }
 
-template <bool HAS_DIR, typename IMG = float>
+template <bool HAS_DIR, typename IMG = float, bool PAD = true>
 __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
 {
     extern __shared__ float sm[];
-    fused_tile<HAS_DIR, IMG>(a, blockIdx.x, sm);
+    fused_tile<HAS_DIR, IMG, PAD>(a, blockIdx.x, sm);
 }
 
 // Batched fused pass: a persistent grid walks the tiles of all pairs.  Mode 0
@@ -542,7 +704,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused_batch(const PairLevel 
         if (HAS_DIR && !(P.st->active && P.st->ls_continue))
             continue;   // uniform over the CTA
         const FusedArgs &a = HAS_DIR ? P.fa_trial : P.fa_init;
-        fused_tile<HAS_DIR, IMG>(a, item - __ldg(tile_off + p), sm);
+        fused_tile<HAS_DIR, IMG, true>(a, item - __ldg(tile_off + p), sm);
         __syncthreads();   // the next tile reuses the shared rings
     }
 }
@@ -620,6 +782,10 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
         s[1] += __ldg(p + NX * NY);
         s[2] += __ldg(p + 2 * NX * NY);
     }
+    // the pass leaves out the factor hbar / 2 of the adjoint and 1 / h_c of the
+    // interpolant gradient: component c of P^T r is hbar / (2 h_c) times the sum
+    const float hh = 0.5f * g.hbar;
+    const float sc[3] = {hh * g.ih[0], hh * g.ih[1], hh * g.ih[2]};
     const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
     const int k = kx + n0 * ky + n01 * kz;
     const int st[3] = {1, n0, n01};
@@ -635,7 +801,7 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
             const float hi = j[e] < g.n[e] - 1 ? __ldg(wc + k + st[e]) : 0.f;
             l = fmaf(lo + hi - 2.f * w0, g.iH2[e], l);
         }
-        grad[c * g.nn + k] = fmaf(alpha_hy, l, s[c]);
+        grad[c * g.nn + k] = fmaf(alpha_hy, l, sc[c] * s[c]);
     }
 }
 
@@ -857,7 +1023,7 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     FusedArgs a;
     a.g = L.geom();
     const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
-    a.T = bf16 ? L.Tb : static_cast<const void *>(L.T);
+    a.T = bf16 ? static_cast<const void *>(L.Tb) : static_cast<const void *>(L.Tp);   // zero-bordered copies
     a.R = bf16 ? L.Rb : static_cast<const void *>(L.R);
     a.ub = ub;
     a.dir = dir;
@@ -875,14 +1041,13 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     static bool attr_set[64] = {};
     const int dev = c->device >= 0 && c->device < 64 ? c->device : 0;
     if (!attr_set[dev]) {
-        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        cudaError_t e = cudaFuncSetAttribute(k_ngf_fused<true, float>, at, (int)SMEM_BYTES);
+        cudaError_t e = set_fused_smem(k_ngf_fused<true, float>);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ngf_fused<false, float>, at, (int)SMEM_BYTES);
+            e = set_fused_smem(k_ngf_fused<false, float>);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ngf_fused<true, __nv_bfloat16>, at, (int)SMEM_BYTES);
+            e = set_fused_smem(k_ngf_fused<true, __nv_bfloat16>);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ngf_fused<false, __nv_bfloat16>, at, (int)SMEM_BYTES);
+            e = set_fused_smem(k_ngf_fused<false, __nv_bfloat16>);
         if (e != cudaSuccess)
             return e;
         attr_set[dev] = true;
@@ -1061,13 +1226,10 @@ void fused_layout_dims(const int m[3], int num_sms, int *tz, int *tiles, size_t 
     *part_floats = (size_t)ncols * sp.planes_before(sp.count()) * NE;
 }
 
+// the explicit-buffer pass reads the caller's unpadded T (bounds-tested corner loads)
 cudaError_t fused_set_smem_limit()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_ngf_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_ngf_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    return e;
+    return set_fused_smem(k_ngf_fused<false, float, false>);
 }
 
 cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float *R, const float *u, float tau,
@@ -1088,7 +1250,7 @@ cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float
     a.part = part;
     a.partials = partials;
     dim3 blk(BX, BY, 1), grd(a.ntx * a.nty * a.split.count(), 1, 1);
-    k_ngf_fused<false><<<grd, blk, SMEM_BYTES, s>>>(a);
+    k_ngf_fused<false, float, false><<<grd, blk, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1113,14 +1275,13 @@ cudaError_t launch_fused_batch(const PairLevel *pl, const int *tile_off, int npa
 {
     const int dev = device >= 0 && device < 64 ? device : 0;
     if (!g_batch_attr_set[dev]) {
-        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        cudaError_t e = cudaFuncSetAttribute(k_ngf_fused_batch<true, float>, at, (int)SMEM_BYTES);
+        cudaError_t e = set_fused_smem(k_ngf_fused_batch<true, float>);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ngf_fused_batch<false, float>, at, (int)SMEM_BYTES);
+            e = set_fused_smem(k_ngf_fused_batch<false, float>);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ngf_fused_batch<true, __nv_bfloat16>, at, (int)SMEM_BYTES);
+            e = set_fused_smem(k_ngf_fused_batch<true, __nv_bfloat16>);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ngf_fused_batch<false, __nv_bfloat16>, at, (int)SMEM_BYTES);
+            e = set_fused_smem(k_ngf_fused_batch<false, __nv_bfloat16>);
         if (e != cudaSuccess)
             return e;
         g_batch_attr_set[dev] = true;

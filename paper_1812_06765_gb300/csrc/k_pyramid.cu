@@ -74,7 +74,49 @@ __global__ void __launch_bounds__(256) k_to_bf16(const float *__restrict__ src, 
         dst[4 * n4 + threadIdx.x] = __float2bfloat16_rn(src[4 * n4 + threadIdx.x]);
 }
 
+__device__ __forceinline__ void pad_store(float *p, float v) { *p = v; }
+__device__ __forceinline__ void pad_store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+// Zero-bordered copy of a volume (dims m) into an array of dims m + 4 with the
+// volume at offset 2 in every dimension: one thread per element of the
+// padded array, so the border is written too.
+template <typename TOUT>
+__global__ void __launch_bounds__(256) k_pad_template(const float *__restrict__ src, int mx, int my, int mz,
+                                                      TOUT *__restrict__ dst)
+{
+    const int px = mx + 4, py = my + 4;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= px || y >= py)
+        return;
+    const int sx = x - 2, sy = y - 2, sz = z - 2;
+    const bool in = (unsigned)sx < (unsigned)mx && (unsigned)sy < (unsigned)my && (unsigned)sz < (unsigned)mz;
+    const float v = in ? __ldg(src + ((size_t)sz * my + sy) * mx + sx) : 0.f;
+    pad_store(dst + ((size_t)z * py + y) * px + x, v);
+}
+
+template <typename TOUT>
+cudaError_t launch_pad(const float *src, const int m[3], TOUT *dst, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    dim3 grd((m[0] + 4 + 31) / 32, (m[1] + 4 + 7) / 8, m[2] + 4);
+    k_pad_template<TOUT><<<grd, blk, 0, s>>>(src, m[0], m[1], m[2], dst);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+long long padded_voxels(const int m[3]) { return (long long)(m[0] + 4) * (m[1] + 4) * (m[2] + 4); }
+
+cudaError_t launch_pad_template(const float *src, const int m[3], float *dst, cudaStream_t s)
+{
+    return launch_pad(src, m, dst, s);
+}
+
+cudaError_t launch_pad_template(const float *src, const int m[3], __nv_bfloat16 *dst, cudaStream_t s)
+{
+    return launch_pad(src, m, dst, s);
+}
 
 cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s)
 {

@@ -17,6 +17,7 @@ void free_level(Level &L)
 {
     cudaFree(L.R);
     cudaFree(L.T);
+    cudaFree(L.Tp);
     cudaFree(L.Rb);
     cudaFree(L.Tb);
     for (int d = 0; d < 3; d++) {
@@ -290,12 +291,17 @@ int allocate_buffers(reg_ctx *c)
         CK(cudaMalloc(&es.part, sizeof(float) * part));
         es.part_floats = part;
     }
-    if (cfg.image_dtype == 1)   // BF16 copies for the levels the fused pass serves
-        for (int l = 0; l < c->levels; l++)
-            if (use_fused(c, l)) {
+    // the fused pass reads T through a zero-bordered copy (FP32, or BF16 beside a BF16 R)
+    for (int l = 0; l < c->levels; l++)
+        if (use_fused(c, l)) {
+            const long long np = padded_voxels(c->L[l].m);
+            if (cfg.image_dtype == 1) {
                 CK(cudaMalloc(&c->L[l].Rb, sizeof(__nv_bfloat16) * c->L[l].nv));
-                CK(cudaMalloc(&c->L[l].Tb, sizeof(__nv_bfloat16) * c->L[l].nv));
+                CK(cudaMalloc(&c->L[l].Tb, sizeof(__nv_bfloat16) * np));
+            } else {
+                CK(cudaMalloc(&c->L[l].Tp, sizeof(float) * np));
             }
+        }
     CK(cudaMalloc(&es.w, sizeof(float) * nmax));
     CK(cudaMalloc(&es.partials, sizeof(double) * maxpart));
     CK(cudaMalloc(&es.scal, sizeof(double) * 4));
@@ -477,12 +483,17 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
     }
     CK(cudaEventRecord(c->ev_side, c->side));
     CK(cudaStreamWaitEvent(c->stream, c->ev_side, 0));
-    for (int l = 0; l < c->levels; l++)   // BF16 copies (image_dtype 1), rounded to nearest even
+    for (int l = 0; l < c->levels; l++) {   // the fused pass's copies; BF16 rounded to nearest even
         if (c->L[l].Rb) {
             CK(launch_to_bf16(c->L[l].R, c->L[l].Rb, c->L[l].nv, c->stream));
-            CK(launch_to_bf16(c->L[l].T, c->L[l].Tb, c->L[l].nv, c->stream));
+            CK(launch_pad_template(c->L[l].T, c->L[l].m, c->L[l].Tb, c->stream));
             c->launches += 2;
         }
+        if (c->L[l].Tp) {
+            CK(launch_pad_template(c->L[l].T, c->L[l].m, c->L[l].Tp, c->stream));
+            c->launches += 1;
+        }
+    }
     // tiling of the fused pass per level: forced, autotuned (at u = 0, with the
     // direction buffer as the zero field) or the default rule
     for (int l = 0; l < c->levels; l++) {
