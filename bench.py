@@ -71,6 +71,9 @@ def parse_args(argv=None):
                     help="time one full-resolution evaluation with each P^T design: fused gather, multi-pass "
                          "gather (Eq. 3), multi-pass atomic scatter, multi-pass 8-colour scatter")
     ap.add_argument("--pairs", type=int, default=None, help="pairs of the uneven batch (workload 4; default 64)")
+    ap.add_argument("--sub-batches", type=int, default=1,
+                    help="workload 4: register the pairs in this many batches one after another, smallest "
+                         "pairs first (each pair is done when its batch is)")
     ap.add_argument("--gen-procs", type=int, default=None, help="processes that generate the batch's pairs")
     ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
                     help="image size of the full-resolution workload (5) instead of its 512^3")
@@ -530,13 +533,21 @@ def run_batch(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     restrict_launches = 2 * (levels - 1)
 
-    def load_all():
-        for i in range(n):
-            regs[i].set_images(Rd[i], Td[i], pairs[i][3])
+    # sub-batches, smallest pairs first: a pair's result is complete when its batch returns
+    nsub = max(1, min(args.sub_batches, n))
+    by_size = sorted(range(n), key=lambda i: int(np.prod(pairs[i][2])))
+    subs = [by_size[k * n // nsub:(k + 1) * n // nsub] for k in range(nsub)]
 
-    def step_batch():
-        load_all()
-        return reg_pkg.register_batch(regs, out="torch")
+    def step_batch(marks=None):
+        res = [None] * n
+        for k, idx in enumerate(subs):
+            for i in idx:
+                regs[i].set_images(Rd[i], Td[i], pairs[i][3])
+            for i, r in zip(idx, reg_pkg.register_batch([regs[i] for i in idx], out="torch")):
+                res[i] = r
+            if marks is not None:
+                marks[k].record(stream)
+        return res
 
     def step_loop(marks=None):
         res = []
@@ -558,15 +569,16 @@ def run_batch(args):
     t_batch, done_batch, launches_batch = [], [], 0
     for _ in range(args.steps):
         flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in subs]
         e0.record(stream)
-        res_b = step_batch()
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
+        res_b = step_batch(marks)
+        marks[-1].synchronize()
+        ms = e0.elapsed_time(marks[-1])
         t_batch.append(ms)
-        done_batch += [ms] * n                      # every result lands when the batch returns
-        launches_batch += res_b[0][1]["kernel_launches"] + restrict_launches * n
+        for k, idx in enumerate(subs):              # every result of a batch lands when it returns
+            done_batch += [e0.elapsed_time(marks[k])] * len(idx)
+        launches_batch += sum(res_b[idx[0]][1]["kernel_launches"] for idx in subs) + restrict_launches * n
     t_loop, done_loop, own_loop, launches_loop = [], [], [], 0
     for _ in range(args.steps):
         flush.zero_()
@@ -608,6 +620,7 @@ def run_batch(args):
             info = regs[i].level_info(lv)
             eval_bytes += res_b[i][1]["evals"][lv] * (8 * int(np.prod(info["dims"])) + 24 * int(np.prod(info["nodes"])))
     eff_gbs = eval_bytes / (statistics.mean(t_batch) * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
 
     # end to end from pinned host images, results back into pinned host memory
     Rh = [torch.from_numpy(p[0]).pin_memory() for p in pairs]
@@ -617,9 +630,10 @@ def run_batch(args):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for i in range(n):
-            regs[i].set_images(Rh[i], Th[i], pairs[i][3])
-        reg_pkg.register_batch(regs, out="pinned")
+        for idx in subs:
+            for i in idx:
+                regs[i].set_images(Rh[i], Th[i], pairs[i][3])
+            reg_pkg.register_batch([regs[i] for i in idx], out="pinned")
         e2e.append(time.perf_counter() - t0)
     e2e_s = dist_reduce(statistics.mean(e2e), "max", dev)
     h2d = sum(8 * int(np.prod(p[2])) for p in pairs)
@@ -639,10 +653,10 @@ def run_batch(args):
                        "max_iter_per_level": c["max_iter"],
                        "l2": "flushed between steps (2x L2 buffer written, untimed); inputs exceed L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "batched": {"pairs_s": pairs_s_batch, "p50_ms": percentile_ms(done_batch, 50),
+            "batched": {"pairs_s": pairs_s_batch, "sub_batches": nsub, "p50_ms": percentile_ms(done_batch, 50),
                         "p99_ms": percentile_ms(done_batch, 99), "step_ms": statistics.mean(t_batch),
-                        "level_device_s": res_b[0][1]["level_seconds"],
-                        "tiling_rule_per_level": res_b[0][1]["tiling"],
+                        "level_device_s": res_b[subs[-1][0]][1]["level_seconds"],
+                        "tiling_rule_per_level": res_b[subs[-1][0]][1]["tiling"],
                         "gpu_launches_per_step": launches_batch // max(1, args.steps)},
             "per_pair_loop": {"pairs_s": pairs_s_loop, "p50_ms": percentile_ms(done_loop, 50),
                               "p99_ms": percentile_ms(done_loop, 99), "step_ms": statistics.mean(t_loop),
@@ -659,7 +673,11 @@ def run_batch(args):
                                          "loop: each pair's single-pair autotuned tiling (tests/test_gpu_batch.py: "
                                          "with the same tiling the two forms are bit-identical)"},
             "effective_eval_gbs": eff_gbs,
-            "roofline": None,
+            "roofline": {"bound": "hbm", "achieved": eff_gbs, "peak": peak, "unit": "GB/s", "frac": eff_gbs / peak,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "what": "whole batched step: every pair's evaluation bytes (read R, T, u, write grad J "
+                                 "per evaluation, all levels) over the batch's step time, which also holds the "
+                                 "L-BFGS vector passes and the pyramids"},
             "e2e": {"value": world * n / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "batch_s": e2e_s},
             "gpu_launches": launches_batch + launches_loop,
