@@ -527,11 +527,12 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     };
 
     // ---- one step of the pipeline; ODD: planes zA + 1 and zA - 5 are odd
-    auto step = [&](int s, auto odd_t) {
+    auto step = [&](int s, auto odd_t, auto full_t) {
+        constexpr bool FULL = decltype(full_t)::value;   // every phase active: no range tests
         constexpr bool ODD = decltype(odd_t)::value;
         const int zA = z0 - 2 + s;
         // ---- A-finish: T~ and the interpolant differences on plane zA
-        if (zA <= zend + 1) {
+        if (FULL || zA <= zend + 1) {
             // corners: 0 = (0,0,0), 1 = (1,0,0), 2 = (0,1,0), 3 = (1,1,0), 4..7 the same at z + 1
             const float2 d00 = sub2(pc[1], pc[0]), d10 = sub2(pc[3], pc[2]);
             const float2 d01 = sub2(pc[5], pc[4]), d11 = sub2(pc[7], pc[6]);
@@ -552,11 +553,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             sts2(gq + 2 * PLANE, gz);
         }
         // ---- A-issue for plane zA + 1
-        if (zA <= zend)
+        if (FULL || zA <= zend)
             a_issue(zA + 1, std::integral_constant<bool, ODD>{}, false);
         // ---- B: v on plane zA - 2 (rows 1 .. 30)
         const int zB = zA - 2;
-        if (zB >= z0 - 1 && zB <= zend) {
+        if (FULL || (zB >= z0 - 1 && zB <= zend)) {
             // the pair's own T~ and R (every row), and its x neighbours from the
             // threads beside it: column 2tx - 1 is thread tx - 1's second column,
             // 2tx + 2 thread tx + 1's first (lanes 0 and 31 get their own values;
@@ -581,7 +582,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                 v[0] = mul2(v[0], MI);
                 v[1] = mul2(v[1], MI);
                 v[2] = mul2(v[2], MI);
-                if (zB >= z0 && zB < zend)
+                if (FULL || (zB >= z0 && zB < zend))
                     psi_sum.add(mul2(psi, MO));
             }
             if (rowB) {
@@ -593,7 +594,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         }
         // ---- C: r on plane zA - 4 (rows 2 .. 29), x reduction into node columns
         const int zC = zA - 4;
-        if (rowC && zC >= z0 && zC < zend) {   // uniform per warp (a warp holds rows 2w, 2w + 1)
+        if (rowC && (FULL || (zC >= z0 && zC < zend))) {   // uniform per warp (a warp holds rows 2w, 2w + 1)
             float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             // v_x of the pair and of its x neighbours (columns 2tx - 1, 2tx + 2) from the threads beside it
             const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + sp;
@@ -627,7 +628,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         // along z: an even plane gives 3/4 to the lower node plane of its interval
         // and 1/4 to the upper, an odd plane the reverse
         const int zD = zA - 5;
-        if (zD >= z0 && zD < zend) {
+        if (FULL || (zD >= z0 && zD < zend)) {
             const float *red = sm + OFF_RED + (ODD ? 1 : 0) * RED_PLANE;
             const int lz = zD - z0;
 #pragma unroll
@@ -672,10 +673,24 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
 
     // z0 is even: zA + 1 is odd on even steps
     const int nsteps = tz + 7;
-    for (int s = 0; s < nsteps; s += 2) {
-        step(s, std::true_type{});
+    // steps s and s + 1 in turn (z0 is even: zA + 1 is odd on even steps); from
+    // step 7 to step tz + 2 every phase is active, and those steps run without
+    // the range tests, so the phases of a step form one block of code the
+    // compiler can interleave
+    int s = 0;
+    for (; s < 8 && s < nsteps; s += 2) {
+        step(s, std::true_type{}, std::false_type{});
         if (s + 1 < nsteps)
-            step(s + 1, std::false_type{});
+            step(s + 1, std::false_type{}, std::false_type{});
+    }
+    for (; s + 1 <= tz + 2; s += 2) {
+        step(s, std::true_type{}, std::true_type{});
+        step(s + 1, std::false_type{}, std::true_type{});
+    }
+    for (; s < nsteps; s += 2) {
+        step(s, std::true_type{}, std::false_type{});
+        if (s + 1 < nsteps)
+            step(s + 1, std::false_type{}, std::false_type{});
     }
     const float2 ps = psi_sum.s;
     double ssum = block_sum_to_f64(ps.x + ps.y, reinterpret_cast<double *>(sm + OFF_RED));
