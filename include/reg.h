@@ -92,7 +92,8 @@ typedef struct reg_config {
                              per geometry for the process; the first call of a geometry
                              synchronises the stream); 0: the model's choice */
     int fused_tz;         /* 0: autotune / model; -1: the throughput rule (fewest z steps in
-                             total over 2, 4, 8, .. 128, the tiling reg_register_batch uses);
+                             total over 2, 4, 8, .. 128) with the fused pass forming the
+                             curvature sum per tile, as reg_register_batch computes it;
                              else this z segment length on every level (even, 2 .. 512) */
     int test_expire_wait; /* test hook, 0 in normal use: 1 makes block 0 of the first L-BFGS
                              direction pass of reg_register arm one bulk-copy stage without
@@ -286,8 +287,8 @@ int reg_register(reg_handle h, float *u_out, int out_is_device, const float *u_i
  * the computation of reg_register with its own configuration, so its result is
  * the one reg_register gives when the pair's handle tiles the fused pass the
  * same way: the batch keeps every SM busy, so it tiles each level by the
- * throughput rule (cfg.fused_tz = -1) whatever tiling the handle's own
- * registrations use.  u_out[i]: the finest displacement of pair i
+ * throughput rule and forms the curvature sum inside the fused pass
+ * (cfg.fused_tz = -1) whatever the handle's own registrations use.  u_out[i]: the finest displacement of pair i
  * (device pointers if out_is_device, else host); stats (nullable) receives n
  * entries (kernel_launches counts the launches of the whole batch).  Work runs
  * on hs[0]'s stream, as one CUDA graph per level, or queued from the host when

@@ -44,6 +44,8 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     a.nty = nty;
     a.part = c->es.part;
     a.partials = c->es.partials;
+    a.w = c->es.w;
+    a.partials_S = c->es.partials + ntx * nty * split.count();   // after the D partials
     P.fa_init = a;
     a.dir = c->lb.pdir;
     a.t_dev = &c->lb.st->t;
@@ -53,7 +55,7 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     P.ncx = (L.n[0] + 31) / 32;
     P.ncy = (L.n[1] + 7) / 8;
     P.nD = ntx * nty * split.count();
-    P.nS = P.ncx * P.ncy * curv_zchunks(L.n[2]);
+    P.nS = P.nD;   // the fused pass writes one S partial per tile
     P.ngather = P.ncx * P.ncy * L.n[2];
     P.w = c->es.w;
     P.pS = c->es.partials + P.nD;
@@ -81,7 +83,7 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
 
 struct BatchDev {
     PairLevel *pl = nullptr;
-    int *off = nullptr;      // [4][npairs + 1]: tiles, gather blocks, vector blocks, curvature blocks
+    int *off = nullptr;      // [3][npairs + 1]: tiles, gather blocks, vector blocks
     int *counters = nullptr; // [4]: runs of the iteration and search conditions, then their last values
 };
 
@@ -126,26 +128,15 @@ cudaError_t while_node(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, 
 
 struct BatchLaunch {
     const BatchDev *d;
-    int npairs, tiles, nodes, chunks, curv;
-    int g_fused, g_nodes, g_chunks, g_curv;
+    int npairs, tiles, nodes, chunks;
+    int g_fused, g_nodes, g_chunks;
     bool bf16;
     int device;
-    cudaStream_t side;             // the curvature pass runs beside the fused pass
-    cudaEvent_t ev_fork, ev_join;
 
     cudaError_t eval(int mode, cudaStream_t s) const
     {
-        cudaError_t e = cudaEventRecord(ev_fork, s);
-        if (e == cudaSuccess)
-            e = cudaStreamWaitEvent(side, ev_fork, 0);
-        if (e == cudaSuccess)
-            e = launch_fused_batch(d->pl, d->off, npairs, tiles, mode, bf16, g_fused, device, s);
-        if (e == cudaSuccess)
-            e = launch_curv_w_batch(d->pl, d->off + 3 * (npairs + 1), npairs, curv, mode, g_curv, side);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(ev_join, side);
-        if (e == cudaSuccess)
-            e = cudaStreamWaitEvent(s, ev_join, 0);
+        // the fused pass also forms each pair's curvature Laplacian and S partials
+        cudaError_t e = launch_fused_batch(d->pl, d->off, npairs, tiles, mode, bf16, g_fused, device, s);
         if (e == cudaSuccess)
             e = launch_gather_batch(d->pl, d->off + (npairs + 1), npairs, nodes, mode, g_nodes, s);
         if (e == cudaSuccess)
@@ -233,9 +224,7 @@ cudaError_t build_batch_graph(const BatchLaunch &B, cudaStream_t cs, cudaGraphEx
         guard.active = false;
         BK(cudaStreamEndCapture(cs, &g2));
     }
-    for (cudaGraph_t g : {G, body, ls_body})   // the curvature pass fills the SMs the fused pass leaves idle
-        BK(set_graph_kernel_priorities(g, curv_w_batch_kernel()));
-    BK(cudaGraphInstantiate(out, G, cudaGraphInstantiateFlagUseNodePriority));
+    BK(cudaGraphInstantiate(out, G, 0));
     cudaGraphDestroy(G);
     return cudaSuccess;
 }
@@ -417,7 +406,7 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     }
     BatchDev d;
     CK(cudaMallocAsync((void **)&d.pl, sizeof(PairLevel) * n, s));
-    CK(cudaMallocAsync((void **)&d.off, sizeof(int) * 4 * (n + 1), s));
+    CK(cudaMallocAsync((void **)&d.off, sizeof(int) * 3 * (n + 1), s));
     CK(cudaMallocAsync((void **)&d.counters, sizeof(int) * 4, s));
     // every pair's own stream work (prolongations, state uploads) is ordered on c0's stream
     for (int i = 0; i < n; i++) {
@@ -427,13 +416,13 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
     long long launches = 0;
     int status = REG_OK;
     std::vector<PairLevel> hpl(n);
-    std::vector<int> hoff(4 * (n + 1));
+    std::vector<int> hoff(3 * (n + 1));
     if (!c0->lev_ev[0])
         for (int i = 0; i <= REG_MAX_LEVELS; i++)
             CK(cudaEventCreate(&c0->lev_ev[i]));
     for (int l = start; l >= 0 && status >= 0; l--) {
         CK(cudaEventRecord(c0->lev_ev[l + 1], s));
-        int tiles = 0, nodes = 0, chunks = 0, curv = 0;
+        int tiles = 0, nodes = 0, chunks = 0;
         // Tiling of the batched level: the batch keeps every SM busy, so the
         // single-pair tiling of each handle is not necessarily the right one.
         // hs[0]'s cfg.fused_tz forces a rule; otherwise the batch autotuner picks
@@ -481,22 +470,18 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
             hoff[i] = tiles;
             hoff[(n + 1) + i] = nodes;
             hoff[2 * (n + 1) + i] = chunks;
-            hoff[3 * (n + 1) + i] = curv;
             tiles += hpl[i].nD;
             nodes += hpl[i].ngather;
             chunks += hpl[i].nchunks;
-            curv += hpl[i].nS;
         }
         hoff[n] = tiles;
         hoff[(n + 1) + n] = nodes;
         hoff[2 * (n + 1) + n] = chunks;
-        hoff[3 * (n + 1) + n] = curv;
         CK(cudaMemcpyAsync(d.pl, hpl.data(), sizeof(PairLevel) * n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d.off, hoff.data(), sizeof(int) * hoff.size(), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(d.counters, 0, sizeof(int) * 4, s));
-        BatchLaunch B{&d, n, tiles, nodes, chunks, curv, cap(tiles, c0->num_sms), cap(nodes, 8LL * c0->num_sms),
-                      cap(chunks, 4LL * c0->num_sms), cap(curv, 8LL * c0->num_sms), bf16, c0->device,
-                      c0->side, c0->ev_fork, c0->ev_join};
+        BatchLaunch B{&d, n, tiles, nodes, chunks, cap(tiles, c0->num_sms), cap(nodes, 8LL * c0->num_sms),
+                      cap(chunks, 4LL * c0->num_sms), bf16, c0->device};
         cudaError_t e = cudaSuccess;
         if (c0->cfg.use_graph) {
             cudaGraphExec_t exec = nullptr;

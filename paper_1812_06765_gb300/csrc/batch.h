@@ -14,7 +14,9 @@ struct FusedArgs {
     FusedSplit split;       // z segments (the same for every tile column)
     int ntx, nty;           // tile columns
     float *part;            // per segment (z order): [tile column][len/2 + 1][NE]
-    double *partials;       // D block partials
+    double *partials;       // D block partials, one per tile
+    float *w;               // curvature Laplacian of every node (3 planes), written by the owning tiles
+    double *partials_S;     // sums of w^2 over each tile's nodes, one per tile
 };
 
 struct PairLevel {
@@ -67,8 +69,6 @@ __device__ __forceinline__ int find_pair(const int *__restrict__ off, int npairs
 // batched launchers (mode 0: objective at u, 1: at the trial point of pairs still searching)
 cudaError_t launch_fused_batch(const PairLevel *pl, const int *tile_off, int npairs, int total, int mode, bool bf16,
                                int grid, int device, cudaStream_t s);
-cudaError_t launch_curv_w_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
-                                cudaStream_t s);
 cudaError_t launch_gather_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
                                 cudaStream_t s);
 cudaError_t launch_finalize_batch(const PairLevel *pl, int npairs, int mode, cudaStream_t s);

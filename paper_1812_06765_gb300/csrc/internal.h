@@ -218,10 +218,16 @@ constexpr long long GATHER_SPLIT_BLOCKS = 4096;
 cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out);
 // the curvature Laplacian kernels that run beside the NGF pass (to tell their graph nodes apart)
 const void *curv_w_kernel();
-const void *curv_w_batch_kernel();
 // kernel nodes of g: low_func at the lowest priority, the others at the highest
 cudaError_t set_graph_kernel_priorities(cudaGraph_t g, const void *low_func);
 int eval_kernel_count(const reg_ctx *c, int level);
+
+// Whether the fused pass forms the curvature Laplacian itself (one S partial
+// per tile) instead of a curvature kernel beside it: the batched form always
+// does (its persistent grid leaves no SM for a pass beside it), and a single
+// registration does with the batch's tiling rule (cfg.fused_tz = -1), so that
+// it computes exactly what the batch computes for that pair.
+inline bool fused_curv_in_pass(const reg_ctx *c) { return c->cfg.fused_tz == -1; }
 
 // the fused pass serves levels whose grids have ratio exactly 2; others use the multi-pass kernels
 inline bool use_fused(const reg_ctx *c, int level)

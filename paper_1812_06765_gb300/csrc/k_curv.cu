@@ -100,21 +100,6 @@ __device__ __forceinline__ bool batch_skip(const PairLevel &P, int mode)
     return mode == 1 && !(P.st->active && P.st->ls_continue);
 }
 
-__global__ void __launch_bounds__(256) k_curv_w_batch(const PairLevel *__restrict__ pl, const int *__restrict__ off,
-                                                      int npairs, int total, int mode)
-{
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int p = find_pair(off, npairs, item);
-        const PairLevel &P = pl[p];
-        if (batch_skip(P, mode))
-            continue;
-        const int lin = item - __ldg(off + p);
-        const int bx = lin % P.ncx, r = lin / P.ncx;
-        curv_w_body(P.geom, P.u, mode ? P.pdir : nullptr, mode ? &P.st->t : nullptr, P.w, P.pS, bx, r % P.ncy,
-                    r / P.ncy, lin);
-        __syncthreads();
-    }
-}
 
 __global__ void __launch_bounds__(512) k_finalize_batch(const PairLevel *__restrict__ pl, int mode)
 {
@@ -127,14 +112,7 @@ __global__ void __launch_bounds__(512) k_finalize_batch(const PairLevel *__restr
 }  // namespace
 
 const void *curv_w_kernel() { return reinterpret_cast<const void *>(k_curv_w); }
-const void *curv_w_batch_kernel() { return reinterpret_cast<const void *>(k_curv_w_batch); }
 
-cudaError_t launch_curv_w_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
-                                cudaStream_t s)
-{
-    k_curv_w_batch<<<grid, dim3(32, 8, 1), 0, s>>>(pl, off, npairs, total, mode);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_finalize_batch(const PairLevel *pl, int npairs, int mode, cudaStream_t s)
 {
@@ -150,10 +128,12 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     int nD = 0;
     cudaError_t e;
     const bool fused = use_fused(c, level);
+    const bool curv_in_pass = fused && fused_curv_in_pass(c);
     // The curvature Laplacian (node pass, HBM-light) runs on the side stream
-    // beside the NGF pass (issue-bound, one CTA per SM): fork before, join
-    // before the gradient assembly.  Captured, the two become parallel graph
-    // branches.
+    // beside the NGF pass (issue-bound, one CTA per SM), in the tail of its last
+    // wave: fork before, join before the gradient assembly.  Captured, the two
+    // become parallel graph branches.  With the batched form's arithmetic the
+    // fused pass forms it itself, with one S partial per tile.
     e = cudaEventRecord(c->ev_fork, s);
     if (e == cudaSuccess)
         e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
@@ -175,9 +155,11 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
     dim3 gw(gn.x, gn.y, curv_zchunks(L.n[2]));
     double *pS = c->es.partials + nD;
-    k_curv_w<<<gw, blk, 0, c->side>>>(g, ub, dir, t_dev, c->es.w, pS);
-    c->launches += 1;
-    e = cudaGetLastError();
+    if (!curv_in_pass) {
+        k_curv_w<<<gw, blk, 0, c->side>>>(g, ub, dir, t_dev, c->es.w, pS);
+        c->launches += 1;
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess)
         e = cudaEventRecord(c->ev_join, c->side);
     if (e == cudaSuccess)
@@ -185,7 +167,7 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     if (e != cudaSuccess)
         return e;
     double hy = L.H[0] * L.H[1] * L.H[2];
-    int nS = (int)(gw.x * gw.y * gw.z);
+    int nS = curv_in_pass ? nD : (int)(gw.x * gw.y * gw.z);
     // grad = (tile partials of P^T r) + alpha hbar_y L^T w, and J, D, S (+ control).  The
     // final reduction reads only the block partials of the kernels before, not the
     // gradient.  On small grids block 0 of the gather runs it first (one launch); on
@@ -238,17 +220,8 @@ int eval_partials_needed(const Level &L)
     return (int)(vox_blocks + node_blocks + 1024);
 }
 
-// Explicit-buffer launches of the curvature Laplacian and of the final
-// reduction, for callers that own every buffer (the allocation-free entry point).
-int curv_blocks(const LevelGeom &g) { return ((g.n[0] + 31) / 32) * ((g.n[1] + 7) / 8) * curv_zchunks(g.n[2]); }
-
-cudaError_t launch_curv_w_raw(const LevelGeom &g, const float *u, float *w, double *partials, cudaStream_t s)
-{
-    dim3 blk(32, 8, 1);
-    dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, curv_zchunks(g.n[2]));
-    k_curv_w<<<gn, blk, 0, s>>>(g, u, nullptr, nullptr, w, partials);
-    return cudaGetLastError();
-}
+// Explicit-buffer launch of the final reduction, for callers that own every
+// buffer (the allocation-free entry point).
 
 cudaError_t launch_finalize_raw(const double *pD, int nD, const double *pS, int nS, double hbar_half, double alpha,
                                 double hy_half, double *scal, cudaStream_t s)

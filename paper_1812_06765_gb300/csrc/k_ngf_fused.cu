@@ -3,9 +3,11 @@
 //   y-hat = P u (Eq. 1), T(x + y-hat) and its interpolant gradient,
 //   the NGF residual of Eq. 2 and v = d psi / d grad T,
 //   g = adjoint central difference of v, r = g grad T (the chain rule),
-// and reduces r to per-tile partial node sums of P^T r (Eq. 3); a second,
+// and reduces r to per-tile partial node sums of P^T r (Eq. 3).  From the node
+// planes it holds anyway it also forms the curvature Laplacian w = mask L u of
+// the nodes the tile owns and their share of S (Sec. 2.1).  A second,
 // node-parallel kernel adds up the (at most 8) tile partials of each node and
-// the curvature gradient.  Nothing per voxel goes to HBM.
+// the curvature gradient alpha hbar_y L^T w.  Nothing per voxel goes to HBM.
 //
 // Tiling.  A CTA of 16 x 32 threads owns a 32 x 32 block of voxel columns:
 // thread (tx, ty) holds the two adjacent columns 2 tx and 2 tx + 1 of row ty.
@@ -79,11 +81,12 @@ constexpr int NCOMB = (TNP + NT - 1) / NT;        // trial node values formed pe
 
 // shared layout (floats).  The ring slot of plane z is z & 3 for T~, R and v;
 // grad T, written 4 steps before it is read, has a ring of 5 slots taken in
-// turn, one per step; node plane K sits in slot K mod 3.  The rings are kept
-// this small so that the CTA's shared memory leaves room for a larger L1,
+// turn, one per step; node plane K sits in slot K & 3 (the curvature of plane
+// K reads planes K - 1 .. K + 1 while plane K + 2 is copied in).  The rings are
+// kept this small so that the CTA's shared memory leaves room for a larger L1,
 // which holds the template samples.
 constexpr int GSLOTS = 5;
-constexpr int NSLOTS = 3;
+constexpr int NSLOTS = 4;
 constexpr int OFF_T = 0;                          // T~ ring [4][PLANE]
 constexpr int OFF_R = OFF_T + 4 * PLANE;          // R ring [4][PLANE]
 constexpr int OFF_V = OFF_R + 4 * PLANE;          // v ring [4][3][PLANE]
@@ -94,7 +97,7 @@ constexpr int OFF_N = OFF_RED + 2 * RED_PLANE;    // node planes [NSLOTS][2][TNP
 constexpr int SMEM_FLOATS = OFF_N + NSLOTS * 2 * TNP;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 static_assert(SMEM_BYTES <= 227 * 1024, "fused pass exceeds the shared memory of one CTA");
-__device__ __forceinline__ int node_slot(int K) { return (K + NSLOTS) % NSLOTS; }   // K >= -1
+__device__ __forceinline__ int node_slot(int K) { return K & (NSLOTS - 1); }   // K >= -1
 
 // The fused kernels' dynamic shared memory, and a carveout preference of just
 // that much (with the 1 KB the system reserves per CTA) in percent of the
@@ -327,8 +330,11 @@ __device__ __forceinline__ void tile_seg_col(const FusedSplit &sp, int ncols, in
 
 // One output tile (launch-order id, see tile_seg_col) of the fused pass; sm is
 // the CTA's dynamic shared memory (SMEM_BYTES).  PAD: a.T is the zero-bordered
-// copy of T (dims m + 4, the image at offset 2 in every dimension).
-template <bool HAS_DIR, typename IMG, bool PAD>
+// copy of T (dims m + 4, the image at offset 2 in every dimension).  CURV: the
+// tile also forms the curvature Laplacian of the nodes it owns (a.w) and their
+// share of S (a.partials_S) - where no separate curvature pass can run beside
+// this one (the persistent batched grid, the allocation-free call).
+template <bool HAS_DIR, typename IMG, bool PAD, bool CURV>
 __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, float *sm)
 {
     const LevelGeom &g = a.g;
@@ -385,6 +391,23 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         const int dc = e / (NX * NY), drem = e - dc * (NX * NY), djy = drem / NX, djx = drem - djy * NX;
         dofs[q] = ((2 * djy) * NX + djx) * 3 + dc;
     }
+    // curvature: entries tid and tid + NT = (component, node row, node column) of the
+    // node columns this tile owns, local columns and rows 1 .. 14 (1 .. 15 in the
+    // last tile column or row) inside the grid; every node has one owner
+    int wo[2] = {-1, -1}, wg[2] = {0, 0};   // offset in a node-plane tile (-1: no entry) and in a plane of w
+    bool wxy[2] = {false, false};           // node interior in x and y
+#pragma unroll
+    for (int q = 0; q < 2 && CURV; q++) {
+        const int e = tid + q * NT;
+        const int dc = e / (NX * NY), drem = e - dc * (NX * NY), ly = drem / NX + 1, lx = drem - (ly - 1) * NX + 1;
+        const int kx = kx0 + lx, ky = ky0 + ly;
+        const bool own = e < NE && (lx < NX || tile_x == a.ntx - 1) && (ly < NY || tile_y == a.nty - 1) &&
+                         kx < g.n[0] && ky < g.n[1];
+        wo[q] = own ? dc * (TNY * TNX) + ly * TNX + lx : -1;
+        wg[q] = dc * (int)g.nn + kx + g.n[0] * ky;
+        wxy[q] = kx >= 1 && kx <= g.n[0] - 2 && ky >= 1 && ky <= g.n[1] - 2;
+    }
+    float wacc = 0.f;          // sum of w^2 over the entries this thread formed
 
     float Uhi[3];              // node plane at the top of the current interval (first node)
     float2 Bhi[3];             // its in-plane part, both columns
@@ -451,6 +474,30 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             bx1 = bx0 + 1;
             by = qb[1] + y + PADO - MAGI;
             bz = qb[2] + z1 + PADO - MAGI;
+            // curvature Laplacian of node plane K1 (Sec. 2.1, reading R6): w = L u on
+            // interior nodes, 0 elsewhere, from planes K1 - 1 .. K1 + 1 of the ring,
+            // for the planes this segment owns (the last segment also its top one)
+            if (CURV && K1 >= (z0 >> 1) && (K1 < (zend >> 1) || zend == mz)) {
+                const float *pw = sm + OFF_N + node_slot(K1) * 2 * TNP;
+                const float *pm = sm + OFF_N + node_slot(K1 - 1) * 2 * TNP;
+                const float *pp = sm + OFF_N + node_slot(K1 + 1) * 2 * TNP;
+                const bool wz = K1 >= 1 && K1 <= g.n[2] - 2;
+                float *wk = a.w + (size_t)K1 * node_plane;
+#pragma unroll
+                for (int q = 0; q < 2; q++)
+                    if (wo[q] >= 0) {
+                        const int o = wo[q];
+                        float lap = 0.f;
+                        if (wxy[q] && wz) {
+                            const float u0 = pw[o];
+                            lap = fmaf(pw[o + 1] - 2.f * u0 + pw[o - 1], g.iH2[0], lap);
+                            lap = fmaf(pw[o + TNX] - 2.f * u0 + pw[o - TNX], g.iH2[1], lap);
+                            lap = fmaf(pp[o] - 2.f * u0 + pm[o], g.iH2[2], lap);
+                        }
+                        wk[wg[q]] = lap;
+                        wacc = fmaf(lap, lap, wacc);
+                    }
+            }
             issue_node_plane(nc, a.ub, a.dir, sm, K1 + 2, g.n[2], node_plane);
             cp_async_commit();
         } else {
@@ -693,16 +740,21 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             step(s + 1, std::false_type{}, std::false_type{});
     }
     const float2 ps = psi_sum.s;
-    double ssum = block_sum_to_f64(ps.x + ps.y, reinterpret_cast<double *>(sm + OFF_RED));
+    const double ssum = block_sum_to_f64(ps.x + ps.y, reinterpret_cast<double *>(sm + OFF_RED));
     if (tid == 0)
         a.partials[tile_lin] = ssum;
+    if (CURV) {
+        const double wsum = block_sum_to_f64(wacc, reinterpret_cast<double *>(sm + OFF_RED));
+        if (tid == 0)
+            a.partials_S[tile_lin] = wsum;
+    }
 }
 
-template <bool HAS_DIR, typename IMG = float, bool PAD = true>
+template <bool HAS_DIR, typename IMG = float, bool PAD = true, bool CURV = false>
 __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
 {
     extern __shared__ float sm[];
-    fused_tile<HAS_DIR, IMG, PAD>(a, blockIdx.x, sm);
+    fused_tile<HAS_DIR, IMG, PAD, CURV>(a, blockIdx.x, sm);
 }
 
 // Batched fused pass: a persistent grid walks the tiles of all pairs.  Mode 0
@@ -719,7 +771,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused_batch(const PairLevel 
         if (HAS_DIR && !(P.st->active && P.st->ls_continue))
             continue;   // uniform over the CTA
         const FusedArgs &a = HAS_DIR ? P.fa_trial : P.fa_init;
-        fused_tile<HAS_DIR, IMG, true>(a, item - __ldg(tile_off + p), sm);
+        fused_tile<HAS_DIR, IMG, true, true>(a, item - __ldg(tile_off + p), sm);
         __syncthreads();   // the next tile reuses the shared rings
     }
 }
@@ -1051,6 +1103,8 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     a.part = c->es.part;
     a.partials = partials;
     const int ntiles = a.ntx * a.nty * a.split.count();
+    a.w = c->es.w;
+    a.partials_S = partials + ntiles;   // the S partials follow the D partials
     dim3 blk(BX, BY, 1), grd(ntiles, 1, 1);
     // the shared rings exceed the 48 KB default; the limit is set once per device
     static bool attr_set[64] = {};
@@ -1063,20 +1117,34 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
             e = set_fused_smem(k_ngf_fused<true, __nv_bfloat16>);
         if (e == cudaSuccess)
             e = set_fused_smem(k_ngf_fused<false, __nv_bfloat16>);
+        if (e == cudaSuccess)
+            e = set_fused_smem(k_ngf_fused<true, float, true, true>);
+        if (e == cudaSuccess)
+            e = set_fused_smem(k_ngf_fused<false, float, true, true>);
+        if (e == cudaSuccess)
+            e = set_fused_smem(k_ngf_fused<true, __nv_bfloat16, true, true>);
+        if (e == cudaSuccess)
+            e = set_fused_smem(k_ngf_fused<false, __nv_bfloat16, true, true>);
         if (e != cudaSuccess)
             return e;
         attr_set[dev] = true;
     }
+    // the curvature Laplacian in the pass (the batched form's arithmetic) or beside it
+    const bool curv = fused_curv_in_pass(c);
     if (bf16) {
-        if (dir)
-            k_ngf_fused<true, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a);
+        if (curv)
+            dir ? k_ngf_fused<true, __nv_bfloat16, true, true><<<grd, blk, SMEM_BYTES, s>>>(a)
+                : k_ngf_fused<false, __nv_bfloat16, true, true><<<grd, blk, SMEM_BYTES, s>>>(a);
         else
-            k_ngf_fused<false, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a);
+            dir ? k_ngf_fused<true, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a)
+                : k_ngf_fused<false, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a);
     } else {
-        if (dir)
-            k_ngf_fused<true, float><<<grd, blk, SMEM_BYTES, s>>>(a);
+        if (curv)
+            dir ? k_ngf_fused<true, float, true, true><<<grd, blk, SMEM_BYTES, s>>>(a)
+                : k_ngf_fused<false, float, true, true><<<grd, blk, SMEM_BYTES, s>>>(a);
         else
-            k_ngf_fused<false, float><<<grd, blk, SMEM_BYTES, s>>>(a);
+            dir ? k_ngf_fused<true, float><<<grd, blk, SMEM_BYTES, s>>>(a)
+                : k_ngf_fused<false, float><<<grd, blk, SMEM_BYTES, s>>>(a);
     }
     *n_partials = ntiles;
     c->launches += 1;
@@ -1244,11 +1312,11 @@ void fused_layout_dims(const int m[3], int num_sms, int *tz, int *tiles, size_t 
 // the explicit-buffer pass reads the caller's unpadded T (bounds-tested corner loads)
 cudaError_t fused_set_smem_limit()
 {
-    return set_fused_smem(k_ngf_fused<false, float, false>);
+    return set_fused_smem(k_ngf_fused<false, float, false, true>);
 }
 
 cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float *R, const float *u, float tau,
-                                 float rho, int num_sms, float *part, double *partials, cudaStream_t s)
+                                 float rho, int num_sms, float *part, double *partials, float *w, cudaStream_t s)
 {
     FusedArgs a;
     a.g = g;
@@ -1265,7 +1333,9 @@ cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float
     a.part = part;
     a.partials = partials;
     dim3 blk(BX, BY, 1), grd(a.ntx * a.nty * a.split.count(), 1, 1);
-    k_ngf_fused<false, float, false><<<grd, blk, SMEM_BYTES, s>>>(a);
+    a.w = w;
+    a.partials_S = partials + grd.x;   // the S partials follow the D partials
+    k_ngf_fused<false, float, false, true><<<grd, blk, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 

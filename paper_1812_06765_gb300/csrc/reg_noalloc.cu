@@ -30,11 +30,9 @@
 void fused_layout_dims(const int m[3], int num_sms, int *tz, int *tiles, size_t *part_floats);
 cudaError_t fused_set_smem_limit();
 cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float *R, const float *u, float tau,
-                                 float rho, int num_sms, float *part, double *partials, cudaStream_t s);
+                                 float rho, int num_sms, float *part, double *partials, float *w, cudaStream_t s);
 cudaError_t launch_gather_grad_raw(const LevelGeom &g, const float *part, int num_sms, const float *w,
                                    float alpha_hy, float *grad, cudaStream_t s);
-int curv_blocks(const LevelGeom &g);
-cudaError_t launch_curv_w_raw(const LevelGeom &g, const float *u, float *w, double *partials, cudaStream_t s);
 cudaError_t launch_finalize_raw(const double *pD, int nD, const double *pS, int nS, double hbar_half, double alpha,
                                 double hy_half, double *scal, cudaStream_t s);
 int set_err(reg_ctx *c, int code, const char *fmt, ...);
@@ -193,7 +191,7 @@ extern "C" int reg_eval_objective_grad_noalloc(const float *R, const float *T, c
     int tz = 0, tiles = 0;
     size_t part_floats = 0;
     fused_layout_dims(g.m, ds.num_sms, &tz, &tiles, &part_floats);
-    const int nS = curv_blocks(g);
+    const int nS = tiles;   // the fused pass writes a D and an S partial per tile
     const size_t partials = (size_t)tiles + (size_t)nS;
     if (part_floats > CAP_PART || w_floats > CAP_W || partials > CAP_PARTIALS)
         return set_err(nullptr, REG_ERR_ARG,
@@ -208,10 +206,9 @@ extern "C" int reg_eval_objective_grad_noalloc(const float *R, const float *T, c
     double *pS = pD + tiles;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // every scratch word read below is written first in the same call, so
-    // nothing has to be cleared between calls
-    e = launch_ngf_fused_raw(g, T, R, u, (float)tau, (float)rho, ds.num_sms, part, pD, s);
-    if (e == cudaSuccess)
-        e = launch_curv_w_raw(g, u, w, pS, s);
+    // nothing has to be cleared between calls; the fused pass also writes the
+    // curvature Laplacian w and the S partials (after the D partials)
+    e = launch_ngf_fused_raw(g, T, R, u, (float)tau, (float)rho, ds.num_sms, part, pD, w, s);
     if (e == cudaSuccess)
         e = launch_gather_grad_raw(g, part, ds.num_sms, w, (float)(alpha * H[0] * H[1] * H[2]), grad, s);
     if (e == cudaSuccess)

@@ -38,8 +38,9 @@ def _cfg(reg_mod, **kw):
 
 @pytest.mark.parametrize("image_dtype", ["f32", "bf16"])
 def test_batch_equals_single_registrations(reg_mod, image_dtype):
-    # the batch tiles every level by the throughput rule; single registrations
-    # with that tiling (fused_tz = -1) must give the same result bit for bit
+    # the batch tiles every level by the throughput rule and forms the curvature
+    # sum in the fused pass; single registrations with that rule (fused_tz = -1)
+    # must give the same result bit for bit
     pairs = _pairs()
     single = []
     for p in pairs:

@@ -62,6 +62,50 @@ def test_eval_parity(reg_mod, orc, impl, case):
     r.close()
 
 
+@pytest.mark.parametrize("case", [c for c in range(len(CASES)) if CASES[c][2] is None])
+def test_curvature_in_fused_pass_parity(reg_mod, orc, case):
+    # fused_tz = -1: the fused pass forms the curvature Laplacian w and one S
+    # partial per tile itself (the batched arithmetic); every node of w and S
+    # must be formed by exactly one tile, ragged tiles and z segments included
+    dims, h, nodes, tau, rho, alpha, amp = CASES[case]
+    R = random_image(dims, 100 + case)
+    T = random_image(dims, 200 + case)
+    cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=-1)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    u = random_field(r.level_info(0)["nodes"], 300 + case, amp)
+    e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
+    assert e["eD"] <= J_RTOL, e
+    assert e["eS"] <= 1e-5, e
+    assert_parity(e)
+    r.close()
+
+
+@pytest.mark.parametrize("seams_only", [False, True])
+def test_curvature_in_fused_pass_z_segments(reg_mod, orc, seams_only):
+    # 300 planes: the throughput rule cuts segments of 64, 64, 64, 64 and 44
+    # planes, which share the node planes 32, 64, 96 and 128; with seams_only
+    # u is non-zero only there and on the node column and row that x and y
+    # tiles share, so a seam node formed twice or never shows in S and grad
+    dims, h, tau, rho, alpha = (30, 26, 300), (1.0, 1.2, 0.9), 0.05, 0.05, 4.0
+    R = random_image(dims, 181)
+    T = random_image(dims, 182)
+    cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=-1)
+    r = reg_mod.Registration(cfg).set_images(R, T, h)
+    z, tiles = r.level_tiling(0)
+    assert z == 64 and tiles == 2 * 1 * 5
+    nodes = r.level_info(0)["nodes"]
+    u = random_field(nodes, 183, 2.0)
+    if seams_only:
+        keep = np.zeros(u.shape[1:], bool)
+        keep[:, :, 14] = True
+        keep[[32, 64, 96, 128], :, :] = True
+        u = np.where(keep[None], u, 0.0).astype(np.float32)
+    e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
+    assert e["eS"] <= 1e-5, e
+    assert_parity(e)
+    r.close()
+
+
 @pytest.mark.parametrize("impl", EVAL_IMPLS)
 def test_eval_T_equals_R_is_zero(reg_mod, impl):
     dims, h = (30, 26, 22), (1.0, 1.0, 1.0)
@@ -226,7 +270,7 @@ def test_autograd_function(reg_mod, orc):
     r.close()
 
 
-@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("impl", [0, 1, "curv-in-pass"])
 def test_seam_nodes_only_field(reg_mod, orc, impl):
     """u non-zero only on the node planes that neighbouring tiles share (x nodes 14
     and 28, y node 14) and on the z node planes where segments of the split meet
@@ -236,8 +280,11 @@ def test_seam_nodes_only_field(reg_mod, orc, impl):
     R = random_image(dims, 171)
     T = random_image(dims, 172)
     split = (40, 1, 10, 2, 10)
-    cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, eval_impl=impl,
-                              fused_split=split if impl == 0 else None)
+    if impl == "curv-in-pass":   # the throughput rule's uniform segments, curvature formed per tile
+        cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=-1)
+    else:
+        cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, eval_impl=impl,
+                                  fused_split=split if impl == 0 else None)
     r = reg_mod.Registration(cfg).set_images(R, T, h)
     nodes = r.level_info(0)["nodes"]
     if impl == 0:
