@@ -41,8 +41,8 @@ L2_BYTES = 129 * 1024 * 1024
 # the translation unit of the fused pass and every header it includes: the
 # committed ncu traffic is valid only for this exact source
 FUSED_KERNEL_SOURCES = ["paper_1812_06765_gb300/csrc/" + f
-                        for f in ("k_ngf_fused.cu", "ngf_math.cuh", "common.cuh", "batch.h", "internal.h",
-                                  "lbfgs_control.cuh", "lbfgs_state.h")] + ["include/reg.h"]
+                        for f in ("k_ngf_fused.cu", "k_pyramid.cu", "ngf_math.cuh", "common.cuh", "batch.h",
+                                  "internal.h", "lbfgs_control.cuh", "lbfgs_state.h")] + ["include/reg.h"]
 
 
 def parse_args(argv=None):
@@ -187,9 +187,12 @@ def source_digest(files):
     return h.hexdigest()[:16]
 
 
-# partial sums one fused-pass tile writes per node plane: 3 components x 15 x 15
-# node columns (a 28 x 28 output tile reaches 28 / 2 + 1 nodes per dimension)
-FUSED_TILE_NODE_ENTRIES = 3 * 15 * 15
+def fused_tile_node_entries():
+    """Partial sums one fused-pass tile writes per node plane: 3 components x the
+    node columns an ox x oy output tile reaches (o / 2 + 1 per dimension)."""
+    from paper_1812_06765_gb300 import _lib
+    ox, oy, _ = _lib.reg_fused_tile_shape()
+    return 3 * (ox // 2 + 1) * (oy // 2 + 1)
 
 
 def committed_profile(kernel, digest, workload_name, split):
@@ -218,7 +221,7 @@ def split_partial_floats_per_column(split):
     """Node planes x entries one tile column keeps over all z segments of a split."""
     l1, n1, l2, n2, lr = split
     planes = n1 * (l1 // 2 + 1) + n2 * (l2 // 2 + 1) + (lr // 2 + 1 if lr else 0)
-    return planes * FUSED_TILE_NODE_ENTRIES
+    return planes * fused_tile_node_entries()
 
 
 def issue_peak_warp_inst_per_s():

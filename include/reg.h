@@ -176,6 +176,12 @@ int reg_level_tiling(reg_handle h, int level, int *tz, int *tiles);
  * num_sms < 1. */
 int reg_fused_split_plan(const int dims[3], int num_sms, int split[5], double *model_steps);
 
+/* (No counterpart in the paper.)  Tile geometry of the fused pass, host only:
+ * *ox, *oy = output voxel columns of a tile along x and y (a tile computes a
+ * 2-voxel halo around them), *ctas_per_sm = the pass's CTAs resident per SM
+ * (the load model's slots per SM).  Any pointer may be NULL.  Returns REG_OK. */
+int reg_fused_tile_shape(int *ox, int *oy, int *ctas_per_sm);
+
 /* The per-dimension grid-conversion tables that reg_set_images uploads for one
  * axis of m voxels of spacing h and n nodes (host only, no GPU; Sec. 2.2,
  * Eq. 3: the index sets and weights of P and P^T are fixed beforehand and
@@ -237,10 +243,10 @@ int reg_last_ngf_ms(reg_handle h, double *ms);
  *     alpha for reg_eval_objective_grad;
  *   jds: device, 3 doubles receiving J, D and S;
  *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
- * Every buffer is the caller's.  The working memory is one fixed 12.5 MiB array
+ * Every buffer is the caller's.  The working memory is one fixed 20.5 MiB array
  * in the library's device image, held by every GPU that loads the library until
  * the process exits; it fits images up to about 136^3 voxels (a 128^3 pair
- * needs 8.3 MiB), and larger sizes are rejected with REG_ERR_ARG before
+ * needs at most 12.3 MiB), and larger sizes are rejected with REG_ERR_ARG before
  * anything is launched, as is any side above 4096 voxels.  No call allocates
  * memory.  The first call on each device looks up the array's device address
  * and sets a kernel attribute for that device (again on the first call after

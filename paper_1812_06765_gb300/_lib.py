@@ -78,6 +78,8 @@ def lib():
         L.reg_level_split.argtypes = [vp, ctypes.c_int, ip]
         L.reg_fused_split_plan.argtypes = [ip, ctypes.c_int, ip, dp]
         L.reg_fused_split_plan.restype = ctypes.c_int
+        L.reg_fused_tile_shape.argtypes = [ip, ip, ip]
+        L.reg_fused_tile_shape.restype = ctypes.c_int
         L.reg_axis_tables.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ip, fp, ip, ip, fp, ctypes.c_int, ip]
         L.reg_axis_tables.restype = ctypes.c_int
         L.reg_get_level_image.argtypes = [vp, ctypes.c_int, ctypes.c_int, fp, ctypes.c_int]
@@ -170,6 +172,13 @@ def reg_fused_split_plan(dims, num_sms):
     steps = ctypes.c_double()
     check(None, lib().reg_fused_split_plan(d, int(num_sms), v, ctypes.byref(steps)))
     return tuple(v), steps.value
+
+
+def reg_fused_tile_shape():
+    """(output columns per tile along x, along y, resident CTAs per SM) of the fused pass; host only."""
+    ox, oy, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(None, lib().reg_fused_tile_shape(ctypes.byref(ox), ctypes.byref(oy), ctypes.byref(k)))
+    return ox.value, oy.value, k.value
 
 
 def reg_axis_tables(m, h, n):

@@ -34,6 +34,7 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     a.g = P.geom;
     a.T = bf16 ? static_cast<const void *>(L.Tb) : static_cast<const void *>(L.Tp);   // zero-bordered copies
     a.R = bf16 ? static_cast<const void *>(L.Rb) : static_cast<const void *>(L.R);
+    a.Rn = bf16 ? nullptr : L.Rn;   // R's normalized gradient field (FP32 images)
     a.ub = c->lb.u;
     a.dir = nullptr;
     a.t_dev = nullptr;
@@ -294,7 +295,7 @@ int batch_tiling_rule(reg_handle *hs, int n, int l, const std::vector<FusedSplit
             if (r >= 0)
                 e = cudaEventRecord(e0, s);
             if (e == cudaSuccess)
-                e = launch_fused_batch(d.pl, d.off, n, tiles, 0, bf16, cap(tiles, c0->num_sms), c0->device, s);
+                e = launch_fused_batch(d.pl, d.off, n, tiles, 0, bf16, cap(tiles, (long long)fused_slots(c0->num_sms)), c0->device, s);
             if (e == cudaSuccess && r >= 0)
                 e = cudaEventRecord(e1, s);
             if (e == cudaSuccess && r >= 0)
@@ -480,7 +481,7 @@ extern "C" int reg_register_batch(reg_handle *hs, int n, float **u_out, int out_
         CK(cudaMemcpyAsync(d.pl, hpl.data(), sizeof(PairLevel) * n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d.off, hoff.data(), sizeof(int) * hoff.size(), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(d.counters, 0, sizeof(int) * 4, s));
-        BatchLaunch B{&d, n, tiles, nodes, chunks, cap(tiles, c0->num_sms), cap(nodes, 8LL * c0->num_sms),
+        BatchLaunch B{&d, n, tiles, nodes, chunks, cap(tiles, (long long)fused_slots(c0->num_sms)), cap(nodes, 8LL * c0->num_sms),
                       cap(chunks, 4LL * c0->num_sms), bf16, c0->device};
         cudaError_t e = cudaSuccess;
         if (c0->cfg.use_graph) {

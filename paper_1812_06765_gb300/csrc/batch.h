@@ -8,6 +8,7 @@
 struct FusedArgs {
     LevelGeom g;
     const void *T, *R;      // images, elements of the kernel's IMG type (float or bf16)
+    const float4 *Rn;       // R's normalized gradient field (FP32 images of a handle; else null)
     const float *ub, *dir;
     const double *t_dev;
     float tau, rho;

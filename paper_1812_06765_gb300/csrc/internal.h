@@ -67,6 +67,9 @@ struct Level {
     // (image_dtype 0) or BF16 (Tb, image_dtype 1, beside the BF16 copy Rb of R)
     float *Tp = nullptr;
     __nv_bfloat16 *Rb = nullptr, *Tb = nullptr;
+    // read by the fused pass beside Tp: R's normalized gradient field (b / ||b||_rho,
+    // rho / ||b||_rho) per voxel, b the central-difference gradient; zero off the interior
+    float4 *Rn = nullptr;
     int *pk0[3] = {nullptr, nullptr, nullptr};
     float *pw1[3] = {nullptr, nullptr, nullptr};
     int *tfirst[3] = {nullptr, nullptr, nullptr};
@@ -159,6 +162,7 @@ cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cu
 long long padded_voxels(const int m[3]);
 cudaError_t launch_pad_template(const float *src, const int m[3], float *dst, cudaStream_t s);
 cudaError_t launch_pad_template(const float *src, const int m[3], __nv_bfloat16 *dst, cudaStream_t s);
+cudaError_t launch_ref_normal_field(const Level &L, double rho, cudaStream_t s);
 cudaError_t launch_prolong(const Level &coarse, const Level &fine, const float *uc, float *uf, cudaStream_t s);
 
 // objective + gradient at u_base + t_scale * dir (dir may be NULL: plain u_base);
@@ -193,6 +197,14 @@ cudaError_t lbfgs_kernels_setup(int device);
 bool fused_eligible(const Level &L);
 size_t fused_part_floats(const Level &L, int num_sms);
 bool fused_tz_valid(int tz);
+// output columns of a fused tile along x and y, and the pass's resident CTAs per SM
+void fused_tile_shape(int *ox, int *oy, int *ctas_per_sm);
+inline int fused_slots(int num_sms)   // CTAs of the fused pass resident on the whole GPU
+{
+    int ox, oy, k;
+    fused_tile_shape(&ox, &oy, &k);
+    return k * num_sms;
+}
 int fused_tz_throughput(const Level &L);
 // tz-plane segments and the remainder
 FusedSplit fused_split_uniform(int tz, int mz);

@@ -9,16 +9,20 @@
 // node-parallel kernel adds up the (at most 8) tile partials of each node and
 // the curvature gradient alpha hbar_y L^T w.  Nothing per voxel goes to HBM.
 //
-// Tiling.  A CTA of 16 x 32 threads owns a 32 x 32 block of voxel columns:
+// Tiling.  A CTA of 16 x 16 threads owns a 32 x 16 block of voxel columns:
 // thread (tx, ty) holds the two adjacent columns 2 tx and 2 tx + 1 of row ty.
-// The inner 28 x 28 columns are the output tile; the 2-voxel halo is what the
+// The inner 28 x 12 columns are the output tile; the 2-voxel halo is what the
 // stencil chain T~ -> a -> v -> g reaches.  The CTA marches along z through a
-// segment of TZ output planes.  With ratio 2 the P weights are 1/4 and 3/4;
+// segment of TZ output planes.  Two CTAs are resident per SM: each step ends
+// in a block barrier, and while one CTA's warps wait there (or all stall in
+// the same phase of the step) the other CTA's warps issue.  A 32 x 32 block
+// of one 512-thread CTA per SM wastes less on the halo (1.31 against 1.52
+// computed columns per output column) but ran 7 % slower.  With ratio 2 the P weights are 1/4 and 3/4;
 // tiles start at even x, so the two columns of a thread always lie in the
 // same node interval (x weights 1/4 and 3/4 of the same nodes), and the node
 // loads, P's integer cell and the x reduction of P^T are shared by the pair.
 // A node gathers voxels 2k-2 .. 2k+1 with weights 1/4, 3/4, 3/4, 1/4 per
-// dimension, so an output tile of 28 x 28 x TZ voxels feeds 15 x 15 x
+// dimension, so an output tile of 28 x 12 x TZ voxels feeds 15 x 7 x
 // (TZ/2 + 1) nodes; neighbouring tiles share one node plane per dimension and
 // the gather kernel sums them.
 //
@@ -67,36 +71,60 @@
 
 namespace {
 
-constexpr int BX = 16, BY = 32;                   // threads; each holds two voxel columns
-constexpr int NT = BX * BY;                       // 512 threads
+constexpr int BX = 16, BY = 16;                   // threads; each holds two voxel columns
+constexpr int CTAS_PER_SM = 2;                    // resident CTAs of the pass per SM
+constexpr int NT = BX * BY;                       // 256 threads
 constexpr int CW = 2 * BX;                        // voxel columns per tile row, halo included
-constexpr int OX = 28, OY = 28;                   // output voxels per tile
-constexpr int NX = OX / 2 + 1, NY = OY / 2 + 1;   // 15 x 15 node columns per tile
-constexpr int NE = 3 * NX * NY;                   // partial entries per node plane (675)
+constexpr int OX = 28, OY = BY - 4;               // output voxels per tile
+constexpr int NX = OX / 2 + 1, NY = OY / 2 + 1;   // 15 x 7 node columns per tile
+constexpr int NE = 3 * NX * NY;                   // partial entries per node plane (315)
 constexpr int PLANE = CW * BY;                    // floats of one shared plane
-constexpr int TNX = BX + 1, TNY = BY / 2 + 1;     // node tile of the columns: 17 x 17
+constexpr int TNX = BX + 1, TNY = BY / 2 + 1;     // node tile of the columns: 17 x 9
 constexpr int TNP = 3 * TNY * TNX;                // floats of one node plane tile per array
 constexpr int NCOPY = (2 * TNP + NT - 1) / NT;    // node-tile entries copied per thread
 constexpr int NCOMB = (TNP + NT - 1) / NT;        // trial node values formed per thread
+static_assert(NE <= 2 * NT, "phases D and the curvature take two partial entries per thread");
+static_assert(OX == CW - 4 && OY == BY - 4, "the output tile is the thread block less a 2-voxel halo");
 
 // shared layout (floats).  The ring slot of plane z is z & 3 for T~, R and v;
 // grad T, written 4 steps before it is read, has a ring of 5 slots taken in
 // turn, one per step; node plane K sits in slot K & 3 (the curvature of plane
 // K reads planes K - 1 .. K + 1 while plane K + 2 is copied in).  The rings are
 // kept this small so that the CTA's shared memory leaves room for a larger L1,
-// which holds the template samples.
+// which holds the template samples.  RN: the pass reads the normalized
+// gradient field of R (a.Rn) into registers and keeps no R ring.
 constexpr int GSLOTS = 5;
 constexpr int NSLOTS = 4;
-constexpr int OFF_T = 0;                          // T~ ring [4][PLANE]
-constexpr int OFF_R = OFF_T + 4 * PLANE;          // R ring [4][PLANE]
-constexpr int OFF_V = OFF_R + 4 * PLANE;          // v ring [4][3][PLANE]
-constexpr int OFF_G = OFF_V + 12 * PLANE;         // grad T ring [GSLOTS][3][PLANE]
 constexpr int RED_PLANE = BY * NX * 3;            // x-reduced rows of one plane [BY][NX][3]
-constexpr int OFF_RED = OFF_G + GSLOTS * 3 * PLANE;   // x-reduced rows [2 steps][RED_PLANE]
-constexpr int OFF_N = OFF_RED + 2 * RED_PLANE;    // node planes [NSLOTS][2][TNP] (u or u + t dir, dir)
-constexpr int SMEM_FLOATS = OFF_N + NSLOTS * 2 * TNP;
-constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
-static_assert(SMEM_BYTES <= 227 * 1024, "fused pass exceeds the shared memory of one CTA");
+template <bool RN>
+struct Smem {
+    static constexpr int T = 0;                       // T~ ring [4][PLANE]
+    static constexpr int R = T + 4 * PLANE;           // R ring [4][PLANE] (without RN: none)
+    static constexpr int V = R + (RN ? 0 : 4 * PLANE);   // v ring [4][3][PLANE]
+    static constexpr int G = V + 12 * PLANE;          // grad T ring [GSLOTS][3][PLANE]
+    static constexpr int RED = G + GSLOTS * 3 * PLANE;   // x-reduced rows [2 steps][RED_PLANE]
+    static constexpr int N = RED + 2 * RED_PLANE;     // node planes [NSLOTS][2][TNP] (u or u + t dir, dir)
+    static constexpr int FLOATS = N + NSLOTS * 2 * TNP;
+    static constexpr size_t BYTES = sizeof(float) * FLOATS;
+    static_assert(BYTES <= 227 * 1024, "fused pass exceeds the shared memory of one CTA");
+    static_assert((R | V | G | RED | N | PLANE) % 2 == 0, "float2 rows need even offsets");
+};
+// The single-pair pass over FP32 images of a handle (zero-bordered T) reads R's
+// normalized gradient field.  R itself is read by BF16 images (the field would
+// undo their memory saving), by the caller's own buffers (no field exists), and
+// by the passes that form the curvature too (the batched pass, whose persistent
+// kernel has no registers left for the field's prefetch and whose pairs would
+// stream 16 bytes per voxel each, and the single-pair form of its arithmetic).
+template <typename IMG, bool PAD, bool CURV>
+__host__ __device__ constexpr bool reads_rn()
+{
+    return PAD && !CURV && std::is_same<IMG, float>::value;
+}
+template <typename IMG, bool PAD, bool CURV>
+__host__ __device__ constexpr size_t smem_bytes()
+{
+    return reads_rn<IMG, PAD, CURV>() ? Smem<true>::BYTES : Smem<false>::BYTES;
+}
 __device__ __forceinline__ int node_slot(int K) { return K & (NSLOTS - 1); }   // K >= -1
 
 // The fused kernels' dynamic shared memory, and a carveout preference of just
@@ -104,15 +132,14 @@ __device__ __forceinline__ int node_slot(int K) { return K & (NSLOTS - 1); }   /
 // SM's 228 KB: the rest of the SM's 256 KB stays L1, where the template's
 // samples are cached.
 template <typename K>
-cudaError_t set_fused_smem(K kernel)
+cudaError_t set_fused_smem(K kernel, size_t bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    const int pct = (int)((100 * (SMEM_BYTES + 1024) + 228 * 1024 - 1) / (228 * 1024));
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const int pct = (int)((100 * CTAS_PER_SM * (bytes + 1024) + 228 * 1024 - 1) / (228 * 1024));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     return e;
 }
-static_assert((OFF_R | OFF_V | OFF_G | OFF_RED | OFF_N | PLANE) % 2 == 0, "float2 rows need even offsets");
 
 // 1.5 * 2^23: adding it rounds a float to an integer (the rounding mode picks
 // which one); the low bits of the sum then hold that integer plus MAGI
@@ -184,6 +211,61 @@ __device__ __forceinline__ float2 ngf_residual2(const float2 a[3], const float2 
     return psi;
 }
 
+// reciprocal in one MUFU instruction (rcp.approx, max error ~1 ulp; the
+// argument is at least tau^2, far above the subnormal range)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// NGF residual of Eq. 2 for both columns from a = grad T~ (3 pairs) and the
+// normalized gradient field of R: bh = b / ||b||_rho and rh = rho / ||b||_rho
+// (zero off the interior, where Eq. 2 has no term).  With na2 = |a|^2 + tau^2
+// and c' = a . bh + tau rh, the cosine is c = c' / sqrt(na2) and
+//   psi = 1 - c^2 = (|a x bh|^2 + |rh a - tau bh|^2) / na2   (no cancellation),
+//   v = d psi / d a = -2 (c' / na2) bh + 2 (c' / na2)^2 a,
+// so one reciprocal per lane serves both.
+__device__ __forceinline__ float2 ngf_residual_rn2(const float2 a[3], const float2 bh[3], float2 rh, float tau,
+                                                   float2 v[3])
+{
+    const float2 TAU = bc2(tau), NTAU = bc2(-tau);
+    const float2 aa = fma2(a[2], a[2], fma2(a[1], a[1], mul2(a[0], a[0])));
+    const float2 ab = fma2(a[2], bh[2], fma2(a[1], bh[1], mul2(a[0], bh[0])));
+    const float2 na2 = add2(aa, bc2(tau * tau));
+    const float2 cx = sub2(mul2(a[1], bh[2]), mul2(a[2], bh[1]));
+    const float2 cy = sub2(mul2(a[2], bh[0]), mul2(a[0], bh[2]));
+    const float2 cz = sub2(mul2(a[0], bh[1]), mul2(a[1], bh[0]));
+    const float2 ex = fma2(rh, a[0], mul2(NTAU, bh[0]));
+    const float2 ey = fma2(rh, a[1], mul2(NTAU, bh[1]));
+    const float2 ez = fma2(rh, a[2], mul2(NTAU, bh[2]));
+    const float2 num = fma2(ez, ez, fma2(ey, ey, fma2(ex, ex, fma2(cz, cz, fma2(cy, cy, mul2(cx, cx))))));
+    const float2 rna2 = make_float2(rcp_approx(na2.x), rcp_approx(na2.y));
+    const float2 psi = mul2(num, rna2);
+    const float2 q = mul2(fma2(TAU, rh, ab), rna2);   // c' / na2
+    const float2 k1 = mul2(bc2(-2.f), q);
+    const float2 k2 = mul2(add2(q, q), q);
+    v[0] = fma2(k1, bh[0], mul2(k2, a[0]));
+    v[1] = fma2(k1, bh[1], mul2(k2, a[1]));
+    v[2] = fma2(k1, bh[2], mul2(k2, a[2]));
+    return psi;
+}
+
+// 16-byte load of data read once (R's normalized gradient field): through the
+// non-coherent path without allocating in L1, which holds the template
+// samples.  Predicated inside the instruction (v keeps its value where pred is
+// false), so that no branch joins behind it: the load stays in flight until
+// its first use a step later.  volatile: it stays where it is issued.
+__device__ __forceinline__ void ld_once4(float4 &v, const float4 *p, bool pred)
+{
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+        "@q ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%5];\n\t}"
+        : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w)
+        : "r"((int)pred), "l"(p));
+}
+
 __device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc, bool valid)
 {
     unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -198,7 +280,7 @@ __device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cas
 __device__ __forceinline__ void sts2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 
 // One thread's share of the cooperative copy of a node plane (u and, with a
-// direction, dir) of the CTA's 17 x 17 node tile: entries tid + q NT.  The
+// direction, dir) of the CTA's 17 x 9 node tile: entries tid + q NT.  The
 // in-plane offsets do not change along z, so they are computed once.
 struct NodeCopy {
     int src[NCOPY];   // offset of the entry's node in plane 0 of u or dir; -1: outside the grid
@@ -225,10 +307,10 @@ __device__ __forceinline__ NodeCopy node_copy_setup(const LevelGeom &g, int kx0,
 }
 
 // copy node plane K into its ring slot; nodes outside the grid read as zero
-__device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float *ub, const float *dir, float *sm,
-                                                 int K, int nz, size_t plane_stride)
+__device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float *ub, const float *dir,
+                                                 float *nodes, int K, int nz, size_t plane_stride)
 {
-    float *dst = sm + OFF_N + node_slot(K) * 2 * TNP;
+    float *dst = nodes + node_slot(K) * 2 * TNP;
     const bool kin = K >= 0 && K < nz;
     const size_t kofs = kin ? plane_stride * (size_t)K : 0;
 #pragma unroll
@@ -243,9 +325,9 @@ __device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float
 // the trial point of node plane K (copied into its ring slot and visible to
 // every thread): u <- u + t dir in place, the same fmaf as the accepted update,
 // so the accepted iterate equals the evaluated one bit for bit
-__device__ __forceinline__ void trial_node_plane(float *sm, int K, float t, int tid)
+__device__ __forceinline__ void trial_node_plane(float *nodes, int K, float t, int tid)
 {
-    float *nu = sm + OFF_N + node_slot(K) * 2 * TNP;
+    float *nu = nodes + node_slot(K) * 2 * TNP;
 #pragma unroll
     for (int q = 0; q < NCOMB; q++) {
         const int e = tid + q * NT;
@@ -257,10 +339,10 @@ __device__ __forceinline__ void trial_node_plane(float *sm, int K, float t, int 
 // displacement plane K of the thread's two columns from the shared node tile:
 // the value at the interval's first node (U, shared) and the bilinear
 // interpolation of the in-plane differences (B, x weight 1/4 and 3/4 per lane)
-__device__ __forceinline__ void column_pair_plane(const float *sm, int K, int lkx, int lky, float2 WY, float U[3],
+__device__ __forceinline__ void column_pair_plane(const float *nodes, int K, int lkx, int lky, float2 WY, float U[3],
                                                   float2 B[3])
 {
-    const float *nu = sm + OFF_N + node_slot(K) * 2 * TNP;
+    const float *nu = nodes + node_slot(K) * 2 * TNP;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const int o = c * (TNY * TNX) + lky * TNX + lkx;
@@ -329,7 +411,7 @@ __device__ __forceinline__ void tile_seg_col(const FusedSplit &sp, int ncols, in
 }
 
 // One output tile (launch-order id, see tile_seg_col) of the fused pass; sm is
-// the CTA's dynamic shared memory (SMEM_BYTES).  PAD: a.T is the zero-bordered
+// the CTA's dynamic shared memory (Smem<RN>::BYTES).  PAD: a.T is the zero-bordered
 // copy of T (dims m + 4, the image at offset 2 in every dimension).  CURV: the
 // tile also forms the curvature Laplacian of the nodes it owns (a.w) and their
 // share of S (a.partials_S) - where no separate curvature pass can run beside
@@ -337,6 +419,8 @@ __device__ __forceinline__ void tile_seg_col(const FusedSplit &sp, int ncols, in
 template <bool HAS_DIR, typename IMG, bool PAD, bool CURV>
 __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, float *sm)
 {
+    constexpr bool RN = reads_rn<IMG, PAD, CURV>();
+    using SL = Smem<RN>;
     const LevelGeom &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int sp = 2 * tx + CW * ty;                  // shared-plane index of the thread's first column
@@ -366,6 +450,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     const size_t node_plane = (size_t)g.n[0] * g.n[1];
     const IMG *Tim = static_cast<const IMG *>(a.T);
     const IMG *Rcol = static_cast<const IMG *>(a.R) + (col_in ? xa + mx * y : 0);
+    // the pair's two 16-byte halves of R's normalized field (stored by column pair)
+    const float4 *Rncol = RN ? a.Rn + (col_in ? xa + mx * y : 0) : nullptr;
     // padded template: row pitch, plane pitch and the largest cell index (padded coordinates)
     const int MXP = mx + 4;
     const int MYP = my + 4;
@@ -380,7 +466,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     // lanes of the NGF residual that count: interior voxels (MI), and of those
     // the output columns, whose psi is summed (MO)
     const float2 MI = make_float2(intA ? 1.f : 0.f, intB ? 1.f : 0.f);
-    const float2 MO = make_float2(intA && outxy ? 1.f : 0.f, intB && outxy ? 1.f : 0.f);
+    const float2 MO = RN ? bc2(outxy ? 1.f : 0.f)   // psi is zero off the interior
+                         : make_float2(intA && outxy ? 1.f : 0.f, intB && outxy ? 1.f : 0.f);
+    // rows 0 and BY - 1 (whose v is never read) take their own row for the missing neighbour
+    const int dyp = ty < BY - 1 ? CW : 0, dym = ty > 0 ? CW : 0;
     // phase D: partial entries tid and tid + NT = (component, node row jy, node column jx)
     bool dD[2];
     int dofs[2];
@@ -392,7 +481,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         dofs[q] = ((2 * djy) * NX + djx) * 3 + dc;
     }
     // curvature: entries tid and tid + NT = (component, node row, node column) of the
-    // node columns this tile owns, local columns and rows 1 .. 14 (1 .. 15 in the
+    // node columns this tile owns, local columns 1 .. 14 and rows 1 .. 6 (to 15 and 7 in the
     // last tile column or row) inside the grid; every node has one owner
     int wo[2] = {-1, -1}, wg[2] = {0, 0};   // offset in a node-plane tile (-1: no entry) and in a plane of w
     bool wxy[2] = {false, false};           // node interior in x and y
@@ -416,14 +505,15 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     bool ok0 = true, ok1 = true;   // displacement of the interval representable, per column
     float2 pc[8];              // corners of the next plane, both columns, loaded a step ahead
     float2 fr[3];              // and their fractions
-    float2 rnext;              // R of the next plane
+    float2 rnext;              // R of the next plane (without RN)
+    float4 bn0 = make_float4(0.f, 0.f, 0.f, 0.f), bn1 = bn0;   // R's normalized field, phase B's next plane (RN)
     float acc_lo[2] = {0.f, 0.f}, hold[2] = {0.f, 0.f};
     KahanF2 psi_sum;
     int gs = 0;                // grad T slot of this step's plane zA; zA - 4 is in slot gs + 1 (mod 5)
 
     // rows of the x-reduction buffers that no output row writes stay zero
     for (int e = tid; e < 2 * RED_PLANE; e += NT)
-        sm[OFF_RED + e] = 0.f;
+        sm[SL::RED + e] = 0.f;
 
     // ---- A-issue of plane z1: at an even plane (the start of node interval
     // z1 / 2), P on the interval; at an odd plane, the trial values of the node
@@ -437,7 +527,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             float Ulo[3];
             float2 Blo[3];
             if (first) {
-                column_pair_plane(sm, K1, tx, lky, WY, Ulo, Blo);
+                column_pair_plane(sm + SL::N, K1, tx, lky, WY, Ulo, Blo);
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
@@ -445,7 +535,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                     Blo[c] = Bhi[c];
                 }
             }
-            column_pair_plane(sm, K1 + 1, tx, lky, WY, Uhi, Bhi);
+            column_pair_plane(sm + SL::N, K1 + 1, tx, lky, WY, Uhi, Bhi);
             // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz) with wz = 1/4 (even z) or
             // 3/4 (odd z).  The sampling coordinate i + y-hat / h is kept as an integer
             // part plus a small fraction; both depend only on the interval and the
@@ -478,9 +568,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             // interior nodes, 0 elsewhere, from planes K1 - 1 .. K1 + 1 of the ring,
             // for the planes this segment owns (the last segment also its top one)
             if (CURV && K1 >= (z0 >> 1) && (K1 < (zend >> 1) || zend == mz)) {
-                const float *pw = sm + OFF_N + node_slot(K1) * 2 * TNP;
-                const float *pm = sm + OFF_N + node_slot(K1 - 1) * 2 * TNP;
-                const float *pp = sm + OFF_N + node_slot(K1 + 1) * 2 * TNP;
+                const float *pw = sm + SL::N + node_slot(K1) * 2 * TNP;
+                const float *pm = sm + SL::N + node_slot(K1 - 1) * 2 * TNP;
+                const float *pp = sm + SL::N + node_slot(K1 + 1) * 2 * TNP;
                 const bool wz = K1 >= 1 && K1 <= g.n[2] - 2;
                 float *wk = a.w + (size_t)K1 * node_plane;
 #pragma unroll
@@ -498,7 +588,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                         wacc = fmaf(lap, lap, wacc);
                     }
             }
-            issue_node_plane(nc, a.ub, a.dir, sm, K1 + 2, g.n[2], node_plane);
+            issue_node_plane(nc, a.ub, a.dir, sm + SL::N, K1 + 2, g.n[2], node_plane);
             cp_async_commit();
         } else {
 #pragma unroll
@@ -506,7 +596,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                 f[c] = fo[c];
             bz += 1;
             if (HAS_DIR)   // copied at the interval start, visible since the last barrier
-                trial_node_plane(sm, (z1 >> 1) + 2, t, tid);
+                trial_node_plane(sm + SL::N, (z1 >> 1) + 2, t, tid);
         }
         // integer cells and fractions of both columns: the sum with 1.5 2^23 rounded
         // down holds floor(f) in its low bits
@@ -570,7 +660,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                     pc[j].x = v[j];
             }
         }
-        rnext = zin ? ldimg2(Rcol + (size_t)sxy * z1) : make_float2(0.f, 0.f);
+        if (!RN)
+            rnext = zin ? ldimg2(Rcol + (size_t)sxy * z1) : make_float2(0.f, 0.f);
     };
 
     // ---- one step of the pipeline; ODD: planes zA + 1 and zA - 5 are odd
@@ -592,9 +683,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             const float2 gy = lerp2(e0, e1, fr[2]);
             const float2 gx = lerp2(lerp2(d00, d10, fr[1]), lerp2(d01, d11, fr[1]), fr[2]);
             const int slot = zA & 3;
-            sts2(sm + OFF_T + slot * PLANE + sp, val);
-            sts2(sm + OFF_R + slot * PLANE + sp, rnext);
-            float *gq = sm + OFF_G + gs * 3 * PLANE + sp;
+            sts2(sm + SL::T + slot * PLANE + sp, val);
+            if (!RN)
+                sts2(sm + SL::R + slot * PLANE + sp, rnext);
+            float *gq = sm + SL::G + gs * 3 * PLANE + sp;
             sts2(gq, gx);
             sts2(gq + PLANE, gy);
             sts2(gq + 2 * PLANE, gz);
@@ -602,15 +694,52 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         // ---- A-issue for plane zA + 1
         if (FULL || zA <= zend)
             a_issue(zA + 1, std::integral_constant<bool, ODD>{}, false);
-        // ---- B: v on plane zA - 2 (rows 1 .. 30)
+        // ---- B: v on plane zA - 2 (rows 1 .. BY - 2)
         const int zB = zA - 2;
-        if (FULL || (zB >= z0 - 1 && zB <= zend)) {
+        if constexpr (RN) {
+            if (FULL || (zB >= z0 - 1 && zB <= zend)) {
+                // R enters through its normalized gradient field, loaded a step ahead
+                // (zero off the interior and off the image): no interior tests, and
+                // rows 0 and BY - 1, whose v is never read, run the same code
+                const int o0 = (zB & 3) * PLANE + sp;
+                const float *T0 = sm + SL::T + o0;
+                const float2 t0 = lds2(T0);
+                const float tl = __shfl_up_sync(0xffffffffu, t0.y, 1, BX);
+                const float tr = __shfl_down_sync(0xffffffffu, t0.x, 1, BX);
+                const int op = ((zB + 1) & 3) * PLANE + sp, om = ((zB - 1) & 3) * PLANE + sp;
+                const float2 typ = lds2(T0 + dyp), tym = lds2(T0 - dym);
+                const float2 tzp = lds2(sm + SL::T + op), tzm = lds2(sm + SL::T + om);
+                const float2 av[3] = {mul2(make_float2(t0.y - tl, tr - t0.x), HX), mul2(sub2(typ, tym), HY),
+                                      mul2(sub2(tzp, tzm), HZ)};
+                // the field is stored by column pair: (bx, bx'), (by, by') | (bz, bz'), (rh, rh')
+                const float2 bh[3] = {make_float2(bn0.x, bn0.y), make_float2(bn0.z, bn0.w),
+                                      make_float2(bn1.x, bn1.y)};
+                float2 v[3];
+                const float2 psi = ngf_residual_rn2(av, bh, make_float2(bn1.z, bn1.w), a.tau, v);
+                if (FULL || (zB >= z0 && zB < zend))
+                    psi_sum.add(mul2(psi, MO));
+                float *vq = sm + SL::V + (zB & 3) * 3 * PLANE + sp;
+                sts2(vq, v[0]);
+                sts2(vq + PLANE, v[1]);
+                sts2(vq + 2 * PLANE, v[2]);
+            }
+            // the field at the next step's plane zB + 1, zero off the image.  In a full
+            // step that plane lies inside the image and the load depends on the
+            // column alone, so a column outside keeps its zeros without a reset
+            const int zn = zB + 1;
+            const bool ld = col_in && (FULL || (zn >= z0 - 1 && zn <= zend && zn >= 0 && zn < mz));
+            if (!FULL)
+                bn0 = bn1 = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *q = Rncol + (size_t)sxy * zn;
+            ld_once4(bn0, q, ld);
+            ld_once4(bn1, q + 1, ld);
+        } else if (FULL || (zB >= z0 - 1 && zB <= zend)) {
             // the pair's own T~ and R (every row), and its x neighbours from the
             // threads beside it: column 2tx - 1 is thread tx - 1's second column,
             // 2tx + 2 thread tx + 1's first (lanes 0 and 31 get their own values;
             // their v is never read)
             const int o0 = (zB & 3) * PLANE + sp;
-            const float *T0 = sm + OFF_T + o0, *R0 = sm + OFF_R + o0;
+            const float *T0 = sm + SL::T + o0, *R0 = sm + SL::R + o0;
             const float2 t0 = lds2(T0), r0 = lds2(R0);
             const float tl = __shfl_up_sync(0xffffffffu, t0.y, 1, BX), tr = __shfl_down_sync(0xffffffffu, t0.x, 1, BX);
             const float rl = __shfl_up_sync(0xffffffffu, r0.y, 1, BX), rr = __shfl_down_sync(0xffffffffu, r0.x, 1, BX);
@@ -618,9 +747,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             if (rowB && (intA || intB) && zB >= 1 && zB <= mz - 2) {
                 const int op = ((zB + 1) & 3) * PLANE + sp, om = ((zB - 1) & 3) * PLANE + sp;
                 const float2 typ = lds2(T0 + CW), tym = lds2(T0 - CW);
-                const float2 tzp = lds2(sm + OFF_T + op), tzm = lds2(sm + OFF_T + om);
+                const float2 tzp = lds2(sm + SL::T + op), tzm = lds2(sm + SL::T + om);
                 const float2 ryp = lds2(R0 + CW), rym = lds2(R0 - CW);
-                const float2 rzp = lds2(sm + OFF_R + op), rzm = lds2(sm + OFF_R + om);
+                const float2 rzp = lds2(sm + SL::R + op), rzm = lds2(sm + SL::R + om);
                 const float2 av[3] = {mul2(make_float2(t0.y - tl, tr - t0.x), HX), mul2(sub2(typ, tym), HY),
                                       mul2(sub2(tzp, tzm), HZ)};
                 const float2 bv[3] = {mul2(make_float2(r0.y - rl, rr - r0.x), HX), mul2(sub2(ryp, rym), HY),
@@ -633,36 +762,36 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                     psi_sum.add(mul2(psi, MO));
             }
             if (rowB) {
-                float *vq = sm + OFF_V + (zB & 3) * 3 * PLANE + sp;
+                float *vq = sm + SL::V + (zB & 3) * 3 * PLANE + sp;
                 sts2(vq, v[0]);
                 sts2(vq + PLANE, v[1]);
                 sts2(vq + 2 * PLANE, v[2]);
             }
         }
-        // ---- C: r on plane zA - 4 (rows 2 .. 29), x reduction into node columns
+        // ---- C: r on plane zA - 4 (rows 2 .. BY - 3), x reduction into node columns
         const int zC = zA - 4;
         if (rowC && (FULL || (zC >= z0 && zC < zend))) {   // uniform per warp (a warp holds rows 2w, 2w + 1)
             float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             // v_x of the pair and of its x neighbours (columns 2tx - 1, 2tx + 2) from the threads beside it
-            const float *V0 = sm + OFF_V + (zC & 3) * 3 * PLANE + sp;
+            const float *V0 = sm + SL::V + (zC & 3) * 3 * PLANE + sp;
             const float2 vx = lds2(V0);
             const float vl = __shfl_up_sync(0xffffffffu, vx.y, 1, BX), vr = __shfl_down_sync(0xffffffffu, vx.x, 1, BX);
             if (outxy && col_in && zC < mz) {
-                const float *Vzm = sm + OFF_V + ((zC - 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
-                const float *Vzp = sm + OFF_V + ((zC + 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
+                const float *Vzm = sm + SL::V + ((zC - 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
+                const float *Vzp = sm + SL::V + ((zC + 1) & 3) * 3 * PLANE + 2 * PLANE + sp;
                 const float2 vyp = lds2(V0 + PLANE + CW), vym = lds2(V0 + PLANE - CW);
                 const float2 vzm = lds2(Vzm), vzp = lds2(Vzp);
                 // adjoint of the central differences (without the factor hbar / 2)
                 const float2 gj = fma2(make_float2(vl - vx.y, vx.x - vr), HX,
                                        fma2(sub2(vym, vyp), HY, mul2(sub2(vzm, vzp), HZ)));
-                const float *gq = sm + OFF_G + (gs == GSLOTS - 1 ? 0 : gs + 1) * 3 * PLANE + sp;
+                const float *gq = sm + SL::G + (gs == GSLOTS - 1 ? 0 : gs + 1) * 3 * PLANE + sp;
                 r[0] = mul2(gj, lds2(gq));
                 r[1] = mul2(gj, lds2(gq + PLANE));
                 r[2] = mul2(gj, lds2(gq + 2 * PLANE));
             }
             // node column j (0..14) gathers columns 2j .. 2j+3 with weights 1/4, 3/4,
             // 3/4, 1/4: the first two are thread j's pair, the last two thread j+1's
-            float *red = sm + OFF_RED + (ODD ? 0 : 1) * RED_PLANE + ty * NX * 3;
+            float *red = sm + SL::RED + (ODD ? 0 : 1) * RED_PLANE + ty * NX * 3;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const float lo = fmaf(0.75f, r[c].y, 0.25f * r[c].x), hi = fmaf(0.25f, r[c].y, 0.75f * r[c].x);
@@ -676,7 +805,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
         // and 1/4 to the upper, an odd plane the reverse
         const int zD = zA - 5;
         if (FULL || (zD >= z0 && zD < zend)) {
-            const float *red = sm + OFF_RED + (ODD ? 1 : 0) * RED_PLANE;
+            const float *red = sm + SL::RED + (ODD ? 1 : 0) * RED_PLANE;
             const int lz = zD - z0;
 #pragma unroll
             for (int q = 0; q < 2; q++)
@@ -703,14 +832,14 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     // the loads of plane z0 - 2
     {
         const int K0 = (z0 - 2) >> 1;
-        issue_node_plane(nc, a.ub, a.dir, sm, K0, g.n[2], node_plane);
-        issue_node_plane(nc, a.ub, a.dir, sm, K0 + 1, g.n[2], node_plane);
+        issue_node_plane(nc, a.ub, a.dir, sm + SL::N, K0, g.n[2], node_plane);
+        issue_node_plane(nc, a.ub, a.dir, sm + SL::N, K0 + 1, g.n[2], node_plane);
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
         if (HAS_DIR) {
-            trial_node_plane(sm, K0, t, tid);
-            trial_node_plane(sm, K0 + 1, t, tid);
+            trial_node_plane(sm + SL::N, K0, t, tid);
+            trial_node_plane(sm + SL::N, K0 + 1, t, tid);
             __syncthreads();
         }
         a_issue(z0 - 2, std::false_type{}, true);
@@ -740,18 +869,18 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             step(s + 1, std::false_type{}, std::false_type{});
     }
     const float2 ps = psi_sum.s;
-    const double ssum = block_sum_to_f64(ps.x + ps.y, reinterpret_cast<double *>(sm + OFF_RED));
+    const double ssum = block_sum_to_f64(ps.x + ps.y, reinterpret_cast<double *>(sm + SL::RED));
     if (tid == 0)
         a.partials[tile_lin] = ssum;
     if (CURV) {
-        const double wsum = block_sum_to_f64(wacc, reinterpret_cast<double *>(sm + OFF_RED));
+        const double wsum = block_sum_to_f64(wacc, reinterpret_cast<double *>(sm + SL::RED));
         if (tid == 0)
             a.partials_S[tile_lin] = wsum;
     }
 }
 
 template <bool HAS_DIR, typename IMG = float, bool PAD = true, bool CURV = false>
-__global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
+__global__ void __launch_bounds__(BX * BY, CTAS_PER_SM) k_ngf_fused(FusedArgs a)
 {
     extern __shared__ float sm[];
     fused_tile<HAS_DIR, IMG, PAD, CURV>(a, blockIdx.x, sm);
@@ -760,7 +889,7 @@ __global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused(FusedArgs a)
 // Batched fused pass: a persistent grid walks the tiles of all pairs.  Mode 0
 // evaluates at u; mode 1 at the trial point, for the pairs still searching.
 template <bool HAS_DIR, typename IMG>
-__global__ void __launch_bounds__(BX * BY, 1) k_ngf_fused_batch(const PairLevel *__restrict__ pl,
+__global__ void __launch_bounds__(BX * BY, CTAS_PER_SM) k_ngf_fused_batch(const PairLevel *__restrict__ pl,
                                                                 const int *__restrict__ tile_off, int npairs,
                                                                 int total)
 {
@@ -954,15 +1083,15 @@ static std::vector<int> tz_splits(int mz)
 }
 
 // Load model of the pass.  A tile costs its planes + 7 steps, times a weight
-// for the share of its 32 x 32 columns inside the image (columns outside skip
+// for the share of its 32 x 16 columns inside the image (columns outside skip
 // the loads, the interpolation and the NGF work; about a third of a step's
-// work remains).  One CTA is resident per SM and the next free SM takes the
-// next tile in launch order (tile_seg_col), so the model replays that order
-// and returns the time the last SM finishes.
+// work remains).  CTAS_PER_SM CTAs are resident per SM, each a slot, and the
+// next free slot takes the next tile in launch order (tile_seg_col), so the
+// model replays that order and returns the time the last slot finishes.
 struct SplitModel {
     std::vector<double> colw;   // weight of each tile column, in column order
     int mz, sms;
-    SplitModel(const int m[3], int num_sms) : mz(m[2]), sms(num_sms > 0 ? num_sms : 1)
+    SplitModel(const int m[3], int num_sms) : mz(m[2]), sms(num_sms > 0 ? CTAS_PER_SM * num_sms : 1)
     {
         const int ntx = (m[0] + OX - 1) / OX, nty = (m[1] + OY - 1) / OY;
         auto frac = [](int t, int o, int width, int extent) {
@@ -1073,6 +1202,13 @@ int fused_tz_throughput(const Level &L)
 
 bool fused_tz_valid(int tz) { return tz >= 2 && tz <= TZ_MAX && tz % 2 == 0; }
 
+void fused_tile_shape(int *ox, int *oy, int *ctas_per_sm)
+{
+    *ox = OX;
+    *oy = OY;
+    *ctas_per_sm = CTAS_PER_SM;
+}
+
 // tile-partial floats of the level, for any split: a tile of a segment of len
 // planes keeps len / 2 + 1 node planes, and the segments' lengths add up to
 // the depth, so a split keeps at most depth / 2 + count <= depth planes per column
@@ -1092,6 +1228,9 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     const bool bf16 = c->cfg.image_dtype == 1 && L.Tb && L.Rb;
     a.T = bf16 ? static_cast<const void *>(L.Tb) : static_cast<const void *>(L.Tp);   // zero-bordered copies
     a.R = bf16 ? L.Rb : static_cast<const void *>(L.R);
+    a.Rn = bf16 ? nullptr : L.Rn;
+    if (!bf16 && !L.Rn)
+        return cudaErrorInvalidValue;   // FP32 handles keep R's normalized field beside the padded T
     a.ub = ub;
     a.dir = dir;
     a.t_dev = t_dev;
@@ -1110,21 +1249,21 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     static bool attr_set[64] = {};
     const int dev = c->device >= 0 && c->device < 64 ? c->device : 0;
     if (!attr_set[dev]) {
-        cudaError_t e = set_fused_smem(k_ngf_fused<true, float>);
+        cudaError_t e = set_fused_smem(k_ngf_fused<true, float>, smem_bytes<float, true, false>());
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused<false, float>);
+            e = set_fused_smem(k_ngf_fused<false, float>, smem_bytes<float, true, false>());
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused<true, __nv_bfloat16>);
+            e = set_fused_smem(k_ngf_fused<true, __nv_bfloat16>, smem_bytes<__nv_bfloat16, true, false>());
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused<false, __nv_bfloat16>);
+            e = set_fused_smem(k_ngf_fused<false, __nv_bfloat16>, smem_bytes<__nv_bfloat16, true, false>());
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused<true, float, true, true>);
+            e = set_fused_smem(k_ngf_fused<true, float, true, true>, smem_bytes<float, true, true>());
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused<false, float, true, true>);
+            e = set_fused_smem(k_ngf_fused<false, float, true, true>, smem_bytes<float, true, true>());
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused<true, __nv_bfloat16, true, true>);
+            e = set_fused_smem(k_ngf_fused<true, __nv_bfloat16, true, true>, smem_bytes<__nv_bfloat16, true, true>());
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused<false, __nv_bfloat16, true, true>);
+            e = set_fused_smem(k_ngf_fused<false, __nv_bfloat16, true, true>, smem_bytes<__nv_bfloat16, true, true>());
         if (e != cudaSuccess)
             return e;
         attr_set[dev] = true;
@@ -1132,19 +1271,25 @@ cudaError_t launch_ngf_fused(reg_ctx *c, int level, const float *ub, const float
     // the curvature Laplacian in the pass (the batched form's arithmetic) or beside it
     const bool curv = fused_curv_in_pass(c);
     if (bf16) {
-        if (curv)
-            dir ? k_ngf_fused<true, __nv_bfloat16, true, true><<<grd, blk, SMEM_BYTES, s>>>(a)
-                : k_ngf_fused<false, __nv_bfloat16, true, true><<<grd, blk, SMEM_BYTES, s>>>(a);
-        else
-            dir ? k_ngf_fused<true, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a)
-                : k_ngf_fused<false, __nv_bfloat16><<<grd, blk, SMEM_BYTES, s>>>(a);
+        if (curv) {
+            constexpr size_t SB = smem_bytes<__nv_bfloat16, true, true>();
+            dir ? k_ngf_fused<true, __nv_bfloat16, true, true><<<grd, blk, SB, s>>>(a)
+                : k_ngf_fused<false, __nv_bfloat16, true, true><<<grd, blk, SB, s>>>(a);
+        } else {
+            constexpr size_t SB = smem_bytes<__nv_bfloat16, true, false>();
+            dir ? k_ngf_fused<true, __nv_bfloat16><<<grd, blk, SB, s>>>(a)
+                : k_ngf_fused<false, __nv_bfloat16><<<grd, blk, SB, s>>>(a);
+        }
     } else {
-        if (curv)
-            dir ? k_ngf_fused<true, float, true, true><<<grd, blk, SMEM_BYTES, s>>>(a)
-                : k_ngf_fused<false, float, true, true><<<grd, blk, SMEM_BYTES, s>>>(a);
-        else
-            dir ? k_ngf_fused<true, float><<<grd, blk, SMEM_BYTES, s>>>(a)
-                : k_ngf_fused<false, float><<<grd, blk, SMEM_BYTES, s>>>(a);
+        if (curv) {
+            constexpr size_t SB = smem_bytes<float, true, true>();
+            dir ? k_ngf_fused<true, float, true, true><<<grd, blk, SB, s>>>(a)
+                : k_ngf_fused<false, float, true, true><<<grd, blk, SB, s>>>(a);
+        } else {
+            constexpr size_t SB = smem_bytes<float, true, false>();
+            dir ? k_ngf_fused<true, float><<<grd, blk, SB, s>>>(a)
+                : k_ngf_fused<false, float><<<grd, blk, SB, s>>>(a);
+        }
     }
     *n_partials = ntiles;
     c->launches += 1;
@@ -1312,7 +1457,7 @@ void fused_layout_dims(const int m[3], int num_sms, int *tz, int *tiles, size_t 
 // the explicit-buffer pass reads the caller's unpadded T (bounds-tested corner loads)
 cudaError_t fused_set_smem_limit()
 {
-    return set_fused_smem(k_ngf_fused<false, float, false, true>);
+    return set_fused_smem(k_ngf_fused<false, float, false, true>, smem_bytes<float, false, true>());
 }
 
 cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float *R, const float *u, float tau,
@@ -1322,6 +1467,7 @@ cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float
     a.g = g;
     a.T = T;
     a.R = R;
+    a.Rn = nullptr;
     a.ub = u;
     a.dir = nullptr;
     a.t_dev = nullptr;
@@ -1335,7 +1481,7 @@ cudaError_t launch_ngf_fused_raw(const LevelGeom &g, const float *T, const float
     dim3 blk(BX, BY, 1), grd(a.ntx * a.nty * a.split.count(), 1, 1);
     a.w = w;
     a.partials_S = partials + grd.x;   // the S partials follow the D partials
-    k_ngf_fused<false, float, false, true><<<grd, blk, SMEM_BYTES, s>>>(a);
+    k_ngf_fused<false, float, false, true><<<grd, blk, smem_bytes<float, false, true>(), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1360,28 +1506,31 @@ cudaError_t launch_fused_batch(const PairLevel *pl, const int *tile_off, int npa
 {
     const int dev = device >= 0 && device < 64 ? device : 0;
     if (!g_batch_attr_set[dev]) {
-        cudaError_t e = set_fused_smem(k_ngf_fused_batch<true, float>);
+        constexpr size_t BF = smem_bytes<float, true, true>(), BH = smem_bytes<__nv_bfloat16, true, true>();
+        cudaError_t e = set_fused_smem(k_ngf_fused_batch<true, float>, BF);
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused_batch<false, float>);
+            e = set_fused_smem(k_ngf_fused_batch<false, float>, BF);
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused_batch<true, __nv_bfloat16>);
+            e = set_fused_smem(k_ngf_fused_batch<true, __nv_bfloat16>, BH);
         if (e == cudaSuccess)
-            e = set_fused_smem(k_ngf_fused_batch<false, __nv_bfloat16>);
+            e = set_fused_smem(k_ngf_fused_batch<false, __nv_bfloat16>, BH);
         if (e != cudaSuccess)
             return e;
         g_batch_attr_set[dev] = true;
     }
     dim3 blk(BX, BY, 1);
     if (bf16) {
+        constexpr size_t SB = smem_bytes<__nv_bfloat16, true, true>();
         if (mode)
-            k_ngf_fused_batch<true, __nv_bfloat16><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+            k_ngf_fused_batch<true, __nv_bfloat16><<<grid, blk, SB, s>>>(pl, tile_off, npairs, total);
         else
-            k_ngf_fused_batch<false, __nv_bfloat16><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+            k_ngf_fused_batch<false, __nv_bfloat16><<<grid, blk, SB, s>>>(pl, tile_off, npairs, total);
     } else {
+        constexpr size_t SB = smem_bytes<float, true, true>();
         if (mode)
-            k_ngf_fused_batch<true, float><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+            k_ngf_fused_batch<true, float><<<grid, blk, SB, s>>>(pl, tile_off, npairs, total);
         else
-            k_ngf_fused_batch<false, float><<<grid, blk, SMEM_BYTES, s>>>(pl, tile_off, npairs, total);
+            k_ngf_fused_batch<false, float><<<grid, blk, SB, s>>>(pl, tile_off, npairs, total);
     }
     return cudaGetLastError();
 }

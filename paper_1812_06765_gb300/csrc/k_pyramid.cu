@@ -95,6 +95,44 @@ __global__ void __launch_bounds__(256) k_pad_template(const float *__restrict__ 
     pad_store(dst + ((size_t)z * py + y) * px + x, v);
 }
 
+// R's normalized gradient field for the fused pass (Eq. 2): R is fixed for the
+// whole registration, so its part of every NGF term is formed once per level.
+// Per voxel, with b the central-difference gradient of R (the differences
+// times 1 / (2 h_c), as the pass forms grad T~): (b / ||b||_rho, rho / ||b||_rho),
+// ||b||_rho = sqrt(|b|^2 + rho^2) with a correctly rounded square root and
+// division; zero on voxels outside the interior, which Eq. 2's sum leaves out.
+// Stored by pairs of columns (x even, x + 1: the two columns a thread of the
+// pass holds), 8 floats per pair: bx, bx', by, by' | bz, bz', rho', rho'',
+// so that every pair of lanes of the pass's packed arithmetic is one 8-byte
+// half of a 16-byte load.  The row length is even, so pair p of a row starts
+// at float 8 p and the array has 4 floats per voxel, as a float4 per voxel.
+__global__ void k_ref_normal_field(const float *__restrict__ R, int mx, int my, int mz, float hx, float hy, float hz,
+                                   float rho, float4 *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= mx || y >= my)
+        return;
+    const size_t sy = (size_t)mx, sz = (size_t)mx * my;
+    const size_t i = x + sy * y + sz * z;
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+    if (x >= 1 && x <= mx - 2 && y >= 1 && y <= my - 2 && z >= 1 && z <= mz - 2) {
+        const float bx = (__ldg(R + i + 1) - __ldg(R + i - 1)) * hx;
+        const float by = (__ldg(R + i + sy) - __ldg(R + i - sy)) * hy;
+        const float bz = (__ldg(R + i + sz) - __ldg(R + i - sz)) * hz;
+        const float nb = sqrtf(fmaf(bz, bz, fmaf(by, by, bx * bx)) + rho * rho);
+        o[0] = bx / nb;
+        o[1] = by / nb;
+        o[2] = bz / nb;
+        o[3] = rho / nb;
+    }
+    float *pair = reinterpret_cast<float *>(out) + 4 * (i - (x & 1));   // 8 floats of the column pair
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+        pair[2 * c + (x & 1)] = o[c];
+}
+
 template <typename TOUT>
 cudaError_t launch_pad(const float *src, const int m[3], TOUT *dst, cudaStream_t s)
 {
@@ -116,6 +154,17 @@ cudaError_t launch_pad_template(const float *src, const int m[3], float *dst, cu
 cudaError_t launch_pad_template(const float *src, const int m[3], __nv_bfloat16 *dst, cudaStream_t s)
 {
     return launch_pad(src, m, dst, s);
+}
+
+cudaError_t launch_ref_normal_field(const Level &L, double rho, cudaStream_t s)
+{
+    // the pass's difference factors: 0.5 * (float)(1 / h), as in grad T~
+    const LevelGeom g = L.geom();
+    dim3 blk(32, 8, 1);
+    dim3 grd((L.m[0] + 31) / 32, (L.m[1] + 7) / 8, L.m[2]);
+    k_ref_normal_field<<<grd, blk, 0, s>>>(L.R, L.m[0], L.m[1], L.m[2], 0.5f * g.ih[0], 0.5f * g.ih[1],
+                                           0.5f * g.ih[2], (float)rho, L.Rn);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s)

@@ -18,6 +18,7 @@ void free_level(Level &L)
     cudaFree(L.R);
     cudaFree(L.T);
     cudaFree(L.Tp);
+    cudaFree(L.Rn);
     cudaFree(L.Rb);
     cudaFree(L.Tb);
     for (int d = 0; d < 3; d++) {
@@ -300,6 +301,7 @@ int allocate_buffers(reg_ctx *c)
                 CK(cudaMalloc(&c->L[l].Tb, sizeof(__nv_bfloat16) * np));
             } else {
                 CK(cudaMalloc(&c->L[l].Tp, sizeof(float) * np));
+                CK(cudaMalloc(&c->L[l].Rn, sizeof(float4) * c->L[l].nv));
             }
         }
     CK(cudaMalloc(&es.w, sizeof(float) * nmax));
@@ -491,7 +493,8 @@ int reg_set_images(reg_handle c, const float *R, const float *T, const int dims[
         }
         if (c->L[l].Tp) {
             CK(launch_pad_template(c->L[l].T, c->L[l].m, c->L[l].Tp, c->stream));
-            c->launches += 1;
+            CK(launch_ref_normal_field(c->L[l], cfg.rho, c->stream));
+            c->launches += 2;
         }
     }
     // tiling of the fused pass per level: forced, autotuned (at u = 0, with the
@@ -551,6 +554,16 @@ int reg_fused_split_plan(const int dims[3], int num_sms, int split[5], double *m
     split[2] = sp.l2;
     split[3] = sp.n2;
     split[4] = sp.lr;
+    return REG_OK;
+}
+
+int reg_fused_tile_shape(int *ox, int *oy, int *ctas_per_sm)
+{
+    int a = 0, b = 0, c = 0;
+    fused_tile_shape(&a, &b, &c);
+    if (ox) *ox = a;
+    if (oy) *oy = b;
+    if (ctas_per_sm) *ctas_per_sm = c;
     return REG_OK;
 }
 

@@ -40,12 +40,13 @@ int set_err(reg_ctx *c, int code, const char *fmt, ...);
 namespace {
 
 // Capacities of the shared scratch (bytes in parentheses):
-//   tile partial sums of P^T r : 2^21 floats      (8 MiB)
+//   tile partial sums of P^T r : 2^22 floats      (16 MiB)
 //   curvature Laplacian w      : 2^20 floats      (4 MiB)
 //   block partial sums         : 2^16 doubles     (512 KiB)
-// 256^3 images do not fit; a 128^3 pair needs about 1.2 M + 0.82 M floats
-// and 2.2 K doubles, and the Laplacian w limits the size to about 136^3.
-constexpr size_t CAP_PART = size_t(1) << 21;
+// 256^3 images do not fit; a 128^3 pair needs at most 2.3 M + 0.82 M floats
+// and a few thousand doubles, and the Laplacian w limits the size to about
+// 136^3 (which needs at most 2.6 M partial floats).
+constexpr size_t CAP_PART = size_t(1) << 22;
 constexpr size_t CAP_W = size_t(1) << 20;
 constexpr size_t CAP_PARTIALS = size_t(1) << 16;
 constexpr size_t OFFB_PART = 0;

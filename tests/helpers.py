@@ -15,6 +15,20 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def fused_tile_columns(dims):
+    """Tile columns of the fused pass over an image (x tiles, y tiles), from the library's tile shape."""
+    from paper_1812_06765_gb300 import _lib
+    ox, oy, _ = _lib.reg_fused_tile_shape()
+    return -(-dims[0] // ox), -(-dims[1] // oy)
+
+
+def fused_seam_nodes(extent, axis):
+    """Node indices that neighbouring fused tiles share along x (axis 0) or y (axis 1)."""
+    from paper_1812_06765_gb300 import _lib
+    o = _lib.reg_fused_tile_shape()[axis]
+    return list(range(o // 2, extent // 2, o // 2))
+
+
 def default_nodes(dims):
     return tuple(int(m) // 2 + 1 for m in dims)
 

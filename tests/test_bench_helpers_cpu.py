@@ -13,8 +13,12 @@ def test_split_lengths_ignore_the_z_order():
 
 
 def test_partial_floats_per_column_count_node_planes():
-    # a segment of len planes keeps len / 2 + 1 node planes of 3 x 15 x 15 entries
-    entries = 3 * 15 * 15
+    # a segment of len planes keeps len / 2 + 1 node planes of 3 x (ox/2 + 1) x (oy/2 + 1)
+    # entries, for the library's ox x oy output tile (3 x 15 x 7 for 28 x 12)
+    from paper_1812_06765_gb300 import build, _lib
+    build.build()
+    ox, oy, _ = _lib.reg_fused_tile_shape()
+    entries = 3 * (ox // 2 + 1) * (oy // 2 + 1)
     assert bench.split_partial_floats_per_column((160, 1, 80, 1, 16)) == (81 + 41 + 9) * entries
     assert bench.split_partial_floats_per_column((4, 16, 0, 0, 0)) == 16 * 3 * entries
     assert bench.split_partial_floats_per_column((0, 0, 0, 0, 70)) == 36 * entries

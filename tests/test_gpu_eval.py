@@ -8,7 +8,7 @@ import pytest
 
 from synth import make_pair, random_image, random_field
 from tests.helpers import (J_RTOL, GRAD_RTOL, assert_parity, check_directional_fd, compare_eval, default_nodes,
-                           full_size_node_bound, rel_l2)
+                           full_size_node_bound, fused_seam_nodes, fused_tile_columns, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
@@ -84,7 +84,7 @@ def test_curvature_in_fused_pass_parity(reg_mod, orc, case):
 def test_curvature_in_fused_pass_z_segments(reg_mod, orc, seams_only):
     # 300 planes: the throughput rule cuts segments of 64, 64, 64, 64 and 44
     # planes, which share the node planes 32, 64, 96 and 128; with seams_only
-    # u is non-zero only there and on the node column and row that x and y
+    # u is non-zero only there and on the node columns and rows that x and y
     # tiles share, so a seam node formed twice or never shows in S and grad
     dims, h, tau, rho, alpha = (30, 26, 300), (1.0, 1.2, 0.9), 0.05, 0.05, 4.0
     R = random_image(dims, 181)
@@ -92,12 +92,14 @@ def test_curvature_in_fused_pass_z_segments(reg_mod, orc, seams_only):
     cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=-1)
     r = reg_mod.Registration(cfg).set_images(R, T, h)
     z, tiles = r.level_tiling(0)
-    assert z == 64 and tiles == 2 * 1 * 5
+    ntx, nty = fused_tile_columns(dims)
+    assert z == 64 and tiles == ntx * nty * 5
     nodes = r.level_info(0)["nodes"]
     u = random_field(nodes, 183, 2.0)
     if seams_only:
         keep = np.zeros(u.shape[1:], bool)
-        keep[:, :, 14] = True
+        keep[:, :, fused_seam_nodes(dims[0], 0)] = True
+        keep[:, fused_seam_nodes(dims[1], 1), :] = True
         keep[[32, 64, 96, 128], :, :] = True
         u = np.where(keep[None], u, 0.0).astype(np.float32)
     e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
@@ -272,8 +274,8 @@ def test_autograd_function(reg_mod, orc):
 
 @pytest.mark.parametrize("impl", [0, 1, "curv-in-pass"])
 def test_seam_nodes_only_field(reg_mod, orc, impl):
-    """u non-zero only on the node planes that neighbouring tiles share (x nodes 14
-    and 28, y node 14) and on the z node planes where segments of the split meet
+    """u non-zero only on the node columns and rows that neighbouring tiles share
+    along x and y and on the z node planes where segments of the split meet
     (20, 25, 30): the displacement jumps across every seam, so a seam node that a
     tile reads or gathers wrongly shows in the per-node bound."""
     dims, h, tau, rho, alpha = (58, 38, 70), (1.2, 0.8, 1.0), 0.05, 0.03, 2.0
@@ -291,8 +293,8 @@ def test_seam_nodes_only_field(reg_mod, orc, impl):
         assert r.level_split(0) == split
     u = random_field(nodes, 173, 2.5)
     keep = np.zeros(u.shape[1:], bool)
-    keep[:, :, [14, 28]] = True
-    keep[:, 14, :] = True
+    keep[:, :, fused_seam_nodes(dims[0], 0)] = True
+    keep[:, fused_seam_nodes(dims[1], 1), :] = True
     keep[[20, 25, 30], :, :] = True
     u = np.where(keep[None], u, 0.0).astype(np.float32)
     e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
@@ -347,7 +349,8 @@ def test_every_fused_tile_depth_matches_oracle(reg_mod, orc, tz):
     cfg = reg_mod.make_config(levels=1, tau=tau, rho=rho, alpha=alpha, fused_tz=tz)
     r = reg_mod.Registration(cfg).set_images(R, T, h)
     z, tiles = r.level_tiling(0)
-    assert z == min(tz, dims[2]) and tiles == 3 * 2 * -(-dims[2] // tz)
+    ntx, nty = fused_tile_columns(dims)
+    assert z == min(tz, dims[2]) and tiles == ntx * nty * -(-dims[2] // tz)
     u = random_field(r.level_info(0)["nodes"], 73, 2.5)
     e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
     assert_parity(e)
@@ -372,7 +375,8 @@ def test_uneven_z_splits_match_oracle(reg_mod, orc, split):
     l1, n1, l2, n2, lr = split
     assert r.level_split(0) == split
     z, tiles = r.level_tiling(0)
-    assert z == max(l1 if n1 else 0, l2 if n2 else 0, lr) and tiles == 3 * 2 * (n1 + n2 + (lr > 0))
+    ntx, nty = fused_tile_columns(dims)
+    assert z == max(l1 if n1 else 0, l2 if n2 else 0, lr) and tiles == ntx * nty * (n1 + n2 + (lr > 0))
     u = random_field(r.level_info(0)["nodes"], 73, 2.5)
     e = compare_eval(r, orc, R, T, dims, h, u, tau, rho, alpha)
     assert_parity(e)

@@ -1,11 +1,12 @@
 """Host logic of the fused pass's z split (no GPU): the load model's plan.
 
-The model: one CTA per SM; a tile costs (planes + 7) pipeline steps times
-0.35 + 0.65 x its share of in-image columns (x columns x0-2 .. x0+29 in
-steps of one, y rows y0-2 .. y0+29, tiles of 28 output columns); the tiles
-launch longest segment group first, then by segment and tile column, each
-taken by the SM that frees first.  The replay below is written from that
-description, independently of the library's C++."""
+The model: k CTAs per SM, each a slot (k and the tile's output columns ox x oy
+come from reg_fused_tile_shape); a tile costs (planes + 7) pipeline steps
+times 0.35 + 0.65 x its share of in-image columns (x columns x0-2 .. x0+ox+1
+in steps of one, y rows y0-2 .. y0+oy+1); the tiles launch longest segment
+group first, then by segment and tile column, each taken by the slot that
+frees first.  The replay below is written from that description,
+independently of the library's C++."""
 import heapq
 
 import pytest
@@ -20,18 +21,25 @@ def libreg():
     return _lib
 
 
+def _shape():
+    from paper_1812_06765_gb300 import _lib
+    build.build()
+    return _lib.reg_fused_tile_shape()
+
+
 def _weights(dims):
+    ox, oy, _ = _shape()
     mx, my = dims[0], dims[1]
-    ntx, nty = -(-mx // 28), -(-my // 28)
-    fx = [sum(0 <= x < mx for x in range(28 * t - 2, 28 * t + 30)) / 32 for t in range(ntx)]
-    fy = [sum(0 <= y < my for y in range(28 * t - 2, 28 * t + 30)) / 32 for t in range(nty)]
+    ntx, nty = -(-mx // ox), -(-my // oy)
+    fx = [sum(0 <= x < mx for x in range(ox * t - 2, ox * t + ox + 2)) / (ox + 4) for t in range(ntx)]
+    fy = [sum(0 <= y < my for y in range(oy * t - 2, oy * t + oy + 2)) / (oy + 4) for t in range(nty)]
     return [0.35 + 0.65 * fx[tx] * fy[ty] for ty in range(nty) for tx in range(ntx)]
 
 
 def _makespan(dims, sms, split):
     l1, n1, l2, n2, lr = split
     groups = sorted([(l1, n1, 0), (l2, n2, 1), (lr, 1 if lr else 0, 2)], key=lambda g: (-g[0], g[2]))
-    free = [0.0] * sms
+    free = [0.0] * (sms * _shape()[2])
     end = 0.0
     for length, count, _ in groups:
         for _ in range(count):
