@@ -228,9 +228,10 @@ struct ChunkRing {
     unsigned long long *full;         // [MAX_STAGES] barriers, static shared memory
     long long n4, first;              // float4 per vector; this block's first chunk
     int gdx, chunks;                  // chunk stride; chunks of this block
+    bool reverse;                     // walk the block's chunks from its last to its first
 
-    __device__ ChunkRing(float4 *b, unsigned long long *f, long long n4_, int bx, int gdx_)
-        : buf(b), full(f), n4(n4_), first(bx), gdx(gdx_)
+    __device__ ChunkRing(float4 *b, unsigned long long *f, long long n4_, int bx, int gdx_, bool reverse_ = false)
+        : buf(b), full(f), n4(n4_), first(bx), gdx(gdx_), reverse(reverse_)
     {
         const long long nch = (n4 + CHUNK4 - 1) / CHUNK4;
         chunks = nch > bx ? (int)((nch - 1 - bx) / gdx + 1) : 0;
@@ -241,7 +242,10 @@ struct ChunkRing {
         }
         __syncthreads();
     }
-    __device__ long long elem0(int k) const { return (first + (long long)k * gdx) * CHUNK4; }
+    __device__ long long elem0(int k) const
+    {
+        return (first + (long long)(reverse ? chunks - 1 - k : k) * gdx) * CHUNK4;
+    }
     __device__ float4 *stage(int k) const { return buf + (size_t)(k % STAGES) * NS * CHUNK4; }
     // thread 0: copy chunk k of the NS source vectors src(i) into its stage;
     // drop (test hook): arm the stage's barrier but issue no copy
@@ -314,7 +318,9 @@ __device__ __forceinline__ bool direction_stream(long long n4, int bx, int gdx, 
                                                  unsigned long long *full, bool drop_first)
 {
     constexpr int NS = 1 + 2 * DC;
-    ChunkRing<NS> ring(buf, full, n4, bx, gdx);
+    // the reverse of the accept pass's order: the chunks that pass read last
+    // (the history's high ends) are still in L2 when this pass starts
+    ChunkRing<NS> ring(buf, full, n4, bx, gdx, true);
     auto src = [&](int i) -> const float4 * { return i == 0 ? g4 : (i <= DC ? P4 + off[i - 1] : Y4 + off[i - 1 - DC]); };
     return stream_chunks<NS>(ring, src, [&](int k, const float4 *sb) {
         const long long e = ring.elem0(k) + threadIdx.x;
