@@ -36,8 +36,8 @@ struct PairLevel {
     LbfgsState *st;
     long long n, stride;    // vector length, ring slot stride
     float *u, *g, *gt, *pdir, *P, *Y;
-    double *lpart;          // vector-pass block partials
-    double *lgpart;         // their group sums
+    float *lpart;           // vector-pass block partials (FP32)
+    float2 *lgpart;         // their group sums (double-float)
     unsigned *lcnt;         // arrival counters of the groups
     int nchunks;            // blocks of the vector passes
     int ntx, nty;           // fused tile columns (also inside fa_*)

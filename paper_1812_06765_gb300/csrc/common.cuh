@@ -99,6 +99,31 @@ struct KahanF {
     }
 };
 
+// Double-float sums: a value as an unevaluated pair hi + lo of FP32 numbers
+// with |lo| <= ulp(hi) / 2, added with Knuth's two-sum (exact error of one
+// addition) and renormalised with Dekker's fast two-sum.  About 48 bits of
+// significand at the cost of a few FP32 instructions: on this GPU an FP64
+// instruction costs about 64 issue cycles, so sums on the critical path of a
+// control phase run faster as double-float than as FP64.  The order of the
+// additions is fixed by the callers, so the sums are deterministic.
+struct DFloat {
+    float hi, lo;
+};
+__device__ __forceinline__ DFloat df_renorm(float s, float e)
+{
+    const float hi = s + e;
+    return DFloat{hi, e - (hi - s)};
+}
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return df_renorm(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ DFloat df_add(DFloat a, float b) { return df_add(a, DFloat{b, 0.f}); }
+__device__ __forceinline__ double df_to_double(DFloat a) { return (double)a.hi + (double)a.lo; }
+
 // Ordered FP64 sum (is_max: max) of count values x[i0], x[i0 + step], ...,
 // starting from s.  The loads go out 8 at a time so that their L2 round trips
 // overlap; the additions keep the index order, so the result is the plain

@@ -103,9 +103,9 @@ struct LbfgsBuffers {
     int slots = 0;
     float *u = nullptr, *pdir = nullptr, *g = nullptr, *gt = nullptr;
     float *P = nullptr, *Y = nullptr;   // slots * n each
-    double *partials = nullptr;
+    float *partials = nullptr;          // FP32 block partials of the vector passes
     int max_partials = 0;
-    double *gpart = nullptr;            // group sums of the vector passes' block partials
+    float2 *gpart = nullptr;            // their group sums, double-float (hi, lo)
     unsigned *cnt = nullptr;            // their arrival counters
     int cnt_len = 0;
     LbfgsState *st = nullptr;           // device

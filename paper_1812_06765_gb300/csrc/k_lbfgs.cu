@@ -28,10 +28,10 @@ constexpr int VT = LB_VT;           // threads of the vector kernels
 
 // Reduce ND per-thread values over the block; entry `imax` (if >= 0) by max,
 // the others by sum, in FP32 and a fixed order (warp shuffles, then the warp
-// totals by one thread per entry); write the block totals as FP64 to
-// out[0 .. ND) for the cross-block FP64 sum.
+// totals by one thread per entry); write the block totals to out[0 .. ND) for
+// the cross-block double-float sum.
 template <int ND>
-__device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, double *out)
+__device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, float *out)
 {
     __shared__ float sm[VT / 32][ND];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -47,7 +47,7 @@ __device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, dou
         float s = sm[0][d];
         for (int w = 1; w < VT / 32; w++)
             s = (d == imax) ? fmaxf(s, sm[w][d]) : s + sm[w][d];
-        out[d] = (double)s;
+        out[d] = s;
     }
 }
 
@@ -55,7 +55,7 @@ __device__ __forceinline__ void block_reduce_write(float (&v)[ND], int imax, dou
 // The arrivals follow the pattern of a grid barrier: block barrier, one
 // thread's fence, atomic; the last block's thread fences again before the
 // block reads the others' partials.  preloaded: ctl_state() holds the state.
-__device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restrict__ partials, int nd, int imax,
+__device__ __forceinline__ void vec_tail(const VecTail &t, const float *__restrict__ partials, int nd, int imax,
                                          int bx, int nblocks, bool preloaded = false)
 {
     __shared__ int s_last;
@@ -74,7 +74,7 @@ __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restr
         __syncthreads();
         if (!s_last)
             return;
-        lb_control_body(t.phase, t.st, partials, nblocks, t.scal, t.h_ls, t.h_iter, t.h_redo, preloaded);
+        lb_control_body(t.phase, t.st, partials, nullptr, nblocks, t.scal, t.h_ls, t.h_iter, t.h_redo, preloaded);
         return;
     }
     __syncthreads();
@@ -89,8 +89,10 @@ __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restr
     __syncthreads();
     if (!s_last)
         return;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x)   // the max entry: a max of absolute values, 0 its identity
-        t.gpart[(size_t)g * nd + d] = ordered_reduce(partials, (long long)g0 * nd + d, gs, nd, d == imax, 0.0);
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {   // the max entry: a max of absolute values
+        const DFloat x = df_ordered_reduce(partials, (long long)g0 * nd + d, gs, nd, d == imax);
+        t.gpart[(size_t)g * nd + d] = make_float2(x.hi, x.lo);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         t.cnt[g] = 0;
@@ -104,7 +106,7 @@ __device__ __forceinline__ void vec_tail(const VecTail &t, const double *__restr
     __syncthreads();
     if (!s_last || t.phase < 0)
         return;
-    lb_control_body(t.phase, t.st, t.gpart, ng, t.scal, t.h_ls, t.h_iter, t.h_redo, preloaded);
+    lb_control_body(t.phase, t.st, nullptr, t.gpart, ng, t.scal, t.h_ls, t.h_iter, t.h_redo, preloaded);
 }
 
 // All vector passes read and write 16-byte vectors: u, g, gt and pdir are
@@ -117,7 +119,7 @@ __device__ __forceinline__ float max4(float4 a)
 }
 
 __device__ __forceinline__ void lb_init_dots_body(long long n, const float *__restrict__ g,
-                                                     double *__restrict__ partials, const VecTail &tail, int bx,
+                                                     float *__restrict__ partials, const VecTail &tail, int bx,
                                                      int gdx)
 {
     float v[2] = {0.f, 0.f};
@@ -138,7 +140,7 @@ __device__ __forceinline__ void lb_init_dots_body(long long n, const float *__re
 }
 
 __global__ void __launch_bounds__(VT) k_lb_init_dots(long long n, const float *__restrict__ g,
-                                                     double *__restrict__ partials, VecTail tail)
+                                                     float *__restrict__ partials, VecTail tail)
 {
     lb_init_dots_body(n, g, partials, tail, blockIdx.x, gridDim.x);
 }
@@ -346,7 +348,7 @@ __device__ __forceinline__ bool direction_stream(long long n4, int bx, int gdx, 
 __device__ __forceinline__ void lb_direction_body(long long n, long long stride, const LbfgsState *st,
                                                      const float *__restrict__ g, const float *__restrict__ P,
                                                      const float *__restrict__ Y, float *__restrict__ pdir,
-                                                     double *__restrict__ partials, int redo, const VecTail &tail,
+                                                     float *__restrict__ partials, int redo, const VecTail &tail,
                                                      int bx, int gdx)
 {
     __shared__ int s_run, s_dc, s_slot[LB_MAXM];
@@ -420,7 +422,7 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
 __global__ void __launch_bounds__(VT) k_lb_direction(long long n, long long stride, const LbfgsState *st,
                                                      const float *__restrict__ g, const float *__restrict__ P,
                                                      const float *__restrict__ Y, float *__restrict__ pdir,
-                                                     double *__restrict__ partials, int redo, VecTail tail)
+                                                     float *__restrict__ partials, int redo, VecTail tail)
 {
     lb_direction_body(n, stride, st, g, P, Y, pdir, partials, redo, tail, blockIdx.x, gridDim.x);
 }
@@ -488,7 +490,7 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
                                                   float *__restrict__ u, float *__restrict__ g,
                                                   const float *__restrict__ gt, const float *__restrict__ pdir,
                                                   float *__restrict__ P, float *__restrict__ Y,
-                                                  double *__restrict__ partials, const VecTail &tail, int bx,
+                                                  float *__restrict__ partials, const VecTail &tail, int bx,
                                                   int gdx)
 {
     __shared__ int s_ok, s_lc, s_free, s_slot[LB_MAXS];
@@ -586,7 +588,7 @@ __global__ void __launch_bounds__(VT) k_lb_accept(long long n, long long stride,
                                                   float *__restrict__ u, float *__restrict__ g,
                                                   const float *__restrict__ gt, const float *__restrict__ pdir,
                                                   float *__restrict__ P, float *__restrict__ Y,
-                                                  double *__restrict__ partials, VecTail tail)
+                                                  float *__restrict__ partials, VecTail tail)
 {
     lb_accept_body(n, stride, st, u, g, gt, pdir, P, Y, partials, tail, blockIdx.x, gridDim.x);
 }
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(512) k_finalize_ctl(const double *__restrict__
 {
     finalize_body(pD, nD, pS, nS, hbar_half, alpha, hy_half, scal);
     __syncthreads();
-    lb_control_body(phase, st, nullptr, 0, scal, h_ls, h_iter, 0ULL);
+    lb_control_body(phase, st, nullptr, nullptr, 0, scal, h_ls, h_iter, 0ULL);
 }
 
 // ---------------------------------------------------------------------------
@@ -635,7 +637,8 @@ __global__ void __launch_bounds__(CT) k_lb_control_batch(const PairLevel *__rest
 {
     const PairLevel &P = pl[blockIdx.x];
     const bool direct = P.nchunks <= LB_DIRECT;   // block partials, else group sums (vec_tail)
-    lb_control_body(phase, P.st, direct ? P.lpart : P.lgpart, direct ? P.nchunks : (P.nchunks + LB_RG - 1) / LB_RG,
+    lb_control_body(phase, P.st, direct ? P.lpart : nullptr, direct ? nullptr : P.lgpart,
+                    direct ? P.nchunks : (P.nchunks + LB_RG - 1) / LB_RG,
                     phase == LB_INIT ? P.scal : P.scal_t, 0ULL, 0ULL, 0ULL);
 }
 
@@ -682,7 +685,7 @@ __device__ __forceinline__ void pair_dot_operands(int d, int count, long long n,
 
 __global__ void __launch_bounds__(VT) k_lb_pair_dots(long long n, int count, const float *__restrict__ S,
                                                      const float *__restrict__ Y, const float *__restrict__ g,
-                                                     double *__restrict__ partials)
+                                                     float *__restrict__ partials)
 {
     const int nd = 2 + 2 * count + 2 * count * count;
     for (int d = 0; d < nd; d++) {
@@ -721,7 +724,7 @@ __global__ void __launch_bounds__(VT) k_lb_direction_plain(long long n, const Lb
     }
 }
 
-__global__ void k_lb_pair_setup(LbfgsState *__restrict__ st, int count, const double *__restrict__ partials,
+__global__ void k_lb_pair_setup(LbfgsState *__restrict__ st, int count, const float *__restrict__ partials,
                                 int nblocks)
 {
     const int nd = 2 + 2 * count + 2 * count * count;

@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(256) k_gather_fin(LevelGeom g, const float *__
         finalize_body(f.pD, f.nD, f.pS, f.nS, f.hbar_half, f.alpha, f.hy_half, f.scal);
         if (f.phase >= 0) {
             __syncthreads();
-            lb_control_body(f.phase, f.st, nullptr, 0, f.scal, f.h_ls, 0ULL, 0ULL);
+            lb_control_body(f.phase, f.st, nullptr, nullptr, 0, f.scal, f.h_ls, 0ULL, 0ULL);
         }
     }
     gather_grad_body(g, part, sp, ntx, nty, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);

@@ -76,34 +76,68 @@ __device__ void set_compact_warp(LbfgsState *st)
 
 __device__ bool finite_d(double x) { return isfinite(x); }
 
-// Cross-block FP64 sum (entry imax: max) of nd values over nblocks block
-// partials (partials[b * nd + d]) in a fixed order.  FP64 instructions cost
-// ~64 cycles per warp instruction whatever the active lanes, so the adds are
-// packed: thread (d, j) sums blocks j, j + J, ... for J groups per value (J
-// about sqrt(nblocks), at most CT / nd), then thread d adds its J group sums.
-__device__ __forceinline__ void control_reduce(const double *__restrict__ partials, int nblocks, int nd, int imax,
-                                               double *red, double *scratch)
+// One entry of a block's partials as a double-float: an FP32 block partial
+// (grids of at most LB_DIRECT blocks) or a double-float group sum.
+__device__ __forceinline__ DFloat df_load(const float *__restrict__ x, long long i)
+{
+    return DFloat{__ldcg(x + i), 0.f};
+}
+__device__ __forceinline__ DFloat df_load(const float2 *__restrict__ x, long long i)
+{
+    const float2 v = __ldcg(x + i);
+    return DFloat{v.x, v.y};
+}
+
+// Ordered double-float sum of count entries x[i0], x[i0 + step], ... (is_max:
+// their maximum; the max entries are maxima of FP32 absolute values, exact in
+// hi).  The loads go out 8 at a time so that their L2 round trips overlap; the
+// additions keep the index order.
+template <typename T>
+__device__ __forceinline__ DFloat df_ordered_reduce(const T *__restrict__ x, long long i0, int count, long long step,
+                                                    bool is_max)
+{
+    DFloat s{0.f, 0.f};
+    for (int k0 = 0; k0 < count; k0 += 8) {
+        DFloat v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            v[k] = k0 + k < count ? df_load(x, i0 + (long long)(k0 + k) * step) : DFloat{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (k0 + k < count)
+                s = is_max ? DFloat{fmaxf(s.hi, v[k].hi), 0.f} : df_add(s, v[k]);
+    }
+    return s;
+}
+
+// Cross-block sum (entry imax: max) of nd values over nparts partials
+// (partials[b * nd + d]) in a fixed order, as double-float: thread (d, j)
+// sums partials j, j + J, ... for J groups per value (J about sqrt(nparts),
+// at most CT / nd), then thread d adds its J group sums and rounds the pair
+// to FP64 in red[d].
+template <typename T>
+__device__ __forceinline__ void control_reduce(const T *__restrict__ partials, int nparts, int nd, int imax,
+                                               double *red, DFloat *scratch)
 {
     const int t = linear_tid();
     int J = 1;
-    while (J * J < nblocks)
+    while (J * J < nparts)
         J++;
     if (J > CT / nd)
         J = CT / nd;
     if (t < nd * J) {
         const int d = t % nd, j = t / nd;
-        // blocks j, j + J, ...; the max entry is a max of absolute values: 0 is its identity
-        const int count = j < nblocks ? (nblocks - j + J - 1) / J : 0;
-        scratch[t] = ordered_reduce(partials, (long long)j * nd + d, count, (long long)J * nd, d == imax, 0.0);
+        const int count = j < nparts ? (nparts - j + J - 1) / J : 0;
+        scratch[t] = df_ordered_reduce(partials, (long long)j * nd + d, count, (long long)J * nd, d == imax);
     }
     __syncthreads();
     if (t < nd) {
-        double s = scratch[t];
+        DFloat s = scratch[t];
         for (int j = 1; j < J; j++) {
-            const double x = scratch[j * nd + t];
-            s = (t == imax) ? fmax(s, x) : s + x;
+            const DFloat x = scratch[j * nd + t];
+            s = (t == imax) ? DFloat{fmaxf(s.hi, x.hi), 0.f} : df_add(s, x);
         }
-        red[t] = s;
+        red[t] = df_to_double(s);
     }
     __syncthreads();
 }
@@ -134,15 +168,17 @@ __device__ __forceinline__ void ctl_state_load(const LbfgsState *gst)
 // other blocks' writes before the block's reads (acquire).
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// The phase's sums come from FP32 block partials pf or double-float group sums
+// pg (nparts of either; both null for the phases that reduce nothing).
 // preloaded: ctl_state() already holds gst (ctl_state_load at the kernel's start)
-__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
-                                                    const double *__restrict__ partials, int nblocks,
+__device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst, const float *__restrict__ pf,
+                                                    const float2 *__restrict__ pg, int nparts,
                                                     const double *__restrict__ scal, unsigned long long h_ls,
                                                     unsigned long long h_iter, unsigned long long h_redo,
                                                     bool preloaded = false)
 {
     __shared__ double red[ND_ACC];
-    __shared__ double scratch[CT];
+    __shared__ DFloat scratch[CT];
     __shared__ int s_store, s_compact;
     constexpr int NW = STATE_WORDS;
     LbfgsState &S = ctl_state();
@@ -156,8 +192,10 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst,
     const int imax = (phase == LB_INIT || phase == LB_ACCEPTED) ? 1 : -1;
     const bool need = phase != LB_ARMIJO && !(phase == LB_ACCEPTED && (!st->active || st->ls != LS_ACCEPTED)) &&
                       !(phase == LB_DIR_REDO && !st->redo_dir) && !(phase == LB_DIR && !st->iter_continue);
-    if (need)
-        control_reduce(partials, nblocks, nd, imax, red, scratch);
+    if (need && pf)
+        control_reduce(pf, nparts, nd, imax, red, scratch);
+    else if (need && pg)
+        control_reduce(pg, nparts, nd, imax, red, scratch);
     __syncthreads();
     if (linear_tid() == 0) {
     s_store = 0;

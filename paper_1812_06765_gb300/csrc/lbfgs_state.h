@@ -59,18 +59,18 @@ struct LbfgsState {
 };
 
 // Cross-block reduction of a vector pass and the control step folded into it.
-// Blocks are grouped LB_RG at a time: the last block of a group (completion
-// order) sums the group's FP64 block partials in block order, and the block
-// that completes the last group runs control phase `phase` on the group sums
-// (-1: none, a separate control kernel follows).  Grids of at most LB_DIRECT
-// blocks skip the group level (one fence, atomic and serial FP64 sum fewer
-// on the critical path): every block arrives on one counter and the control
-// reduces the block partials themselves.  The sums do not depend on the
-// completion order.
+// Each block writes its FP32 partials.  Blocks are grouped LB_RG at a time:
+// the last block of a group (completion order) sums the group's partials in
+// block order as double-float pairs, and the block that completes the last
+// group runs control phase `phase` on the group sums (-1: none, a separate
+// control kernel follows).  Grids of at most LB_DIRECT blocks skip the group
+// level (one fence, atomic and serial sum fewer on the critical path): every
+// block arrives on one counter and the control reduces the block partials
+// themselves.  The sums do not depend on the completion order.
 #define LB_RG 16
 #define LB_DIRECT 256
 struct VecTail {
-    double *gpart;                   // [groups][nd] group sums
+    float2 *gpart;                   // [groups][nd] group sums, double-float (hi, lo)
     unsigned *cnt;                   // [groups + 1] arrival counters, zero between launches
     int phase;
     LbfgsState *st;

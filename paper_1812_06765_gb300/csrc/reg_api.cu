@@ -320,10 +320,10 @@ int allocate_buffers(reg_ctx *c)
     CK(cudaMalloc(&b.Y, sizeof(float) * nring * b.slots));
     // the largest per-block layout is that of reg_lbfgs_direction's pair dots
     b.max_partials = 4 * c->num_sms * (2 + 2 * LB_MAXM + 2 * LB_MAXM * LB_MAXM) + 1024;
-    CK(cudaMalloc(&b.partials, sizeof(double) * b.max_partials));
+    CK(cudaMalloc(&b.partials, sizeof(float) * b.max_partials));
     {   // group sums and arrival counters of the vector passes (<= 4 blocks per SM)
         const int groups = (4 * c->num_sms + LB_RG - 1) / LB_RG;
-        CK(cudaMalloc(&b.gpart, sizeof(double) * groups * (2 + 4 * LB_MAXS)));
+        CK(cudaMalloc(&b.gpart, sizeof(float2) * groups * (2 + 4 * LB_MAXS)));
         b.cnt_len = groups + 1;
         CK(cudaMalloc(&b.cnt, sizeof(unsigned) * b.cnt_len));
         CK(cudaMemset(b.cnt, 0, sizeof(unsigned) * b.cnt_len));
