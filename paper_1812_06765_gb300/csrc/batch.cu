@@ -53,11 +53,10 @@ void fill_pair_level(reg_ctx *c, int level, PairLevel &P)
     P.fa_trial = a;
     P.ntx = ntx;
     P.nty = nty;
-    P.ncx = (L.n[0] + 31) / 32;
-    P.ncy = (L.n[1] + 7) / 8;
+    P.gbx = gather_runs_per_plane(L.n);
     P.nD = ntx * nty * split.count();
     P.nS = P.nD;   // the fused pass writes one S partial per tile
-    P.ngather = P.ncx * P.ncy * L.n[2];
+    P.ngather = P.gbx * L.n[2];
     P.w = c->es.w;
     P.pS = c->es.partials + P.nD;
     const double hy = L.H[0] * L.H[1] * L.H[2];

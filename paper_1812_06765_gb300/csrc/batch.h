@@ -28,7 +28,7 @@ struct PairLevel {
     float *w;               // curvature Laplacian scratch
     double *pS;             // curvature block partials (after the fused-pass partials)
     int nD, nS;             // block partials of D and of S (= curvature blocks)
-    int ngather;            // gather blocks (32 x 8 nodes of one plane)
+    int ngather;            // gather blocks (GATHER_NODES nodes of one plane each)
     double hbar_half, alpha, hy_half;
     float alpha_hy;
     double *scal, *scal_t;  // [J, D, S] at u and at the trial point
@@ -41,7 +41,7 @@ struct PairLevel {
     unsigned *lcnt;         // arrival counters of the groups
     int nchunks;            // blocks of the vector passes
     int ntx, nty;           // fused tile columns (also inside fa_*)
-    int ncx, ncy;           // curvature / gather blocks along x and y (32 x 8 nodes each)
+    int gbx;                // gather blocks per node plane
 };
 
 // prefix sums of per-pair item counts: item i belongs to pair p with

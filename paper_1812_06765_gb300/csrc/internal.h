@@ -226,6 +226,12 @@ cudaError_t launch_ngf_multipass(reg_ctx *c, int level, const float *ub, const f
 cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alpha_hy, float *grad, cudaStream_t s);
 // gather grids from this many blocks up run the final reduction beside the gather (side stream)
 constexpr long long GATHER_SPLIT_BLOCKS = 4096;
+// The node gather of the fused pass: a block takes GATHER_NODES consecutive
+// nodes of one node plane (runs along x, then y); grid = runs per plane x planes.
+constexpr int GATHER_NODES = 256;
+inline int gather_runs_per_plane(const int n[3]) { return (n[0] * n[1] + GATHER_NODES - 1) / GATHER_NODES; }
+inline dim3 gather_grid(const int n[3]) { return dim3(gather_runs_per_plane(n), n[2], 1); }
+inline long long gather_blocks(const int n[3]) { return (long long)gather_runs_per_plane(n) * n[2]; }
 
 cudaError_t build_level_graph(reg_ctx *c, int level, cudaGraphExec_t *out);
 // the curvature Laplacian kernels that run beside the NGF pass (to tell their graph nodes apart)

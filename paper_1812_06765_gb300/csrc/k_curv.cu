@@ -173,8 +173,7 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     // gradient.  On small grids block 0 of the gather runs it first (one launch); on
     // large ones it is a one-block kernel on the side stream beside the gather, since
     // the control code in the gather would cost the large grid occupancy.
-    const long long gather_blocks = (long long)gn.x * gn.y * gn.z;
-    if (fused && gather_blocks < GATHER_SPLIT_BLOCKS)
+    if (fused && gather_blocks(L.n) < GATHER_SPLIT_BLOCKS)
         return launch_gather_fin(c, level, c->es.w, (float)(c->cfg.alpha * hy), grad, nD, pS, nS, scal_out,
                                  ctl_phase, s);
     if (fused) {

@@ -931,40 +931,65 @@ __device__ __forceinline__ void node_seg(const FusedSplit &sp, int kz, int &s, i
 }
 
 // grad J at node k = sum of the tile partials that contain k (P^T r) plus
-// alpha hbar_y L^T w (curvature), one thread per node, 3 components.
-// Along x and y the node's owner tile column is t = min(k / 14, nt - 1) at
-// local index j = k - 14 t; when j = 0 and t > 0 the lower column also holds
-// it, at j = 14.  Along z its owner is the segment holding its node plane
+// alpha hbar_y L^T w (curvature), one thread per node, 3 components.  A block
+// takes GATHER_NODES consecutive nodes of one node plane (bx-th run of plane
+// kz), so that no lane idles at the end of a row.  Along x and y the node's
+// owner tile column is t = min(k / (o/2), nt - 1) at local index
+// j = k - (o/2) t; when j = 0 and t > 0 the lower column also holds it, at
+// j = o/2.  Along z its owner is the segment holding its node plane
 // (node_seg); at the segment's first plane the previous segment also holds it,
 // at its last plane.  The up to 8 partials are added owner first, lower x
-// before lower y before lower z.
+// before lower y before lower z.  Every thread of the block calls it (it has
+// block barriers).
 __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float *__restrict__ part,
                                                  const FusedSplit &sp, int ntx, int nty,
                                                  const float *__restrict__ w, float alpha_hy,
-                                                 float *__restrict__ grad, int bx, int by, int bz)
+                                                 float *__restrict__ grad, int bx, int kz)
 {
-    const int kx = bx * blockDim.x + threadIdx.x;
-    const int ky = by * blockDim.y + threadIdx.y;
-    const int kz = bz;
-    if (kx >= g.n[0] || ky >= g.n[1])
-        return;   // (only this function: a caller's barrier after it is still reached)
+    // the plane's z bookkeeping, the same for the whole block: the owner
+    // segment's partial plane and tile-column stride, and the previous
+    // segment's when it also holds the plane
+    __shared__ long long s_zo, s_zl;
+    __shared__ int s_so, s_sl;
+    if (threadIdx.x == 0) {
+        int so, jz, z0, len;
+        node_seg(sp, kz, so, jz);
+        const long long ncols = (long long)ntx * nty;
+        sp.seg(so, z0, len);
+        s_so = (len / 2 + 1) * NE;
+        s_zo = sp.planes_before(so) * ncols * NE + (long long)jz * NE;
+        s_sl = 0;
+        s_zl = -1;
+        if (jz == 0 && so > 0) {
+            sp.seg(so - 1, z0, len);
+            s_sl = (len / 2 + 1) * NE;
+            s_zl = sp.planes_before(so - 1) * ncols * NE + (long long)(len / 2) * NE;
+        }
+    }
+    __syncthreads();
+    const long long zo = s_zo, zl = s_zl;
+    const int stride_o = s_so, stride_l = s_sl;
+    __syncthreads();   // a caller's next block item may overwrite them
+    const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
+    const int i = bx * GATHER_NODES + threadIdx.x;   // node of the plane
+    if (i >= n01)
+        return;   // (after the barriers: a caller's barrier after it is still reached)
+    // ky = i / n0: a float estimate, exact after one correction either way
+    int ky = (int)((float)i * __frcp_rn((float)n0));
+    int kx = i - ky * n0;
+    if (kx < 0) {
+        ky--;
+        kx += n0;
+    } else if (kx >= n0) {
+        ky++;
+        kx -= n0;
+    }
     const int tx = min(kx / (NX - 1), ntx - 1), ty = min(ky / (NY - 1), nty - 1);
     const int jx = kx - (NX - 1) * tx, jy = ky - (NY - 1) * ty;
-    int so, jz;
-    node_seg(sp, kz, so, jz);
-    const bool lx = jx == 0 && tx > 0, ly = jy == 0 && ty > 0, lz = jz == 0 && so > 0;
-    const long long ncols = (long long)ntx * nty, col = tx + (long long)ntx * ty;
-    int z0, len;
-    sp.seg(so, z0, len);
-    const long long stride_o = (long long)(len / 2 + 1) * NE;   // one tile column of the owner segment
-    const float *po = part + sp.planes_before(so) * ncols * NE + col * stride_o + (jz * NE + jy * NX + jx);
-    long long stride_l = stride_o;
-    const float *pl = po;
-    if (lz) {   // the previous segment's last node plane
-        sp.seg(so - 1, z0, len);
-        stride_l = (long long)(len / 2 + 1) * NE;
-        pl = part + sp.planes_before(so - 1) * ncols * NE + col * stride_l + ((len / 2) * NE + jy * NX + jx);
-    }
+    const bool lx = jx == 0 && tx > 0, ly = jy == 0 && ty > 0, lz = zl >= 0;
+    const long long col = tx + (long long)ntx * ty;
+    const float *po = part + zo + col * stride_o + (jy * NX + jx);
+    const float *pl = lz ? part + zl + col * stride_l + (jy * NX + jx) : po;
     float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 8; q++) {
@@ -972,7 +997,7 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
         if ((ux && !lx) || (uy && !ly) || (uz && !lz))
             continue;
         const long long stride = uz ? stride_l : stride_o;
-        // the lower column's copy: one column back, local index 14 instead of 0
+        // the lower column's copy: one column back, local index o/2 instead of 0
         const float *p = (uz ? pl : po) + (ux ? -stride + (NX - 1) : 0) + (uy ? -stride * ntx + (NY - 1) * NX : 0);
         s[0] += __ldg(p);
         s[1] += __ldg(p + NX * NY);
@@ -982,8 +1007,7 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
     // interpolant gradient: component c of P^T r is hbar / (2 h_c) times the sum
     const float hh = 0.5f * g.hbar;
     const float sc[3] = {hh * g.ih[0], hh * g.ih[1], hh * g.ih[2]};
-    const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
-    const int k = kx + n0 * ky + n01 * kz;
+    const int k = i + n01 * kz;
     const int st[3] = {1, n0, n01};
     const int j[3] = {kx, ky, kz};
 #pragma unroll
@@ -1001,11 +1025,12 @@ __device__ __forceinline__ void gather_grad_body(const LevelGeom &g, const float
     }
 }
 
-__global__ void __launch_bounds__(256) k_gather_grad(LevelGeom g, const float *__restrict__ part, FusedSplit sp,
-                                                     int ntx, int nty, const float *__restrict__ w, float alpha_hy,
-                                                     float *__restrict__ grad)
+__global__ void __launch_bounds__(GATHER_NODES) k_gather_grad(LevelGeom g, const float *__restrict__ part,
+                                                              FusedSplit sp, int ntx, int nty,
+                                                              const float *__restrict__ w, float alpha_hy,
+                                                              float *__restrict__ grad)
 {
-    gather_grad_body(g, part, sp, ntx, nty, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
+    gather_grad_body(g, part, sp, ntx, nty, w, alpha_hy, grad, blockIdx.x, blockIdx.y);
 }
 
 // The end of an evaluation in the gather launch.  The final reduction reads
@@ -1023,18 +1048,19 @@ struct FinArgs {
     unsigned long long h_ls;
 };
 
-__global__ void __launch_bounds__(256) k_gather_fin(LevelGeom g, const float *__restrict__ part, FusedSplit sp,
-                                                    int ntx, int nty, const float *__restrict__ w, float alpha_hy,
-                                                    float *__restrict__ grad, FinArgs f)
+__global__ void __launch_bounds__(GATHER_NODES) k_gather_fin(LevelGeom g, const float *__restrict__ part,
+                                                             FusedSplit sp, int ntx, int nty,
+                                                             const float *__restrict__ w, float alpha_hy,
+                                                             float *__restrict__ grad, FinArgs f)
 {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
         finalize_body(f.pD, f.nD, f.pS, f.nS, f.hbar_half, f.alpha, f.hy_half, f.scal);
         if (f.phase >= 0) {
             __syncthreads();
             lb_control_body(f.phase, f.st, nullptr, nullptr, 0, f.scal, f.h_ls, 0ULL, 0ULL);
         }
     }
-    gather_grad_body(g, part, sp, ntx, nty, w, alpha_hy, grad, blockIdx.x, blockIdx.y, blockIdx.z);
+    gather_grad_body(g, part, sp, ntx, nty, w, alpha_hy, grad, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace
@@ -1302,8 +1328,7 @@ cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha
     const Level &L = c->L[level];
     const FusedSplit sp = fused_split(L, c->num_sms);
     const int ntx = (L.m[0] + OX - 1) / OX, nty = (L.m[1] + OY - 1) / OY;
-    dim3 blk(32, 8, 1);
-    dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
+    const dim3 gn = gather_grid(L.n);
     FinArgs f;
     f.pD = c->es.partials;
     f.nD = nD;
@@ -1316,7 +1341,7 @@ cudaError_t launch_gather_fin(reg_ctx *c, int level, const float *w, float alpha
     f.phase = phase;
     f.st = c->lb.st;
     f.h_ls = phase >= 0 ? lbfgs_graph_handle_ls() : 0ULL;
-    k_gather_fin<<<gn, blk, 0, s>>>(L.geom(), c->es.part, sp, ntx, nty, w, alpha_hy, grad, f);
+    k_gather_fin<<<gn, GATHER_NODES, 0, s>>>(L.geom(), c->es.part, sp, ntx, nty, w, alpha_hy, grad, f);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -1326,9 +1351,7 @@ cudaError_t launch_gather_grad(reg_ctx *c, int level, const float *w, float alph
     const Level &L = c->L[level];
     const FusedSplit sp = fused_split(L, c->num_sms);
     const int ntx = (L.m[0] + OX - 1) / OX, nty = (L.m[1] + OY - 1) / OY;
-    dim3 blk(32, 8, 1);
-    dim3 gn((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]);
-    k_gather_grad<<<gn, blk, 0, s>>>(L.geom(), c->es.part, sp, ntx, nty, w, alpha_hy, grad);
+    k_gather_grad<<<gather_grid(L.n), GATHER_NODES, 0, s>>>(L.geom(), c->es.part, sp, ntx, nty, w, alpha_hy, grad);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -1490,9 +1513,7 @@ cudaError_t launch_gather_grad_raw(const LevelGeom &g, const float *part, int nu
 {
     const FusedSplit sp = fused_split_dims(g.m, num_sms);
     const int ntx = (g.m[0] + OX - 1) / OX, nty = (g.m[1] + OY - 1) / OY;
-    dim3 blk(32, 8, 1);
-    dim3 gn((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]);
-    k_gather_grad<<<gn, blk, 0, s>>>(g, part, sp, ntx, nty, w, alpha_hy, grad);
+    k_gather_grad<<<gather_grid(g.n), GATHER_NODES, 0, s>>>(g, part, sp, ntx, nty, w, alpha_hy, grad);
     return cudaGetLastError();
 }
 
@@ -1537,7 +1558,7 @@ cudaError_t launch_fused_batch(const PairLevel *pl, const int *tile_off, int npa
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_gather_batch(const PairLevel *__restrict__ pl, const int *__restrict__ off,
+__global__ void __launch_bounds__(GATHER_NODES) k_gather_batch(const PairLevel *__restrict__ pl, const int *__restrict__ off,
                                                       int npairs, int total, int mode)
 {
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
@@ -1546,10 +1567,9 @@ __global__ void __launch_bounds__(256) k_gather_batch(const PairLevel *__restric
         if (mode == 1 && !(P.st->active && P.st->ls_continue))
             continue;
         const int lin = item - __ldg(off + p);
-        const int bx = lin % P.ncx, r = lin / P.ncx;
         const FusedArgs &a = P.fa_init;
-        gather_grad_body(P.geom, a.part, a.split, a.ntx, a.nty, P.w, P.alpha_hy, mode ? P.gt : P.g, bx,
-                         r % P.ncy, r / P.ncy);
+        gather_grad_body(P.geom, a.part, a.split, a.ntx, a.nty, P.w, P.alpha_hy, mode ? P.gt : P.g, lin % P.gbx,
+                         lin / P.gbx);
     }
 }
 
@@ -1558,7 +1578,7 @@ __global__ void __launch_bounds__(256) k_gather_batch(const PairLevel *__restric
 cudaError_t launch_gather_batch(const PairLevel *pl, const int *off, int npairs, int total, int mode, int grid,
                                 cudaStream_t s)
 {
-    k_gather_batch<<<grid, dim3(32, 8, 1), 0, s>>>(pl, off, npairs, total, mode);
+    k_gather_batch<<<grid, GATHER_NODES, 0, s>>>(pl, off, npairs, total, mode);
     return cudaGetLastError();
 }
 
