@@ -88,15 +88,21 @@ static_assert(OX == CW - 4 && OY == BY - 4, "the output tile is the thread block
 
 // shared layout (floats).  The ring slot of plane z is z & 3 for T~, R and v;
 // grad T, written 4 steps before it is read, has a ring of 5 slots taken in
-// turn, one per step; node plane K sits in slot K & 3 (the curvature of plane
-// K reads planes K - 1 .. K + 1 while plane K + 2 is copied in).  The rings are
+// turn, one per step; node plane K sits in slot K mod node_slots (below).  The rings are
 // kept this small so that the CTA's shared memory leaves room for a larger L1,
 // which holds the template samples.  RN: the pass reads the normalized
 // gradient field of R (a.Rn) into registers and keeps no R ring.
 constexpr int GSLOTS = 5;
-constexpr int NSLOTS = 4;
+// node-plane slots: 4 where the tile forms the curvature (plane K - 1 .. K + 1
+// read while K + 2 is copied in), else 2 (plane K + 1 read while K + 2 is
+// copied in: plane K's values live on in registers)
+template <bool CURV>
+__host__ __device__ constexpr int node_slots()
+{
+    return CURV ? 4 : 2;
+}
 constexpr int RED_PLANE = BY * NX * 3;            // x-reduced rows of one plane [BY][NX][3]
-template <bool RN>
+template <bool RN, int NSLOTS>
 struct Smem {
     static constexpr int T = 0;                       // T~ ring [4][PLANE]
     static constexpr int R = T + 4 * PLANE;           // R ring [4][PLANE] (without RN: none)
@@ -123,9 +129,13 @@ __host__ __device__ constexpr bool reads_rn()
 template <typename IMG, bool PAD, bool CURV>
 __host__ __device__ constexpr size_t smem_bytes()
 {
-    return reads_rn<IMG, PAD, CURV>() ? Smem<true>::BYTES : Smem<false>::BYTES;
+    return reads_rn<IMG, PAD, CURV>() ? Smem<true, node_slots<CURV>()>::BYTES : Smem<false, node_slots<CURV>()>::BYTES;
 }
-__device__ __forceinline__ int node_slot(int K) { return K & (NSLOTS - 1); }   // K >= -1
+template <int NSL>
+__device__ __forceinline__ int node_slot(int K)   // K >= -1
+{
+    return K & (NSL - 1);
+}
 
 // The fused kernels' dynamic shared memory, and a carveout preference of just
 // that much (with the 1 KB the system reserves per CTA) in percent of the
@@ -307,10 +317,11 @@ __device__ __forceinline__ NodeCopy node_copy_setup(const LevelGeom &g, int kx0,
 }
 
 // copy node plane K into its ring slot; nodes outside the grid read as zero
+template <int NSL>
 __device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float *ub, const float *dir,
                                                  float *nodes, int K, int nz, size_t plane_stride)
 {
-    float *dst = nodes + node_slot(K) * 2 * TNP;
+    float *dst = nodes + node_slot<NSL>(K) * 2 * TNP;
     const bool kin = K >= 0 && K < nz;
     const size_t kofs = kin ? plane_stride * (size_t)K : 0;
 #pragma unroll
@@ -325,9 +336,10 @@ __device__ __forceinline__ void issue_node_plane(const NodeCopy &nc, const float
 // the trial point of node plane K (copied into its ring slot and visible to
 // every thread): u <- u + t dir in place, the same fmaf as the accepted update,
 // so the accepted iterate equals the evaluated one bit for bit
+template <int NSL>
 __device__ __forceinline__ void trial_node_plane(float *nodes, int K, float t, int tid)
 {
-    float *nu = nodes + node_slot(K) * 2 * TNP;
+    float *nu = nodes + node_slot<NSL>(K) * 2 * TNP;
 #pragma unroll
     for (int q = 0; q < NCOMB; q++) {
         const int e = tid + q * NT;
@@ -339,10 +351,11 @@ __device__ __forceinline__ void trial_node_plane(float *nodes, int K, float t, i
 // displacement plane K of the thread's two columns from the shared node tile:
 // the value at the interval's first node (U, shared) and the bilinear
 // interpolation of the in-plane differences (B, x weight 1/4 and 3/4 per lane)
+template <int NSL>
 __device__ __forceinline__ void column_pair_plane(const float *nodes, int K, int lkx, int lky, float2 WY, float U[3],
                                                   float2 B[3])
 {
-    const float *nu = nodes + node_slot(K) * 2 * TNP;
+    const float *nu = nodes + node_slot<NSL>(K) * 2 * TNP;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const int o = c * (TNY * TNX) + lky * TNX + lkx;
@@ -411,7 +424,7 @@ __device__ __forceinline__ void tile_seg_col(const FusedSplit &sp, int ncols, in
 }
 
 // One output tile (launch-order id, see tile_seg_col) of the fused pass; sm is
-// the CTA's dynamic shared memory (Smem<RN>::BYTES).  PAD: a.T is the zero-bordered
+// the CTA's dynamic shared memory (Smem<RN, NSL>::BYTES).  PAD: a.T is the zero-bordered
 // copy of T (dims m + 4, the image at offset 2 in every dimension).  CURV: the
 // tile also forms the curvature Laplacian of the nodes it owns (a.w) and their
 // share of S (a.partials_S) - where no separate curvature pass can run beside
@@ -420,7 +433,8 @@ template <bool HAS_DIR, typename IMG, bool PAD, bool CURV>
 __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, float *sm)
 {
     constexpr bool RN = reads_rn<IMG, PAD, CURV>();
-    using SL = Smem<RN>;
+    constexpr int NSL = node_slots<CURV>();
+    using SL = Smem<RN, NSL>;
     const LevelGeom &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int sp = 2 * tx + CW * ty;                  // shared-plane index of the thread's first column
@@ -527,7 +541,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             float Ulo[3];
             float2 Blo[3];
             if (first) {
-                column_pair_plane(sm + SL::N, K1, tx, lky, WY, Ulo, Blo);
+                column_pair_plane<NSL>(sm + SL::N, K1, tx, lky, WY, Ulo, Blo);
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
@@ -535,7 +549,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                     Blo[c] = Bhi[c];
                 }
             }
-            column_pair_plane(sm + SL::N, K1 + 1, tx, lky, WY, Uhi, Bhi);
+            column_pair_plane<NSL>(sm + SL::N, K1 + 1, tx, lky, WY, Uhi, Bhi);
+            if (first && NSL == 2)
+                __syncthreads();   // plane K1's slot takes plane K1 + 2 below (first call: every thread)
             // y-hat = U_lo + lerp(B_lo, (U_hi - U_lo) + B_hi, wz) with wz = 1/4 (even z) or
             // 3/4 (odd z).  The sampling coordinate i + y-hat / h is kept as an integer
             // part plus a small fraction; both depend only on the interval and the
@@ -568,9 +584,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
             // interior nodes, 0 elsewhere, from planes K1 - 1 .. K1 + 1 of the ring,
             // for the planes this segment owns (the last segment also its top one)
             if (CURV && K1 >= (z0 >> 1) && (K1 < (zend >> 1) || zend == mz)) {
-                const float *pw = sm + SL::N + node_slot(K1) * 2 * TNP;
-                const float *pm = sm + SL::N + node_slot(K1 - 1) * 2 * TNP;
-                const float *pp = sm + SL::N + node_slot(K1 + 1) * 2 * TNP;
+                const float *pw = sm + SL::N + node_slot<NSL>(K1) * 2 * TNP;
+                const float *pm = sm + SL::N + node_slot<NSL>(K1 - 1) * 2 * TNP;
+                const float *pp = sm + SL::N + node_slot<NSL>(K1 + 1) * 2 * TNP;
                 const bool wz = K1 >= 1 && K1 <= g.n[2] - 2;
                 float *wk = a.w + (size_t)K1 * node_plane;
 #pragma unroll
@@ -588,7 +604,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                         wacc = fmaf(lap, lap, wacc);
                     }
             }
-            issue_node_plane(nc, a.ub, a.dir, sm + SL::N, K1 + 2, g.n[2], node_plane);
+            issue_node_plane<NSL>(nc, a.ub, a.dir, sm + SL::N, K1 + 2, g.n[2], node_plane);
             cp_async_commit();
         } else {
 #pragma unroll
@@ -596,7 +612,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
                 f[c] = fo[c];
             bz += 1;
             if (HAS_DIR)   // copied at the interval start, visible since the last barrier
-                trial_node_plane(sm + SL::N, (z1 >> 1) + 2, t, tid);
+                trial_node_plane<NSL>(sm + SL::N, (z1 >> 1) + 2, t, tid);
         }
         // integer cells and fractions of both columns: the sum with 1.5 2^23 rounded
         // down holds floor(f) in its low bits
@@ -832,14 +848,14 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &a, int tile_id, floa
     // the loads of plane z0 - 2
     {
         const int K0 = (z0 - 2) >> 1;
-        issue_node_plane(nc, a.ub, a.dir, sm + SL::N, K0, g.n[2], node_plane);
-        issue_node_plane(nc, a.ub, a.dir, sm + SL::N, K0 + 1, g.n[2], node_plane);
+        issue_node_plane<NSL>(nc, a.ub, a.dir, sm + SL::N, K0, g.n[2], node_plane);
+        issue_node_plane<NSL>(nc, a.ub, a.dir, sm + SL::N, K0 + 1, g.n[2], node_plane);
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
         if (HAS_DIR) {
-            trial_node_plane(sm + SL::N, K0, t, tid);
-            trial_node_plane(sm + SL::N, K0 + 1, t, tid);
+            trial_node_plane<NSL>(sm + SL::N, K0, t, tid);
+            trial_node_plane<NSL>(sm + SL::N, K0 + 1, t, tid);
             __syncthreads();
         }
         a_issue(z0 - 2, std::false_type{}, true);
