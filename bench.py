@@ -41,8 +41,8 @@ L2_BYTES = 129 * 1024 * 1024
 # the translation unit of the fused pass and every header it includes: the
 # committed ncu traffic is valid only for this exact source
 FUSED_KERNEL_SOURCES = ["paper_1812_06765_gb300/csrc/" + f
-                        for f in ("k_ngf_fused.cu", "k_pyramid.cu", "ngf_math.cuh", "common.cuh", "batch.h",
-                                  "internal.h", "lbfgs_control.cuh", "lbfgs_state.h")] + ["include/reg.h"]
+                        for f in ("k_ngf_fused.cu", "fused_pass.cuh", "k_pyramid.cu", "ngf_math.cuh", "common.cuh",
+                                  "batch.h", "internal.h", "lbfgs_control.cuh", "lbfgs_state.h")] + ["include/reg.h"]
 
 
 def parse_args(argv=None):

@@ -82,3 +82,6 @@ cudaError_t launch_lb_control_batch(const PairLevel *pl, int npairs, int phase, 
 cudaError_t launch_batch_condition(const PairLevel *pl, int npairs, int which, unsigned long long h, int *counters,
                                    cudaStream_t s);
 void fused_tiling(const Level &L, int num_sms, FusedSplit *split, int *ntx, int *nty);
+// arguments of the fused pass of one handle's level; *ntiles = its tiles
+FusedArgs fused_args(const reg_ctx *c, int level, const float *ub, const float *dir, const double *t_dev,
+                     double *partials, int *ntiles);

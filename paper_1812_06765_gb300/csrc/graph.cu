@@ -204,7 +204,7 @@ int eval_kernel_count(const reg_ctx *c, int level)
 {
     if (use_fused(c, level)) {   // fused pass, curvature, gather (+ the final reduction beside it on large grids)
         const Level &L = c->L[level];
-        return (gather_blocks(L.n) < GATHER_SPLIT_BLOCKS ? 3 : 4) - (fused_curv_in_pass(c) ? 1 : 0);
+        return (gather_blocks(L.n) < GATHER_SPLIT_BLOCKS ? 3 : 4) - (fused_curv_in_pass(c, level) ? 1 : 0);
     }
     static const int ngf[3] = {4, 3, 10};   // multi-pass NGF kernels per P^T variant
     return ngf[mp_pt_variant(c, level)] + 3;   // + curvature, its gradient, final reduction

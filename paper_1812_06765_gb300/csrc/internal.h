@@ -108,6 +108,7 @@ struct LbfgsBuffers {
     float2 *gpart = nullptr;            // their group sums, double-float (hi, lo)
     unsigned *cnt = nullptr;            // their arrival counters
     int cnt_len = 0;
+    unsigned *gbar = nullptr;           // [arrivals, generation, flags] of the whole-level kernel's grid barrier
     LbfgsState *st = nullptr;           // device
     LbfgsState *st_host = nullptr;      // pinned mirror
     double *scal_t = nullptr;           // [J, D, S] of the trial point
@@ -181,6 +182,9 @@ cudaError_t lbfgs_launch_init(reg_ctx *c, int level, cudaStream_t s);
 cudaError_t lbfgs_launch_direction_level(reg_ctx *c, int level, cudaStream_t s);
 cudaError_t lbfgs_launch_trial(reg_ctx *c, int level, cudaStream_t s);
 cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s);
+// the whole loop of a small level as one cooperative kernel (after lbfgs_launch_init)
+bool lbfgs_level_loop_ok(reg_ctx *c, int level);
+cudaError_t lbfgs_launch_level_loop(reg_ctx *c, int level, cudaStream_t s);
 void lbfgs_set_graph_handles(unsigned long long h_ls, unsigned long long h_iter, unsigned long long h_redo);
 unsigned long long lbfgs_graph_handle_ls();
 cudaError_t lbfgs_launch_direction(reg_ctx *c, int level, cudaStream_t s);
@@ -240,17 +244,31 @@ const void *curv_w_kernel();
 cudaError_t set_graph_kernel_priorities(cudaGraph_t g, const void *low_func);
 int eval_kernel_count(const reg_ctx *c, int level);
 
-// Whether the fused pass forms the curvature Laplacian itself (one S partial
-// per tile) instead of a curvature kernel beside it: the batched form always
-// does (its persistent grid leaves no SM for a pass beside it), and a single
-// registration does with the batch's tiling rule (cfg.fused_tz = -1), so that
-// it computes exactly what the batch computes for that pair.
-inline bool fused_curv_in_pass(const reg_ctx *c) { return c->cfg.fused_tz == -1; }
-
 // the fused pass serves levels whose grids have ratio exactly 2; others use the multi-pass kernels
 inline bool use_fused(const reg_ctx *c, int level)
 {
     return c->cfg.eval_impl == 0 && fused_eligible(c->L[level]);
+}
+
+// Levels of at most WHOLE_LEVEL_MAX_NODES nodes are small: a level graph runs
+// them as one cooperative kernel (every iteration of the level, a grid barrier
+// between phases) where the fused pass serves them, their images are FP32 and
+// the device supports cooperative launches (lbfgs_launch_level_loop).  Larger
+// levels lose more to the kernel's single 200 KB block per SM (one fused-pass
+// CTA per SM instead of two) than they gain (a 65^3-node level took 1.3x).
+constexpr long long WHOLE_LEVEL_MAX_NODES = 40000;
+inline bool small_level(const reg_ctx *c, int level) { return c->L[level].nn <= WHOLE_LEVEL_MAX_NODES; }
+
+// Whether the fused pass forms the curvature Laplacian itself (one S partial
+// per tile) instead of a curvature kernel beside it: the batched form always
+// does (its persistent grid leaves no SM for a pass beside it), a single
+// registration does with the batch's tiling rule (cfg.fused_tz = -1), so that
+// it computes exactly what the batch computes for that pair, and on small
+// levels, whose whole-level kernel has no second stream (queued from the host
+// they take the same arithmetic).
+inline bool fused_curv_in_pass(const reg_ctx *c, int level)
+{
+    return c->cfg.fused_tz == -1 || small_level(c, level);
 }
 
 // P^T of the multi-pass path: 0 node-centric gather (Eq. 3; eval_impl 0 and 1),

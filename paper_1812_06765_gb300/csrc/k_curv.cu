@@ -128,7 +128,7 @@ cudaError_t launch_eval(reg_ctx *c, int level, const float *ub, const float *dir
     int nD = 0;
     cudaError_t e;
     const bool fused = use_fused(c, level);
-    const bool curv_in_pass = fused && fused_curv_in_pass(c);
+    const bool curv_in_pass = fused && fused_curv_in_pass(c, level);
     // The curvature Laplacian (node pass, HBM-light) runs on the side stream
     // beside the NGF pass (issue-bound, one CTA per SM), in the tail of its last
     // wave: fork before, join before the gradient assembly.  Captured, the two

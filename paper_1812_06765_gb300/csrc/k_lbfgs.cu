@@ -19,6 +19,7 @@
 #include <atomic>
 
 #include "batch.h"
+#include "fused_pass.cuh"
 #include "internal.h"
 #include "lbfgs_control.cuh"
 
@@ -405,11 +406,12 @@ __device__ __forceinline__ void lb_direction_body(long long n, long long stride,
             atomicOr(const_cast<int *>(&st->wait_err), 1);
         if (bx == 0 && threadIdx.x < (n & 3)) {
             const long long e = 4 * n4 + threadIdx.x;
-            float gv = g[e], p = cg * gv;
+            float gv = __ldcg(g + e), p = cg * gv;
 #pragma unroll
             for (int j = 0; j < LB_MAXM; j++)
                 if (j < dc)
-                    p = fmaf(cp[j], P[(size_t)s_slot[j] * stride + e], fmaf(cy[j], Y[(size_t)s_slot[j] * stride + e], p));
+                    p = fmaf(cp[j], __ldcg(P + (size_t)s_slot[j] * stride + e),
+                             fmaf(cy[j], __ldcg(Y + (size_t)s_slot[j] * stride + e), p));
             pdir[e] = p;
             v[0] = fmaf(gv, p, v[0]);
             v[1] = fmaf(p, p, v[1]);
@@ -548,7 +550,7 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
             atomicOr(const_cast<int *>(&st->wait_err), 1);
         if (bx == 0 && threadIdx.x < (n & 3)) {
             const long long e = 4 * n4 + threadIdx.x;
-            float gn = gt[e], go = g[e], pf = pdir[e], uu = u[e], yn;
+            float gn = __ldcg(gt + e), go = __ldcg(g + e), pf = __ldcg(pdir + e), uu = __ldcg(u + e), yn;
             accept_elem(gn, go, pf, uu, t, yn);
             u[e] = uu;
             g[e] = gn;
@@ -559,7 +561,7 @@ __device__ __forceinline__ void lb_accept_body(long long n, long long stride, co
 #pragma unroll
             for (int j = 0; j < LB_MAXM; j++)
                 if (j < np) {   // unrolled with a predicate so that v stays in registers
-                    float pj = P[(size_t)s_slot[j] * stride + e], yj = Y[(size_t)s_slot[j] * stride + e];
+                    float pj = __ldcg(P + (size_t)s_slot[j] * stride + e), yj = __ldcg(Y + (size_t)s_slot[j] * stride + e);
                     v[2 + 4 * j] = fmaf(pj, gn, v[2 + 4 * j]);
                     v[3 + 4 * j] = fmaf(yj, gn, v[3 + 4 * j]);
                     v[4 + 4 * j] = fmaf(pj, yn, v[4 + 4 * j]);
@@ -765,6 +767,139 @@ __global__ void k_lb_pair_setup(LbfgsState *__restrict__ st, int count, const fl
         set_compact_warp(st);
 }
 
+// ---------------------------------------------------------------------------
+// Whole-level loop of small levels (Sec. 2.1: L-BFGS with Armijo backtracking
+// in the multilevel scheme).  One cooperative launch runs every iteration of
+// the level with the level graph's device code: the direction pass, the p0
+// redo when its control asks for one, each line-search trial (the fused pass
+// at u + t p with the curvature formed in the pass, then the node gather with
+// the final reduction and the Armijo decision in block 0) and the accept pass.
+// A grid barrier replaces each kernel boundary; the control phases still run
+// in the block that completes each cross-block reduction.  On levels of a few
+// thousand to a few hundred thousand nodes the kernel boundaries, conditional
+// nodes and ramp-ups of the graph cost as much as the work.
+// ---------------------------------------------------------------------------
+struct LevelLoopArgs {
+    FusedArgs fa;               // trial point: ub = u, dir = pdir, t_dev = &st->t
+    int ntiles;                 // tiles of the fused pass
+    int gather_items, gather_runs;   // gather blocks, and runs per node plane
+    float alpha_hy;             // alpha hbar_y of the curvature gradient
+    double hbar_half, alpha, hy_half;
+    double *scal_t;             // [J, D, S] of the trial point
+    long long n, stride;        // vector length, ring slot stride
+    float *u, *g, *gt, *pdir, *P, *Y;
+    float *partials;            // FP32 block partials of the vector passes
+    int nvec;                   // blocks of the vector passes (as the level graph's)
+    VecTail tdir, tredo, tacc;  // their folded reductions and control phases
+    LbfgsState *st;
+    unsigned *bar;              // [arrivals, generation, flag snapshot] of the grid barrier
+    int max_steps;              // bound on the loop bodies and trials
+};
+
+__device__ __forceinline__ int ld_flag(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+
+// loop flags of the state, as the block that releases a grid barrier saw them
+constexpr unsigned F_ITER = 1u, F_REDO = 2u, F_LS = 4u, F_ERR = 8u;
+
+// Grid-wide barrier of the cooperative launch (every block resident): block
+// barrier, one thread's release fence and arrival.  The last block to arrive
+// takes a snapshot of the state's loop flags (iteration, p0 redo, line search,
+// copy-wait error), resets the count and advances the generation; the others
+// wait for it, at most WAIT_NS, and read the snapshot.  Every block so takes
+// the loop decisions from the same flags, whatever a control phase writes
+// later.  Returns false, and the caller's block leaves the kernel, on an
+// error flag or an expired wait (which flags the state: the level stops; the
+// other blocks leave at their next barrier).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, LbfgsState *st, unsigned &flags)
+{
+    __shared__ unsigned s_flags;
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1, *snap = bar + 2;
+        const unsigned g0 = *gen;
+        int ok = 1;
+        fence_acq_rel_gpu();   // this block's writes, before its arrival is counted
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            fence_acq_rel_gpu();   // every block's writes, before the snapshot reads them
+            *snap = (ld_flag(&st->iter_continue) ? F_ITER : 0u) | (ld_flag(&st->redo_dir) ? F_REDO : 0u) |
+                    (ld_flag(&st->ls_continue) ? F_LS : 0u) | (ld_flag(&st->wait_err) ? F_ERR : 0u);
+            bar[0] = 0;
+            fence_acq_rel_gpu();   // the snapshot and the reset, before the release
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g0) {
+                if (global_ns() - t0 > WAIT_NS) {
+                    ok = 0;
+                    atomicOr(&st->wait_err, 1);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        fence_acq_rel_gpu();   // the snapshot and every block's writes, before this block reads them
+        s_flags = *snap;
+        s_ok = ok && !(s_flags & F_ERR);
+    }
+    __syncthreads();
+    flags = s_flags;
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(VT, 1) k_level_loop(LevelLoopArgs a)
+{
+    extern __shared__ float4 dyn4[];
+    float *sm = reinterpret_cast<float *>(dyn4);
+    const unsigned nb = gridDim.x;
+    const int bx = blockIdx.x;
+    LbfgsState *st = a.st;
+    unsigned f = 0;
+    int steps = 0;
+    if (!grid_barrier(a.bar, nb, st, f))   // the first snapshot
+        return;
+    while ((f & F_ITER) && steps++ < a.max_steps) {
+        if (bx < a.nvec)
+            lb_direction_body(a.n, a.stride, st, a.g, a.P, a.Y, a.pdir, a.partials, 0, a.tdir, bx, a.nvec);
+        if (!grid_barrier(a.bar, nb, st, f))
+            return;
+        if (f & F_REDO) {
+            if (bx < a.nvec)
+                lb_direction_body(a.n, a.stride, st, a.g, a.P, a.Y, a.pdir, a.partials, 1, a.tredo, bx, a.nvec);
+            if (!grid_barrier(a.bar, nb, st, f))
+                return;
+        }
+        while ((f & F_LS) && steps++ < a.max_steps) {
+            for (int tile = bx; tile < a.ntiles; tile += nb) {
+                fused_tile<true, float, true, true>(a.fa, tile, sm);
+                __syncthreads();   // the next tile reuses the shared rings
+            }
+            if (!grid_barrier(a.bar, nb, st, f))
+                return;
+            if (bx == 0) {   // J, D, S of the trial point and the Armijo decision, then its gather share
+                finalize_body(a.fa.partials, a.ntiles, a.fa.partials_S, a.ntiles, a.hbar_half, a.alpha, a.hy_half,
+                              a.scal_t);
+                __syncthreads();
+                lb_control_body(LB_ARMIJO, st, nullptr, nullptr, 0, a.scal_t, 0ULL, 0ULL, 0ULL);
+            }
+            for (int item = bx; item < a.gather_items; item += nb)
+                gather_grad_body<true>(a.fa.g, a.fa.part, a.fa.split, a.fa.ntx, a.fa.nty, a.fa.w, a.alpha_hy, a.gt,
+                                       item % a.gather_runs, item / a.gather_runs);
+            if (!grid_barrier(a.bar, nb, st, f))
+                return;
+        }
+        if (bx < a.nvec)
+            lb_accept_body(a.n, a.stride, st, a.u, a.g, a.gt, a.pdir, a.P, a.Y, a.partials, a.tacc, bx, a.nvec);
+        if (!grid_barrier(a.bar, nb, st, f))
+            return;
+    }
+    if (steps > a.max_steps && bx == 0 && threadIdx.x == 0) {   // cannot happen with the control's own bounds
+        st->status = -6;
+        st->done = 1;
+        st->iter_continue = 0;
+    }
+}
+
 }  // namespace
 
 // Blocks of the vector passes that fit on one SM at once (the fewer of the
@@ -786,6 +921,8 @@ cudaError_t lbfgs_kernels_setup(int device)
         e = cudaFuncSetAttribute(k_lb_accept, at, VEC_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_lb_vector_batch, at, VEC_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_level_loop, at, VEC_SMEM);
     if (e == cudaSuccess)
         done[dev].store(true);
     return e;
@@ -917,6 +1054,75 @@ cudaError_t lbfgs_launch_accept_level(reg_ctx *c, int level, cudaStream_t s)
                                   c->lb.partials, tail_of(c, LB_ACCEPTED, nullptr, false, true));
     c->launches += 1;
     return cudaGetLastError();
+}
+
+// Blocks of the whole-level kernel (all resident at once), 0 where the device
+// has no cooperative launch.  Cached per device.
+static int level_loop_grid(reg_ctx *c)
+{
+    static std::atomic<int> cached[64];
+    const int dev = c->device >= 0 && c->device < 64 ? c->device : 0;
+    int v = cached[dev].load();
+    if (v != 0)
+        return v > 0 ? v : 0;
+    int coop = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+        lbfgs_kernels_setup(c->device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, VT, VEC_SMEM) != cudaSuccess) {
+        (void)cudaGetLastError();
+        per_sm = 0;
+    }
+    v = per_sm > 0 ? per_sm * c->num_sms : -1;
+    cached[dev].store(v);
+    return v > 0 ? v : 0;
+}
+
+bool lbfgs_level_loop_ok(reg_ctx *c, int level)
+{
+    if (!c->cfg.use_graph || !use_fused(c, level) || !small_level(c, level) || c->cfg.image_dtype != 0)
+        return false;
+    const int grid = level_loop_grid(c);
+    return grid > 0 && num_blocks_for(c, (3 * c->L[level].nn + 3) / 4, VT) <= grid;
+}
+
+cudaError_t lbfgs_launch_level_loop(reg_ctx *c, int level, cudaStream_t s)
+{
+    const Level &L = c->L[level];
+    LevelLoopArgs a;
+    a.fa = fused_args(c, level, c->lb.u, c->lb.pdir, &c->lb.st->t, c->es.partials, &a.ntiles);
+    a.gather_runs = gather_runs_per_plane(L.n);
+    a.gather_items = a.gather_runs * L.n[2];
+    const double hy = L.H[0] * L.H[1] * L.H[2];
+    a.alpha_hy = (float)(c->cfg.alpha * hy);
+    a.hbar_half = 0.5 * L.h[0] * L.h[1] * L.h[2];
+    a.alpha = c->cfg.alpha;
+    a.hy_half = 0.5 * hy;
+    a.scal_t = c->lb.scal_t;
+    a.n = 3 * L.nn;
+    a.stride = ring_stride(a.n);
+    a.u = c->lb.u;
+    a.g = c->lb.g;
+    a.gt = c->lb.gt;
+    a.pdir = c->lb.pdir;
+    a.P = c->lb.P;
+    a.Y = c->lb.Y;
+    a.partials = c->lb.partials;
+    a.nvec = num_blocks_for(c, (a.n + 3) / 4, VT);
+    a.tdir = tail_of(c, LB_DIR, nullptr, false, false);
+    a.tredo = tail_of(c, LB_DIR_REDO, nullptr, false, false);
+    a.tacc = tail_of(c, LB_ACCEPTED, nullptr, false, false);
+    a.st = c->lb.st;
+    a.bar = c->lb.gbar;
+    a.max_steps = 4 * (c->cfg.max_iter[level] + 1) * (c->cfg.max_backtracks + 1) + 16;
+    // a launch that ended at an expired barrier may have left arrivals behind
+    cudaError_t e = cudaMemsetAsync(c->lb.gbar, 0, 3 * sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    void *args[] = {&a};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_level_loop), dim3(level_loop_grid(c)),
+                                    dim3(VT), args, VEC_SMEM, s);
+    c->launches += 1;
+    return e;
 }
 
 // evaluation reduction with a control phase (k_curv.cu calls this for trial points)

@@ -160,7 +160,7 @@ __device__ __forceinline__ void ctl_state_load(const LbfgsState *gst)
     int *dst = reinterpret_cast<int *>(&ctl_state());
     const int *src = reinterpret_cast<const int *>(gst);
     for (int i = linear_tid(); i < STATE_WORDS; i += nthreads())
-        dst[i] = src[i];
+        dst[i] = __ldcg(src + i);   // through L2: other blocks' control phases write it within a launch
 }
 
 // Fence of one thread after a block barrier: with the barrier it orders the
@@ -202,9 +202,9 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst, cons
     s_compact = 0;
     switch (phase) {
     case LB_INIT: {
-        st->J = scal[0];
-        st->D = scal[1];
-        st->S = scal[2];
+        st->J = __ldcg(scal);   // the objective's scalars, through L2 (written within a launch)
+        st->D = __ldcg(scal + 1);
+        st->S = __ldcg(scal + 2);
         st->J0 = st->J;
         st->gg = red[0];
         st->ginf = red[1];
@@ -263,9 +263,9 @@ __device__ __forceinline__ void lb_control_body(int phase, LbfgsState *gst, cons
     case LB_ARMIJO: {
         if (!st->active || !st->ls_continue)   // this pair is not searching (batched levels)
             break;
-        st->Jt = scal[0];
-        st->Dt = scal[1];
-        st->St = scal[2];
+        st->Jt = __ldcg(scal);
+        st->Dt = __ldcg(scal + 1);
+        st->St = __ldcg(scal + 2);
         st->evals++;
         if (finite_d(st->Jt) && st->Jt <= st->J + st->c1 * st->t * st->gtp) {
             st->ls = LS_ACCEPTED;

@@ -61,6 +61,7 @@ void free_buffers(reg_ctx *c)
     cudaFree(b.Y);
     cudaFree(b.partials);
     cudaFree(b.gpart);
+    cudaFree(b.gbar);
     cudaFree(b.cnt);
     cudaFree(b.st);
     cudaFree(b.scal_t);
@@ -327,6 +328,8 @@ int allocate_buffers(reg_ctx *c)
         b.cnt_len = groups + 1;
         CK(cudaMalloc(&b.cnt, sizeof(unsigned) * b.cnt_len));
         CK(cudaMemset(b.cnt, 0, sizeof(unsigned) * b.cnt_len));
+        CK(cudaMalloc(&b.gbar, 3 * sizeof(unsigned)));
+        CK(cudaMemset(b.gbar, 0, 3 * sizeof(unsigned)));
     }
     CK(cudaMalloc(&b.st, sizeof(LbfgsState)));
     CK(cudaMalloc(&b.scal_t, sizeof(double) * 4));
@@ -737,6 +740,11 @@ int run_level_host(reg_ctx *c, int level)
 // the device state once, after the level.
 int run_level_graph(reg_ctx *c, int level)
 {
+    if (lbfgs_level_loop_ok(c, level)) {   // a small level: one cooperative kernel for its loop
+        CK(lbfgs_launch_init(c, level, c->stream));
+        CK(lbfgs_launch_level_loop(c, level, c->stream));
+        return read_state(c);
+    }
     if (!c->iter_graph[level]) {
         cudaError_t e = build_level_graph(c, level, &c->iter_graph[level]);
         if (e != cudaSuccess) {
