@@ -444,7 +444,8 @@ def run_ours(args):
                        "fused_tz_per_level": [reg.level_tiling(lv)[0] for lv in range(levels)],
                        "fused_split_per_level": [list(reg.level_split(lv)) for lv in range(levels)],
                        "tiling": "autotuned (z split timed per level)" if reg.cfg.autotune else "load model",
-                       "lbfgs_loop": "one CUDA graph per level" if reg.cfg.use_graph else "host-driven",
+                       "lbfgs_loop": ("one CUDA graph per level; levels of at most 40k nodes one cooperative "
+                                      "kernel" if reg.cfg.use_graph else "host-driven"),
                        "l2": "flushed between steps (2x L2 buffer written, untimed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "image_shape_zyx": list(mz)},
@@ -456,8 +457,11 @@ def run_ours(args):
                          "algorithmic_bytes": kernel_bytes, "overhead_bytes": part_bytes, "launch_ms": ngf_ms,
                          "peak_kind": peak_kind,
                          "note": "algorithmic bytes: read R, T, u and write grad J once per evaluation; "
-                                 "overhead: the tile partials the pass writes for the node gather; the pass is "
-                                 "bound by instruction issue and L1, not HBM: see the ncu summary"},
+                                 "overhead: the tile partials the pass writes for the node gather; traffic also "
+                                 "holds R's normalized gradient field, which the pass reads instead of R (16 "
+                                 "bytes per voxel instead of 4, formed once per level: bytes traded for "
+                                 "instructions); the pass is bound by latency and instruction issue, not HBM: "
+                                 "see the ncu summary"},
             "issue_roofline": issue,
             "eval_roofline": {"bound": "hbm", "achieved": eval_achieved, "peak": peak, "unit": "GB/s",
                               "frac": eval_achieved / peak, "algorithmic_bytes": eval_bytes, "eval_ms": eval_ms,
